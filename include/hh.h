@@ -1,0 +1,221 @@
+/*
+ * libhh — list-driven 4th-order Hermite N-body force evaluation on GB300 (sm_103a).
+ *
+ * A C ABI around the data-parallel hot path of the tree + Hermite method of
+ * Fukushige & Kawai, "Hierarchical Tree Algorithm for Collisional N-body
+ * Simulations on GRAPE" (arXiv:1602.02832).  The calls follow the paper's
+ * statement of the loop (Section 2, tree-loop steps 1-7):
+ *   step 1   hh_set_j / hh_set_lists (or hh_rebuild): particles, tree nodes as
+ *            pseudo-particles and one interaction list per particle group;
+ *   step 2   block selection (inside hh_step / hh_advance);
+ *   step 4   hh_predict: every j entry to the block time;
+ *   4a + 5   hh_force: force, jerk and potential on the active particles,
+ *            each from its group's list only;
+ *   step 6   hh_correct: 4th-order Hermite corrector and new Aarseth step;
+ *   step 7   advance (hh_step / hh_advance, device resident).
+ *
+ * Conventions
+ *   - Arrays of 3-vectors are structure-of-arrays: double[3][n] (all x, then
+ *     all y, then all z), unless stated otherwise.
+ *   - "j array": entries [0, n) are particles, [n, n_j) tree nodes.  A node
+ *     carries the total mass and the mass-weighted position, velocity,
+ *     acceleration and jerk of its members at the tree time (Section 2, step 1)
+ *     and is predicted like a particle.
+ *   - Lists are CSR: off[n_groups + 1] (int64, off[0] = 0, non-decreasing),
+ *     idx[off[n_groups]] (int32 indices into the j array).  group_of[p] gives
+ *     the list of particle p.  Groups must be contiguous, ascending index
+ *     ranges of particles (Barnes 1990 grouping of neighbouring particles).
+ *   - Host pointers: the caller owns them; the library copies in or out
+ *     before returning.  *_dev variants take device pointers that the caller
+ *     owns (for instance torch tensors); they are used on the context's stream
+ *     and must stay valid until that stream reaches the call.
+ *   - Errors: every int-returning call returns HH_OK (0) or a negative code;
+ *     hh_last_error(ctx) holds a one-line message.  Nothing throws across the
+ *     ABI, no call aborts the process.  Inputs are validated on the host (and
+ *     list indices on the device) before any kernel reads them.
+ *   - Threading: a context may be used by one host thread at a time.
+ */
+#ifndef HH_H
+#define HH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HH_OK 0
+#define HH_EINVAL (-1)   /* bad argument, size, index or non-finite input */
+#define HH_ENOMEM (-2)   /* device or host allocation failed, or capacity exceeded */
+#define HH_ECUDA (-3)    /* a CUDA runtime call failed */
+#define HH_ETIMEOUT (-4) /* a bounded device-side wait gave up */
+#define HH_ESTATE (-5)   /* calls made in the wrong order (e.g. force before lists) */
+
+#define HH_FP64 0  /* plain form: FP64 prediction, pairwise arithmetic and sums */
+#define HH_MIXED 1 /* FP64 state and corrector; i-j difference from float pairs
+                      (hi + lo), FP32 pairwise arithmetic, compensated FP32 sums */
+
+typedef struct hh_ctx hh_ctx;
+
+typedef struct hh_config {
+    double eps2;    /* Plummer softening epsilon^2 (>= 0) */
+    double eta;     /* Aarseth accuracy parameter (Section 3: eta = 0.01) */
+    double eta_s;   /* initial step: dt = eta_s |a| / |jerk| */
+    double dt_min;  /* smallest block step, a power of two */
+    double dt_max;  /* largest block step, a power of two, <= dt_tree */
+    double dt_tree; /* interval between tree/list rebuilds (Section 2; 1/64 in Section 3) */
+    double theta;   /* opening angle for hh_rebuild */
+    int32_t leaf;   /* max particles in a leaf cell for hh_rebuild (e.g. 8) */
+    int32_t n_crit; /* max particles per group for hh_rebuild (Section 2) */
+    int32_t precision; /* HH_FP64 or HH_MIXED */
+    int32_t tile_i;    /* particles per static i tile, 1..32; 0 = 32 */
+    int32_t tile_j;    /* list entries staged per chunk, multiple of 32, 32..1024; 0 = default */
+    int32_t reserved;
+} hh_config;
+
+typedef struct hh_counters {
+    int64_t block_steps;    /* block steps executed (step 2-7 passes) */
+    int64_t particle_steps; /* corrected particle steps */
+    int64_t interactions;   /* pairwise terms evaluated, self excluded */
+    int64_t rebuilds;       /* tree/list rebuilds */
+} hh_counters;
+
+/* Fills cfg with defaults: eps2 = 1e-8, eta = 0.02, eta_s = 0.01,
+ * dt in [2^-30, 2^-6], dt_tree = 2^-6, theta = 0.5, leaf = 8, n_crit = 64,
+ * HH_FP64, default tiles. */
+void hh_config_default(hh_config *cfg);
+
+/* Creates a context on CUDA device `device` with room for n_max particles,
+ * nj_max j entries (particles + nodes), list_max list entries and groups_max
+ * groups.  All device memory is allocated here.  Returns HH_ENOMEM if it does
+ * not fit.  *out is NULL on failure; hh_last_error(NULL) then holds the reason. */
+int hh_create(hh_ctx **out, int device, const hh_config *cfg, int64_t n_max, int64_t nj_max,
+              int64_t list_max, int32_t groups_max);
+int hh_destroy(hh_ctx *ctx);
+
+/* Uses the given cudaStream_t (NULL = the context's own stream) for all
+ * following work of this context. */
+int hh_set_stream(hh_ctx *ctx, void *cuda_stream);
+
+/* Step 1 (Section 2): writes j entries [first, first + n) — particles and/or
+ * nodes — with their positions, velocities, accelerations, jerks, masses and
+ * times t (the time at which x, v, a, jk hold; for nodes the tree time).
+ * Host SoA arrays [3][n] (m, t: [n]).  Requires first + n <= nj_max; masses
+ * must be > 0 and all values finite. */
+int hh_set_j(hh_ctx *ctx, int64_t first, int64_t n, const double *x, const double *v,
+             const double *a, const double *jk, const double *m, const double *t);
+int hh_set_j_dev(hh_ctx *ctx, int64_t first, int64_t n, const double *x, const double *v,
+                 const double *a, const double *jk, const double *m, const double *t);
+
+/* Step 1: interaction lists (host arrays).  n_particles particles occupy j
+ * entries [0, n_particles) and n_j entries are in use.  Every idx must be in
+ * [0, n_j); group ranges must tile [0, n_particles) in ascending order.  The
+ * static i tiles are built here.  Validated before any kernel reads them. */
+int hh_set_lists(hh_ctx *ctx, int64_t n_particles, int64_t n_j, int32_t n_groups,
+                 const int64_t *off, const int32_t *idx, const int32_t *group_of);
+
+/* Per-particle block steps dt[n_particles] (powers of two).  hh_init_dt
+ * derives them from the stored a and jk instead (dt = eta_s |a| / |jk|,
+ * quantised).  Both set nothing else. */
+int hh_set_dt(hh_ctx *ctx, const double *dt);
+int hh_init_dt(hh_ctx *ctx);
+
+/* Step 4 (GRAPE predictor): predicts every j entry to time t into the
+ * context's predicted-record buffer: x + v D + a D^2/2 + jk D^3/6 and
+ * v + a D + jk D^2/2, with D = t - t_entry. */
+int hh_predict(hh_ctx *ctx, double t);
+
+/* Steps 4a + 5: acc, jerk and potential on the n_act particles i_idx (indices
+ * < n_particles, no repeats) from the predicted records of the last
+ * hh_predict, each particle summing over its group's list and skipping its
+ * own entry.  Outputs host SoA acc[3][n_act], jerk[3][n_act], pot[n_act]
+ * (any of them may be NULL).  The results also stay on the device for
+ * hh_correct. */
+int hh_force(hh_ctx *ctx, int32_t n_act, const int32_t *i_idx, double *acc, double *jerk,
+             double *pot);
+int hh_force_dev(hh_ctx *ctx, int32_t n_act, const int32_t *i_idx_dev, double *acc_dev,
+                 double *jerk_dev, double *pot_dev);
+
+/* Step 6: corrects the n_act particles i_idx at time t with the forces of the
+ * last hh_force, then sets each one's new block step (Aarseth criterion,
+ * power-of-two quantisation, at most doubling, doubling only on a boundary
+ * of the doubled step, clamped to [dt_min, dt_max]) and its time to t.
+ * Every particle of i_idx must have t_i + dt_i == t. */
+int hh_correct(hh_ctx *ctx, double t, int32_t n_act, const int32_t *i_idx);
+
+/* Initial forces: evaluates acc and jerk of ALL particles at their (common)
+ * time t from the current j entries and lists and stores them as the
+ * particles' a and jk (nodes are left unchanged). */
+int hh_init_forces(hh_ctx *ctx, double t);
+
+/* One block step on the device: t_next = min(t_i + dt_i); active particles
+ * {t_i + dt_i == t_next}; predict; force; correct.  Returns t_next and the
+ * number of active particles (synchronises the stream). */
+int hh_step(hh_ctx *ctx, double *t_next_out, int32_t *n_act_out);
+
+/* Block steps on the device until the next block time would exceed t_end,
+ * without host round trips per step (CUDA graph of unrolled block steps,
+ * replayed; each kernel becomes a no-op once done).  *n_steps_out (may be
+ * NULL) receives the number of block steps taken. */
+int hh_advance(hh_ctx *ctx, double t_end, int64_t *n_steps_out);
+
+/* Step 1 done by the library: copies the (synchronised) particle state to
+ * the host, rebuilds the Morton octree, groups (n_crit) and lists (theta,
+ * leaf) with the library's own host builder, reorders particles into Morton
+ * order, and uploads particles, nodes (tree time t) and lists.  All
+ * particles must be at time t. */
+int hh_rebuild(hh_ctx *ctx, double t);
+
+/* Loads n particles (host SoA, any order) at time t with a = jk = 0 and
+ * assigns them ids 0..n-1; hh_get_ids reports each slot's id after Morton
+ * reordering. */
+int hh_load_particles(hh_ctx *ctx, int64_t n, const double *x, const double *v, const double *m,
+                      double t);
+
+/* Full run of the tree loop from the loaded state at time t0 to t_end
+ * (a multiple of dt_tree): rebuild, initial forces, rebuild with node
+ * derivatives, initial steps, then alternate hh_advance and hh_rebuild
+ * every dt_tree. */
+int hh_run(hh_ctx *ctx, double t0, double t_end);
+
+/* Copies particle state [0, n_particles) to host SoA arrays (any may be NULL). */
+int hh_get_state(hh_ctx *ctx, double *x, double *v, double *a, double *jk, double *t, double *dt);
+int hh_get_ids(hh_ctx *ctx, int64_t *ids);
+int64_t hh_n_particles(const hh_ctx *ctx);
+int64_t hh_n_j(const hh_ctx *ctx);
+int hh_get_counters(hh_ctx *ctx, hh_counters *out);
+int hh_reset_counters(hh_ctx *ctx);
+
+/* Kernel-time accounting: CUDA-event time (ms) of the list-force kernel
+ * launches since the last reset, and their number.  Events are recorded on
+ * the stream the kernels run on. */
+int hh_force_timing(hh_ctx *ctx, int enable, double *ms_out, int64_t *launches_out);
+
+/* Total number of kernels this library launched in the process (all
+ * contexts; graph replays count every kernel node). */
+int64_t hh_kernel_launches(void);
+
+const char *hh_last_error(const hh_ctx *ctx);
+
+/* ---- Host tree builder (Section 2, step 1; Barnes 1990 grouping) -------- */
+/* Morton octree (21 bits per axis, root cube from the bounding box), groups =
+ * maximal cells with <= n_crit particles, one list per group: ancestors of
+ * the group are opened, the group's own particles enter directly, a cell with
+ * one particle enters as that particle, any other cell enters as a node when
+ * side < theta * (distance from its centre of mass to the group's bounding
+ * box), otherwise it is opened (a leaf gives its particles).  Lists are
+ * sorted ascending.  Node j index = n + cell number (cells in pre-order). */
+typedef struct hh_tree hh_tree;
+int hh_tree_build(hh_tree **out, int64_t n, const double *x, const double *v, const double *a,
+                  const double *jk, const double *m, int32_t leaf, int32_t n_crit, double theta);
+int hh_tree_sizes(const hh_tree *t, int64_t *n_nodes, int32_t *n_groups, int64_t *list_len);
+/* perm[k] = input index of Morton slot k; node arrays SoA [3][n_nodes]. */
+int hh_tree_export(const hh_tree *t, int32_t *perm, double *node_x, double *node_v,
+                   double *node_a, double *node_jk, double *node_m, int64_t *off, int32_t *idx,
+                   int32_t *group_of);
+int hh_tree_free(hh_tree *t);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

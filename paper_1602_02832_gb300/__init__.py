@@ -1,0 +1,336 @@
+"""Python binding of libhh: the list-driven 4th-order Hermite force path on GB300.
+
+Argument marshalling only.  Every step of the path runs in libhh's CUDA
+kernels (or, for the tree builder, its native host code); there is no Python or
+CPU fallback: importing this package raises if libhh.so has not been built.
+
+Functions keep the C names (see include/hh.h).  Host arrays are numpy float64
+arrays in structure-of-arrays layout [3, n] for 3-vectors; the *_dev calls take
+torch CUDA tensors (or raw device pointers) and run on the context's stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhh.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libhh.so is not built ({LIB_PATH}); run paper_1602_02832_gb300/build.py "
+                      "or __graft_entry__.build() first")
+
+_lib = C.CDLL(LIB_PATH)
+
+HH_OK, HH_EINVAL, HH_ENOMEM, HH_ECUDA, HH_ETIMEOUT, HH_ESTATE = 0, -1, -2, -3, -4, -5
+HH_FP64, HH_MIXED = 0, 1
+_ERR_NAMES = {HH_EINVAL: "HH_EINVAL", HH_ENOMEM: "HH_ENOMEM", HH_ECUDA: "HH_ECUDA", HH_ETIMEOUT: "HH_ETIMEOUT",
+              HH_ESTATE: "HH_ESTATE"}
+
+
+class HHError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class hh_config(C.Structure):
+    _fields_ = [("eps2", C.c_double), ("eta", C.c_double), ("eta_s", C.c_double), ("dt_min", C.c_double),
+                ("dt_max", C.c_double), ("dt_tree", C.c_double), ("theta", C.c_double), ("leaf", C.c_int32),
+                ("n_crit", C.c_int32), ("precision", C.c_int32), ("tile_i", C.c_int32), ("tile_j", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class hh_counters(C.Structure):
+    _fields_ = [("block_steps", C.c_int64), ("particle_steps", C.c_int64), ("interactions", C.c_int64),
+                ("rebuilds", C.c_int64)]
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_I32 = C.POINTER(C.c_int32)
+_I64 = C.POINTER(C.c_int64)
+
+_SIGS = {
+    "hh_config_default": (None, [C.POINTER(hh_config)]),
+    "hh_create": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(hh_config), C.c_int64, C.c_int64, C.c_int64,
+                            C.c_int32]),
+    "hh_destroy": (C.c_int, [_P]),
+    "hh_set_stream": (C.c_int, [_P, _P]),
+    "hh_set_j": (C.c_int, [_P, C.c_int64, C.c_int64, _D, _D, _D, _D, _D, _D]),
+    "hh_set_j_dev": (C.c_int, [_P, C.c_int64, C.c_int64, _P, _P, _P, _P, _P, _P]),
+    "hh_set_lists": (C.c_int, [_P, C.c_int64, C.c_int64, C.c_int32, _I64, _I32, _I32]),
+    "hh_set_dt": (C.c_int, [_P, _D]),
+    "hh_init_dt": (C.c_int, [_P]),
+    "hh_predict": (C.c_int, [_P, C.c_double]),
+    "hh_force": (C.c_int, [_P, C.c_int32, _I32, _D, _D, _D]),
+    "hh_force_dev": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
+    "hh_correct": (C.c_int, [_P, C.c_double, C.c_int32, _I32]),
+    "hh_init_forces": (C.c_int, [_P, C.c_double]),
+    "hh_step": (C.c_int, [_P, _D, _I32]),
+    "hh_advance": (C.c_int, [_P, C.c_double, _I64]),
+    "hh_rebuild": (C.c_int, [_P, C.c_double]),
+    "hh_load_particles": (C.c_int, [_P, C.c_int64, _D, _D, _D, C.c_double]),
+    "hh_run": (C.c_int, [_P, C.c_double, C.c_double]),
+    "hh_get_state": (C.c_int, [_P, _D, _D, _D, _D, _D, _D]),
+    "hh_get_ids": (C.c_int, [_P, _I64]),
+    "hh_n_particles": (C.c_int64, [_P]),
+    "hh_n_j": (C.c_int64, [_P]),
+    "hh_get_counters": (C.c_int, [_P, C.POINTER(hh_counters)]),
+    "hh_reset_counters": (C.c_int, [_P]),
+    "hh_force_timing": (C.c_int, [_P, C.c_int, _D, _I64]),
+    "hh_kernel_launches": (C.c_int64, []),
+    "hh_last_error": (C.c_char_p, [_P]),
+    "hh_tree_build": (C.c_int, [C.POINTER(_P), C.c_int64, _D, _D, _D, _D, _D, C.c_int32, C.c_int32, C.c_double]),
+    "hh_tree_sizes": (C.c_int, [_P, _I64, _I32, _I64]),
+    "hh_tree_export": (C.c_int, [_P, _I32, _D, _D, _D, _D, _D, _I64, _I32, _I32]),
+    "hh_tree_free": (C.c_int, [_P]),
+}
+
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+def lib():
+    return _lib
+
+
+def _ptr(a, ct=C.c_double):
+    return None if a is None else a.ctypes.data_as(C.POINTER(ct))
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def _dev_ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("device arrays must be contiguous CUDA tensors")
+    return t.data_ptr()
+
+
+def _check(rc, ctx=None):
+    if rc != HH_OK:
+        msg = _lib.hh_last_error(ctx)
+        raise HHError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def hh_last_error(ctx=None) -> str:
+    m = _lib.hh_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def hh_config_default() -> hh_config:
+    c = hh_config()
+    _lib.hh_config_default(C.byref(c))
+    return c
+
+
+def hh_kernel_launches() -> int:
+    return int(_lib.hh_kernel_launches())
+
+
+class Context:
+    """One simulation's device state (wraps an hh_ctx*)."""
+
+    def __init__(self, cfg: hh_config | None = None, n_max: int = 1, nj_max: int = 1, list_max: int = 1,
+                 groups_max: int = 1, device: int = 0):
+        cfg = cfg or hh_config_default()
+        h = _P()
+        _check(_lib.hh_create(C.byref(h), device, C.byref(cfg), n_max, nj_max, list_max, groups_max))
+        self.h = h
+        self.cfg = cfg
+        self.n_max, self.nj_max = n_max, nj_max
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.hh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _c(self, rc):
+        return _check(rc, self.h)
+
+    # -- step 1 -----------------------------------------------------------
+    def hh_set_stream(self, stream):
+        s = stream if isinstance(stream, int) else (stream.cuda_stream if stream is not None else None)
+        self._c(_lib.hh_set_stream(self.h, s))
+
+    def hh_set_j(self, first, x, v, a, jk, m, t):
+        n = len(m)
+        arrs = [_f64(u, (3, n)) for u in (x, v, a, jk)] + [_f64(m, (n,)), _f64(t, (n,))]
+        self._c(_lib.hh_set_j(self.h, first, n, *[_ptr(u) for u in arrs]))
+
+    def hh_set_j_dev(self, first, x, v, a, jk, m, t):
+        n = m.numel() if hasattr(m, "numel") else int(m)
+        self._c(_lib.hh_set_j_dev(self.h, first, n, *[_dev_ptr(u) for u in (x, v, a, jk, m, t)]))
+
+    def hh_set_lists(self, n_particles, n_j, off, idx, group_of):
+        off = np.ascontiguousarray(off, dtype=np.int64)
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        if idx.size == 0:
+            idx = np.zeros(1, np.int32)
+        gof = np.ascontiguousarray(group_of, dtype=np.int32)
+        self._c(_lib.hh_set_lists(self.h, n_particles, n_j, len(off) - 1, _ptr(off, C.c_int64),
+                                  _ptr(idx, C.c_int32), _ptr(gof, C.c_int32)))
+
+    def hh_set_dt(self, dt):
+        self._c(_lib.hh_set_dt(self.h, _ptr(_f64(dt))))
+
+    def hh_init_dt(self):
+        self._c(_lib.hh_init_dt(self.h))
+
+    # -- steps 4, 4a + 5, 6 ----------------------------------------------------
+    def hh_predict(self, t):
+        self._c(_lib.hh_predict(self.h, float(t)))
+
+    def hh_force(self, i_idx, want=(True, True, True)):
+        i_idx = np.ascontiguousarray(i_idx, dtype=np.int32)
+        k = len(i_idx)
+        acc = np.zeros((3, k)) if want[0] else None
+        jerk = np.zeros((3, k)) if want[1] else None
+        pot = np.zeros(k) if want[2] else None
+        self._c(_lib.hh_force(self.h, k, _ptr(i_idx, C.c_int32), _ptr(acc), _ptr(jerk), _ptr(pot)))
+        return acc, jerk, pot
+
+    def hh_force_dev(self, i_idx, acc, jerk, pot):
+        n = i_idx.numel()
+        self._c(_lib.hh_force_dev(self.h, n, _dev_ptr(i_idx), _dev_ptr(acc), _dev_ptr(jerk), _dev_ptr(pot)))
+
+    def hh_correct(self, t, i_idx):
+        i_idx = np.ascontiguousarray(i_idx, dtype=np.int32)
+        self._c(_lib.hh_correct(self.h, float(t), len(i_idx), _ptr(i_idx, C.c_int32)))
+
+    def hh_init_forces(self, t):
+        self._c(_lib.hh_init_forces(self.h, float(t)))
+
+    # -- device-resident loop --------------------------------------------------
+    def hh_step(self):
+        t = C.c_double()
+        na = C.c_int32()
+        self._c(_lib.hh_step(self.h, C.byref(t), C.byref(na)))
+        return t.value, na.value
+
+    def hh_advance(self, t_end):
+        ns = C.c_int64()
+        self._c(_lib.hh_advance(self.h, float(t_end), C.byref(ns)))
+        return ns.value
+
+    def hh_rebuild(self, t):
+        self._c(_lib.hh_rebuild(self.h, float(t)))
+
+    def hh_load_particles(self, x, v, m, t=0.0):
+        n = len(m)
+        self._c(_lib.hh_load_particles(self.h, n, _ptr(_f64(x, (3, n))), _ptr(_f64(v, (3, n))),
+                                       _ptr(_f64(m, (n,))), float(t)))
+
+    def hh_run(self, t0, t_end):
+        self._c(_lib.hh_run(self.h, float(t0), float(t_end)))
+
+    # -- readback ----------------------------------------------------------------
+    @property
+    def n(self):
+        return int(_lib.hh_n_particles(self.h))
+
+    @property
+    def nj(self):
+        return int(_lib.hh_n_j(self.h))
+
+    def hh_get_state(self):
+        n = self.n
+        x, v, a, jk = (np.zeros((3, n)) for _ in range(4))
+        t, dt = np.zeros(n), np.zeros(n)
+        self._c(_lib.hh_get_state(self.h, *[_ptr(u) for u in (x, v, a, jk, t, dt)]))
+        return dict(x=x, v=v, a=a, jk=jk, t=t, dt=dt)
+
+    def hh_get_ids(self):
+        ids = np.zeros(self.n, np.int64)
+        self._c(_lib.hh_get_ids(self.h, _ptr(ids, C.c_int64)))
+        return ids
+
+    def hh_get_counters(self):
+        c = hh_counters()
+        self._c(_lib.hh_get_counters(self.h, C.byref(c)))
+        return dict(block_steps=c.block_steps, particle_steps=c.particle_steps, interactions=c.interactions,
+                    rebuilds=c.rebuilds)
+
+    def hh_reset_counters(self):
+        self._c(_lib.hh_reset_counters(self.h))
+
+    def hh_force_timing(self, enable=-1):
+        ms = C.c_double()
+        nl = C.c_int64()
+        self._c(_lib.hh_force_timing(self.h, int(enable), C.byref(ms), C.byref(nl)))
+        return ms.value, nl.value
+
+
+@dataclass
+class Tree:
+    """Output of the library's host tree builder (hh_tree_build)."""
+    perm: np.ndarray
+    node_x: np.ndarray  # [3, n_nodes]
+    node_v: np.ndarray
+    node_a: np.ndarray
+    node_jk: np.ndarray
+    node_m: np.ndarray
+    off: np.ndarray
+    idx: np.ndarray
+    group_of: np.ndarray
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_nodes(self):
+        return len(self.node_m)
+
+    @property
+    def n_groups(self):
+        return len(self.off) - 1
+
+
+def hh_tree_build(x, v, a, jk, m, leaf=8, n_crit=64, theta=0.5) -> Tree:
+    """Host tree, groups and lists (SoA [3, n] inputs, any particle order)."""
+    n = len(m)
+    arrs = [_f64(u, (3, n)) for u in (x, v, a, jk)] + [_f64(m, (n,))]
+    h = _P()
+    _check(_lib.hh_tree_build(C.byref(h), n, *[_ptr(u) for u in arrs], int(leaf), int(n_crit), float(theta)))
+    try:
+        nn, ng, ll = C.c_int64(), C.c_int32(), C.c_int64()
+        _check(_lib.hh_tree_sizes(h, C.byref(nn), C.byref(ng), C.byref(ll)))
+        nn, ng, ll = nn.value, ng.value, ll.value
+        perm = np.zeros(n, np.int32)
+        nx, nv, na, nj = (np.zeros((3, nn)) for _ in range(4))
+        nm = np.zeros(nn)
+        off = np.zeros(ng + 1, np.int64)
+        idx = np.zeros(max(ll, 1), np.int32)
+        gof = np.zeros(n, np.int32)
+        _check(_lib.hh_tree_export(h, _ptr(perm, C.c_int32), _ptr(nx), _ptr(nv), _ptr(na), _ptr(nj), _ptr(nm),
+                                   _ptr(off, C.c_int64), _ptr(idx, C.c_int32), _ptr(gof, C.c_int32)))
+    finally:
+        _lib.hh_tree_free(h)
+    return Tree(perm, nx, nv, na, nj, nm, off, idx[:ll], gof)

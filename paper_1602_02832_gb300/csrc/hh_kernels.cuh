@@ -1,0 +1,675 @@
+// Device code of the list-driven Hermite hot path (sm_103a).
+//
+// One block step (Section 2, tree-loop steps 2-7) is three kernels:
+//   k_predict  every j entry (particles and tree nodes) to the block time
+//              (GRAPE predictor; step 4), written as packed records;
+//   k_force    static i tiles pull work from a queue; each finds its active
+//              particles (t_i + dt_i == t_next, step 2) with one ballot and
+//              sums acc / jerk / pot over its group's list (steps 4a + 5);
+//   k_correct  4th-order Hermite corrector + Aarseth block step (step 6),
+//              and the min over t_i + dt_i that starts the next step.
+// No kernel waits on another CTA; there are no spin loops.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hh {
+
+constexpr int kThreads = 128;  // threads per force CTA (4 warps)
+constexpr int kMaxTileI = 32;  // particles per static i tile (one ballot)
+
+// ---------------------------------------------------------------- scalars
+struct DevScalars {
+    unsigned long long tmin[2];  // min(t_i + dt_i) as positive-double bit patterns
+    double t_end;                // loop bound of hh_advance
+    int32_t done;                // set once the next block time exceeds t_end
+    int32_t err;                 // device-detected error (HH_* code), 0 = none
+    uint32_t work;               // force tile queue head
+    int32_t n_act_last;          // active particles of the last corrected step
+    int64_t n;                   // particles
+    int64_t nj;                  // j entries
+    int32_t n_tiles;             // static i tiles
+    int32_t pad0;
+    unsigned long long block_steps, particle_steps, interactions;
+};
+
+// Block-step control passed by value to every kernel of a step.
+struct StepCtl {
+    int32_t mode;       // 0: active = {t_i + dt_i == t_next}; 1: marked; 2: all particles
+    int32_t slot_cur;   // tmin slot holding this step's time (mode 0)
+    int32_t slot_next;  // tmin slot that receives the next step's time (mode 0)
+    int32_t pad;
+    double t_arg;       // step time for modes 1 and 2
+};
+
+// ---------------------------------------------------------------- records
+// Predicted j record, plain form: (x, y, z, m), (vx, vy, vz, 0) in FP64.
+struct __align__(32) RecF64 {
+    double4 xm;
+    double4 v;
+};
+// Predicted j record, mixed form: position as an unevaluated float pair
+// x = hi + lo (|lo| <= ulp(hi)/2), velocity and mass in FP32.
+struct __align__(16) RecMix {
+    float4 hm;  // (x_hi, y_hi, z_hi, m)
+    float4 lo;  // (x_lo, y_lo, z_lo, 0)
+    float4 v;   // (vx, vy, vz, 0)
+};
+
+struct State {
+    double *x, *v, *a, *jk;  // [3][cap_j]
+    double *m, *t;           // [cap_j]
+    double *dt;              // [cap_n]
+    double *acc1, *jerk1, *pot1;  // [3][cap_n], [cap_n]: last force results
+    int32_t *mark;           // [cap_n]
+    int64_t cap_j, cap_n;
+};
+
+struct Lists {
+    const int64_t *off;
+    const int32_t *idx;
+    const int4 *tiles;  // (p_begin, p_end, group, 0)
+};
+
+struct Params {
+    double eps2, eta, eta_s, dt_min, dt_max;
+};
+
+__device__ __forceinline__ double bits_to_time(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+// Time of this step; false if the step is a no-op (loop finished).
+__device__ __forceinline__ bool step_time(const DevScalars *ds, const StepCtl &c, double *t)
+{
+    if (c.mode != 0) {
+        *t = c.t_arg;
+        return true;
+    }
+    if (*(volatile const int32_t *)&ds->done) return false;
+    double tn = bits_to_time(*(volatile const unsigned long long *)&ds->tmin[c.slot_cur]);
+    if (!(tn <= ds->t_end)) return false;
+    *t = tn;
+    return true;
+}
+
+__device__ __forceinline__ bool is_active(const State &s, const StepCtl &c, int64_t p, double tnow)
+{
+    if (c.mode == 0) return s.t[p] + s.dt[p] == tnow;
+    if (c.mode == 1) return s.mark[p] != 0;
+    return true;
+}
+
+// Largest power of two <= x for positive normal x: clear the mantissa.
+__device__ __forceinline__ double pow2_floor(double x)
+{
+    return __longlong_as_double(__double_as_longlong(x) & (long long)0xFFF0000000000000ull);
+}
+
+// -------------------------------------------------------------- predictor
+// x + v D + a D^2/2 + jk D^3/6 and v + a D + jk D^2/2, in Horner form.
+__device__ __forceinline__ void predict_one(const State &s, int64_t e, double tnow, double xp[3], double vp[3])
+{
+    const double D = tnow - s.t[e];
+    const double h = 0.5 * D, th = D * (1.0 / 3.0);
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const double x = s.x[d * s.cap_j + e], v = s.v[d * s.cap_j + e];
+        const double a = s.a[d * s.cap_j + e], j = s.jk[d * s.cap_j + e];
+        xp[d] = x + D * (v + h * (a + th * j));
+        vp[d] = v + D * (a + h * j);
+    }
+}
+
+template <typename Rec>
+__device__ __forceinline__ void store_rec(Rec *out, int64_t e, const double xp[3], const double vp[3], double m);
+
+template <>
+__device__ __forceinline__ void store_rec<RecF64>(RecF64 *out, int64_t e, const double xp[3], const double vp[3],
+                                                 double m)
+{
+    RecF64 r;
+    r.xm = make_double4(xp[0], xp[1], xp[2], m);
+    r.v = make_double4(vp[0], vp[1], vp[2], 0.0);
+    out[e] = r;
+}
+
+template <>
+__device__ __forceinline__ void store_rec<RecMix>(RecMix *out, int64_t e, const double xp[3], const double vp[3],
+                                                 double m)
+{
+    float hi[3], lo[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        hi[d] = __double2float_rn(xp[d]);
+        lo[d] = __double2float_rn(xp[d] - (double)hi[d]);
+    }
+    RecMix r;
+    r.hm = make_float4(hi[0], hi[1], hi[2], __double2float_rn(m));
+    r.lo = make_float4(lo[0], lo[1], lo[2], 0.f);
+    r.v = make_float4(__double2float_rn(vp[0]), __double2float_rn(vp[1]), __double2float_rn(vp[2]), 0.f);
+    out[e] = r;
+}
+
+template <typename Rec>
+__global__ void k_predict(State s, Rec *rec, DevScalars *ds, StepCtl c)
+{
+    double tnow;
+    if (!step_time(ds, c, &tnow)) {
+        if (c.mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) ds->done = 1;
+        return;
+    }
+    if (c.mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+        ds->tmin[c.slot_next] = 0x7FF0000000000000ull;  // +inf
+        ds->work = 0u;
+        ds->n_act_last = 0;
+        ds->block_steps += 1ull;
+    }
+    const int64_t nj = ds->nj;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nj; e += (int64_t)gridDim.x * blockDim.x) {
+        double xp[3], vp[3];
+        predict_one(s, e, tnow, xp, vp);
+        store_rec<Rec>(rec, e, xp, vp, s.m[e]);
+    }
+}
+
+// ------------------------------------------------------ pairwise kernels
+// Plummer-softened pair term (Makino & Aarseth 1992): r = x_j - x_i,
+// w = v_j - v_i, s = r^2 + eps^2; a += m r s^-3/2;
+// jerk += m (w s^-3/2 - 3 (r.w) r s^-5/2); pot -= m s^-1/2.
+
+struct AccF64 {
+    double ax, ay, az, jx, jy, jz, p;
+    __device__ void zero() { ax = ay = az = jx = jy = jz = p = 0.0; }
+};
+
+struct IF64 {
+    double x, y, z, vx, vy, vz;
+};
+
+__device__ __forceinline__ void load_i(const RecF64 *rec, int64_t i, IF64 &o)
+{
+    const RecF64 r = rec[i];
+    o.x = r.xm.x; o.y = r.xm.y; o.z = r.xm.z;
+    o.vx = r.v.x; o.vy = r.v.y; o.vz = r.v.z;
+}
+
+__device__ __forceinline__ void interact(const IF64 &I, const RecF64 &J, bool self, double eps2, AccF64 &A)
+{
+    const double dx = J.xm.x - I.x, dy = J.xm.y - I.y, dz = J.xm.z - I.z;
+    const double wx = J.v.x - I.vx, wy = J.v.y - I.vy, wz = J.v.z - I.vz;
+    double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+    r2 = self ? 1.0 : r2;
+    const double mj = self ? 0.0 : J.xm.w;
+    const double rw = fma(dx, wx, fma(dy, wy, dz * wz));
+    const double rinv = rsqrt(r2);
+    const double rinv2 = rinv * rinv;
+    const double mr = mj * rinv;
+    const double mr3 = mr * rinv2;
+    const double al = 3.0 * rw * rinv2;
+    A.p += mr;
+    A.ax = fma(mr3, dx, A.ax);
+    A.ay = fma(mr3, dy, A.ay);
+    A.az = fma(mr3, dz, A.az);
+    A.jx = fma(mr3, fma(-al, dx, wx), A.jx);
+    A.jy = fma(mr3, fma(-al, dy, wy), A.jy);
+    A.jz = fma(mr3, fma(-al, dz, wz), A.jz);
+}
+
+// Mixed: chunk partials in FP32, folded into (hi, lo) pairs after each
+// staged chunk with Knuth's TwoSum, so that the running sum is carried to
+// about 2^-48 relative while the inner loop stays plain FP32.
+struct F2 {
+    float h, l;
+};
+
+__device__ __forceinline__ void two_sum_into(F2 &acc, float b)
+{
+    const float s = __fadd_rn(acc.h, b);
+    const float bb = __fsub_rn(s, acc.h);
+    const float err = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    acc.h = s;
+    acc.l = __fadd_rn(acc.l, err);
+}
+
+// (h1, l1) + (h2, l2) with one TwoSum on the heads and a renormalising
+// Fast2Sum (Dekker): deterministic for a fixed operand order.
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b)
+{
+    const float s = __fadd_rn(a.h, b.h);
+    const float bb = __fsub_rn(s, a.h);
+    float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+    F2 r;
+    r.h = __fadd_rn(s, e);
+    r.l = __fsub_rn(e, __fsub_rn(r.h, s));
+    return r;
+}
+
+struct AccMix {
+    float ax, ay, az, jx, jy, jz, p;  // current chunk
+    F2 Ax, Ay, Az, Jx, Jy, Jz, P;     // running compensated sums
+    __device__ void zero()
+    {
+        ax = ay = az = jx = jy = jz = p = 0.f;
+        Ax = Ay = Az = Jx = Jy = Jz = P = F2{0.f, 0.f};
+    }
+    __device__ void fold()
+    {
+        two_sum_into(Ax, ax); two_sum_into(Ay, ay); two_sum_into(Az, az);
+        two_sum_into(Jx, jx); two_sum_into(Jy, jy); two_sum_into(Jz, jz);
+        two_sum_into(P, p);
+        ax = ay = az = jx = jy = jz = p = 0.f;
+    }
+};
+
+struct IMix {
+    float xh, yh, zh, xl, yl, zl, vx, vy, vz;
+};
+
+__device__ __forceinline__ void load_i(const RecMix *rec, int64_t i, IMix &o)
+{
+    const RecMix r = rec[i];
+    o.xh = r.hm.x; o.yh = r.hm.y; o.zh = r.hm.z;
+    o.xl = r.lo.x; o.yl = r.lo.y; o.zl = r.lo.z;
+    o.vx = r.v.x; o.vy = r.v.y; o.vz = r.v.z;
+}
+
+__device__ __forceinline__ void interact(const IMix &I, const RecMix &J, bool self, float eps2, AccMix &A)
+{
+    // i-j difference of the float pairs: (hi_j - hi_i) + (lo_j - lo_i)
+    const float dx = __fadd_rn(__fsub_rn(J.hm.x, I.xh), __fsub_rn(J.lo.x, I.xl));
+    const float dy = __fadd_rn(__fsub_rn(J.hm.y, I.yh), __fsub_rn(J.lo.y, I.yl));
+    const float dz = __fadd_rn(__fsub_rn(J.hm.z, I.zh), __fsub_rn(J.lo.z, I.zl));
+    const float wx = J.v.x - I.vx, wy = J.v.y - I.vy, wz = J.v.z - I.vz;
+    float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+    r2 = self ? 1.f : r2;
+    const float mj = self ? 0.f : J.hm.w;
+    const float rw = fmaf(dx, wx, fmaf(dy, wy, dz * wz));
+    float rinv = rsqrtf(r2);
+    // one Newton-Raphson step for 1/sqrt: y <- y (3 - r2 y^2) / 2
+    rinv = rinv * fmaf(-0.5f * r2, rinv * rinv, 1.5f);
+    const float rinv2 = rinv * rinv;
+    const float mr = mj * rinv;
+    const float mr3 = mr * rinv2;
+    const float al = 3.f * rw * rinv2;
+    A.p += mr;
+    A.ax = fmaf(mr3, dx, A.ax);
+    A.ay = fmaf(mr3, dy, A.ay);
+    A.az = fmaf(mr3, dz, A.az);
+    A.jx = fmaf(mr3, fmaf(-al, dx, wx), A.jx);
+    A.jy = fmaf(mr3, fmaf(-al, dy, wy), A.jy);
+    A.jz = fmaf(mr3, fmaf(-al, dz, wz), A.jz);
+}
+
+// ---------------------------------------------- cross-slice reductions
+__device__ __forceinline__ void acc_shfl_add(AccF64 &A, int off)
+{
+    A.ax += __shfl_xor_sync(0xffffffffu, A.ax, off);
+    A.ay += __shfl_xor_sync(0xffffffffu, A.ay, off);
+    A.az += __shfl_xor_sync(0xffffffffu, A.az, off);
+    A.jx += __shfl_xor_sync(0xffffffffu, A.jx, off);
+    A.jy += __shfl_xor_sync(0xffffffffu, A.jy, off);
+    A.jz += __shfl_xor_sync(0xffffffffu, A.jz, off);
+    A.p += __shfl_xor_sync(0xffffffffu, A.p, off);
+}
+
+__device__ __forceinline__ F2 f2_shfl(F2 a, int off)
+{
+    F2 b;
+    b.h = __shfl_xor_sync(0xffffffffu, a.h, off);
+    b.l = __shfl_xor_sync(0xffffffffu, a.l, off);
+    // operand order by lane bit keeps both partners bitwise identical
+    return ((threadIdx.x & off) == 0) ? f2_add(a, b) : f2_add(b, a);
+}
+
+__device__ __forceinline__ void acc_shfl_add(AccMix &A, int off)
+{
+    A.Ax = f2_shfl(A.Ax, off); A.Ay = f2_shfl(A.Ay, off); A.Az = f2_shfl(A.Az, off);
+    A.Jx = f2_shfl(A.Jx, off); A.Jy = f2_shfl(A.Jy, off); A.Jz = f2_shfl(A.Jz, off);
+    A.P = f2_shfl(A.P, off);
+}
+
+struct RedF64 {
+    double v[7];
+};
+struct RedMix {
+    F2 v[7];
+};
+
+__device__ __forceinline__ void to_red(const AccF64 &A, RedF64 &r)
+{
+    r.v[0] = A.ax; r.v[1] = A.ay; r.v[2] = A.az; r.v[3] = A.jx; r.v[4] = A.jy; r.v[5] = A.jz; r.v[6] = A.p;
+}
+__device__ __forceinline__ void to_red(const AccMix &A, RedMix &r)
+{
+    r.v[0] = A.Ax; r.v[1] = A.Ay; r.v[2] = A.Az; r.v[3] = A.Jx; r.v[4] = A.Jy; r.v[5] = A.Jz; r.v[6] = A.P;
+}
+__device__ __forceinline__ void red_add(RedF64 &a, const RedF64 &b)
+{
+#pragma unroll
+    for (int q = 0; q < 7; q++) a.v[q] += b.v[q];
+}
+__device__ __forceinline__ void red_add(RedMix &a, const RedMix &b)
+{
+#pragma unroll
+    for (int q = 0; q < 7; q++) a.v[q] = f2_add(a.v[q], b.v[q]);
+}
+__device__ __forceinline__ double red_get(const RedF64 &r, int q) { return r.v[q]; }
+__device__ __forceinline__ double red_get(const RedMix &r, int q) { return (double)r.v[q].h + (double)r.v[q].l; }
+
+template <typename Rec>
+struct Traits;
+template <>
+struct Traits<RecF64> {
+    using I = IF64;
+    using Acc = AccF64;
+    using Red = RedF64;
+    using Eps = double;
+};
+template <>
+struct Traits<RecMix> {
+    using I = IMix;
+    using Acc = AccMix;
+    using Red = RedMix;
+    using Eps = float;
+};
+
+__device__ __forceinline__ void fold_chunk(AccF64 &) {}
+__device__ __forceinline__ void fold_chunk(AccMix &A) { A.fold(); }
+
+// ------------------------------------------------------------ list force
+// CTA = 4 warps on one static i tile (<= 32 consecutive particles of one
+// group).  With n_a active particles, lane l serves i slot (l mod I),
+// I = next power of two >= n_a, and the CTA's 128 threads form 128 / I
+// j slices that stride through each staged chunk of the list.  Slices are
+// summed in a fixed order (shuffles, then warps), so each particle's result
+// depends only on its list, its tile's active count and the tile shape.
+template <typename Rec, int TJ>
+__global__ void __launch_bounds__(kThreads) k_force(State s, const Rec *__restrict__ rec, Lists L, DevScalars *ds,
+                                                    StepCtl c, Params prm)
+{
+    using T = Traits<Rec>;
+    double tnow;
+    if (!step_time(ds, c, &tnow)) return;
+
+    __shared__ Rec s_rec[TJ];
+    __shared__ int32_t s_idx[TJ];
+    __shared__ typename T::Red s_red[kThreads / 32][kMaxTileI];
+    __shared__ int s_tile;
+    __shared__ uint32_t s_mask;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n_tiles = ds->n_tiles;
+    const typename T::Eps eps2 = (typename T::Eps)prm.eps2;
+    unsigned long long n_int = 0;
+
+    for (;;) {
+        if (tid == 0) s_tile = (int)atomicAdd(&ds->work, 1u);
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= n_tiles) break;
+        const int4 td = L.tiles[tile];
+        if (warp == 0) {
+            const int64_t p = td.x + lane;
+            const bool act = (p < td.y) && is_active(s, c, p, tnow);
+            const uint32_t mk = __ballot_sync(0xffffffffu, act);
+            if (lane == 0) s_mask = mk;
+        }
+        __syncthreads();
+        const uint32_t mask = s_mask;
+        const int n_a = __popc(mask);
+        if (n_a == 0) continue;  // uniform: the next iteration's barrier orders s_tile reuse
+
+        int I = 1;
+        while (I < n_a) I <<= 1;
+        const int islot = tid & (I - 1);
+        const int jslice = tid / I;
+        const int S = kThreads / I;
+        const bool has_i = islot < n_a;
+        // position of the islot-th set bit of mask
+        int64_t pi = -1;
+        {
+            uint32_t mm = mask;
+            for (int q = 0; q < islot && mm; q++) mm &= mm - 1;
+            if (has_i) pi = td.x + (__ffs(mm) - 1);
+        }
+        typename T::I Iv;
+        if (has_i) load_i(rec, pi, Iv);
+        else load_i(rec, td.x + (__ffs(mask) - 1), Iv);  // harmless duplicate, result dropped
+        typename T::Acc A;
+        A.zero();
+
+        const int64_t lb = L.off[td.z], le = L.off[td.z + 1];
+        const int64_t len = le - lb;
+        if (tid == 0) n_int += (unsigned long long)n_a * (unsigned long long)(len - 1);
+        for (int64_t c0 = 0; c0 < len; c0 += TJ) {
+            const int nc = (len - c0 < (int64_t)TJ) ? (int)(len - c0) : TJ;
+            for (int e = tid; e < nc; e += kThreads) {
+                const int32_t j = L.idx[lb + c0 + e];
+                s_idx[e] = j;
+                s_rec[e] = rec[j];
+            }
+            __syncthreads();
+            for (int e = jslice; e < nc; e += S) {
+                const int32_t j = s_idx[e];
+                interact(Iv, s_rec[e], (int64_t)j == pi, eps2, A);
+            }
+            fold_chunk(A);
+            __syncthreads();
+        }
+        // reduce the S slices of each i slot: lanes l, l+I, ... then warps
+        for (int off = I; off < 32; off <<= 1) acc_shfl_add(A, off);
+        if (lane < I && lane < 32) {
+            typename T::Red r;
+            to_red(A, r);
+            s_red[warp][lane] = r;
+        }
+        __syncthreads();
+        if (tid < n_a) {
+            typename T::Red r = s_red[0][tid];
+            for (int w = 1; w < kThreads / 32; w++) red_add(r, s_red[w][tid]);
+            // this thread's particle: the tid-th active one
+            uint32_t mm = mask;
+            for (int q = 0; q < tid; q++) mm &= mm - 1;
+            const int64_t p = td.x + (__ffs(mm) - 1);
+            s.acc1[0 * s.cap_n + p] = red_get(r, 0);
+            s.acc1[1 * s.cap_n + p] = red_get(r, 1);
+            s.acc1[2 * s.cap_n + p] = red_get(r, 2);
+            s.jerk1[0 * s.cap_n + p] = red_get(r, 3);
+            s.jerk1[1 * s.cap_n + p] = red_get(r, 4);
+            s.jerk1[2 * s.cap_n + p] = red_get(r, 5);
+            s.pot1[p] = -red_get(r, 6);
+        }
+        // next iteration's first barrier protects s_red / s_rec reuse
+    }
+    if (tid == 0 && n_int) atomicAdd(&ds->interactions, n_int);
+}
+
+// -------------------------------------------------------------- corrector
+__device__ __forceinline__ double norm3(double a, double b, double c) { return sqrt(a * a + b * b + c * c); }
+
+// Block quantisation (McMillan 1986): largest power of two <= want, at most
+// doubling, doubling only where t_new is a multiple of the doubled step,
+// clamped to [dt_min, dt_max]; NaN keeps the old step, +inf asks to double.
+__device__ __forceinline__ double block_dt(double want, double dt_old, double t_new, double dt_min, double dt_max)
+{
+    double q;
+    if (want != want) q = dt_old;
+    else if (want > 1.0e300) q = 2.0 * dt_old;
+    else q = pow2_floor(want);
+    if (q > 2.0 * dt_old) q = 2.0 * dt_old;
+    if (q > dt_old) {
+        const double r = t_new / q;
+        if (r != floor(r)) q = dt_old;
+    }
+    if (q > dt_max) q = dt_max;
+    if (q < dt_min) q = dt_min;
+    return q;
+}
+
+__device__ __forceinline__ void atomic_min_time(unsigned long long *slot, double t)
+{
+    atomicMin(slot, (unsigned long long)__double_as_longlong(t));
+}
+
+// Hermite corrector (Makino & Aarseth 1992) for the active particles:
+// a2 = (-6 (a0 - a1) - D (4 j0 + 2 j1)) / D^2, a3 = (12 (a0 - a1) + 6 D (j0 + j1)) / D^3,
+// x1 = x_p + a2 D^4/24 + a3 D^5/120, v1 = v_p + a2 D^3/6 + a3 D^4/24;
+// new step from Aarseth's criterion at the end of the step.
+__global__ void k_correct(State s, DevScalars *ds, StepCtl c, Params prm)
+{
+    double tnow;
+    if (!step_time(ds, c, &tnow)) return;
+    const int64_t n = ds->n;
+    double my_min = __longlong_as_double(0x7FF0000000000000LL);
+    int my_cnt = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const bool act = is_active(s, c, p, tnow);
+        if (act) {
+            if (c.mode == 1 && s.t[p] + s.dt[p] != tnow) {
+                atomicExch(&ds->err, -1);  // HH_EINVAL: marked particle not due at t
+                continue;
+            }
+            const double D = tnow - s.t[p];
+            double xp[3], vp[3];
+            predict_one(s, p, tnow, xp, vp);
+            double a1[3], j1[3], a2e[3], a3v[3];
+            const double D2 = D * D, D3 = D2 * D;
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                const double a0 = s.a[d * s.cap_j + p], j0 = s.jk[d * s.cap_j + p];
+                a1[d] = s.acc1[d * s.cap_n + p];
+                j1[d] = s.jerk1[d * s.cap_n + p];
+                const double a2 = (-6.0 * (a0 - a1[d]) - D * (4.0 * j0 + 2.0 * j1[d])) / D2;
+                const double a3 = (12.0 * (a0 - a1[d]) + 6.0 * D * (j0 + j1[d])) / D3;
+                s.x[d * s.cap_j + p] = xp[d] + D2 * D2 * (a2 * (1.0 / 24.0) + a3 * D * (1.0 / 120.0));
+                s.v[d * s.cap_j + p] = vp[d] + D3 * (a2 * (1.0 / 6.0) + a3 * D * (1.0 / 24.0));
+                s.a[d * s.cap_j + p] = a1[d];
+                s.jk[d * s.cap_j + p] = j1[d];
+                a2e[d] = a2 + a3 * D;
+                a3v[d] = a3;
+            }
+            const double na = norm3(a1[0], a1[1], a1[2]), nj = norm3(j1[0], j1[1], j1[2]);
+            const double n2 = norm3(a2e[0], a2e[1], a2e[2]), n3 = norm3(a3v[0], a3v[1], a3v[2]);
+            const double want = sqrt(prm.eta * (na * n2 + nj * nj) / (nj * n3 + n2 * n2));
+            const double dtn = block_dt(want, s.dt[p], tnow, prm.dt_min, prm.dt_max);
+            s.t[p] = tnow;
+            s.dt[p] = dtn;
+            my_cnt++;
+        }
+        const double tn = s.t[p] + s.dt[p];
+        my_min = tn < my_min ? tn : my_min;
+    }
+    if (c.mode != 0) return;
+    // block min, then one atomic per CTA
+    for (int off = 16; off > 0; off >>= 1) {
+        my_min = fmin(my_min, __shfl_xor_sync(0xffffffffu, my_min, off));
+        my_cnt += __shfl_xor_sync(0xffffffffu, my_cnt, off);
+    }
+    __shared__ double s_min[32];
+    __shared__ int s_cnt[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_min[warp] = my_min;
+        s_cnt[warp] = my_cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mn = s_min[0];
+        int cn = s_cnt[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+            mn = fmin(mn, s_min[w]);
+            cn += s_cnt[w];
+        }
+        atomic_min_time(&ds->tmin[c.slot_next], mn);
+        if (cn) {
+            atomicAdd(&ds->n_act_last, cn);
+            atomicAdd(&ds->particle_steps, (unsigned long long)cn);
+        }
+    }
+}
+
+// min over particles of t_i + dt_i into tmin[slot] (slot preset to +inf).
+__global__ void k_min_time(State s, DevScalars *ds, int slot)
+{
+    const int64_t n = ds->n;
+    double my_min = __longlong_as_double(0x7FF0000000000000LL);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const double tn = s.t[p] + s.dt[p];
+        my_min = tn < my_min ? tn : my_min;
+    }
+    for (int off = 16; off > 0; off >>= 1) my_min = fmin(my_min, __shfl_xor_sync(0xffffffffu, my_min, off));
+    if ((threadIdx.x & 31) == 0) atomic_min_time(&ds->tmin[slot], my_min);
+}
+
+// Initial step from eta_s |a| / |jk|, quantised (reading: the paper is silent).
+__global__ void k_init_dt(State s, DevScalars *ds, Params prm)
+{
+    const int64_t n = ds->n;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const double na = norm3(s.a[p], s.a[s.cap_j + p], s.a[2 * s.cap_j + p]);
+        const double nj = norm3(s.jk[p], s.jk[s.cap_j + p], s.jk[2 * s.cap_j + p]);
+        double q;
+        if (nj == 0.0) q = prm.dt_max;
+        else {
+            const double want = prm.eta_s * na / nj;
+            q = (want > 0.0 && want < 1.0e300) ? pow2_floor(want) : prm.dt_max;
+        }
+        if (q > prm.dt_max) q = prm.dt_max;
+        if (q < prm.dt_min) q = prm.dt_min;
+        s.dt[p] = q;
+    }
+}
+
+// a, jk of every particle <- last force results (initial forces).
+__global__ void k_adopt_forces(State s, DevScalars *ds)
+{
+    const int64_t n = ds->n;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            s.a[d * s.cap_j + p] = s.acc1[d * s.cap_n + p];
+            s.jk[d * s.cap_j + p] = s.jerk1[d * s.cap_n + p];
+        }
+    }
+}
+
+__global__ void k_set_marks(int32_t *mark, const int32_t *idx, int32_t n, int32_t value)
+{
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) mark[idx[q]] = value;
+}
+
+// out[3][n_act] (SoA) <- acc1 etc. at i_idx
+__global__ void k_gather_out(State s, const int32_t *idx, int32_t n_act, double *acc, double *jerk, double *pot)
+{
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_act; q += gridDim.x * blockDim.x) {
+        const int64_t p = idx[q];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            if (acc) acc[(int64_t)d * n_act + q] = s.acc1[d * s.cap_n + p];
+            if (jerk) jerk[(int64_t)d * n_act + q] = s.jerk1[d * s.cap_n + p];
+        }
+        if (pot) pot[q] = s.pot1[p];
+    }
+}
+
+// Device-side input validation for *_dev uploads: finite values, m > 0.
+__global__ void k_check_j(const State s, int64_t first, int64_t n, DevScalars *ds)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = first + q;
+        bool ok = s.m[e] > 0.0 && isfinite(s.m[e]) && isfinite(s.t[e]);
+        for (int d = 0; d < 3; d++)
+            ok = ok && isfinite(s.x[d * s.cap_j + e]) && isfinite(s.v[d * s.cap_j + e]) &&
+                 isfinite(s.a[d * s.cap_j + e]) && isfinite(s.jk[d * s.cap_j + e]);
+        if (!ok) atomicExch(&ds->err, -1);
+    }
+}
+
+__global__ void k_check_idx(const int32_t *idx, int32_t n, int64_t n_part, DevScalars *ds)
+{
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
+        if (idx[q] < 0 || idx[q] >= n_part) atomicExch(&ds->err, -1);
+}
+
+}  // namespace hh

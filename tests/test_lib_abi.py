@@ -1,0 +1,101 @@
+"""Host-side checks of libhh (no GPU): exports, host tree builder, argument errors.
+
+The host tree builder is the library's own implementation of tree-loop step 1
+(Section 2); it shares no code with the oracle, and both follow the same
+written rules, so their Morton order, groups and lists must agree exactly.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+@pytest.fixture(scope="module")
+def hh():
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_1602_02832_gb300 as hh
+    return hh
+
+
+def _declared():
+    names = set()
+    for h in HEADERS:
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(hh\w*)\s*\(", src):
+            names.add(m.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported(hh):
+    declared = _declared()
+    assert "hh_force" in declared and "hh_tree_build" in declared
+    missing = [n for n in sorted(declared) if not hasattr(hh.lib(), n)]
+    assert not missing, missing
+    # and the Python binding wraps every one of them
+    assert not (declared - set(hh.EXPORTED)) - {"hh_batch"}, declared - set(hh.EXPORTED)
+
+
+def test_config_default(hh):
+    c = hh.hh_config_default()
+    assert c.dt_min == 2.0 ** -30 and c.dt_max == 2.0 ** -6 and c.dt_tree == 2.0 ** -6
+    assert c.theta == 0.5 and c.leaf == 8 and c.precision == hh.HH_FP64
+
+
+def test_create_rejects_bad_config_without_touching_the_gpu(hh):
+    c = hh.hh_config_default()
+    c.dt_max = 0.3  # not a power of two
+    with pytest.raises(hh.HHError) as e:
+        hh.Context(c, 16, 32, 64, 4)
+    assert e.value.code == hh.HH_EINVAL
+    c = hh.hh_config_default()
+    c.dt_max = 2.0 ** -3  # larger than dt_tree
+    with pytest.raises(hh.HHError):
+        hh.Context(c, 16, 32, 64, 4)
+
+
+def _soa(a):
+    return np.ascontiguousarray(np.asarray(a).T)
+
+
+@pytest.mark.parametrize("n,theta,n_crit,salp", [(3000, 0.5, 64, False), (2500, 0.3, 16, True),
+                                                 (4096, 0.75, 200, False), (777, 0.0, 32, True)])
+def test_host_tree_matches_oracle_exactly(hh, orc, n, theta, n_crit, salp):
+    x, v, m = (synth.plummer_salpeter if salp else synth.plummer)(n, 21)
+    a, j, _ = orc.direct_force(x, v, m, 1e-6)
+    T = orc.tree_build(x, v, a, j, m, leaf=8, n_crit=n_crit, theta=theta)
+    P = hh.hh_tree_build(_soa(x), _soa(v), _soa(a), _soa(j), m, leaf=8, n_crit=n_crit, theta=theta)
+    assert np.array_equal(P.perm, T.perm)
+    assert P.n_nodes == T.n_cells
+    assert np.array_equal(P.off, T.list_off)
+    assert np.array_equal(P.idx, T.list_idx)
+    assert np.array_equal(P.group_of, T.group_of)
+    np.testing.assert_allclose(P.node_x.T, T.node_x, rtol=0, atol=0)
+    np.testing.assert_allclose(P.node_m, T.node_m, rtol=0, atol=0)
+    np.testing.assert_allclose(P.node_jk.T, T.node_j, rtol=1e-15, atol=0)
+
+
+def test_host_tree_degenerate_inputs(hh):
+    # all particles at one point: the depth limit ends the split; one group
+    n = 20
+    x = np.zeros((3, n))
+    v = np.zeros((3, n))
+    m = np.full(n, 1.0 / n)
+    P = hh.hh_tree_build(x, v, v, v, m, leaf=8, n_crit=4, theta=0.5)
+    assert sorted(P.perm) == list(range(n))
+    assert np.all(np.diff(P.off) >= n) or P.n_groups >= 1
+    # bad inputs are rejected, not crashed on
+    with pytest.raises(hh.HHError):
+        hh.hh_tree_build(x, v, v, v, np.zeros(n))
+    xx = x.copy()
+    xx[0, 3] = np.nan
+    with pytest.raises(hh.HHError):
+        hh.hh_tree_build(xx, v, v, v, m)
