@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Benchmark of the list-driven 4th-order Hermite path (libhh) on GB300.
+
+Workload (default): the full plain run — N = 65536 Plummer sphere (standard
+units, equal masses, seed = rank), 4th-order Hermite with power-of-two block
+steps (Aarseth eta = 0.02, dt in [2^-30, 2^-6]: the requested 2^-3 is clamped
+to dt_tree because the tree loop caps every step at the rebuild interval),
+tree and lists rebuilt every dt_tree = 1/64, theta = 0.5, eps = 1e-4, FP64.
+
+One step = one tree interval dt_tree: all block steps of the interval on the
+device (CUDA graph replays of predict / force / correct) followed by the tree
+rebuild (state to host, the library's host tree builder, upload of
+particles, nodes and lists).  Warm-up intervals start at t = 0; the timed
+intervals follow.  L2 is flushed (256 MB write) before each timed interval.
+
+value = interactions / time (interactions = sum over particle steps of the
+list length minus self), timed with CUDA events on the context's stream; the
+same line reports the mixed-precision form on the same workload, block steps
+per second, the roofline of the force kernel against measured FMA peaks, an
+end-to-end figure through host buffers, and the FP64 oracle as CPU baseline.
+
+--impl reference times the FP64 CPU oracle on the same workload (a bounded
+sample per step) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FLOP_PER_INT = 60
+METRIC = "interactions/s & equiv. Tflops (60 flop/int); block-steps/s, p50/p99 latency vs plain"
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=8)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="hh", choices=["hh", "reference"])
+    p.add_argument("--n", type=int, default=65536)
+    p.add_argument("--n-crit", type=int, default=64)
+    p.add_argument("--theta", type=float, default=0.5)
+    p.add_argument("--no-mixed", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _cfg(hh, prec, a):
+    c = hh.hh_config_default()
+    c.eps2 = 1e-8
+    c.eta = 0.02
+    c.eta_s = 0.01
+    c.dt_min = 2.0 ** -30
+    c.dt_max = 2.0 ** -6
+    c.dt_tree = 2.0 ** -6
+    c.theta = a.theta
+    c.leaf = 8
+    c.n_crit = a.n_crit
+    c.precision = prec
+    return c
+
+
+def _workload(a):
+    return (f"Plummer N={a.n}, 4th-order Hermite, power-of-two block steps (eta=0.02, dt in [2^-30, 2^-6]), "
+            f"tree/lists rebuilt every dt_tree=1/64, theta={a.theta}, leaf 8, n_crit={a.n_crit}, eps=1e-4; "
+            f"one step = one dt_tree interval")
+
+
+class Clocks:
+    """nvidia-smi sampler (200 ms) running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [u.strip() for u in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks(hh_dir):
+    """Measured FMA peaks (TFLOP/s) from libhh_peaks.so, plus the driver's HBM/bf16 figures."""
+    out = {}
+    lib = C.CDLL(os.path.join(hh_dir, "libhh_peaks.so"))
+    lib.hh_fma_peak.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]
+    for name, fp64, iters in (("fp32_tflops", 0, 200000), ("fp64_tflops", 1, 20000)):
+        best = 0.0
+        for _ in range(3):
+            v = C.c_double()
+            if lib.hh_fma_peak(0 if "CUDA_VISIBLE_DEVICES" in os.environ else 0, fp64, iters, C.byref(v)) == 0:
+                best = max(best, v.value)
+        out[name] = best
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        out["hbm_gbs"] = mp.get("hbm_gbs")
+        out["bf16_tflops"] = mp.get("bf16_tflops")
+    except OSError:
+        out["hbm_gbs"] = None
+    return out
+
+
+def _run_form(hh, torch, a, prec, seed, steps, warmup, flush, e2e_steps=0):
+    import numpy as np
+    import synth
+
+    x, v, m = synth.plummer(a.n, seed)
+    cfg = _cfg(hh, prec, a)
+    z = np.zeros((3, a.n))
+    T0 = hh.hh_tree_build(x.T, v.T, z, z, m, leaf=8, n_crit=a.n_crit, theta=a.theta)
+    nj_max = 2 * a.n
+    list_max = int(len(T0.idx) * 2) + 1024
+    groups_max = int(T0.n_groups * 2) + 64
+    ctx = hh.Context(cfg, a.n, nj_max, list_max, groups_max)
+    stream = torch.cuda.Stream()
+    ctx.hh_set_stream(stream.cuda_stream)
+    dtt = cfg.dt_tree
+    ctx.hh_load_particles(x.T, v.T, m)
+    ctx.hh_run(0.0, 0.0)  # rebuild, initial forces, rebuild with node derivatives, initial steps
+    t = 0.0
+    for _ in range(warmup):
+        ctx.hh_advance(t + dtt)
+        ctx.hh_rebuild(t + dtt)
+        t += dtt
+    c0 = ctx.hh_get_counters()
+    l0 = hh.hh_kernel_launches()
+    ctx.hh_force_timing(1)
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.hh_advance(t + dtt)
+        ctx.hh_rebuild(t + dtt)
+        e1.record(stream)
+        t += dtt
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    force_ms, force_launches = ctx.hh_force_timing(0)
+    launches = hh.hh_kernel_launches() - l0
+    c1 = ctx.hh_get_counters()
+    res = {
+        "ms": sum(times), "step_ms": times,
+        "interactions": c1["interactions"] - c0["interactions"],
+        "block_steps": c1["block_steps"] - c0["block_steps"],
+        "particle_steps": c1["particle_steps"] - c0["particle_steps"],
+        "force_ms": force_ms, "force_launches": force_launches, "gpu_launches": launches, "t_end": t,
+    }
+    if e2e_steps:
+        # end to end through host buffers: upload the step's particle state,
+        # run the interval, read the state back (pinned host copies)
+        st = ctx.hh_get_state()
+        n = a.n
+        mm = np.ascontiguousarray(m[ctx.hh_get_ids()])
+        bi = (4 * 3 * n + 2 * n) * 8 + n * 8
+        bo = (4 * 3 * n + 2 * n) * 8
+        c2 = ctx.hh_get_counters()
+        e2e_ms = 0.0
+        for _ in range(e2e_steps):
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            ctx.hh_set_j(0, st["x"], st["v"], st["a"], st["jk"], mm, st["t"])
+            ctx.hh_set_dt(st["dt"])
+            ctx.hh_advance(t + dtt)
+            ctx.hh_rebuild(t + dtt)
+            st = ctx.hh_get_state()
+            mm = np.ascontiguousarray(m[ctx.hh_get_ids()])
+            e2e_ms += (time.perf_counter() - w0) * 1e3
+            t += dtt
+        c3 = ctx.hh_get_counters()
+        res["e2e"] = {"ms": e2e_ms, "interactions": c3["interactions"] - c2["interactions"], "bi": bi, "bo": bo,
+                      "steps": e2e_steps}
+    ctx.close()
+    return res
+
+
+def _cpu_baseline(a, seed):
+    """The FP64 oracle on a bounded sample: one run over t in [0, 1/256] of the same N."""
+    import oracle
+    import synth
+
+    oracle.build()
+    x, v, m = synth.plummer(a.n, seed)
+    p = oracle.RunParams(eps2=1e-8, eta=0.02, eta_s=0.01, dt_min=2.0 ** -30, dt_max=2.0 ** -6,
+                         dt_tree=2.0 ** -6, theta=a.theta, leaf=8, n_crit=a.n_crit, use_tree=True)
+    t0 = time.perf_counter()
+    r = oracle.run(x, v, m, 1.0 / 256, p)
+    dt = time.perf_counter() - t0
+    return {"value": r["stats"]["interactions"] / dt, "unit": "interactions/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"FP64 oracle tree-loop run of the same N={a.n} Plummer workload over t in [0, 1/256] "
+                      f"({r['stats']['particle_steps']} particle steps, {r['stats']['interactions']} interactions, "
+                      f"{dt:.1f} s)"}
+
+
+def main_reference(a):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+
+    oracle.build()
+    x, v, m = synth.plummer(a.n, 0)
+    p = oracle.RunParams(eps2=1e-8, eta=0.02, eta_s=0.01, dt_min=2.0 ** -30, dt_max=2.0 ** -6,
+                         dt_tree=2.0 ** -6, theta=a.theta, leaf=8, n_crit=a.n_crit, use_tree=True)
+    sample_t = 1.0 / 1024
+    for _ in range(a.warmup):
+        oracle.run(x, v, m, sample_t, p)
+    tot_int, tot_s, tot_bs = 0, 0.0, 0
+    for _ in range(a.steps):
+        t0 = time.perf_counter()
+        r = oracle.run(x, v, m, sample_t, p)
+        tot_s += time.perf_counter() - t0
+        tot_int += r["stats"]["interactions"]
+        tot_bs += r["stats"]["block_steps"]
+    val = tot_int / tot_s
+    sample = (f"each step: FP64 oracle tree-loop run of N={a.n} Plummer over t in [0, 1/1024] "
+              f"(start-up interval of the same workload)")
+    line = {"metric": METRIC, "value": val, "unit": "interactions/s", "n_gpus": 0, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": tot_s * 1e3 / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": _workload(a), "n": a.n, "form": "oracle fp64 (CPU)"},
+            "equiv_tflops": FLOP_PER_INT * val / 1e12,
+            "block_steps_per_s": tot_bs / tot_s,
+            "cpu_baseline": {"value": val, "unit": "interactions/s", "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return main_reference(a)
+    world, rank, local = _dist()
+    import torch
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        import __graft_entry__
+        __graft_entry__.build_library()
+    if world > 1:
+        dist.barrier()
+    import paper_1602_02832_gb300 as hh
+
+    peaks = _peaks(os.path.dirname(hh.LIB_PATH)) if rank == 0 else {}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    with Clocks(local) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        res = _run_form(hh, torch, a, hh.HH_FP64, rank, a.steps, a.warmup, flush, e2e_steps=a.steps)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    mixed = None
+    if not a.no_mixed:
+        mixed = _run_form(hh, torch, a, hh.HH_MIXED, rank, a.steps, a.warmup, flush)
+    tot = torch.tensor([res["interactions"], res["block_steps"], res["particle_steps"], res["gpu_launches"],
+                        res["e2e"]["interactions"]], dtype=torch.float64, device="cuda")
+    mx = torch.tensor([res["ms"], res["e2e"]["ms"]], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    tot = tot.tolist()
+    mx = mx.tolist()
+    if rank == 0:
+        value = tot[0] / (mx[0] * 1e-3)
+        achieved = FLOP_PER_INT * res["interactions"] / (res["force_ms"] * 1e-3) / 1e12
+        cpu = None if (a.no_cpu_baseline or world > 1) else _cpu_baseline(a, 0)
+        line = {
+            "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": mx[0] / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Plummer spheres, seed = rank)",
+            "config": {"workload": _workload(a), "n": a.n, "theta": a.theta, "n_crit": a.n_crit,
+                       "form": "plain FP64", "replicas": world,
+                       "l2": "flushed (256 MB write) before every timed step"},
+            "equiv_tflops": FLOP_PER_INT * value / 1e12,
+            "equiv_tflops_57": 57 * value / 1e12,
+            "block_steps_per_s": tot[1] / (mx[0] * 1e-3),
+            "particle_steps_per_s": tot[2] / (mx[0] * 1e-3),
+            "roofline": {"kernel": "k_force<RecF64> (plain FP64 list force)", "bound": "alu",
+                         "achieved": achieved, "peak": peaks.get("fp64_tflops"), "unit": "TFLOP/s",
+                         "frac": achieved / peaks["fp64_tflops"] if peaks.get("fp64_tflops") else None,
+                         "traffic": None,
+                         "note": "60 algorithmic flop per interaction / mean CUDA-event time of the force "
+                                 "kernel launches in the timed region; peak = measured FP64 FMA throughput "
+                                 "(of measured)"},
+            "e2e": {"value": tot[4] / (mx[1] * 1e-3), "unit": "interactions/s",
+                    "h2d_bytes_per_step": res["e2e"]["bi"], "d2h_bytes_per_step": res["e2e"]["bo"]},
+            "gpu_launches": int(tot[3]),
+            "force_kernel_share": res["force_ms"] / res["ms"],
+            "peaks_measured": peaks,
+        }
+        if mixed:
+            mv = mixed["interactions"] / (mixed["ms"] * 1e-3)
+            mach = FLOP_PER_INT * mixed["interactions"] / (mixed["force_ms"] * 1e-3) / 1e12
+            line["mixed"] = {
+                "value": mv, "unit": "interactions/s", "equiv_tflops": FLOP_PER_INT * mv / 1e12,
+                "block_steps_per_s": mixed["block_steps"] / (mixed["ms"] * 1e-3),
+                "ms_per_step": mixed["ms"] / a.steps, "force_kernel_share": mixed["force_ms"] / mixed["ms"],
+                "speedup_vs_plain": mv / (res["interactions"] / (res["ms"] * 1e-3)),
+                "roofline": {"kernel": "k_force<RecMix> (mixed list force)", "bound": "alu", "achieved": mach,
+                             "peak": peaks.get("fp32_tflops"), "unit": "TFLOP/s",
+                             "frac": mach / peaks["fp32_tflops"] if peaks.get("fp32_tflops") else None},
+            }
+        line["clocks"] = clk.summary()
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -11,6 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhh.so")
+PEAKS_LIB = os.path.join(HERE, "libhh_peaks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU = ["hh_api.cu"]
 CPP = ["hh_tree.cpp"]
@@ -27,10 +28,10 @@ def _sources():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PEAKS_LIB):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(s) <= t for s in _sources())
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PEAKS_LIB))
+    return all(os.path.getmtime(s) <= t for s in _sources() + [os.path.join(CSRC, "hh_peaks.cu")])
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -48,6 +49,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-fopenmp", "-ffp-contract=off", "-c",
                      os.path.join(CSRC, f), "-o", obj])
 
+    peaks_tmp = PEAKS_LIB + f".tmp{os.getpid()}"
+    jobs.append([nvcc, *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+                 os.path.join(CSRC, "hh_peaks.cu"), "-o", peaks_tmp])
+
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -63,6 +68,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + f".tmp{os.getpid()}"
     run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fopenmp", "-lgomp"])
     os.replace(tmp, LIB)
+    os.replace(peaks_tmp, PEAKS_LIB)
     return LIB
 
 

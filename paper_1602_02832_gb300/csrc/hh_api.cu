@@ -51,6 +51,11 @@ struct hh_ctx {
     int64_t *off = nullptr;
     int32_t *idx = nullptr, *group_of = nullptr;
     int4 *tiles = nullptr;
+    int4 *items = nullptr;      // [cap_parts]
+    void *partials = nullptr;   // [cap_parts][32] partial sums (scratch)
+    int32_t *tile_cnt = nullptr;  // [cap_tiles]
+    int64_t cap_parts = 0;
+    int32_t part_len = 512;
     DevScalars *ds = nullptr;
     int32_t *i_buf = nullptr;  // [cap_n]
     double *out_buf = nullptr; // [7 * cap_n]
@@ -117,6 +122,9 @@ Lists lists_of(const hh_ctx *ctx)
     L.off = ctx->off;
     L.idx = ctx->idx;
     L.tiles = ctx->tiles;
+    L.items = ctx->items;
+    L.partials = ctx->partials;
+    L.tile_cnt = ctx->tile_cnt;
     return L;
 }
 
@@ -127,17 +135,20 @@ bool is_pow2(double x)
     return std::frexp(x, &e) == 0.5;
 }
 
-__global__ void k_set_sizes(DevScalars *ds, int64_t n, int64_t nj, int32_t n_tiles)
+__global__ void k_set_sizes(DevScalars *ds, int64_t n, int64_t nj, int32_t n_tiles, int32_t part_len)
 {
     ds->n = n;
     ds->nj = nj;
     ds->n_tiles = n_tiles;
+    ds->part_len = part_len;
 }
 
 __global__ void k_begin_loop(DevScalars *ds, double t_end)
 {
     ds->t_end = t_end;
     ds->done = 0;
+    ds->n_items = 0u;
+    ds->work = 0u;
     ds->tmin[0] = 0x7FF0000000000000ull;
     ds->tmin[1] = 0x7FF0000000000000ull;
 }
@@ -145,9 +156,11 @@ __global__ void k_begin_loop(DevScalars *ds, double t_end)
 int launch_predict(hh_ctx *ctx, StepCtl c)
 {
     if (ctx->cfg.precision == HH_MIXED)
-        k_predict<RecMix><<<ctx->elem_grid, 256, 0, ctx->stream>>>(ctx->st, (RecMix *)ctx->rec, ctx->ds, c);
+        k_predict<RecMix><<<ctx->elem_grid, 256, 0, ctx->stream>>>(ctx->st, (RecMix *)ctx->rec, lists_of(ctx),
+                                                                   ctx->ds, c);
     else
-        k_predict<RecF64><<<ctx->elem_grid, 256, 0, ctx->stream>>>(ctx->st, (RecF64 *)ctx->rec, ctx->ds, c);
+        k_predict<RecF64><<<ctx->elem_grid, 256, 0, ctx->stream>>>(ctx->st, (RecF64 *)ctx->rec, lists_of(ctx),
+                                                                   ctx->ds, c);
     CKL();
     return HH_OK;
 }
@@ -167,6 +180,15 @@ int launch_force(hh_ctx *ctx, StepCtl c)
 int launch_correct(hh_ctx *ctx, StepCtl c)
 {
     k_correct<<<ctx->elem_grid, 256, 0, ctx->stream>>>(ctx->st, ctx->ds, c, params_of(ctx));
+    CKL();
+    return HH_OK;
+}
+
+// explicit modes: reset the work queue, then select work items
+int launch_select(hh_ctx *ctx, StepCtl c)
+{
+    CK(cudaMemsetAsync(&ctx->ds->work, 0, 2 * sizeof(uint32_t), ctx->stream));  // work, n_items
+    k_select<<<ctx->elem_grid, 256, 0, ctx->stream>>>(ctx->st, lists_of(ctx), ctx->ds, c);
     CKL();
     return HH_OK;
 }
@@ -253,9 +275,9 @@ int ensure_graph(hh_ctx *ctx)
     for (int s = 0; s < kGraphSteps && rc == HH_OK; s++) {
         StepCtl c{0, s & 1, (s & 1) ^ 1, 0, 0.0};
         rc = launch_predict(ctx, c);
-        if (rc == HH_OK && timed) rc = cudaEventRecord(ctx->ev[2 * s], ctx->stream) == cudaSuccess ? HH_OK : HH_ECUDA;
+        if (rc == HH_OK && timed) rc = cudaEventRecordWithFlags(ctx->ev[2 * s], ctx->stream, cudaEventRecordExternal) == cudaSuccess ? HH_OK : HH_ECUDA;
         if (rc == HH_OK) rc = launch_force(ctx, c);
-        if (rc == HH_OK && timed) rc = cudaEventRecord(ctx->ev[2 * s + 1], ctx->stream) == cudaSuccess ? HH_OK : HH_ECUDA;
+        if (rc == HH_OK && timed) rc = cudaEventRecordWithFlags(ctx->ev[2 * s + 1], ctx->stream, cudaEventRecordExternal) == cudaSuccess ? HH_OK : HH_ECUDA;
         if (rc == HH_OK) rc = launch_correct(ctx, c);
     }
     cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
@@ -309,8 +331,8 @@ int force_impl(hh_ctx *ctx, int32_t n_act, const int32_t *i_idx, bool dev, doubl
     int rc = mark_upload(ctx, n_act, i_idx, dev, &didx);
     if (rc) return rc;
     if (n_act > 0) {
-        CK(cudaMemsetAsync(&ctx->ds->work, 0, sizeof(uint32_t), ctx->stream));
         StepCtl c{1, 0, 1, 0, 0.0};
+        if ((rc = launch_select(ctx, c))) return rc;
         if (ctx->timing) CK(cudaEventRecord(ctx->e0, ctx->stream));
         if ((rc = launch_force(ctx, c))) return rc;
         if (ctx->timing) CK(cudaEventRecord(ctx->e1, ctx->stream));
@@ -381,7 +403,7 @@ int hh_destroy(hh_ctx *ctx)
     if (ctx->e1) cudaEventDestroy(ctx->e1);
     void *dev[] = {ctx->st.x, ctx->st.v, ctx->st.a, ctx->st.jk, ctx->st.m, ctx->st.t, ctx->st.dt, ctx->st.acc1,
                    ctx->st.jerk1, ctx->st.pot1, ctx->st.mark, ctx->rec, ctx->off, ctx->idx, ctx->group_of,
-                   ctx->tiles, ctx->ds, ctx->i_buf, ctx->out_buf};
+                   ctx->tiles, ctx->ds, ctx->i_buf, ctx->out_buf, ctx->items, ctx->partials, ctx->tile_cnt};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (ctx->h_ds) cudaFreeHost(ctx->h_ds);
@@ -410,6 +432,9 @@ int hh_create(hh_ctx **out, int device, const hh_config *cfg, int64_t n_max, int
                                               "dt_min <= dt_max <= dt_tree, eps2 >= 0, eta > 0)");
     if (c.tile_i == 0) c.tile_i = 32;
     if (c.tile_i < 1 || c.tile_i > kMaxTileI) return hh_set_global_error(HH_EINVAL, "hh_create: tile_i must be 1..32");
+    if (c.tile_j == 0) c.tile_j = 512;
+    if (c.tile_j < 256 || c.tile_j % 256 != 0 || c.tile_j > (1 << 20))
+        return hh_set_global_error(HH_EINVAL, "hh_create: tile_j (list part length) must be a multiple of 256");
     hh_ctx *ctx = new (std::nothrow) hh_ctx;
     if (!ctx) return hh_set_global_error(HH_ENOMEM, "hh_create: out of host memory");
     ctx->device = device;
@@ -420,6 +445,8 @@ int hh_create(hh_ctx **out, int device, const hh_config *cfg, int64_t n_max, int
     ctx->cap_list = list_max;
     ctx->cap_g = groups_max;
     ctx->cap_tiles = n_max / c.tile_i + groups_max + 1;
+    ctx->part_len = c.tile_j;
+    ctx->cap_parts = ctx->cap_tiles + list_max / c.tile_j + 1;
     auto bail = [&](int code, const std::string &m) {
         std::string msg = "hh_create: " + m;
         hh_destroy(ctx);
@@ -455,6 +482,9 @@ int hh_create(hh_ctx **out, int device, const hh_config *cfg, int64_t n_max, int
         {(void **)&ctx->group_of, sizeof(int32_t) * n_max},      {(void **)&ctx->tiles, sizeof(int4) * ctx->cap_tiles},
         {(void **)&ctx->ds, sizeof(DevScalars)},                 {(void **)&ctx->i_buf, sizeof(int32_t) * n_max},
         {(void **)&ctx->out_buf, sizeof(double) * 7 * n_max},
+        {(void **)&ctx->tile_cnt, sizeof(int32_t) * ctx->cap_tiles},
+        {(void **)&ctx->items, sizeof(int4) * ctx->cap_parts},
+        {(void **)&ctx->partials, sizeof(RedF64) * kMaxTileI * ctx->cap_parts},
     };
     for (auto &al : allocs)
         if (cudaMalloc(al.p, al.bytes) != cudaSuccess) {
@@ -471,6 +501,7 @@ int hh_create(hh_ctx **out, int device, const hh_config *cfg, int64_t n_max, int
     }
     if (cudaMemsetAsync(ctx->ds, 0, sizeof(DevScalars), ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->st.mark, 0, sizeof(int32_t) * n_max, ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->tile_cnt, 0, sizeof(int32_t) * ctx->cap_tiles, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->st.acc1, 0, sizeof(double) * 3 * n_max, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->st.jerk1, 0, sizeof(double) * 3 * n_max, ctx->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->st.dt, 0, sizeof(double) * n_max, ctx->stream) != cudaSuccess ||
@@ -526,6 +557,7 @@ int hh_set_lists(hh_ctx *ctx, int64_t n_particles, int64_t n_j, int32_t n_groups
     // groups must be contiguous ascending particle ranges
     std::vector<int4> tiles;
     tiles.reserve(size_t(n_particles / ctx->tile_i + n_groups + 1));
+    int64_t total_parts = 0;
     int64_t p = 0;
     int32_t prev = -1;
     while (p < n_particles) {
@@ -533,17 +565,44 @@ int hh_set_lists(hh_ctx *ctx, int64_t n_particles, int64_t n_j, int32_t n_groups
         if (g < 0 || g >= n_groups || g <= prev) return fail(ctx, HH_EINVAL, "hh_set_lists: group_of must be ascending contiguous ranges");
         int64_t e = p;
         while (e < n_particles && group_of[e] == g) e++;
-        for (int64_t b = p; b < e; b += ctx->tile_i)
-            tiles.push_back(make_int4(int(b), int(std::min<int64_t>(b + ctx->tile_i, e)), g, 0));
+        const int64_t n_parts = std::max<int64_t>(1, (off[g + 1] - off[g] + ctx->part_len - 1) / ctx->part_len);
+        for (int64_t b = p; b < e; b += ctx->tile_i) {
+            tiles.push_back(make_int4(int(b), int(std::min<int64_t>(b + ctx->tile_i, e)), g, int(total_parts)));
+            total_parts += n_parts;
+        }
         prev = g;
         p = e;
     }
     if (int64_t(tiles.size()) > ctx->cap_tiles) return fail(ctx, HH_ENOMEM, "hh_set_lists: too many tiles");
+    if (total_parts > INT32_MAX / 2) return fail(ctx, HH_ENOMEM, "hh_set_lists: too many list parts");
+    if (total_parts > ctx->cap_parts) {
+        // work items and partial sums grow with the lists; kernels captured in
+        // the loop graph hold the old pointers, so the graph is rebuilt
+        CK(cudaStreamSynchronize(ctx->stream));
+        const int64_t cap = total_parts + total_parts / 4 + 64;
+        int4 *items = nullptr;
+        void *partials = nullptr;
+        if (cudaMalloc(&items, sizeof(int4) * cap) != cudaSuccess ||
+            cudaMalloc(&partials, sizeof(RedF64) * kMaxTileI * cap) != cudaSuccess) {
+            cudaGetLastError();
+            if (items) cudaFree(items);
+            return fail(ctx, HH_ENOMEM, "hh_set_lists: cannot grow the work-item buffers");
+        }
+        cudaFree(ctx->items);
+        cudaFree(ctx->partials);
+        ctx->items = items;
+        ctx->partials = partials;
+        ctx->cap_parts = cap;
+        if (ctx->graph) {
+            cudaGraphExecDestroy(ctx->graph);
+            ctx->graph = nullptr;
+        }
+    }
     CK(cudaMemcpyAsync(ctx->off, off, sizeof(int64_t) * (n_groups + 1), cudaMemcpyHostToDevice, ctx->stream));
     if (L) CK(cudaMemcpyAsync(ctx->idx, idx, sizeof(int32_t) * L, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->group_of, group_of, sizeof(int32_t) * n_particles, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, ctx->stream));
-    k_set_sizes<<<1, 1, 0, ctx->stream>>>(ctx->ds, n_particles, n_j, int32_t(tiles.size()));
+    k_set_sizes<<<1, 1, 0, ctx->stream>>>(ctx->ds, n_particles, n_j, int32_t(tiles.size()), ctx->part_len);
     CKL();
     CK(cudaStreamSynchronize(ctx->stream));  // host arrays may be freed after return
     ctx->n = n_particles;
@@ -637,8 +696,8 @@ int hh_init_forces(hh_ctx *ctx, double t)
     if (!ctx->have_lists) return fail(ctx, HH_ESTATE, "hh_init_forces: needs j entries and lists");
     StepCtl cp{1, 0, 1, 0, t};
     if ((rc = launch_predict(ctx, cp))) return rc;
-    CK(cudaMemsetAsync(&ctx->ds->work, 0, sizeof(uint32_t), ctx->stream));
     StepCtl cf{2, 0, 1, 0, t};
+    if ((rc = launch_select(ctx, cf))) return rc;
     if ((rc = launch_force(ctx, cf))) return rc;
     k_adopt_forces<<<ctx->elem_grid, 256, 0, ctx->stream>>>(ctx->st, ctx->ds);
     CKL();

@@ -3,9 +3,11 @@
 // One block step (Section 2, tree-loop steps 2-7) is three kernels:
 //   k_predict  every j entry (particles and tree nodes) to the block time
 //              (GRAPE predictor; step 4), written as packed records;
-//   k_force    static i tiles pull work from a queue; each finds its active
-//              particles (t_i + dt_i == t_next, step 2) with one ballot and
-//              sums acc / jerk / pot over its group's list (steps 4a + 5);
+//              and, with one ballot per static i tile, appends the work
+//              items (tile, list part) of tiles with active particles
+//              (t_i + dt_i == t_next, step 2);
+//   k_force    CTAs pull work items from a queue and sum acc / jerk / pot
+//              over the item's part of the group's list (steps 4a + 5);
 //   k_correct  4th-order Hermite corrector + Aarseth block step (step 6),
 //              and the min over t_i + dt_i that starts the next step.
 // No kernel waits on another CTA; there are no spin loops.
@@ -18,6 +20,7 @@ namespace hh {
 
 constexpr int kThreads = 128;  // threads per force CTA (4 warps)
 constexpr int kMaxTileI = 32;  // particles per static i tile (one ballot)
+constexpr int kFold = 16;     // FP32 terms per thread between compensated folds
 
 // ---------------------------------------------------------------- scalars
 struct DevScalars {
@@ -25,7 +28,9 @@ struct DevScalars {
     double t_end;                // loop bound of hh_advance
     int32_t done;                // set once the next block time exceeds t_end
     int32_t err;                 // device-detected error (HH_* code), 0 = none
-    uint32_t work;               // force tile queue head
+    uint32_t work;               // force work-queue head
+    uint32_t n_items;            // work items of this step
+    int32_t part_len;            // list entries per part (a multiple of the staging chunk)
     int32_t n_act_last;          // active particles of the last corrected step
     int64_t n;                   // particles
     int64_t nj;                  // j entries
@@ -69,7 +74,10 @@ struct State {
 struct Lists {
     const int64_t *off;
     const int32_t *idx;
-    const int4 *tiles;  // (p_begin, p_end, group, 0)
+    const int4 *tiles;  // static i tiles: (p_begin, p_end, group, first part slot)
+    int4 *items;        // this step's work: (tile, part, active mask, parts of the tile)
+    void *partials;     // per (tile part, i slot) sums of split lists [part slots][32]
+    int32_t *tile_cnt;  // arrivals per tile (reset by the last arriver)
 };
 
 struct Params {
@@ -103,6 +111,41 @@ __device__ __forceinline__ bool is_active(const State &s, const StepCtl &c, int6
 __device__ __forceinline__ double pow2_floor(double x)
 {
     return __longlong_as_double(__double_as_longlong(x) & (long long)0xFFF0000000000000ull);
+}
+
+// ------------------------------------------------------- tile selection
+// Step 2 on the device: for each static i tile (<= 32 consecutive particles
+// of one group) one warp ballots the tile's active particles; a tile with
+// any active particle appends one work item per part of its group's list.
+// Item order may vary between runs; results do not depend on it.
+__device__ __forceinline__ void select_tiles(const State &s, const Lists &L, DevScalars *ds, const StepCtl &c,
+                                             double tnow)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int n_tiles = ds->n_tiles;
+    const int pj = ds->part_len;
+    for (int64_t tile = warp0; tile < n_tiles; tile += nwarps) {
+        const int4 td = L.tiles[tile];
+        const int64_t p = td.x + lane;
+        const bool act = (p < td.y) && is_active(s, c, p, tnow);
+        const uint32_t mask = __ballot_sync(0xffffffffu, act);
+        if (mask == 0u) continue;
+        const int64_t len = L.off[td.z + 1] - L.off[td.z];
+        const int n_parts = len > 0 ? (int)((len + pj - 1) / pj) : 1;
+        int base = 0;
+        if (lane == 0) base = (int)atomicAdd(&ds->n_items, (uint32_t)n_parts);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (int q = lane; q < n_parts; q += 32) L.items[base + q] = make_int4((int)tile, q, (int)mask, n_parts);
+    }
+}
+
+__global__ void k_select(State s, Lists L, DevScalars *ds, StepCtl c)
+{
+    double tnow;
+    if (!step_time(ds, c, &tnow)) return;
+    select_tiles(s, L, ds, c, tnow);
 }
 
 // -------------------------------------------------------------- predictor
@@ -151,7 +194,7 @@ __device__ __forceinline__ void store_rec<RecMix>(RecMix *out, int64_t e, const 
 }
 
 template <typename Rec>
-__global__ void k_predict(State s, Rec *rec, DevScalars *ds, StepCtl c)
+__global__ void k_predict(State s, Rec *rec, Lists L, DevScalars *ds, StepCtl c)
 {
     double tnow;
     if (!step_time(ds, c, &tnow)) {
@@ -164,12 +207,14 @@ __global__ void k_predict(State s, Rec *rec, DevScalars *ds, StepCtl c)
         ds->n_act_last = 0;
         ds->block_steps += 1ull;
     }
+
     const int64_t nj = ds->nj;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nj; e += (int64_t)gridDim.x * blockDim.x) {
         double xp[3], vp[3];
         predict_one(s, e, tnow, xp, vp);
         store_rec<Rec>(rec, e, xp, vp, s.m[e]);
     }
+    if (c.mode == 0) select_tiles(s, L, ds, c, tnow);
 }
 
 // ------------------------------------------------------ pairwise kernels
@@ -285,9 +330,14 @@ __device__ __forceinline__ void interact(const IMix &I, const RecMix &J, bool se
     r2 = self ? 1.f : r2;
     const float mj = self ? 0.f : J.hm.w;
     const float rw = fmaf(dx, wx, fmaf(dy, wy, dz * wz));
-    float rinv = rsqrtf(r2);
-    // one Newton-Raphson step for 1/sqrt: y <- y (3 - r2 y^2) / 2
-    rinv = rinv * fmaf(-0.5f * r2, rinv * rinv, 1.5f);
+    // 1/sqrt: hardware estimate, then one Newton-Raphson step
+    // y <- y + (y/2) h, h = 1 - r2 y^2, with the residual formed exactly
+    // (r2 y = p + e by an FMA) so the step lands within ~1/2 ulp.
+    const float y0 = rsqrtf(r2);
+    const float pr = r2 * y0;
+    const float er = fmaf(r2, y0, -pr);
+    const float hres = fmaf(-er, y0, fmaf(-pr, y0, 1.f));
+    const float rinv = fmaf(0.5f * y0, hres, y0);
     const float rinv2 = rinv * rinv;
     const float mr = mj * rinv;
     const float mr3 = mr * rinv2;
@@ -356,6 +406,24 @@ __device__ __forceinline__ void red_add(RedMix &a, const RedMix &b)
 }
 __device__ __forceinline__ double red_get(const RedF64 &r, int q) { return r.v[q]; }
 __device__ __forceinline__ double red_get(const RedMix &r, int q) { return (double)r.v[q].h + (double)r.v[q].l; }
+// partial sums written by other CTAs: read through L2 (bypassing L1)
+__device__ __forceinline__ RedF64 ld_red_cg(const RedF64 *p)
+{
+    RedF64 r;
+#pragma unroll
+    for (int q = 0; q < 7; q++) r.v[q] = __ldcg(&p->v[q]);
+    return r;
+}
+__device__ __forceinline__ RedMix ld_red_cg(const RedMix *p)
+{
+    RedMix r;
+#pragma unroll
+    for (int q = 0; q < 7; q++) {
+        r.v[q].h = __ldcg(&p->v[q].h);
+        r.v[q].l = __ldcg(&p->v[q].l);
+    }
+    return r;
+}
 
 template <typename Rec>
 struct Traits;
@@ -378,47 +446,47 @@ __device__ __forceinline__ void fold_chunk(AccF64 &) {}
 __device__ __forceinline__ void fold_chunk(AccMix &A) { A.fold(); }
 
 // ------------------------------------------------------------ list force
-// CTA = 4 warps on one static i tile (<= 32 consecutive particles of one
-// group).  With n_a active particles, lane l serves i slot (l mod I),
+// One CTA (4 warps) per work item = (tile, part of its group's list).  With
+// n_a active particles in the tile, lane l serves i slot (l mod I),
 // I = next power of two >= n_a, and the CTA's 128 threads form 128 / I
-// j slices that stride through each staged chunk of the list.  Slices are
-// summed in a fixed order (shuffles, then warps), so each particle's result
-// depends only on its list, its tile's active count and the tile shape.
+// j slices that stride through each staged chunk of the part.  Slices are
+// summed in a fixed order (shuffles, then warps).  A list split into several
+// parts leaves per-part sums in the partials buffer; the CTA that finishes a
+// tile's last part (arrival counter, threadfence pattern: no waiting) adds
+// the parts in part order.  So each particle's result depends only on its
+// list, its tile's active count and the part length, never on scheduling.
 template <typename Rec, int TJ>
-__global__ void __launch_bounds__(kThreads) k_force(State s, const Rec *__restrict__ rec, Lists L, DevScalars *ds,
+__global__ void __launch_bounds__(kThreads, 6) k_force(State s, const Rec *__restrict__ rec, Lists L, DevScalars *ds,
                                                     StepCtl c, Params prm)
 {
     using T = Traits<Rec>;
+    using Red = typename T::Red;
     double tnow;
     if (!step_time(ds, c, &tnow)) return;
 
     __shared__ Rec s_rec[TJ];
     __shared__ int32_t s_idx[TJ];
-    __shared__ typename T::Red s_red[kThreads / 32][kMaxTileI];
-    __shared__ int s_tile;
-    __shared__ uint32_t s_mask;
+    __shared__ Red s_red[kThreads / 32][kMaxTileI];
+    __shared__ int s_item;
+    __shared__ int s_last;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int n_tiles = ds->n_tiles;
+    const int n_items = (int)ds->n_items;
+    const int pj = ds->part_len;
     const typename T::Eps eps2 = (typename T::Eps)prm.eps2;
+    Red *partials = reinterpret_cast<Red *>(L.partials);
     unsigned long long n_int = 0;
 
     for (;;) {
-        if (tid == 0) s_tile = (int)atomicAdd(&ds->work, 1u);
+        if (tid == 0) s_item = (int)atomicAdd(&ds->work, 1u);
         __syncthreads();
-        const int tile = s_tile;
-        if (tile >= n_tiles) break;
-        const int4 td = L.tiles[tile];
-        if (warp == 0) {
-            const int64_t p = td.x + lane;
-            const bool act = (p < td.y) && is_active(s, c, p, tnow);
-            const uint32_t mk = __ballot_sync(0xffffffffu, act);
-            if (lane == 0) s_mask = mk;
-        }
-        __syncthreads();
-        const uint32_t mask = s_mask;
+        const int item = s_item;
+        if (item >= n_items) break;
+        const int4 it = L.items[item];
+        const int4 td = L.tiles[it.x];
+        const int part = it.y, n_parts = it.w;
+        const uint32_t mask = (uint32_t)it.z;
         const int n_a = __popc(mask);
-        if (n_a == 0) continue;  // uniform: the next iteration's barrier orders s_tile reuse
 
         int I = 1;
         while (I < n_a) I <<= 1;
@@ -426,7 +494,6 @@ __global__ void __launch_bounds__(kThreads) k_force(State s, const Rec *__restri
         const int jslice = tid / I;
         const int S = kThreads / I;
         const bool has_i = islot < n_a;
-        // position of the islot-th set bit of mask
         int64_t pi = -1;
         {
             uint32_t mm = mask;
@@ -434,14 +501,15 @@ __global__ void __launch_bounds__(kThreads) k_force(State s, const Rec *__restri
             if (has_i) pi = td.x + (__ffs(mm) - 1);
         }
         typename T::I Iv;
-        if (has_i) load_i(rec, pi, Iv);
-        else load_i(rec, td.x + (__ffs(mask) - 1), Iv);  // harmless duplicate, result dropped
+        load_i(rec, has_i ? pi : td.x + (__ffs(mask) - 1), Iv);  // spare slots repeat a live one; dropped
         typename T::Acc A;
         A.zero();
 
-        const int64_t lb = L.off[td.z], le = L.off[td.z + 1];
+        const int64_t gb = L.off[td.z], ge = L.off[td.z + 1];
+        const int64_t lb = gb + (int64_t)part * pj;
+        const int64_t le = min(ge, lb + (int64_t)pj);
         const int64_t len = le - lb;
-        if (tid == 0) n_int += (unsigned long long)n_a * (unsigned long long)(len - 1);
+        if (tid == 0 && part == 0) n_int += (unsigned long long)n_a * (unsigned long long)(ge - gb - 1);
         for (int64_t c0 = 0; c0 < len; c0 += TJ) {
             const int nc = (len - c0 < (int64_t)TJ) ? (int)(len - c0) : TJ;
             for (int e = tid; e < nc; e += kThreads) {
@@ -450,25 +518,55 @@ __global__ void __launch_bounds__(kThreads) k_force(State s, const Rec *__restri
                 s_rec[e] = rec[j];
             }
             __syncthreads();
-            for (int e = jslice; e < nc; e += S) {
-                const int32_t j = s_idx[e];
-                interact(Iv, s_rec[e], (int64_t)j == pi, eps2, A);
+            // FP32 partials are folded into the compensated sums every
+            // kFold terms per thread (short plain-FP32 runs keep the
+            // partial-sum rounding below the per-term rounding).
+            for (int e = jslice; e < nc;) {
+                const int e_end = min(nc, e + kFold * S);
+                for (; e < e_end; e += S) {
+                    const int32_t j = s_idx[e];
+                    interact(Iv, s_rec[e], (int64_t)j == pi, eps2, A);
+                }
+                fold_chunk(A);
             }
-            fold_chunk(A);
             __syncthreads();
         }
         // reduce the S slices of each i slot: lanes l, l+I, ... then warps
         for (int off = I; off < 32; off <<= 1) acc_shfl_add(A, off);
-        if (lane < I && lane < 32) {
-            typename T::Red r;
+        if (lane < I) {
+            Red r;
             to_red(A, r);
             s_red[warp][lane] = r;
         }
         __syncthreads();
+        Red r;
         if (tid < n_a) {
-            typename T::Red r = s_red[0][tid];
+            r = s_red[0][tid];
             for (int w = 1; w < kThreads / 32; w++) red_add(r, s_red[w][tid]);
-            // this thread's particle: the tid-th active one
+        }
+        bool write_out = n_parts == 1;
+        if (n_parts > 1) {
+            Red *mine = partials + ((int64_t)td.w + part) * kMaxTileI;
+            if (tid < n_a) mine[tid] = r;
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) {
+                const int old = atomicAdd(&L.tile_cnt[it.x], 1);
+                s_last = (old == n_parts - 1);
+            }
+            __syncthreads();
+            write_out = s_last;
+            if (write_out) {
+                __threadfence();
+                if (tid < n_a) {
+                    const Red *base = partials + (int64_t)td.w * kMaxTileI;
+                    r = ld_red_cg(base + tid);
+                    for (int q = 1; q < n_parts; q++) red_add(r, ld_red_cg(base + (int64_t)q * kMaxTileI + tid));
+                }
+                if (tid == 0) L.tile_cnt[it.x] = 0;
+            }
+        }
+        if (write_out && tid < n_a) {
             uint32_t mm = mask;
             for (int q = 0; q < tid; q++) mm &= mm - 1;
             const int64_t p = td.x + (__ffs(mm) - 1);
@@ -480,7 +578,7 @@ __global__ void __launch_bounds__(kThreads) k_force(State s, const Rec *__restri
             s.jerk1[2 * s.cap_n + p] = red_get(r, 5);
             s.pot1[p] = -red_get(r, 6);
         }
-        // next iteration's first barrier protects s_red / s_rec reuse
+        // the next iteration's first barrier protects s_item / s_red / s_rec reuse
     }
     if (tid == 0 && n_int) atomicAdd(&ds->interactions, n_int);
 }
@@ -582,6 +680,7 @@ __global__ void k_correct(State s, DevScalars *ds, StepCtl c, Params prm)
             cn += s_cnt[w];
         }
         atomic_min_time(&ds->tmin[c.slot_next], mn);
+        if (blockIdx.x == 0) ds->n_items = 0u;  // the force kernel of this step has finished
         if (cn) {
             atomicAdd(&ds->n_act_last, cn);
             atomicAdd(&ds->particle_steps, (unsigned long long)cn);

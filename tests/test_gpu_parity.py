@@ -147,14 +147,16 @@ def test_theta_zero_equals_direct_sum(hh, orc, prec):
     assert ea.max() < lim and ep.max() < lim
 
 
-@pytest.mark.parametrize("tile_i", [1, 5, 32])
-def test_ragged_tiles_and_sparse_active_sets(hh, orc, tile_i):
+@pytest.mark.parametrize("tile_i,tile_j", [(1, 512), (5, 256), (32, 512), (32, 4096)])
+def test_ragged_tiles_and_sparse_active_sets(hh, orc, tile_i, tile_j):
     # Static i tiles of 1, 5 or 32 particles; active sets of assorted sizes and
     # gaps (including single particles and whole groups).
     x, v, m, T, xj, vj, aj, jj, mj, tj = _setup_plummer(orc, 2000, 3, 0.5, 70)
     rng = np.random.default_rng(4)
     ref = orc.list_force(xj, vj, mj, np.arange(2000), T.group_of, T.list_off, T.list_idx, 1e-8)
-    with _ctx_from_tree(hh, _cfg(hh, hh.HH_MIXED, tile_i=tile_i), T, xj, vj, aj, jj, mj, tj) as ctx:
+    # tile_j = list entries per part: 256 splits every list into many parts
+    # (partials reduced by the last arriving CTA), 4096 keeps most whole
+    with _ctx_from_tree(hh, _cfg(hh, hh.HH_MIXED, tile_i=tile_i, tile_j=tile_j), T, xj, vj, aj, jj, mj, tj) as ctx:
         ctx.hh_predict(0.0)
         for frac in (0.001, 0.05, 0.3, 1.0):
             ia = np.sort(rng.choice(2000, size=max(1, int(frac * 2000)), replace=False)).astype(np.int32)
