@@ -197,6 +197,46 @@ int64_t hh_kernel_launches(void);
 
 const char *hh_last_error(const hh_ctx *ctx);
 
+/* ---- Allocation-free force call ---------------------------------------- */
+/* The paper has no counterpart to this call.  It is the list force of steps
+ * 4a + 5 (the same kernel as hh_force) for callers that cannot allocate
+ * device memory: code whose device memory all comes from another allocator
+ * or pool, and loops that must not call cudaMalloc / cudaFree because those
+ * calls synchronise the whole device.  It calls no cudaMalloc, cudaFree or
+ * other allocating routine.  Its scratch (packed j records, i tiles, work
+ * items, per-part partial sums, counters) is one fixed array of about 25 MB
+ * in libhh's own device memory (a file-scope __device__ array) that every
+ * GPU which loads libhh holds until the process exits.
+ *
+ * Inputs, device pointers owned by the caller: j entries already predicted
+ * to the force time, xj[3][n_j] and vj[3][n_j] (SoA) and mj[n_j]; CSR lists
+ * off[n_groups + 1] and idx[off[n_groups]] (indices into the j entries);
+ * the active particles as j indices i_idx[n_act] with their list numbers
+ * gid[n_act].  Consecutive actives with the same gid share i tiles, so
+ * ordering the actives by list is faster but not required.  Each active
+ * particle skips the list entry equal to its own index.  Outputs, device,
+ * caller-owned: acc[3][n_act], jerk[3][n_act], pot[n_act] by active position.
+ * stream: a cudaStream_t (NULL = the legacy default stream).
+ *
+ * Limits: n_j <= 131072, n_act <= 65536, and at most 8192 work items of
+ * (i tile, 2048-entry part of its list).  Sizes above the first two are
+ * rejected with HH_EINVAL before any GPU work; too many work items return
+ * HH_ENOMEM and device inputs with bad offsets or indices return HH_EINVAL,
+ * both detected on the device before the force kernel reads anything, and
+ * no output is written then.  The message is in hh_last_error(NULL).
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one scratch array, which
+ * keeps the last call's contents; each call clears what must start at zero.
+ * Calls whose kernels overlap on the GPU (other streams, other host threads)
+ * race on the scratch and must be serialised by the caller.  The call
+ * synchronises `stream` before it returns. */
+int hh_force_static(int device, int precision, double eps2, int64_t n_j, const double *xj, const double *vj,
+                    const double *mj, int32_t n_groups, const int64_t *off, const int32_t *idx, int32_t n_act,
+                    const int32_t *i_idx, const int32_t *gid, double *acc, double *jerk, double *pot,
+                    void *stream);
+
 /* ---- Host tree builder (Section 2, step 1; Barnes 1990 grouping) -------- */
 /* Morton octree (21 bits per axis, root cube from the bounding box), groups =
  * maximal cells with <= n_crit particles, one list per group: ancestors of

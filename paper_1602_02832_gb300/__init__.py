@@ -88,6 +88,8 @@ _SIGS = {
     "hh_tree_sizes": (C.c_int, [_P, _I64, _I32, _I64]),
     "hh_tree_export": (C.c_int, [_P, _I32, _D, _D, _D, _D, _D, _I64, _I32, _I32]),
     "hh_tree_free": (C.c_int, [_P]),
+    "hh_force_static": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_int64, _P, _P, _P, C.c_int32, _P, _P, C.c_int32,
+                                  _P, _P, _P, _P, _P, _P]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -334,3 +336,18 @@ def hh_tree_build(x, v, a, jk, m, leaf=8, n_crit=64, theta=0.5) -> Tree:
     finally:
         _lib.hh_tree_free(h)
     return Tree(perm, nx, nv, na, nj, nm, off, idx[:ll], gof)
+
+
+def hh_force_static(xj, vj, mj, off, idx, i_idx, gid, acc, jerk, pot, eps2=1e-8, precision=HH_FP64, device=0,
+                    stream=None):
+    """Allocation-free list force on caller-owned device arrays (CUDA tensors
+    or raw device pointers; shapes as in include/hh.h).  Raises HHError."""
+    n_j = mj.numel() if hasattr(mj, "numel") else None
+    n_groups = (off.numel() - 1) if hasattr(off, "numel") else None
+    n_act = i_idx.numel() if hasattr(i_idx, "numel") else None
+    if n_j is None or n_groups is None or n_act is None:
+        raise ValueError("pass tensors for mj, off and i_idx (sizes are taken from them)")
+    s = stream if isinstance(stream, int) else (stream.cuda_stream if stream is not None else None)
+    _check(_lib.hh_force_static(int(device), int(precision), float(eps2), n_j, _dev_ptr(xj), _dev_ptr(vj),
+                                _dev_ptr(mj), n_groups, _dev_ptr(off), _dev_ptr(idx), n_act, _dev_ptr(i_idx),
+                                _dev_ptr(gid), _dev_ptr(acc), _dev_ptr(jerk), _dev_ptr(pot), s))

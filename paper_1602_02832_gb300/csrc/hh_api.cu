@@ -125,6 +125,7 @@ Lists lists_of(const hh_ctx *ctx)
     L.items = ctx->items;
     L.partials = ctx->partials;
     L.tile_cnt = ctx->tile_cnt;
+    L.i_map = nullptr;
     return L;
 }
 

@@ -78,6 +78,7 @@ struct Lists {
     int4 *items;        // this step's work: (tile, part, active mask, parts of the tile)
     void *partials;     // per (tile part, i slot) sums of split lists [part slots][32]
     int32_t *tile_cnt;  // arrivals per tile (reset by the last arriver)
+    const int32_t *i_map;  // optional: i slot position -> j index (kMapI kernels only)
 };
 
 struct Params {
@@ -141,7 +142,7 @@ __device__ __forceinline__ void select_tiles(const State &s, const Lists &L, Dev
     }
 }
 
-__global__ void k_select(State s, Lists L, DevScalars *ds, StepCtl c)
+static __global__ void k_select(State s, Lists L, DevScalars *ds, StepCtl c)
 {
     double tnow;
     if (!step_time(ds, c, &tnow)) return;
@@ -455,7 +456,7 @@ __device__ __forceinline__ void fold_chunk(AccMix &A) { A.fold(); }
 // tile's last part (arrival counter, threadfence pattern: no waiting) adds
 // the parts in part order.  So each particle's result depends only on its
 // list, its tile's active count and the part length, never on scheduling.
-template <typename Rec, int TJ>
+template <typename Rec, int TJ, bool kMapI = false>
 __global__ void __launch_bounds__(kThreads, 6) k_force(State s, const Rec *__restrict__ rec, Lists L, DevScalars *ds,
                                                     StepCtl c, Params prm)
 {
@@ -500,8 +501,14 @@ __global__ void __launch_bounds__(kThreads, 6) k_force(State s, const Rec *__res
             for (int q = 0; q < islot && mm; q++) mm &= mm - 1;
             if (has_i) pi = td.x + (__ffs(mm) - 1);
         }
+        int64_t pload = has_i ? pi : td.x + (__ffs(mask) - 1);  // spare slots repeat a live one; dropped
+        if constexpr (kMapI) {
+            // slots are positions in a caller's active list; i is its j index
+            pload = L.i_map[pload];
+            if (has_i) pi = pload;
+        }
         typename T::I Iv;
-        load_i(rec, has_i ? pi : td.x + (__ffs(mask) - 1), Iv);  // spare slots repeat a live one; dropped
+        load_i(rec, pload, Iv);
         typename T::Acc A;
         A.zero();
 
@@ -614,7 +621,7 @@ __device__ __forceinline__ void atomic_min_time(unsigned long long *slot, double
 // a2 = (-6 (a0 - a1) - D (4 j0 + 2 j1)) / D^2, a3 = (12 (a0 - a1) + 6 D (j0 + j1)) / D^3,
 // x1 = x_p + a2 D^4/24 + a3 D^5/120, v1 = v_p + a2 D^3/6 + a3 D^4/24;
 // new step from Aarseth's criterion at the end of the step.
-__global__ void k_correct(State s, DevScalars *ds, StepCtl c, Params prm)
+static __global__ void k_correct(State s, DevScalars *ds, StepCtl c, Params prm)
 {
     double tnow;
     if (!step_time(ds, c, &tnow)) return;
@@ -689,7 +696,7 @@ __global__ void k_correct(State s, DevScalars *ds, StepCtl c, Params prm)
 }
 
 // min over particles of t_i + dt_i into tmin[slot] (slot preset to +inf).
-__global__ void k_min_time(State s, DevScalars *ds, int slot)
+static __global__ void k_min_time(State s, DevScalars *ds, int slot)
 {
     const int64_t n = ds->n;
     double my_min = __longlong_as_double(0x7FF0000000000000LL);
@@ -702,7 +709,7 @@ __global__ void k_min_time(State s, DevScalars *ds, int slot)
 }
 
 // Initial step from eta_s |a| / |jk|, quantised (reading: the paper is silent).
-__global__ void k_init_dt(State s, DevScalars *ds, Params prm)
+static __global__ void k_init_dt(State s, DevScalars *ds, Params prm)
 {
     const int64_t n = ds->n;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
@@ -721,7 +728,7 @@ __global__ void k_init_dt(State s, DevScalars *ds, Params prm)
 }
 
 // a, jk of every particle <- last force results (initial forces).
-__global__ void k_adopt_forces(State s, DevScalars *ds)
+static __global__ void k_adopt_forces(State s, DevScalars *ds)
 {
     const int64_t n = ds->n;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
@@ -733,13 +740,13 @@ __global__ void k_adopt_forces(State s, DevScalars *ds)
     }
 }
 
-__global__ void k_set_marks(int32_t *mark, const int32_t *idx, int32_t n, int32_t value)
+static __global__ void k_set_marks(int32_t *mark, const int32_t *idx, int32_t n, int32_t value)
 {
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) mark[idx[q]] = value;
 }
 
 // out[3][n_act] (SoA) <- acc1 etc. at i_idx
-__global__ void k_gather_out(State s, const int32_t *idx, int32_t n_act, double *acc, double *jerk, double *pot)
+static __global__ void k_gather_out(State s, const int32_t *idx, int32_t n_act, double *acc, double *jerk, double *pot)
 {
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_act; q += gridDim.x * blockDim.x) {
         const int64_t p = idx[q];
@@ -753,7 +760,7 @@ __global__ void k_gather_out(State s, const int32_t *idx, int32_t n_act, double 
 }
 
 // Device-side input validation for *_dev uploads: finite values, m > 0.
-__global__ void k_check_j(const State s, int64_t first, int64_t n, DevScalars *ds)
+static __global__ void k_check_j(const State s, int64_t first, int64_t n, DevScalars *ds)
 {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t e = first + q;
@@ -765,7 +772,7 @@ __global__ void k_check_j(const State s, int64_t first, int64_t n, DevScalars *d
     }
 }
 
-__global__ void k_check_idx(const int32_t *idx, int32_t n, int64_t n_part, DevScalars *ds)
+static __global__ void k_check_idx(const int32_t *idx, int32_t n, int64_t n_part, DevScalars *ds)
 {
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
         if (idx[q] < 0 || idx[q] >= n_part) atomicExch(&ds->err, -1);
