@@ -52,6 +52,7 @@ def _args():
     p.add_argument("--n-crit", type=int, default=64)
     p.add_argument("--theta", type=float, default=0.5)
     p.add_argument("--no-mixed", action="store_true")
+    p.add_argument("--mixed-only", action="store_true", help="run only the mixed form (profiling aid)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -314,6 +315,12 @@ def main():
 
     peaks = _peaks(os.path.dirname(hh.LIB_PATH)) if rank == 0 else {}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    if a.mixed_only:
+        r = _run_form(hh, torch, a, hh.HH_MIXED, rank, a.steps, a.warmup, flush)
+        if rank == 0:
+            print(json.dumps({"form": "mixed", "value": r["interactions"] / (r["ms"] * 1e-3), "ms": r["ms"],
+                              "force_ms": r["force_ms"]}), flush=True)
+        return 0
     with Clocks(local) as clk:
         if world > 1:
             dist.barrier()

@@ -69,7 +69,7 @@ typedef struct hh_config {
     int32_t n_crit; /* max particles per group for hh_rebuild (Section 2) */
     int32_t precision; /* HH_FP64 or HH_MIXED */
     int32_t tile_i;    /* particles per static i tile, 1..32; 0 = 32 */
-    int32_t tile_j;    /* list entries staged per chunk, multiple of 32, 32..1024; 0 = default */
+    int32_t tile_j;    /* list entries per work item (part of a list), multiple of 256; 0 = 512 */
     int32_t reserved;
 } hh_config;
 

@@ -59,8 +59,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError("build failed: " + " ".join(cmd) + "\n" + r.stdout + r.stderr)
         return r.stdout + r.stderr
 
-    with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
-        logs = list(ex.map(run, jobs))
+    try:
+        with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+            logs = list(ex.map(run, jobs))
+    except Exception:
+        if os.path.exists(peaks_tmp):
+            os.remove(peaks_tmp)
+        raise
     if verbose:
         for lg in logs:
             sys.stderr.write(lg)
