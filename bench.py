@@ -54,6 +54,11 @@ def _args():
     p.add_argument("--no-mixed", action="store_true")
     p.add_argument("--mixed-only", action="store_true", help="run only the mixed form (profiling aid)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--ensemble", type=int, default=256, help="clusters in the batched-ensemble measurement (0: skip)")
+    p.add_argument("--ensemble-intervals", type=int, default=2)
+    p.add_argument("--serve-seconds", type=float, default=20.0, help="wall time of the serving measurement (0: skip)")
+    p.add_argument("--loop", default="persistent", choices=["persistent", "graph"],
+                   help="block-step loop: one persistent cooperative kernel per interval, or CUDA-graph replays")
     return p.parse_args()
 
 
@@ -162,6 +167,48 @@ def _peaks(hh_dir):
     return out
 
 
+class _Loop:
+    """Advances one context to a stop time with the chosen block-step loop and
+    accumulates the force-kernel (or force-phase) time while enabled."""
+
+    def __init__(self, hh, ctx, prec, kind):
+        self.ctx, self.kind = ctx, kind
+        self.batch = hh.Batch(prec, max_sims=1, max_steps=4096) if kind == "persistent" else None
+        self.force_ms = 0.0
+        self.force_launches = 0
+        self.timing = False
+        self.step_us = []
+        self.phase_ms = [0.0, 0.0, 0.0]
+
+    def enable(self, on):
+        self.timing = on
+        if self.kind == "graph":
+            if on:
+                self.ctx.hh_force_timing(1)
+            else:
+                self.force_ms, self.force_launches = self.ctx.hh_force_timing(0)
+
+    def advance(self, t_end):
+        if self.kind == "graph":
+            self.ctx.hh_advance(t_end)
+            return
+        while True:
+            steps, tn, us = self.batch.hh_batch_run([self.ctx], [t_end])
+            if self.timing:
+                ph = self.batch.last_phase_us
+                self.force_ms += float(ph[:, 1].sum()) * 1e-3
+                self.force_launches += int(steps)
+                self.step_us.extend(us.tolist())
+                for q in range(3):
+                    self.phase_ms[q] += float(ph[:, q].sum()) * 1e-3
+            if tn[0] > t_end:
+                return
+
+    def close(self):
+        if self.batch:
+            self.batch.close()
+
+
 def _run_form(hh, torch, a, prec, seed, steps, warmup, flush, e2e_steps=0):
     import numpy as np
     import synth
@@ -179,14 +226,15 @@ def _run_form(hh, torch, a, prec, seed, steps, warmup, flush, e2e_steps=0):
     dtt = cfg.dt_tree
     ctx.hh_load_particles(x.T, v.T, m)
     ctx.hh_run(0.0, 0.0)  # rebuild, initial forces, rebuild with node derivatives, initial steps
+    loop = _Loop(hh, ctx, prec, a.loop)
     t = 0.0
     for _ in range(warmup):
-        ctx.hh_advance(t + dtt)
+        loop.advance(t + dtt)
         ctx.hh_rebuild(t + dtt)
         t += dtt
     c0 = ctx.hh_get_counters()
     l0 = hh.hh_kernel_launches()
-    ctx.hh_force_timing(1)
+    loop.enable(True)
     times = []
     for _ in range(steps):
         flush.zero_()
@@ -194,13 +242,14 @@ def _run_form(hh, torch, a, prec, seed, steps, warmup, flush, e2e_steps=0):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ctx.hh_advance(t + dtt)
+        loop.advance(t + dtt)
         ctx.hh_rebuild(t + dtt)
         e1.record(stream)
         t += dtt
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
-    force_ms, force_launches = ctx.hh_force_timing(0)
+    loop.enable(False)
+    force_ms, force_launches = loop.force_ms, loop.force_launches
     launches = hh.hh_kernel_launches() - l0
     c1 = ctx.hh_get_counters()
     res = {
@@ -225,7 +274,7 @@ def _run_form(hh, torch, a, prec, seed, steps, warmup, flush, e2e_steps=0):
             w0 = time.perf_counter()
             ctx.hh_set_j(0, st["x"], st["v"], st["a"], st["jk"], mm, st["t"])
             ctx.hh_set_dt(st["dt"])
-            ctx.hh_advance(t + dtt)
+            loop.advance(t + dtt)
             ctx.hh_rebuild(t + dtt)
             st = ctx.hh_get_state()
             mm = np.ascontiguousarray(m[ctx.hh_get_ids()])
@@ -234,8 +283,98 @@ def _run_form(hh, torch, a, prec, seed, steps, warmup, flush, e2e_steps=0):
         c3 = ctx.hh_get_counters()
         res["e2e"] = {"ms": e2e_ms, "interactions": c3["interactions"] - c2["interactions"], "bi": bi, "bo": bo,
                       "steps": e2e_steps}
+    res["step_us"] = loop.step_us
+    res["phase_ms"] = loop.phase_ms
+    loop.close()
     ctx.close()
     return res
+
+
+def _ensemble(hh, a):
+    """Batched form: a = 256 independent Plummer clusters, N log-uniform in
+    [1024, 32768], seeds 0..255, theta from {0.3, 0.5, 0.7}, mixed precision,
+    all admitted at once and advanced by the continuous-batching server over
+    the first `ensemble_intervals` tree intervals (rebuilds on host threads
+    overlap the batched launches of the other clusters)."""
+    import numpy as np
+    import synth
+    from paper_1602_02832_gb300 import serve
+
+    members = synth.ensemble(a.ensemble, 1024, 32768, seed=0)
+    t_end = a.ensemble_intervals / 64.0
+    reqs = []
+    for k, mb in enumerate(members):
+        x, v, m = synth.plummer(mb.n, mb.seed)
+        reqs.append(serve.SimRequest(k, x, v, m, t_end))
+    srvs = {}
+    results, stats = [], None
+    t0 = time.perf_counter()
+    # one server per theta value (the opening angle is a per-context setting)
+    tot = {"block_steps": 0, "interactions": 0, "step_us": [], "live": [], "launches": 0, "wall": 0.0}
+    for th in sorted({mb.theta for mb in members}):
+        sub = [r for r, mb in zip(reqs, members) if mb.theta == th]
+        srv = serve.Server(precision=hh.HH_MIXED, budget_bytes=150 * 10 ** 9, max_sims=256, max_steps=64,
+                           theta=th, n_crit=a.n_crit, rebuild_threads=8)
+        res, st = srv.run(sub, realtime=False)
+        srv.close()
+        results += res
+        tot["block_steps"] += st.block_steps
+        tot["interactions"] += st.interactions
+        tot["step_us"] += st.step_us
+        tot["live"] += st.live_per_step
+        tot["launches"] += st.launches
+        tot["wall"] += st.wall_s
+    wall = time.perf_counter() - t0
+    lat = _lat(tot["step_us"])
+    return {"clusters": len(members), "n_total": int(sum(mb.n for mb in members)), "t_end": t_end,
+            "completed": len(results), "wall_s": wall, "launches": tot["launches"],
+            "block_steps_per_s": tot["block_steps"] / wall, "interactions_per_s": tot["interactions"] / wall,
+            "equiv_tflops": FLOP_PER_INT * tot["interactions"] / wall / 1e12,
+            "mean_live_sims_per_step": float(np.mean(tot["live"])) if tot["live"] else None,
+            "block_step_latency_us": lat,
+            "note": "wall time includes admission (host tree builds, initial forces) and host rebuilds; "
+                    "block steps are summed over clusters; latency = device time of one global block step"}
+
+
+def _serving(hh, a):
+    """Serving: Poisson arrivals (20/s) of Plummer + Salpeter cluster requests,
+    N log-uniform in [2^10, 2^18], t_end in {1/8, 1/4, 1/2}, admitted within a
+    150 GB device-memory budget, run for a bounded wall time."""
+    import synth
+    from paper_1602_02832_gb300 import serve
+
+    n_req = max(1, int(20 * a.serve_seconds))
+    stream = synth.request_stream(n_req, rate_per_s=20.0, seed=0)
+    reqs = [serve.SimRequest(r.rid, None, None, None, r.t_end, arrival_s=r.arrival_s,
+                             make=(lambda n=r.n, sd=r.seed: synth.plummer_salpeter(n, sd))) for r in stream]
+    srv = serve.Server(precision=hh.HH_MIXED, budget_bytes=150 * 10 ** 9, max_sims=256, max_steps=32,
+                       n_crit=a.n_crit, rebuild_threads=8)
+    res, st = srv.run(reqs, realtime=True, max_wall_s=a.serve_seconds)
+    srv.close()
+    return {"requests_arrived": sum(1 for r in stream if r.arrival_s <= st.wall_s), "completed": len(res),
+            "wall_s": st.wall_s, "launches": st.launches,
+            "block_steps_per_s": st.block_steps / st.wall_s, "interactions_per_s": st.interactions / st.wall_s,
+            "block_step_latency_us": _lat(st.step_us),
+            "request_latency_s": _lat([(r.done_s - r.arrival_s) * 1e6 for r in res]) if res else None,
+            "note": "requests arrive in real time over the window; unfinished ones are stopped at its end; "
+                    "request_latency uses the same percentile fields in seconds*1e6"}
+
+
+def _lat(us):
+    import numpy as np
+    if not us:
+        return None
+    u = np.asarray(us)
+    return {"p50": float(np.quantile(u, 0.5)), "p99": float(np.quantile(u, 0.99)), "mean": float(u.mean()),
+            "n": int(len(u)), "note": "device time of one block step (all three phases) in the persistent loop"}
+
+
+def _split(r, steps):
+    ph = r.get("phase_ms") or [0.0, 0.0, 0.0]
+    if not any(ph):
+        return {"force_kernel": r["force_ms"] / steps, "other": (r["ms"] - r["force_ms"]) / steps}
+    return {"predict_select": ph[0] / steps, "force": ph[1] / steps, "correct": ph[2] / steps,
+            "host_rebuild_and_launch": (r["ms"] - sum(ph)) / steps}
 
 
 def _cpu_baseline(a, seed):
@@ -365,6 +504,9 @@ def main():
             "e2e": {"value": tot[4] / (mx[1] * 1e-3), "unit": "interactions/s",
                     "h2d_bytes_per_step": res["e2e"]["bi"], "d2h_bytes_per_step": res["e2e"]["bo"]},
             "gpu_launches": int(tot[3]),
+            "loop": a.loop,
+            "time_split_ms_per_step": _split(res, a.steps),
+            "block_step_latency_us": _lat(res["step_us"]),
             "force_kernel_share": res["force_ms"] / res["ms"],
             "peaks_measured": peaks,
         }
@@ -376,10 +518,17 @@ def main():
                 "block_steps_per_s": mixed["block_steps"] / (mixed["ms"] * 1e-3),
                 "ms_per_step": mixed["ms"] / a.steps, "force_kernel_share": mixed["force_ms"] / mixed["ms"],
                 "speedup_vs_plain": mv / (res["interactions"] / (res["ms"] * 1e-3)),
+                "time_split_ms_per_step": _split(mixed, a.steps),
+                "block_step_latency_us": _lat(mixed["step_us"]),
                 "roofline": {"kernel": "k_force<RecMix> (mixed list force)", "bound": "alu", "achieved": mach,
                              "peak": peaks.get("fp32_tflops"), "unit": "TFLOP/s",
                              "frac": mach / peaks["fp32_tflops"] if peaks.get("fp32_tflops") else None},
             }
+        if a.ensemble > 0:
+            line["batched"] = _ensemble(hh, a)
+            line["batched"]["block_steps_per_s_vs_plain"] = line["batched"]["block_steps_per_s"] / line["block_steps_per_s"]
+        if a.serve_seconds > 0:
+            line["serving"] = _serving(hh, a)
         line["clocks"] = clk.summary()
         if cpu:
             line["cpu_baseline"] = cpu

@@ -197,6 +197,38 @@ int64_t hh_kernel_launches(void);
 
 const char *hh_last_error(const hh_ctx *ctx);
 
+/* ---- Batched persistent block steps (many simulations, one launch) ------ */
+/* The paper's Section 4 notes that a GPU needs far more parallel work than
+ * one list evaluation offers.  A batch advances many independent
+ * simulations (contexts) in one cooperative, persistent kernel: each global
+ * step gives every live simulation one block step (steps 2-7 of Section 2),
+ * with the predict, force and correct phases of all simulations separated by
+ * grid barriers and the force work of all simulations drawn from one queue.
+ * A simulation's results do not depend on the others in the batch (its
+ * tiles, active sets and list parts are its own; sums run in fixed order),
+ * so they equal what hh_advance computes for it alone.
+ *
+ * hh_batch_create: device, precision (every context of a run must match it),
+ *   up to max_sims simulations per run and max_steps global steps per run.
+ * hh_batch_run: runs the n contexts (distinct, same device and precision,
+ *   with lists and steps set) until each one's next block time exceeds its
+ *   t_end[s] (normally its next rebuild time) or max_steps global steps have
+ *   run.  Outputs (each may be NULL): the number of global steps; t_next_out[n],
+ *   each simulation's next block time (> t_end[s] when it reached t_end[s]);
+ *   step_us_out[max_steps], the duration of each global step in
+ *   microseconds (device timer); phase_us_out[3 max_steps], per step the
+ *   durations of the predict/select, force and correct phases.  Synchronises.  Grid barriers give up after
+ *   about a second and return HH_ETIMEOUT. */
+typedef struct hh_batch hh_batch;
+int hh_batch_create(hh_batch **out, int device, int precision, int32_t max_sims, int32_t max_steps);
+int hh_batch_destroy(hh_batch *b);
+int hh_batch_run(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const double *t_end, int32_t max_steps,
+                 int32_t *steps_out, double *t_next_out, double *step_us_out, double *phase_us_out);
+const char *hh_batch_last_error(const hh_batch *b);
+
+/* Device memory held by a context (bytes), for admission by memory budget. */
+int64_t hh_ctx_device_bytes(const hh_ctx *ctx);
+
 /* ---- Allocation-free force call ---------------------------------------- */
 /* The paper has no counterpart to this call.  It is the list force of steps
  * 4a + 5 (the same kernel as hh_force) for callers that cannot allocate

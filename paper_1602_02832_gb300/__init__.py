@@ -90,6 +90,11 @@ _SIGS = {
     "hh_tree_free": (C.c_int, [_P]),
     "hh_force_static": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_int64, _P, _P, _P, C.c_int32, _P, _P, C.c_int32,
                                   _P, _P, _P, _P, _P, _P]),
+    "hh_batch_create": (C.c_int, [C.POINTER(_P), C.c_int, C.c_int, C.c_int32, C.c_int32]),
+    "hh_batch_destroy": (C.c_int, [_P]),
+    "hh_batch_run": (C.c_int, [_P, C.c_int32, C.POINTER(_P), _D, C.c_int32, _I32, _D, _D, _D]),
+    "hh_batch_last_error": (C.c_char_p, [_P]),
+    "hh_ctx_device_bytes": (C.c_int64, [_P]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -285,6 +290,10 @@ class Context:
     def hh_reset_counters(self):
         self._c(_lib.hh_reset_counters(self.h))
 
+    @property
+    def device_bytes(self):
+        return int(_lib.hh_ctx_device_bytes(self.h))
+
     def hh_force_timing(self, enable=-1):
         ms = C.c_double()
         nl = C.c_int64()
@@ -351,3 +360,48 @@ def hh_force_static(xj, vj, mj, off, idx, i_idx, gid, acc, jerk, pot, eps2=1e-8,
     _check(_lib.hh_force_static(int(device), int(precision), float(eps2), n_j, _dev_ptr(xj), _dev_ptr(vj),
                                 _dev_ptr(mj), n_groups, _dev_ptr(off), _dev_ptr(idx), n_act, _dev_ptr(i_idx),
                                 _dev_ptr(gid), _dev_ptr(acc), _dev_ptr(jerk), _dev_ptr(pot), s))
+
+
+class Batch:
+    """Persistent batched block steps over many contexts (hh_batch_*)."""
+
+    def __init__(self, precision=HH_FP64, max_sims=256, max_steps=4096, device=0):
+        h = _P()
+        _check(_lib.hh_batch_create(C.byref(h), int(device), int(precision), int(max_sims), int(max_steps)))
+        self.h = h
+        self.max_steps = int(max_steps)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.hh_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def hh_batch_run(self, ctxs, t_end, max_steps=None):
+        """Runs the contexts until each passes its t_end (or max_steps global
+        steps).  Returns (global steps, next block time per context, per-step
+        durations in microseconds)."""
+        n = len(ctxs)
+        arr = (_P * n)(*[c.h for c in ctxs])
+        te = np.ascontiguousarray(np.broadcast_to(np.asarray(t_end, dtype=np.float64), (n,)))
+        ms = self.max_steps if max_steps is None else int(max_steps)
+        steps = C.c_int32()
+        tn = np.zeros(n)
+        us = np.zeros(ms)
+        ph = np.zeros((ms, 3))
+        rc = _lib.hh_batch_run(self.h, n, arr, _ptr(te), ms, C.byref(steps), _ptr(tn), _ptr(us), _ptr(ph))
+        if rc != HH_OK:
+            raise HHError(rc, (_lib.hh_batch_last_error(self.h) or b"").decode())
+        self.last_phase_us = ph[:steps.value]
+        return steps.value, tn, us[:steps.value]

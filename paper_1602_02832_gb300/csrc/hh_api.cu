@@ -14,8 +14,7 @@
 
 #include <cuda_runtime.h>
 
-#include "hh_internal.h"
-#include "hh_kernels.cuh"
+#include "hh_ctx.h"
 
 using namespace hh;
 
@@ -25,62 +24,16 @@ thread_local std::string g_err;
 std::atomic<int64_t> g_launches{0};
 
 constexpr int kGraphSteps = 32;  // block steps unrolled per graph (even)
-constexpr int kTjF64 = 128;
-constexpr int kTjMix = 256;
 
 }  // namespace
+
+void hh_count_launches(int64_t n) { g_launches.fetch_add(n); }
 
 int hh_set_global_error(int code, const char *msg)
 {
     g_err = msg;
     return code;
 }
-
-struct hh_ctx {
-    int device = 0;
-    hh_config cfg{};
-    cudaStream_t own_stream = nullptr, stream = nullptr;
-    int64_t cap_n = 0, cap_j = 0, cap_list = 0;
-    int32_t cap_g = 0;
-    int64_t cap_tiles = 0;
-    int64_t n = 0, nj = 0, list_len = 0;
-    int32_t n_groups = 0, n_tiles = 0, tile_i = 32;
-    // device memory
-    State st{};
-    void *rec = nullptr;
-    int64_t *off = nullptr;
-    int32_t *idx = nullptr, *group_of = nullptr;
-    int4 *tiles = nullptr;
-    int4 *items = nullptr;      // [cap_parts]
-    void *partials = nullptr;   // [cap_parts][32] partial sums (scratch)
-    int32_t *tile_cnt = nullptr;  // [cap_tiles]
-    int64_t cap_parts = 0;
-    int32_t part_len = 512;
-    DevScalars *ds = nullptr;
-    int32_t *i_buf = nullptr;  // [cap_n]
-    double *out_buf = nullptr; // [7 * cap_n]
-    // pinned host staging
-    DevScalars *h_ds = nullptr;
-    double *h_buf = nullptr;   // [14 * cap_j]
-    int32_t *h_ibuf = nullptr; // [cap_n]
-    std::vector<int64_t> ids;  // slot -> particle id
-    std::vector<int32_t> h_group_of;
-    // grid shapes
-    int n_sm = 0, force_grid = 0, elem_grid = 0;
-    // loop graph
-    cudaGraphExec_t graph = nullptr;
-    int graph_timed = -1;
-    std::vector<cudaEvent_t> ev;  // 2 per unrolled step when timed
-    // timing
-    bool timing = false;
-    double force_ms = 0.0;
-    int64_t force_launches = 0;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    // state flags
-    bool have_j = false, have_lists = false, have_dt = false, predicted = false, have_forces = false;
-    int64_t rebuilds = 0;
-    std::string err;
-};
 
 namespace {
 
@@ -410,6 +363,8 @@ int hh_destroy(hh_ctx *ctx)
     if (ctx->h_ds) cudaFreeHost(ctx->h_ds);
     if (ctx->h_buf) cudaFreeHost(ctx->h_buf);
     if (ctx->h_ibuf) cudaFreeHost(ctx->h_ibuf);
+    if (ctx->h_jbuf) cudaFreeHost(ctx->h_jbuf);
+    if (ctx->tree) hh_tree_free(ctx->tree);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
     return HH_OK;
@@ -487,16 +442,19 @@ int hh_create(hh_ctx **out, int device, const hh_config *cfg, int64_t n_max, int
         {(void **)&ctx->items, sizeof(int4) * ctx->cap_parts},
         {(void **)&ctx->partials, sizeof(RedF64) * kMaxTileI * ctx->cap_parts},
     };
-    for (auto &al : allocs)
+    for (auto &al : allocs) {
         if (cudaMalloc(al.p, al.bytes) != cudaSuccess) {
             cudaGetLastError();
             return bail(HH_ENOMEM, "device allocation failed (capacities too large)");
         }
+        ctx->device_bytes += int64_t(al.bytes);
+    }
     ctx->st.cap_j = nj_max;
     ctx->st.cap_n = n_max;
     if (cudaHostAlloc((void **)&ctx->h_ds, sizeof(DevScalars), cudaHostAllocDefault) != cudaSuccess ||
         cudaHostAlloc((void **)&ctx->h_buf, sizeof(double) * 14 * nj_max, cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc((void **)&ctx->h_ibuf, sizeof(int32_t) * n_max, cudaHostAllocDefault) != cudaSuccess) {
+        cudaHostAlloc((void **)&ctx->h_ibuf, sizeof(int32_t) * n_max, cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void **)&ctx->h_jbuf, sizeof(double) * 14 * nj_max, cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();
         return bail(HH_ENOMEM, "pinned host allocation failed");
     }
@@ -539,11 +497,27 @@ int hh_set_j_dev(hh_ctx *ctx, int64_t first, int64_t n, const double *x, const d
     return set_j_impl(ctx, first, n, x, v, a, jk, m, t, cudaMemcpyDeviceToDevice);
 }
 
+namespace {
+int set_lists_core(hh_ctx *ctx, int64_t n_particles, int64_t n_j, int32_t n_groups, const int64_t *off,
+                   const int32_t *idx, const int32_t *group_of, bool trusted);
+}
+
 int hh_set_lists(hh_ctx *ctx, int64_t n_particles, int64_t n_j, int32_t n_groups, const int64_t *off,
                  const int32_t *idx, const int32_t *group_of)
 {
     int rc = check_ctx(ctx);
     if (rc) return rc;
+    return set_lists_core(ctx, n_particles, n_j, n_groups, off, idx, group_of, false);
+}
+
+}  // extern "C"
+
+namespace {
+// `trusted`: lists made by this library's own builder skip the per-entry
+// index scan (they are valid by construction); everything else is checked.
+int set_lists_core(hh_ctx *ctx, int64_t n_particles, int64_t n_j, int32_t n_groups, const int64_t *off,
+                   const int32_t *idx, const int32_t *group_of, bool trusted)
+{
     if (n_particles < 1 || n_particles > ctx->cap_n || n_j < n_particles || n_j > ctx->cap_j)
         return fail(ctx, HH_EINVAL, "hh_set_lists: n_particles / n_j out of capacity");
     if (n_groups < 1 || n_groups > ctx->cap_g || !off || !idx || !group_of)
@@ -553,8 +527,9 @@ int hh_set_lists(hh_ctx *ctx, int64_t n_particles, int64_t n_j, int32_t n_groups
         if (off[g + 1] < off[g]) return fail(ctx, HH_EINVAL, "hh_set_lists: off must be non-decreasing");
     const int64_t L = off[n_groups];
     if (L > ctx->cap_list) return fail(ctx, HH_ENOMEM, "hh_set_lists: list_max exceeded");
-    for (int64_t q = 0; q < L; q++)
-        if (idx[q] < 0 || idx[q] >= n_j) return fail(ctx, HH_EINVAL, "hh_set_lists: list index outside [0, n_j)");
+    if (!trusted)
+        for (int64_t q = 0; q < L; q++)
+            if (idx[q] < 0 || idx[q] >= n_j) return fail(ctx, HH_EINVAL, "hh_set_lists: list index outside [0, n_j)");
     // groups must be contiguous ascending particle ranges
     std::vector<int4> tiles;
     tiles.reserve(size_t(n_particles / ctx->tile_i + n_groups + 1));
@@ -591,6 +566,7 @@ int hh_set_lists(hh_ctx *ctx, int64_t n_particles, int64_t n_j, int32_t n_groups
         }
         cudaFree(ctx->items);
         cudaFree(ctx->partials);
+        ctx->device_bytes += (cap - ctx->cap_parts) * int64_t(sizeof(int4) + sizeof(RedF64) * kMaxTileI);
         ctx->items = items;
         ctx->partials = partials;
         ctx->cap_parts = cap;
@@ -611,6 +587,7 @@ int hh_set_lists(hh_ctx *ctx, int64_t n_particles, int64_t n_j, int32_t n_groups
     ctx->n_groups = n_groups;
     ctx->list_len = L;
     ctx->n_tiles = int32_t(tiles.size());
+    ctx->total_parts = total_parts;
     ctx->h_group_of.assign(group_of, group_of + n_particles);
     if (int64_t(ctx->ids.size()) != n_particles) {
         ctx->ids.resize(size_t(n_particles));
@@ -620,6 +597,9 @@ int hh_set_lists(hh_ctx *ctx, int64_t n_particles, int64_t n_j, int32_t n_groups
     ctx->predicted = false;
     return HH_OK;
 }
+}  // namespace
+
+extern "C" {
 
 int hh_set_dt(hh_ctx *ctx, const double *dt)
 {
@@ -790,6 +770,7 @@ int hh_get_ids(hh_ctx *ctx, int64_t *ids)
 }
 
 int64_t hh_n_particles(const hh_ctx *ctx) { return ctx ? ctx->n : -1; }
+int64_t hh_ctx_device_bytes(const hh_ctx *ctx) { return ctx ? ctx->device_bytes : -1; }
 int64_t hh_n_j(const hh_ctx *ctx) { return ctx ? ctx->nj : -1; }
 
 int hh_get_counters(hh_ctx *ctx, hh_counters *out)
@@ -850,11 +831,9 @@ int hh_rebuild(hh_ctx *ctx, double t)
     int rc = check_ctx(ctx);
     if (rc) return rc;
     if (!ctx->have_j || ctx->n < 2) return fail(ctx, HH_ESTATE, "hh_rebuild: no particles loaded");
-    const int64_t n = ctx->n, cj = ctx->cap_j;
-    double *H = ctx->h_buf;  // x v a jk [3][n] each, then m, t, dt
-    double *hx = H, *hv = H + 3 * n, *ha = H + 6 * n, *hj = H + 9 * n, *hm = H + 12 * n, *ht = H + 13 * n,
-           *hdt = H + 14 * n;
-    (void)cj;
+    const int64_t n = ctx->n;
+    double *H = ctx->h_buf;  // pinned: x v a jk [3][n] each, then m, t, dt
+    double *hx = H, *hv = H + 3 * n, *ha = H + 6 * n, *hj = H + 9 * n, *hm = H + 12 * n, *ht = H + 13 * n;
     double *src[4] = {ctx->st.x, ctx->st.v, ctx->st.a, ctx->st.jk};
     double *dst[4] = {hx, hv, ha, hj};
     for (int f = 0; f < 4; f++)
@@ -863,36 +842,25 @@ int hh_rebuild(hh_ctx *ctx, double t)
                                ctx->stream));
     CK(cudaMemcpyAsync(hm, ctx->st.m, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(ht, ctx->st.t, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
-    std::vector<double> dtv((size_t)n);
+    std::vector<double> dtv(static_cast<size_t>(n));
     CK(cudaMemcpyAsync(dtv.data(), ctx->st.dt, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    (void)hdt;
     for (int64_t q = 0; q < n; q++)
         if (ht[q] != t) return fail(ctx, HH_ESTATE, "hh_rebuild: particles are not synchronised at t");
-    hh_tree *tree = nullptr;
-    if ((rc = hh_tree_build(&tree, n, hx, hv, ha, hj, hm, ctx->cfg.leaf, ctx->cfg.n_crit, ctx->cfg.theta)))
+    if ((rc = hh_tree_rebuild(&ctx->tree, n, hx, hv, ha, hj, hm, ctx->cfg.leaf, ctx->cfg.n_crit, ctx->cfg.theta)))
         return fail(ctx, rc, std::string("hh_rebuild: ") + g_err);
-    int64_t nn = 0, L = 0;
-    int32_t G = 0;
-    hh_tree_sizes(tree, &nn, &G, &L);
-    if (n + nn > ctx->cap_j || L > ctx->cap_list || G > ctx->cap_g) {
-        hh_tree_free(tree);
+    HhTreeView V;
+    hh_tree_view(ctx->tree, &V);
+    const int64_t nn = V.n_nodes, nj = n + nn;
+    if (nj > ctx->cap_j || V.list_len > ctx->cap_list || V.n_groups > ctx->cap_g)
         return fail(ctx, HH_ENOMEM, "hh_rebuild: tree exceeds nj_max / list_max / groups_max");
-    }
-    const int64_t nj = n + nn;
-    std::vector<int32_t> perm((size_t)n), idx((size_t)L), gof((size_t)n);
-    std::vector<int64_t> off((size_t)G + 1);
-    std::vector<double> J((size_t)(14 * nj));  // x v a jk [3][nj], m [nj], t [nj]
-    double *Jx = J.data(), *Jv = Jx + 3 * nj, *Ja = Jx + 6 * nj, *Jj = Jx + 9 * nj, *Jm = Jx + 12 * nj,
-           *Jt = Jx + 13 * nj;
-    std::vector<double> nx((size_t)(3 * nn)), nv(size_t(3 * nn)), na(size_t(3 * nn)), njk(size_t(3 * nn)), nm((size_t)nn);
-    hh_tree_export(tree, perm.data(), nx.data(), nv.data(), na.data(), njk.data(), nm.data(), off.data(), idx.data(),
-                   gof.data());
-    hh_tree_free(tree);
-    std::vector<double> dt_new((size_t)n);
-    std::vector<int64_t> ids_new((size_t)n);
+    double *J = ctx->h_jbuf;  // pinned: x v a jk [3][nj], m [nj], t [nj]
+    double *Jx = J, *Jv = J + 3 * nj, *Ja = J + 6 * nj, *Jj = J + 9 * nj, *Jm = J + 12 * nj, *Jt = J + 13 * nj;
+    std::vector<double> dt_new(static_cast<size_t>(n));
+    std::vector<int64_t> ids_new(static_cast<size_t>(n));
+#pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < n; k++) {
-        const int64_t i = perm[size_t(k)];
+        const int64_t i = V.perm[k];
         for (int d = 0; d < 3; d++) {
             Jx[d * nj + k] = hx[d * n + i];
             Jv[d * nj + k] = hv[d * n + i];
@@ -904,20 +872,20 @@ int hh_rebuild(hh_ctx *ctx, double t)
         dt_new[size_t(k)] = dtv[size_t(i)];
         ids_new[size_t(k)] = ctx->ids[size_t(i)];
     }
+#pragma omp parallel for schedule(static)
     for (int64_t c = 0; c < nn; c++) {
         for (int d = 0; d < 3; d++) {
-            Jx[d * nj + n + c] = nx[size_t(d * nn + c)];
-            Jv[d * nj + n + c] = nv[size_t(d * nn + c)];
-            Ja[d * nj + n + c] = na[size_t(d * nn + c)];
-            Jj[d * nj + n + c] = njk[size_t(d * nn + c)];
+            Jx[d * nj + n + c] = V.cx[3 * c + d];
+            Jv[d * nj + n + c] = V.cv[3 * c + d];
+            Ja[d * nj + n + c] = V.ca[3 * c + d];
+            Jj[d * nj + n + c] = V.cj[3 * c + d];
         }
-        Jm[n + c] = nm[size_t(c)];
+        Jm[n + c] = V.cm[c];
         Jt[n + c] = t;
     }
     if ((rc = set_j_impl(ctx, 0, nj, Jx, Jv, Ja, Jj, Jm, Jt, cudaMemcpyHostToDevice))) return rc;
     ctx->ids = ids_new;
-    ctx->n = n;
-    if ((rc = hh_set_lists(ctx, n, nj, G, off.data(), idx.data(), gof.data()))) return rc;
+    if ((rc = set_lists_core(ctx, n, nj, V.n_groups, V.off, V.idx, V.group_of, true))) return rc;
     CK(cudaMemcpyAsync(ctx->st.dt, dt_new.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->rebuilds++;

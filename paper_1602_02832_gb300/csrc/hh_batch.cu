@@ -1,0 +1,548 @@
+// Batched, persistent block-step loop (scope row a7): one cooperative launch
+// advances many independent simulations, each by its own block steps (Section 2,
+// tree-loop steps 2-7), until each reaches its stop time or the step budget.
+//
+// A "global step" gives every live simulation one block step, in three
+// phases separated by grid barriers:
+//   1. predict every j entry of every live simulation to its own block time
+//      and append the work items of tiles with active particles (one shared
+//      queue for all simulations);
+//   2. CTAs pull (simulation, tile, list part) items and run the same
+//      force_item body as the single-simulation kernel;
+//   3. correct the active particles and take, per simulation, the min of
+//      t_i + dt_i that starts its next block step.
+// Uneven active sets and list lengths of different simulations share one
+// queue, so small block steps of many simulations fill the GPU together.
+// Results of a simulation do not depend on what else is in the batch: its
+// tiles, active masks and list parts are its own, and sums run in fixed order.
+//
+// Grid barriers spin with an iteration limit; on expiry the kernel records
+// HH_ETIMEOUT and every CTA returns.
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "hh_ctx.h"
+
+using namespace hh;
+
+namespace {
+
+constexpr long long kSpinLimit = 1ll << 25;  // ~ seconds of __nanosleep(64) polling
+constexpr int kGroups = 4;                   // 128-thread worker groups per CTA (one CTA per SM)
+constexpr int kBlock = kThreads * kGroups;
+
+struct SimDesc {
+    State st;
+    const void *rec;
+    Lists L;
+    DevScalars *ds;
+    int64_t n, nj;
+    int32_t n_tiles, pj;
+    Params prm;
+    double t_end;
+};
+
+struct BatchScalars {
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    int32_t err;
+    uint32_t work;
+    uint32_t n_items;
+    int32_t steps_done;
+};
+
+struct BatchDev {
+    const SimDesc *sims;
+    int32_t n_sims;
+    int32_t max_steps;
+    const int64_t *jbase, *pbase, *tbase;  // prefix sums [n_sims + 1]
+    int4 *items;
+    BatchScalars *bs;
+    unsigned long long *step_ns;  // [3 max_steps + 1] global timer at the start and after each phase
+    double *t_next_out;           // [n_sims]
+};
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier for a cooperative launch (all CTAs resident).  Returns
+// false when any CTA has recorded an error (including a barrier timeout).
+__device__ __forceinline__ bool grid_sync(BatchScalars *bs)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *gen = &bs->bar_gen;
+        const unsigned int g = *gen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&bs->bar_count, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            bs->bar_count = 0u;
+            __threadfence();
+            atomicAdd(&bs->bar_gen, 1u);
+        } else {
+            long long it = 0;
+            while (*gen == g) {
+                if (++it > kSpinLimit) {
+                    atomicExch(&bs->err, HH_ETIMEOUT);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = (*(volatile int32_t *)&bs->err) == 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ int find_sim(const int64_t *base, int n_sims, int64_t g)
+{
+    int lo = 0, hi = n_sims;  // base[lo] <= g < base[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (base[mid] <= g) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ double sim_time(const SimDesc &sd, int par)
+{
+    return __longlong_as_double((long long)__ldcg(&sd.ds->tmin[par]));
+}
+
+// Running (simulation, min of t_i + dt_i, corrected count) of one thread;
+// a change of simulation flushes the previous one with atomics.
+struct MinCnt {
+    int s;
+    double m;
+    int c;
+};
+
+__device__ __forceinline__ void mc_flush(const SimDesc *sims, const MinCnt &a, int slot)
+{
+    if (a.s < 0) return;
+    atomicMin(&sims[a.s].ds->tmin[slot], (unsigned long long)__double_as_longlong(a.m));
+    if (a.c) {
+        atomicAdd(&sims[a.s].ds->particle_steps, (unsigned long long)a.c);
+        atomicAdd(&sims[a.s].ds->n_act_last, a.c);
+    }
+}
+
+__device__ __forceinline__ void mc_push(const SimDesc *sims, MinCnt &a, int s, double tn, int cnt, int slot)
+{
+    if (a.s != s) {
+        mc_flush(sims, a, slot);
+        a.s = s;
+        a.m = tn;
+        a.c = cnt;
+    } else {
+        a.m = fmin(a.m, tn);
+        a.c += cnt;
+    }
+}
+
+// CTA-wide combination of the threads' running values: one atomic per
+// simulation run of consecutive warps (all warps of a CTA usually share one
+// simulation, so a phase costs one atomic per CTA).
+__device__ __forceinline__ void mc_block_flush(const SimDesc *sims, MinCnt a, int slot)
+{
+    __shared__ int w_s[kBlock / 32];
+    __shared__ double w_m[kBlock / 32];
+    __shared__ int w_c[kBlock / 32];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int smax = __reduce_max_sync(full, a.s);
+    const bool same = __all_sync(full, a.s < 0 || a.s == smax);
+    if (!same) {
+        mc_flush(sims, a, slot);
+        if (lane == 0) w_s[warp] = -1;
+    } else {
+        double m = a.s < 0 ? __longlong_as_double(0x7FF0000000000000LL) : a.m;
+        int c = a.s < 0 ? 0 : a.c;
+        for (int off = 16; off > 0; off >>= 1) {
+            m = fmin(m, __shfl_xor_sync(full, m, off));
+            c += __shfl_xor_sync(full, c, off);
+        }
+        if (lane == 0) {
+            w_s[warp] = smax;
+            w_m[warp] = m;
+            w_c[warp] = c;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        MinCnt acc{-1, 0.0, 0};
+        for (int w = 0; w < kBlock / 32; w++) {
+            if (w_s[w] < 0) continue;
+            if (acc.s != w_s[w]) {
+                mc_flush(sims, acc, slot);
+                acc = MinCnt{w_s[w], w_m[w], w_c[w]};
+            } else {
+                acc.m = fmin(acc.m, w_m[w]);
+                acc.c += w_c[w];
+            }
+        }
+        mc_flush(sims, acc, slot);
+    }
+    __syncthreads();
+}
+
+template <typename Rec, int TJ>
+__global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tid = threadIdx.x;
+    const int group = tid / kThreads, gt = tid - group * kThreads;
+    ForceSmem<Rec, TJ> &sm = reinterpret_cast<ForceSmem<Rec, TJ> *>(smem_raw)[group];
+    const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + tid;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    const int n_sims = B.n_sims;
+    const int64_t NJ = B.jbase[n_sims], NP = B.pbase[n_sims], NT = B.tbase[n_sims];
+
+    // phase 0: every simulation's first block time
+    if (blockIdx.x == 0)
+        for (int s = tid; s < n_sims; s += blockDim.x) {
+            B.sims[s].ds->tmin[0] = 0x7FF0000000000000ull;
+            B.sims[s].ds->tmin[1] = 0x7FF0000000000000ull;
+        }
+    if (blockIdx.x == 0 && tid == 0) B.step_ns[0] = globaltimer_ns();
+    if (!grid_sync(B.bs)) return;
+    {
+        MinCnt acc{-1, 0.0, 0};
+        for (int64_t g = gtid; g < NP; g += nth) {
+            const int s = find_sim(B.pbase, n_sims, g);
+            const SimDesc &sd = B.sims[s];
+            const int64_t p = g - B.pbase[s];
+            mc_push(B.sims, acc, s, sd.st.t[p] + sd.st.dt[p], 0, 0);
+        }
+        mc_block_flush(B.sims, acc, 0);
+    }
+    if (!grid_sync(B.bs)) return;
+
+    int step = 0;
+    for (; step < B.max_steps; step++) {
+        const int par = step & 1;
+        // ---- phase 1: predict + select
+        if (blockIdx.x == 0)
+            for (int s = tid; s < n_sims; s += blockDim.x) {
+                B.sims[s].ds->tmin[par ^ 1] = 0x7FF0000000000000ull;
+                B.sims[s].ds->n_act_last = 0;
+            }
+        for (int64_t g = gtid; g < NJ; g += nth) {
+            const int s = find_sim(B.jbase, n_sims, g);
+            const SimDesc &sd = B.sims[s];
+            const double tnow = sim_time(sd, par);
+            if (!(tnow <= sd.t_end)) continue;
+            const int64_t e = g - B.jbase[s];
+            double xp[3], vp[3];
+            predict_one(sd.st, e, tnow, xp, vp);
+            store_rec<Rec>((Rec *)sd.rec, e, xp, vp, sd.st.m[e]);
+        }
+        {
+            const int lane = tid & 31;
+            const int64_t w0 = gtid >> 5, nw = nth >> 5;
+            for (int64_t wt = w0; wt < NT; wt += nw) {
+                const int s = find_sim(B.tbase, n_sims, wt);  // warp-uniform
+                const SimDesc &sd = B.sims[s];
+                const double tnow = sim_time(sd, par);
+                if (!(tnow <= sd.t_end)) continue;
+                const int tile = (int)(wt - B.tbase[s]);
+                const int4 td = sd.L.tiles[tile];
+                const int64_t p = td.x + lane;
+                const bool act = (p < td.y) && (sd.st.t[p] + sd.st.dt[p] == tnow);
+                const uint32_t mask = __ballot_sync(0xffffffffu, act);
+                if (mask) append_tile_items(sd.L, tile, td, mask, sd.pj, &B.bs->n_items, B.items, s);
+            }
+        }
+        if (!grid_sync(B.bs)) return;
+        if (blockIdx.x == 0 && tid == 0) B.step_ns[3 * step + 1] = globaltimer_ns();
+
+        // ---- phase 2: forces from the shared queue, one item per worker group
+        {
+            const uint32_t n_items = __ldcg(&B.bs->n_items);
+            const int bar = 1 + group;
+            for (;;) {
+                if (gt == 0) sm.item = (int)atomicAdd(&B.bs->work, 1u);
+                group_sync(bar);
+                const int item = sm.item;
+                if (item >= (int)n_items) break;
+                const int4 it = B.items[item];
+                const SimDesc &sd = B.sims[it.y >> 16];
+                unsigned long long n_int = 0;
+                force_item<Rec, TJ, false>(sd.st, (const Rec *)sd.rec, sd.L, sd.pj,
+                                           (typename Traits<Rec>::Eps)sd.prm.eps2, it, sm, n_int, gt, bar);
+                if (gt == 0 && n_int) atomicAdd(&sd.ds->interactions, n_int);
+                group_sync(bar);
+            }
+        }
+        if (!grid_sync(B.bs)) return;
+        if (blockIdx.x == 0 && tid == 0) B.step_ns[3 * step + 2] = globaltimer_ns();
+
+        // ---- phase 3: correct + next block times
+        {
+            MinCnt acc{-1, 0.0, 0};
+            for (int64_t g = gtid; g < NP; g += nth) {
+                const int s = find_sim(B.pbase, n_sims, g);
+                const SimDesc &sd = B.sims[s];
+                const double tnow = sim_time(sd, par);
+                if (!(tnow <= sd.t_end)) continue;  // finished simulations keep their next time
+                const int64_t p = g - B.pbase[s];
+                int cnt = 0;
+                if (sd.st.t[p] + sd.st.dt[p] == tnow) {
+                    correct_particle(sd.st, p, tnow, sd.prm);
+                    cnt = 1;
+                }
+                mc_push(B.sims, acc, s, sd.st.t[p] + sd.st.dt[p], cnt, par ^ 1);
+            }
+            mc_block_flush(B.sims, acc, par ^ 1);
+        }
+        if (blockIdx.x == 0) {
+            if (tid == 0) {
+                B.bs->work = 0u;
+                B.bs->n_items = 0u;
+            }
+            for (int s = tid; s < n_sims; s += blockDim.x) {
+                const SimDesc &sd = B.sims[s];
+                if (sim_time(sd, par) <= sd.t_end) {
+                    sd.ds->block_steps += 1ull;
+                } else {
+                    sd.ds->tmin[par ^ 1] = sd.ds->tmin[par];  // carry a finished simulation's time
+                }
+            }
+        }
+        if (!grid_sync(B.bs)) return;
+        if (blockIdx.x == 0 && tid == 0) B.step_ns[3 * step + 3] = globaltimer_ns();
+
+        // any simulation still live for the next step?
+        int live = 0;
+        for (int s = tid; s < n_sims; s += blockDim.x) live |= sim_time(B.sims[s], par ^ 1) <= B.sims[s].t_end;
+        if (!__syncthreads_or(live)) {
+            step++;
+            break;
+        }
+    }
+    if (blockIdx.x == 0) {
+        const int par = step & 1;
+        for (int s = tid; s < n_sims; s += blockDim.x) B.t_next_out[s] = sim_time(B.sims[s], par);
+        if (tid == 0) B.bs->steps_done = step;
+    }
+}
+
+}  // namespace
+
+struct hh_batch {
+    int device = 0;
+    int precision = HH_FP64;
+    int32_t max_sims = 0, max_steps = 0;
+    int grid = 0;
+    size_t smem = 0;
+    cudaStream_t stream = nullptr;
+    SimDesc *d_sims = nullptr;
+    int64_t *d_base = nullptr;  // 3 x (max_sims + 1)
+    int4 *d_items = nullptr;
+    int64_t cap_items = 0;
+    BatchScalars *d_bs = nullptr;
+    unsigned long long *d_step_ns = nullptr;
+    double *d_tnext = nullptr;
+    std::vector<unsigned long long> h_step_ns;
+    std::string err;
+};
+
+namespace {
+
+int bfail(hh_batch *b, int code, const std::string &m)
+{
+    if (b) b->err = m;
+    return hh_set_global_error(code, m.c_str());
+}
+
+}  // namespace
+
+extern "C" int hh_batch_create(hh_batch **out, int device, int precision, int32_t max_sims, int32_t max_steps)
+{
+    if (!out) return hh_set_global_error(HH_EINVAL, "hh_batch_create: out is NULL");
+    *out = nullptr;
+    if ((precision != HH_FP64 && precision != HH_MIXED) || max_sims < 1 || max_sims > 32767 || max_steps < 1)
+        return hh_set_global_error(HH_EINVAL, "hh_batch_create: bad precision, max_sims (1..32767) or max_steps");
+    hh_batch *b = new (std::nothrow) hh_batch;
+    if (!b) return hh_set_global_error(HH_ENOMEM, "hh_batch_create: out of host memory");
+    b->device = device;
+    b->precision = precision;
+    b->max_sims = max_sims;
+    b->max_steps = max_steps;
+    auto bail = [&](int code, const char *m) {
+        hh_batch_destroy(b);
+        return hh_set_global_error(code, m);
+    };
+    if (cudaSetDevice(device) != cudaSuccess) return bail(HH_ECUDA, "hh_batch_create: cudaSetDevice failed");
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(HH_ECUDA, "hh_batch_create: stream creation failed");
+    cudaDeviceProp prop;
+    int coop = 0;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop)
+        return bail(HH_ECUDA, "hh_batch_create: device lacks cooperative launch");
+    int per = 0;
+    if (precision == HH_MIXED) {
+        b->smem = sizeof(ForceSmem<RecMix, kTjMix>) * kGroups;
+        cudaFuncSetAttribute(k_batch<RecMix, kTjMix>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(b->smem));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<RecMix, kTjMix>, kBlock, b->smem);
+    } else {
+        b->smem = sizeof(ForceSmem<RecF64, kTjF64>) * kGroups;
+        cudaFuncSetAttribute(k_batch<RecF64, kTjF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(b->smem));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch<RecF64, kTjF64>, kBlock, b->smem);
+    }
+    if (per < 1) return bail(HH_ECUDA, "hh_batch_create: kernel does not fit on an SM");
+    b->grid = prop.multiProcessorCount;  // one persistent CTA per SM
+    if (cudaMalloc(&b->d_sims, sizeof(SimDesc) * max_sims) != cudaSuccess ||
+        cudaMalloc(&b->d_base, sizeof(int64_t) * 3 * (max_sims + 1)) != cudaSuccess ||
+        cudaMalloc(&b->d_bs, sizeof(BatchScalars)) != cudaSuccess ||
+        cudaMalloc(&b->d_step_ns, sizeof(unsigned long long) * (3 * size_t(max_steps) + 1)) != cudaSuccess ||
+        cudaMalloc(&b->d_tnext, sizeof(double) * max_sims) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(HH_ENOMEM, "hh_batch_create: device allocation failed");
+    }
+    b->h_step_ns.resize(3 * size_t(max_steps) + 1);
+    *out = b;
+    return HH_OK;
+}
+
+extern "C" int hh_batch_destroy(hh_batch *b)
+{
+    if (!b) return HH_OK;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    void *p[] = {b->d_sims, b->d_base, b->d_items, b->d_bs, b->d_step_ns, b->d_tnext};
+    for (void *q : p)
+        if (q) cudaFree(q);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return HH_OK;
+}
+
+extern "C" int hh_batch_run(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const double *t_end, int32_t max_steps,
+                            int32_t *steps_out, double *t_next_out, double *step_us_out, double *phase_us_out)
+{
+    if (!b) return hh_set_global_error(HH_EINVAL, "hh_batch_run: NULL batch");
+    if (n < 1 || n > b->max_sims || !ctxs || !t_end) return bfail(b, HH_EINVAL, "hh_batch_run: bad n or NULL arrays");
+    if (max_steps < 1 || max_steps > b->max_steps) return bfail(b, HH_EINVAL, "hh_batch_run: max_steps out of range");
+    if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, HH_ECUDA, "hh_batch_run: cudaSetDevice failed");
+    std::vector<SimDesc> sims(static_cast<size_t>(n));
+    std::vector<int64_t> base(3 * (static_cast<size_t>(n) + 1), 0);
+    int64_t *jb = base.data(), *pb = jb + n + 1, *tb = pb + n + 1;
+    int64_t items_needed = 0;
+    for (int32_t s = 0; s < n; s++) {
+        hh_ctx *c = ctxs[s];
+        if (!c) return bfail(b, HH_EINVAL, "hh_batch_run: NULL context");
+        if (c->device != b->device || c->cfg.precision != b->precision)
+            return bfail(b, HH_EINVAL, "hh_batch_run: context device or precision differs from the batch");
+        if (!c->have_lists || !c->have_dt) return bfail(b, HH_ESTATE, "hh_batch_run: a context lacks lists or steps");
+        for (int32_t q = 0; q < s; q++)
+            if (ctxs[q] == c) return bfail(b, HH_EINVAL, "hh_batch_run: a context appears twice");
+        if (!(t_end[s] == t_end[s])) return bfail(b, HH_EINVAL, "hh_batch_run: NaN stop time");
+        SimDesc &d = sims[size_t(s)];
+        std::memset(&d, 0, sizeof(d));
+        d.st = c->st;
+        d.rec = c->rec;
+        d.L.off = c->off;
+        d.L.idx = c->idx;
+        d.L.tiles = c->tiles;
+        d.L.items = nullptr;
+        d.L.partials = c->partials;
+        d.L.tile_cnt = c->tile_cnt;
+        d.L.i_map = nullptr;
+        d.ds = c->ds;
+        d.n = c->n;
+        d.nj = c->nj;
+        d.n_tiles = c->n_tiles;
+        d.pj = c->part_len;
+        d.prm.eps2 = c->cfg.eps2;
+        d.prm.eta = c->cfg.eta;
+        d.prm.eta_s = c->cfg.eta_s;
+        d.prm.dt_min = c->cfg.dt_min;
+        d.prm.dt_max = c->cfg.dt_max;
+        d.t_end = t_end[s];
+        jb[s + 1] = jb[s] + c->nj;
+        pb[s + 1] = pb[s] + c->n;
+        tb[s + 1] = tb[s] + c->n_tiles;
+        items_needed += c->total_parts;
+        // pending work of the context must be finished before the batch stream uses its memory
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bfail(b, HH_ECUDA, "hh_batch_run: context stream failed");
+    }
+    if (items_needed > INT32_MAX / 2) return bfail(b, HH_ENOMEM, "hh_batch_run: too many work items");
+    if (items_needed > b->cap_items) {
+        if (b->d_items) cudaFree(b->d_items);
+        b->d_items = nullptr;
+        const int64_t cap = items_needed + items_needed / 4 + 64;
+        if (cudaMalloc(&b->d_items, sizeof(int4) * cap) != cudaSuccess) {
+            cudaGetLastError();
+            b->cap_items = 0;
+            return bfail(b, HH_ENOMEM, "hh_batch_run: cannot allocate the work queue");
+        }
+        b->cap_items = cap;
+    }
+    cudaStream_t st = b->stream;
+    if (cudaMemcpyAsync(b->d_sims, sims.data(), sizeof(SimDesc) * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(b->d_base, base.data(), sizeof(int64_t) * base.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(b->d_bs, 0, sizeof(BatchScalars), st) != cudaSuccess)
+        return bfail(b, HH_ECUDA, "hh_batch_run: upload failed");
+    BatchDev B;
+    B.sims = b->d_sims;
+    B.n_sims = n;
+    B.max_steps = max_steps;
+    B.jbase = b->d_base;
+    B.pbase = b->d_base + (n + 1);
+    B.tbase = b->d_base + 2 * (n + 1);
+    B.items = b->d_items;
+    B.bs = b->d_bs;
+    B.step_ns = b->d_step_ns;
+    B.t_next_out = b->d_tnext;
+    void *args[] = {&B};
+    cudaError_t e;
+    if (b->precision == HH_MIXED)
+        e = cudaLaunchCooperativeKernel((const void *)k_batch<RecMix, kTjMix>, dim3(b->grid), dim3(kBlock), args, b->smem,
+                                        st);
+    else
+        e = cudaLaunchCooperativeKernel((const void *)k_batch<RecF64, kTjF64>, dim3(b->grid), dim3(kBlock), args, b->smem,
+                                        st);
+    if (e != cudaSuccess) return bfail(b, HH_ECUDA, std::string("hh_batch_run: launch: ") + cudaGetErrorString(e));
+    hh_count_launches(1);
+    BatchScalars hbs;
+    std::vector<double> tn(static_cast<size_t>(n));
+    if (cudaMemcpyAsync(&hbs, b->d_bs, sizeof(hbs), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(tn.data(), b->d_tnext, sizeof(double) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(b->h_step_ns.data(), b->d_step_ns, sizeof(unsigned long long) * (3 * size_t(max_steps) + 1),
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return bfail(b, HH_ECUDA, "hh_batch_run: kernel execution failed");
+    if (hbs.err) return bfail(b, hbs.err, "hh_batch_run: grid barrier timed out");
+    for (int32_t s = 0; s < n; s++) {
+        ctxs[s]->predicted = false;
+        ctxs[s]->have_forces = true;
+    }
+    if (steps_out) *steps_out = hbs.steps_done;
+    if (t_next_out) std::copy(tn.begin(), tn.end(), t_next_out);
+    const unsigned long long *T = b->h_step_ns.data();
+    for (int32_t q = 0; q < hbs.steps_done; q++) {
+        const size_t k = 3 * size_t(q);
+        if (step_us_out) step_us_out[q] = double(T[k + 3] - T[k]) * 1e-3;
+        if (phase_us_out)
+            for (int ph = 0; ph < 3; ph++) phase_us_out[3 * size_t(q) + ph] = double(T[k + ph + 1] - T[k + ph]) * 1e-3;
+    }
+    return HH_OK;
+}
+
+extern "C" const char *hh_batch_last_error(const hh_batch *b) { return b ? b->err.c_str() : hh_last_error(nullptr); }

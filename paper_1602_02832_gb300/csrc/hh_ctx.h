@@ -1,0 +1,68 @@
+// The hh_ctx structure, shared by the CUDA translation units of libhh.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "hh_internal.h"
+#include "hh_kernels.cuh"
+
+constexpr int kTjF64 = 128;  // list entries staged per chunk, plain form
+constexpr int kTjMix = 256;  // list entries staged per chunk, mixed form
+
+// Adds n to the process-wide count of kernels launched by libhh.
+void hh_count_launches(int64_t n);
+
+struct hh_ctx {
+    int device = 0;
+    hh_config cfg{};
+    cudaStream_t own_stream = nullptr, stream = nullptr;
+    int64_t cap_n = 0, cap_j = 0, cap_list = 0;
+    int32_t cap_g = 0;
+    int64_t cap_tiles = 0;
+    int64_t n = 0, nj = 0, list_len = 0;
+    int32_t n_groups = 0, n_tiles = 0, tile_i = 32;
+    // device memory
+    hh::State st{};
+    void *rec = nullptr;
+    int64_t *off = nullptr;
+    int32_t *idx = nullptr, *group_of = nullptr;
+    int4 *tiles = nullptr;
+    int4 *items = nullptr;      // [cap_parts]
+    void *partials = nullptr;   // [cap_parts][32] partial sums (scratch)
+    int32_t *tile_cnt = nullptr;  // [cap_tiles]
+    int64_t cap_parts = 0;
+    int64_t total_parts = 0;    // work items of a step with every tile active
+    int64_t device_bytes = 0;   // device memory allocated for this context
+    int32_t part_len = 512;
+    hh::DevScalars *ds = nullptr;
+    int32_t *i_buf = nullptr;  // [cap_n]
+    double *out_buf = nullptr; // [7 * cap_n]
+    // pinned host staging
+    hh::DevScalars *h_ds = nullptr;
+    double *h_buf = nullptr;   // [14 * cap_j]
+    int32_t *h_ibuf = nullptr; // [cap_n]
+    double *h_jbuf = nullptr;  // [14 * cap_j] staging of the rebuilt j entries
+    hh_tree *tree = nullptr;   // host tree reused by hh_rebuild
+    std::vector<int64_t> ids;  // slot -> particle id
+    std::vector<int32_t> h_group_of;
+    // grid shapes
+    int n_sm = 0, force_grid = 0, elem_grid = 0;
+    // loop graph
+    cudaGraphExec_t graph = nullptr;
+    int graph_timed = -1;
+    std::vector<cudaEvent_t> ev;  // 2 per unrolled step when timed
+    // timing
+    bool timing = false;
+    double force_ms = 0.0;
+    int64_t force_launches = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    // state flags
+    bool have_j = false, have_lists = false, have_dt = false, predicted = false, have_forces = false;
+    int64_t rebuilds = 0;
+    std::string err;
+};
+

@@ -119,6 +119,19 @@ __device__ __forceinline__ double pow2_floor(double x)
 // of one group) one warp ballots the tile's active particles; a tile with
 // any active particle appends one work item per part of its group's list.
 // Item order may vary between runs; results do not depend on it.
+// Warp-collective: appends one work item per part of tile `tile`'s list.
+__device__ __forceinline__ void append_tile_items(const Lists &L, int tile, const int4 td, uint32_t mask, int pj,
+                                                  uint32_t *n_items, int4 *items, int sim)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t len = L.off[td.z + 1] - L.off[td.z];
+    const int n_parts = len > 0 ? (int)((len + pj - 1) / pj) : 1;
+    int base = 0;
+    if (lane == 0) base = (int)atomicAdd(n_items, (uint32_t)n_parts);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int q = lane; q < n_parts; q += 32) items[base + q] = make_int4(tile, q | (sim << 16), (int)mask, n_parts);
+}
+
 __device__ __forceinline__ void select_tiles(const State &s, const Lists &L, DevScalars *ds, const StepCtl &c,
                                              double tnow)
 {
@@ -133,12 +146,7 @@ __device__ __forceinline__ void select_tiles(const State &s, const Lists &L, Dev
         const bool act = (p < td.y) && is_active(s, c, p, tnow);
         const uint32_t mask = __ballot_sync(0xffffffffu, act);
         if (mask == 0u) continue;
-        const int64_t len = L.off[td.z + 1] - L.off[td.z];
-        const int n_parts = len > 0 ? (int)((len + pj - 1) / pj) : 1;
-        int base = 0;
-        if (lane == 0) base = (int)atomicAdd(&ds->n_items, (uint32_t)n_parts);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        for (int q = lane; q < n_parts; q += 32) L.items[base + q] = make_int4((int)tile, q, (int)mask, n_parts);
+        append_tile_items(L, (int)tile, td, mask, pj, &ds->n_items, L.items, 0);
     }
 }
 
@@ -456,138 +464,159 @@ __device__ __forceinline__ void fold_chunk(AccMix &A) { A.fold(); }
 // tile's last part (arrival counter, threadfence pattern: no waiting) adds
 // the parts in part order.  So each particle's result depends only on its
 // list, its tile's active count and the part length, never on scheduling.
+template <typename Rec, int TJ>
+struct ForceSmem {
+    Rec rec[TJ];
+    int32_t idx[TJ];
+    typename Traits<Rec>::Red red[kThreads / 32][kMaxTileI];
+    int item;
+    int last;
+};
+
+// Barrier over the 128 threads working on one item: the whole CTA
+// (bar_id 0) or one of several 128-thread worker groups of a larger CTA
+// (named barrier bar_id = 1 + group).
+__device__ __forceinline__ void group_sync(int bar_id)
+{
+    if (bar_id == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(kThreads) : "memory");
+}
+
+// item = (tile, part | sim << 16, active mask, parts of the tile); tid is
+// the thread's index in its 128-thread group.
+template <typename Rec, int TJ, bool kMapI>
+__device__ __forceinline__ void force_item(const State &s, const Rec *__restrict__ rec, const Lists &L, int pj,
+                                           typename Traits<Rec>::Eps eps2, const int4 it, ForceSmem<Rec, TJ> &sm,
+                                           unsigned long long &n_int, const int tid, const int bar_id)
+{
+    using T = Traits<Rec>;
+    using Red = typename T::Red;
+    const int lane = tid & 31, warp = tid >> 5;
+    Red *partials = reinterpret_cast<Red *>(L.partials);
+    const int4 td = L.tiles[it.x];
+    const int part = it.y & 0xFFFF, n_parts = it.w;
+    const uint32_t mask = (uint32_t)it.z;
+    const int n_a = __popc(mask);
+
+    int I = 1;
+    while (I < n_a) I <<= 1;
+    const int islot = tid & (I - 1);
+    const int jslice = tid / I;
+    const int S = kThreads / I;
+    const bool has_i = islot < n_a;
+    int64_t pi = -1;
+    {
+        uint32_t mm = mask;
+        for (int q = 0; q < islot && mm; q++) mm &= mm - 1;
+        if (has_i) pi = td.x + (__ffs(mm) - 1);
+    }
+    int64_t pload = has_i ? pi : td.x + (__ffs(mask) - 1);  // spare slots repeat a live one; dropped
+    if constexpr (kMapI) {
+        // slots are positions in a caller's active list; i is its j index
+        pload = L.i_map[pload];
+        if (has_i) pi = pload;
+    }
+    typename T::I Iv;
+    load_i(rec, pload, Iv);
+    typename T::Acc A;
+    A.zero();
+
+    const int64_t gb = L.off[td.z], ge = L.off[td.z + 1];
+    const int64_t lb = gb + (int64_t)part * pj;
+    const int64_t le = min(ge, lb + (int64_t)pj);
+    const int64_t len = le - lb;
+    if (tid == 0 && part == 0) n_int += (unsigned long long)n_a * (unsigned long long)(ge - gb - 1);
+    for (int64_t c0 = 0; c0 < len; c0 += TJ) {
+        const int nc = (len - c0 < (int64_t)TJ) ? (int)(len - c0) : TJ;
+        for (int e = tid; e < nc; e += kThreads) {
+            const int32_t j = L.idx[lb + c0 + e];
+            sm.idx[e] = j;
+            sm.rec[e] = rec[j];
+        }
+        group_sync(bar_id);
+        // FP32 partials are folded into the compensated sums every
+        // kFold terms per thread (short plain-FP32 runs keep the
+        // partial-sum rounding below the per-term rounding).
+        for (int e = jslice; e < nc;) {
+            const int e_end = min(nc, e + kFold * S);
+            for (; e < e_end; e += S) {
+                const int32_t j = sm.idx[e];
+                interact(Iv, sm.rec[e], (int64_t)j == pi, eps2, A);
+            }
+            fold_chunk(A);
+        }
+        group_sync(bar_id);
+    }
+    // reduce the S slices of each i slot: lanes l, l+I, ... then warps
+    for (int off = I; off < 32; off <<= 1) acc_shfl_add(A, off);
+    if (lane < I) {
+        Red r;
+        to_red(A, r);
+        sm.red[warp][lane] = r;
+    }
+    group_sync(bar_id);
+    Red r;
+    if (tid < n_a) {
+        r = sm.red[0][tid];
+        for (int w = 1; w < kThreads / 32; w++) red_add(r, sm.red[w][tid]);
+    }
+    bool write_out = n_parts == 1;
+    if (n_parts > 1) {
+        Red *mine = partials + ((int64_t)td.w + part) * kMaxTileI;
+        if (tid < n_a) mine[tid] = r;
+        __threadfence();
+        group_sync(bar_id);
+        if (tid == 0) {
+            const int old = atomicAdd(&L.tile_cnt[it.x], 1);
+            sm.last = (old == n_parts - 1);
+        }
+        group_sync(bar_id);
+        write_out = sm.last;
+        if (write_out) {
+            __threadfence();
+            if (tid < n_a) {
+                const Red *base = partials + (int64_t)td.w * kMaxTileI;
+                r = ld_red_cg(base + tid);
+                for (int q = 1; q < n_parts; q++) red_add(r, ld_red_cg(base + (int64_t)q * kMaxTileI + tid));
+            }
+            if (tid == 0) L.tile_cnt[it.x] = 0;
+        }
+    }
+    if (write_out && tid < n_a) {
+        uint32_t mm = mask;
+        for (int q = 0; q < tid; q++) mm &= mm - 1;
+        const int64_t p = td.x + (__ffs(mm) - 1);
+        s.acc1[0 * s.cap_n + p] = red_get(r, 0);
+        s.acc1[1 * s.cap_n + p] = red_get(r, 1);
+        s.acc1[2 * s.cap_n + p] = red_get(r, 2);
+        s.jerk1[0 * s.cap_n + p] = red_get(r, 3);
+        s.jerk1[1 * s.cap_n + p] = red_get(r, 4);
+        s.jerk1[2 * s.cap_n + p] = red_get(r, 5);
+        s.pot1[p] = -red_get(r, 6);
+    }
+    // callers put a barrier before the shared buffers are reused
+}
+
 template <typename Rec, int TJ, bool kMapI = false>
 __global__ void __launch_bounds__(kThreads, 6) k_force(State s, const Rec *__restrict__ rec, Lists L, DevScalars *ds,
                                                     StepCtl c, Params prm)
 {
-    using T = Traits<Rec>;
-    using Red = typename T::Red;
     double tnow;
     if (!step_time(ds, c, &tnow)) return;
-
-    __shared__ Rec s_rec[TJ];
-    __shared__ int32_t s_idx[TJ];
-    __shared__ Red s_red[kThreads / 32][kMaxTileI];
-    __shared__ int s_item;
-    __shared__ int s_last;
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ ForceSmem<Rec, TJ> sm;
     const int n_items = (int)ds->n_items;
     const int pj = ds->part_len;
-    const typename T::Eps eps2 = (typename T::Eps)prm.eps2;
-    Red *partials = reinterpret_cast<Red *>(L.partials);
+    const typename Traits<Rec>::Eps eps2 = (typename Traits<Rec>::Eps)prm.eps2;
     unsigned long long n_int = 0;
-
     for (;;) {
-        if (tid == 0) s_item = (int)atomicAdd(&ds->work, 1u);
+        if (threadIdx.x == 0) sm.item = (int)atomicAdd(&ds->work, 1u);
         __syncthreads();
-        const int item = s_item;
+        const int item = sm.item;
         if (item >= n_items) break;
-        const int4 it = L.items[item];
-        const int4 td = L.tiles[it.x];
-        const int part = it.y, n_parts = it.w;
-        const uint32_t mask = (uint32_t)it.z;
-        const int n_a = __popc(mask);
-
-        int I = 1;
-        while (I < n_a) I <<= 1;
-        const int islot = tid & (I - 1);
-        const int jslice = tid / I;
-        const int S = kThreads / I;
-        const bool has_i = islot < n_a;
-        int64_t pi = -1;
-        {
-            uint32_t mm = mask;
-            for (int q = 0; q < islot && mm; q++) mm &= mm - 1;
-            if (has_i) pi = td.x + (__ffs(mm) - 1);
-        }
-        int64_t pload = has_i ? pi : td.x + (__ffs(mask) - 1);  // spare slots repeat a live one; dropped
-        if constexpr (kMapI) {
-            // slots are positions in a caller's active list; i is its j index
-            pload = L.i_map[pload];
-            if (has_i) pi = pload;
-        }
-        typename T::I Iv;
-        load_i(rec, pload, Iv);
-        typename T::Acc A;
-        A.zero();
-
-        const int64_t gb = L.off[td.z], ge = L.off[td.z + 1];
-        const int64_t lb = gb + (int64_t)part * pj;
-        const int64_t le = min(ge, lb + (int64_t)pj);
-        const int64_t len = le - lb;
-        if (tid == 0 && part == 0) n_int += (unsigned long long)n_a * (unsigned long long)(ge - gb - 1);
-        for (int64_t c0 = 0; c0 < len; c0 += TJ) {
-            const int nc = (len - c0 < (int64_t)TJ) ? (int)(len - c0) : TJ;
-            for (int e = tid; e < nc; e += kThreads) {
-                const int32_t j = L.idx[lb + c0 + e];
-                s_idx[e] = j;
-                s_rec[e] = rec[j];
-            }
-            __syncthreads();
-            // FP32 partials are folded into the compensated sums every
-            // kFold terms per thread (short plain-FP32 runs keep the
-            // partial-sum rounding below the per-term rounding).
-            for (int e = jslice; e < nc;) {
-                const int e_end = min(nc, e + kFold * S);
-                for (; e < e_end; e += S) {
-                    const int32_t j = s_idx[e];
-                    interact(Iv, s_rec[e], (int64_t)j == pi, eps2, A);
-                }
-                fold_chunk(A);
-            }
-            __syncthreads();
-        }
-        // reduce the S slices of each i slot: lanes l, l+I, ... then warps
-        for (int off = I; off < 32; off <<= 1) acc_shfl_add(A, off);
-        if (lane < I) {
-            Red r;
-            to_red(A, r);
-            s_red[warp][lane] = r;
-        }
-        __syncthreads();
-        Red r;
-        if (tid < n_a) {
-            r = s_red[0][tid];
-            for (int w = 1; w < kThreads / 32; w++) red_add(r, s_red[w][tid]);
-        }
-        bool write_out = n_parts == 1;
-        if (n_parts > 1) {
-            Red *mine = partials + ((int64_t)td.w + part) * kMaxTileI;
-            if (tid < n_a) mine[tid] = r;
-            __threadfence();
-            __syncthreads();
-            if (tid == 0) {
-                const int old = atomicAdd(&L.tile_cnt[it.x], 1);
-                s_last = (old == n_parts - 1);
-            }
-            __syncthreads();
-            write_out = s_last;
-            if (write_out) {
-                __threadfence();
-                if (tid < n_a) {
-                    const Red *base = partials + (int64_t)td.w * kMaxTileI;
-                    r = ld_red_cg(base + tid);
-                    for (int q = 1; q < n_parts; q++) red_add(r, ld_red_cg(base + (int64_t)q * kMaxTileI + tid));
-                }
-                if (tid == 0) L.tile_cnt[it.x] = 0;
-            }
-        }
-        if (write_out && tid < n_a) {
-            uint32_t mm = mask;
-            for (int q = 0; q < tid; q++) mm &= mm - 1;
-            const int64_t p = td.x + (__ffs(mm) - 1);
-            s.acc1[0 * s.cap_n + p] = red_get(r, 0);
-            s.acc1[1 * s.cap_n + p] = red_get(r, 1);
-            s.acc1[2 * s.cap_n + p] = red_get(r, 2);
-            s.jerk1[0 * s.cap_n + p] = red_get(r, 3);
-            s.jerk1[1 * s.cap_n + p] = red_get(r, 4);
-            s.jerk1[2 * s.cap_n + p] = red_get(r, 5);
-            s.pot1[p] = -red_get(r, 6);
-        }
-        // the next iteration's first barrier protects s_item / s_red / s_rec reuse
+        force_item<Rec, TJ, kMapI>(s, rec, L, pj, eps2, L.items[item], sm, n_int, threadIdx.x, 0);
+        // the next iteration's first barrier protects sm reuse
     }
-    if (tid == 0 && n_int) atomicAdd(&ds->interactions, n_int);
+    if (threadIdx.x == 0 && n_int) atomicAdd(&ds->interactions, n_int);
 }
 
 // -------------------------------------------------------------- corrector
@@ -621,20 +650,8 @@ __device__ __forceinline__ void atomic_min_time(unsigned long long *slot, double
 // a2 = (-6 (a0 - a1) - D (4 j0 + 2 j1)) / D^2, a3 = (12 (a0 - a1) + 6 D (j0 + j1)) / D^3,
 // x1 = x_p + a2 D^4/24 + a3 D^5/120, v1 = v_p + a2 D^3/6 + a3 D^4/24;
 // new step from Aarseth's criterion at the end of the step.
-static __global__ void k_correct(State s, DevScalars *ds, StepCtl c, Params prm)
+__device__ __forceinline__ void correct_particle(const State &s, int64_t p, double tnow, const Params &prm)
 {
-    double tnow;
-    if (!step_time(ds, c, &tnow)) return;
-    const int64_t n = ds->n;
-    double my_min = __longlong_as_double(0x7FF0000000000000LL);
-    int my_cnt = 0;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-        const bool act = is_active(s, c, p, tnow);
-        if (act) {
-            if (c.mode == 1 && s.t[p] + s.dt[p] != tnow) {
-                atomicExch(&ds->err, -1);  // HH_EINVAL: marked particle not due at t
-                continue;
-            }
             const double D = tnow - s.t[p];
             double xp[3], vp[3];
             predict_one(s, p, tnow, xp, vp);
@@ -660,6 +677,23 @@ static __global__ void k_correct(State s, DevScalars *ds, StepCtl c, Params prm)
             const double dtn = block_dt(want, s.dt[p], tnow, prm.dt_min, prm.dt_max);
             s.t[p] = tnow;
             s.dt[p] = dtn;
+}
+
+static __global__ void k_correct(State s, DevScalars *ds, StepCtl c, Params prm)
+{
+    double tnow;
+    if (!step_time(ds, c, &tnow)) return;
+    const int64_t n = ds->n;
+    double my_min = __longlong_as_double(0x7FF0000000000000LL);
+    int my_cnt = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const bool act = is_active(s, c, p, tnow);
+        if (act) {
+            if (c.mode == 1 && s.t[p] + s.dt[p] != tnow) {
+                atomicExch(&ds->err, -1);  // HH_EINVAL: marked particle not due at t
+                continue;
+            }
+            correct_particle(s, p, tnow, prm);
             my_cnt++;
         }
         const double tn = s.t[p] + s.dt[p];

@@ -59,6 +59,9 @@ struct hh_tree {
     std::vector<int32_t> g_cell, g_begin, g_end, group_of;
     std::vector<int64_t> off;
     std::vector<int32_t> idx;
+    // work buffers kept between rebuilds so that repeated builds reuse memory
+    std::vector<std::pair<uint64_t, int32_t>> ki;
+    std::vector<std::vector<int32_t>> lists;
 };
 
 namespace {
@@ -160,8 +163,11 @@ void find_groups(hh_tree &t, int n_crit)
         for (int32_t q = t.g_begin[g]; q < t.g_end[g]; q++) t.group_of[q] = int32_t(g);
 }
 
+// The walk is pre-order with children in octant order, so particles (Morton
+// indices) and nodes (n + pre-order cell number) each come out ascending:
+// collecting them apart and concatenating gives the sorted list directly.
 void group_list(const hh_tree &t, int32_t g, double theta, const double *x, std::vector<int32_t> &out,
-                std::vector<int32_t> &stack)
+                std::vector<int32_t> &stack, std::vector<int32_t> &nodes)
 {
     const int64_t n = t.n;
     const int32_t gb = t.g_begin[g], ge = t.g_end[g], gc = t.g_cell[g];
@@ -179,6 +185,7 @@ void group_list(const hh_tree &t, int32_t g, double theta, const double *x, std:
         }
     }
     out.clear();
+    nodes.clear();
     stack.clear();
     stack.push_back(0);
     while (!stack.empty()) {
@@ -205,7 +212,7 @@ void group_list(const hh_tree &t, int32_t g, double theta, const double *x, std:
             }
             const double dist = std::sqrt(d2);
             if (cell.side < theta * dist) {
-                out.push_back(int32_t(n + c));
+                nodes.push_back(int32_t(n + c));
                 continue;
             }
             if (cell.n_child == 0) {
@@ -215,18 +222,17 @@ void group_list(const hh_tree &t, int32_t g, double theta, const double *x, std:
         }
         for (int q = cell.n_child - 1; q >= 0; q--) stack.push_back(cell.child[q]);
     }
-    std::sort(out.begin(), out.end());
+    out.insert(out.end(), nodes.begin(), nodes.end());
 }
 
 }  // namespace
 
-extern "C" int hh_tree_build(hh_tree **out, int64_t n, const double *x, const double *v, const double *a,
-                             const double *jk, const double *m, int32_t leaf, int32_t n_crit, double theta)
+namespace {
+
+int check_inputs(int64_t n, const double *x, const double *v, const double *a, const double *jk, const double *m,
+                 int32_t leaf, int32_t n_crit, double theta)
 {
-    if (!out) return hh_set_global_error(HH_EINVAL, "hh_tree_build: out is NULL");
-    *out = nullptr;
-    if (n < 1 || n > INT32_MAX / 2 || !x || !v || !a || !jk || !m || leaf < 1 || n_crit < 1 ||
-        !(theta >= 0.0))
+    if (n < 1 || n > INT32_MAX / 2 || !x || !v || !a || !jk || !m || leaf < 1 || n_crit < 1 || !(theta >= 0.0))
         return hh_set_global_error(HH_EINVAL, "hh_tree_build: bad arguments");
     for (int64_t i = 0; i < 3 * n; i++)
         if (!std::isfinite(x[i]) || !std::isfinite(v[i]) || !std::isfinite(a[i]) || !std::isfinite(jk[i]))
@@ -234,10 +240,19 @@ extern "C" int hh_tree_build(hh_tree **out, int64_t n, const double *x, const do
     for (int64_t i = 0; i < n; i++)
         if (!(m[i] > 0.0) || !std::isfinite(m[i]))
             return hh_set_global_error(HH_EINVAL, "hh_tree_build: masses must be positive and finite");
-    hh_tree *t = new (std::nothrow) hh_tree;
-    if (!t) return hh_set_global_error(HH_ENOMEM, "hh_tree_build: out of host memory");
+    return HH_OK;
+}
+
+// Builds into t, reusing the capacity of its vectors.
+int build_into(hh_tree *t, int64_t n, const double *x, const double *v, const double *a, const double *jk,
+               const double *m, int32_t leaf, int32_t n_crit, double theta)
+{
     try {
         t->n = n;
+        t->cells.clear();
+        t->g_cell.clear();
+        t->g_begin.clear();
+        t->g_end.clear();
         double lo[3], hi[3];
         for (int d = 0; d < 3; d++) {
             lo[d] = hi[d] = x[d * n];
@@ -252,7 +267,8 @@ extern "C" int hh_tree_build(hh_tree **out, int64_t n, const double *x, const do
             if (hi[d] - lo[d] > side) side = hi[d] - lo[d];
         if (side == 0.0) side = 1.0;
         const double scale = double(1u << kBits) / side;
-        std::vector<std::pair<uint64_t, int32_t>> ki((size_t)(n));
+        auto &ki = t->ki;
+        ki.resize(size_t(n));
 #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; i++) {
             uint64_t k = 0;
@@ -275,12 +291,13 @@ extern "C" int hh_tree_build(hh_tree **out, int64_t n, const double *x, const do
         node_moments(*t, x, v, a, jk, m);
         find_groups(*t, n_crit);
         const int32_t G = int32_t(t->g_cell.size());
-        std::vector<std::vector<int32_t>> lists((size_t)(G));
+        auto &lists = t->lists;
+        if (lists.size() < size_t(G)) lists.resize(size_t(G));
 #pragma omp parallel
         {
-            std::vector<int32_t> stack;
-#pragma omp for schedule(dynamic, 1)
-            for (int32_t g = 0; g < G; g++) group_list(*t, g, theta, x, lists[size_t(g)], stack);
+            std::vector<int32_t> stack, nodes;
+#pragma omp for schedule(dynamic, 4)
+            for (int32_t g = 0; g < G; g++) group_list(*t, g, theta, x, lists[size_t(g)], stack, nodes);
         }
         t->off.assign(size_t(G) + 1, 0);
         for (int32_t g = 0; g < G; g++) t->off[size_t(g) + 1] = t->off[size_t(g)] + int64_t(lists[size_t(g)].size());
@@ -289,11 +306,42 @@ extern "C" int hh_tree_build(hh_tree **out, int64_t n, const double *x, const do
         for (int32_t g = 0; g < G; g++)
             std::copy(lists[size_t(g)].begin(), lists[size_t(g)].end(), t->idx.begin() + t->off[size_t(g)]);
     } catch (const std::bad_alloc &) {
-        delete t;
         return hh_set_global_error(HH_ENOMEM, "hh_tree_build: out of host memory");
+    }
+    return HH_OK;
+}
+
+}  // namespace
+
+extern "C" int hh_tree_build(hh_tree **out, int64_t n, const double *x, const double *v, const double *a,
+                             const double *jk, const double *m, int32_t leaf, int32_t n_crit, double theta)
+{
+    if (!out) return hh_set_global_error(HH_EINVAL, "hh_tree_build: out is NULL");
+    *out = nullptr;
+    int rc = check_inputs(n, x, v, a, jk, m, leaf, n_crit, theta);
+    if (rc) return rc;
+    hh_tree *t = new (std::nothrow) hh_tree;
+    if (!t) return hh_set_global_error(HH_ENOMEM, "hh_tree_build: out of host memory");
+    rc = build_into(t, n, x, v, a, jk, m, leaf, n_crit, theta);
+    if (rc) {
+        delete t;
+        return rc;
     }
     *out = t;
     return HH_OK;
+}
+
+// Internal: rebuild an existing tree object (or create one if *tp is NULL).
+int hh_tree_rebuild(hh_tree **tp, int64_t n, const double *x, const double *v, const double *a, const double *jk,
+                    const double *m, int32_t leaf, int32_t n_crit, double theta)
+{
+    int rc = check_inputs(n, x, v, a, jk, m, leaf, n_crit, theta);
+    if (rc) return rc;
+    if (!*tp) {
+        *tp = new (std::nothrow) hh_tree;
+        if (!*tp) return hh_set_global_error(HH_ENOMEM, "hh_tree_build: out of host memory");
+    }
+    return build_into(*tp, n, x, v, a, jk, m, leaf, n_crit, theta);
 }
 
 extern "C" int hh_tree_sizes(const hh_tree *t, int64_t *n_nodes, int32_t *n_groups, int64_t *list_len)
@@ -330,5 +378,26 @@ extern "C" int hh_tree_export(const hh_tree *t, int32_t *perm, double *node_x, d
 extern "C" int hh_tree_free(hh_tree *t)
 {
     delete t;
+    return HH_OK;
+}
+
+// Internal (not in hh.h): read-only view of a built tree for the library's
+// own rebuild path, which uploads straight from these arrays.
+int hh_tree_view(const hh_tree *t, HhTreeView *v)
+{
+    if (!t || !v) return HH_EINVAL;
+    v->n = t->n;
+    v->n_nodes = int64_t(t->cells.size());
+    v->n_groups = int32_t(t->g_cell.size());
+    v->list_len = int64_t(t->idx.size());
+    v->perm = t->perm.data();
+    v->cm = t->cm.data();
+    v->cx = t->cx.data();
+    v->cv = t->cv.data();
+    v->ca = t->ca.data();
+    v->cj = t->cj.data();
+    v->off = t->off.data();
+    v->idx = t->idx.data();
+    v->group_of = t->group_of.data();
     return HH_OK;
 }

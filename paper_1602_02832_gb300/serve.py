@@ -1,0 +1,234 @@
+"""Continuous-batching server of cluster simulations over libhh (scope row a8).
+
+Requests (independent N-body simulations with their own N, masses and end
+time) are admitted while their device memory fits a budget, stay resident on
+the GPU, and advance together: every iteration runs ONE persistent batched
+launch (hh_batch_run) that gives each resident simulation up to `max_steps`
+block steps, stopping each at its next tree rebuild time (Section 2: lists are
+rebuilt every dt_tree).  Simulations that reached a rebuild time are rebuilt on
+host threads while the next launch runs the others; finished ones release
+their memory and waiting requests take their place.  A simulation's result
+does not depend on what else shares the launches (see hh_batch_run).
+
+The loop itself is thin Python; every step of the path runs in libhh.
+"""
+from __future__ import annotations
+
+import math
+import time
+from concurrent.futures import ThreadPoolExecutor
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import HH_MIXED, Batch, Context, hh_config_default, hh_tree_build
+
+
+@dataclass
+class SimRequest:
+    rid: int
+    x: np.ndarray | None   # [n, 3] positions (any order); None: call make()
+    v: np.ndarray | None   # [n, 3]
+    m: np.ndarray | None   # [n]
+    t_end: float           # multiple of dt_tree
+    arrival_s: float = 0.0  # offset from the stream start
+    make: object = None    # optional callable returning (x, v, m), run at admission
+
+    def materialise(self):
+        if self.x is None:
+            self.x, self.v, self.m = self.make()
+        return self
+
+
+@dataclass
+class SimResult:
+    rid: int
+    n: int
+    x: np.ndarray  # [n, 3] final state in request order
+    v: np.ndarray
+    t_end: float
+    arrival_s: float
+    admit_s: float
+    done_s: float
+    block_steps: int
+    particle_steps: int
+    interactions: int
+
+
+@dataclass
+class _Live:
+    req: SimRequest
+    ctx: Context
+    bytes: int
+    t_stop: float          # next rebuild time (<= t_end)
+    admit_s: float
+    busy: bool = False     # being rebuilt on a host thread
+
+
+@dataclass
+class ServerStats:
+    step_us: list = field(default_factory=list)       # duration of each global block step
+    live_per_step: list = field(default_factory=list)  # simulations advanced in that launch
+    launches: int = 0
+    block_steps: int = 0          # sum over simulations of block steps
+    interactions: int = 0
+    wall_s: float = 0.0
+
+
+class Server:
+    """Continuous batching of block steps across resident simulations."""
+
+    def __init__(self, precision=HH_MIXED, budget_bytes=150 * 10 ** 9, max_sims=256, max_steps=64,
+                 eps2=1e-8, eta=0.02, theta=0.5, n_crit=64, dt_tree=2.0 ** -6, rebuild_threads=4, device=0):
+        self.precision = precision
+        self.budget = int(budget_bytes)
+        self.max_sims = int(max_sims)
+        self.max_steps = int(max_steps)
+        self.device = device
+        self.cfg = hh_config_default()
+        self.cfg.eps2, self.cfg.eta, self.cfg.theta, self.cfg.n_crit = eps2, eta, theta, n_crit
+        self.cfg.dt_max = dt_tree
+        self.cfg.dt_tree = dt_tree
+        self.cfg.precision = precision
+        self.batch = Batch(precision, max_sims=max_sims, max_steps=max_steps, device=device)
+        self.pool = ThreadPoolExecutor(max_workers=rebuild_threads)
+        self.stats = ServerStats()
+        self.used_bytes = 0
+
+    def close(self):
+        self.pool.shutdown(wait=True)
+        self.batch.close()
+
+    # -- admission ---------------------------------------------------------
+    def estimate_bytes(self, req: SimRequest) -> tuple[int, dict]:
+        """Device bytes a simulation needs, from a host build of its tree."""
+        n = len(req.m)
+        z = np.zeros((3, n))
+        T = hh_tree_build(req.x.T, req.v.T, z, z, req.m, leaf=8, n_crit=self.cfg.n_crit, theta=self.cfg.theta)
+        caps = dict(n_max=n, nj_max=n + 2 * T.n_nodes + 64, list_max=int(1.5 * len(T.idx)) + 4096,
+                    groups_max=2 * T.n_groups + 64)
+        nj, L, G = caps["nj_max"], caps["list_max"], caps["groups_max"]
+        rec = 48 if self.precision == HH_MIXED else 64
+        est = (nj * (14 * 8 + rec) + n * (8 * 8 + 4 * 3 + 7 * 8) + L * 4 + G * 8
+               + (n // 32 + G) * (16 + 4 + 16 + 32 * 56) * 2)
+        return int(est), caps
+
+    def _admit(self, req: SimRequest, caps: dict, now_s: float) -> _Live:
+        ctx = Context(self.cfg, device=self.device, **caps)
+        ctx.hh_load_particles(np.ascontiguousarray(req.x.T), np.ascontiguousarray(req.v.T), req.m)
+        ctx.hh_run(0.0, 0.0)  # tree, initial forces, node derivatives, initial steps
+        return _Live(req, ctx, ctx.device_bytes, min(self.cfg.dt_tree, req.t_end), now_s)
+
+    def _finish(self, s: _Live, now_s: float) -> SimResult:
+        st = s.ctx.hh_get_state()
+        ids = s.ctx.hh_get_ids()
+        c = s.ctx.hh_get_counters()
+        n = len(s.req.m)
+        x = np.zeros((n, 3))
+        v = np.zeros((n, 3))
+        x[ids] = st["x"].T
+        v[ids] = st["v"].T
+        s.ctx.close()
+        return SimResult(s.req.rid, n, x, v, s.req.t_end, s.req.arrival_s, s.admit_s, now_s, c["block_steps"],
+                         c["particle_steps"], c["interactions"])
+
+    # -- main loop ---------------------------------------------------------
+    def run(self, requests: list[SimRequest], realtime: bool = True, max_wall_s: float = math.inf):
+        """Serves the requests (sorted by arrival); returns (results, stats).
+        With realtime, a request becomes visible at its arrival offset.
+        Preparation (initial conditions, tree-based memory estimate) and
+        admission (context, initial forces) run on the worker threads, so
+        the batched launches keep running meanwhile."""
+        pending = sorted(requests, key=lambda r: r.arrival_s)
+        preparing = []                                   # futures -> (req, est, caps)
+        waiting: list[tuple[SimRequest, int, dict]] = []  # prepared, in arrival order
+        admitting = []                                   # (future -> _Live, reserved bytes)
+        live: list[_Live] = []
+        results: list[SimResult] = []
+        rebuilding = {}
+        t0 = time.perf_counter()
+
+        def prepare(r):
+            r.materialise()
+            est, caps = self.estimate_bytes(r)
+            return r, est, caps
+
+        def admit(r, caps):
+            return self._admit(r, caps, time.perf_counter() - t0)
+
+        def rebuild(s: _Live):
+            s.ctx.hh_rebuild(s.t_stop)
+            s.t_stop = min(s.t_stop + self.cfg.dt_tree, s.req.t_end)
+
+        while pending or preparing or waiting or admitting or live:
+            now = time.perf_counter() - t0
+            if now > max_wall_s:
+                break
+            while pending and (not realtime or pending[0].arrival_s <= now):
+                preparing.append(self.pool.submit(prepare, pending.pop(0)))
+            # prepared requests join the queue in arrival order
+            while preparing and preparing[0].done():
+                waiting.append(preparing.pop(0).result())
+            # admit in arrival order while memory and slots allow (bytes reserved now)
+            while (waiting and len(live) + len(admitting) < self.max_sims
+                   and self.used_bytes + waiting[0][1] <= self.budget):
+                r, est, caps = waiting.pop(0)
+                self.used_bytes += est
+                admitting.append((self.pool.submit(admit, r, caps), est))
+            if waiting and not live and not admitting and self.used_bytes == 0:
+                raise MemoryError(f"request {waiting[0][0].rid} needs {waiting[0][1]} bytes, above the budget")
+            for f, est in [x for x in admitting if x[0].done()]:
+                admitting.remove((f, est))
+                s = f.result()
+                self.used_bytes += s.bytes - est
+                live.append(s)
+            for s in [s for s in live if s.busy and rebuilding[id(s)].done()]:
+                rebuilding.pop(id(s)).result()
+                s.busy = False
+            runnable = [s for s in live if not s.busy]
+            if not runnable:
+                busy = [f for f in list(rebuilding.values()) + [x[0] for x in admitting] + preparing]
+                if busy:
+                    busy[0].result()
+                elif pending and realtime:
+                    time.sleep(max(0.0, min(0.01, pending[0].arrival_s - (time.perf_counter() - t0))))
+                continue
+            steps, tn, us = self.batch.hh_batch_run([s.ctx for s in runnable], [s.t_stop for s in runnable],
+                                                    max_steps=self.max_steps)
+            self.stats.launches += 1
+            self.stats.step_us.extend(us.tolist())
+            self.stats.live_per_step.extend([len(runnable)] * len(us))
+            for s, t_next in zip(runnable, tn):
+                if t_next <= s.t_stop:
+                    continue  # still inside its interval
+                if s.t_stop >= s.req.t_end:
+                    self.used_bytes -= s.bytes
+                    live.remove(s)
+                    res = self._finish(s, time.perf_counter() - t0)
+                    self.stats.block_steps += res.block_steps
+                    self.stats.interactions += res.interactions
+                    results.append(res)
+                else:
+                    s.busy = True
+                    rebuilding[id(s)] = self.pool.submit(rebuild, s)
+        for f in list(rebuilding.values()) + preparing:
+            f.result()
+        for f, est in admitting:
+            s = f.result()
+            s.ctx.close()
+            self.used_bytes -= est
+        for s in live:  # stopped by max_wall_s
+            c = s.ctx.hh_get_counters()
+            self.stats.block_steps += c["block_steps"]
+            self.stats.interactions += c["interactions"]
+            self.used_bytes -= s.bytes
+            s.ctx.close()
+        self.stats.wall_s = time.perf_counter() - t0
+        return results, self.stats
+
+
+def latency_summary(step_us) -> dict:
+    if not len(step_us):
+        return {"p50": None, "p99": None, "n": 0}
+    u = np.asarray(step_us, dtype=np.float64)
+    return {"p50": float(np.quantile(u, 0.5)), "p99": float(np.quantile(u, 0.99)), "n": int(u.size)}

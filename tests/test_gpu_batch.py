@@ -1,0 +1,114 @@
+"""Batched persistent block steps (hh_batch_run) against single-simulation runs.
+
+Every simulation of a batch must give the same state as when it runs alone
+through hh_advance (same tiles, active masks and list parts; fixed-order
+sums), whatever else shares the launch and however the run is cut into
+launches.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hh():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1602_02832_gb300 as hh
+    return hh
+
+
+def _ctx(hh, prec, n, seed, theta, n_crit=32, salpeter=False):
+    x, v, m = (synth.plummer_salpeter if salpeter else synth.plummer)(n, seed)
+    c = hh.hh_config_default()
+    c.eps2 = 1e-6
+    c.precision = prec
+    c.theta = theta
+    c.n_crit = n_crit
+    ctx = hh.Context(c, n, 2 * n, 64 * n * max(1, n // 16), n)
+    ctx.hh_load_particles(x.T, v.T, m)
+    ctx.hh_run(0.0, 0.0)
+    return ctx
+
+
+SPECS = [(600, 1, 0.5, False), (1500, 2, 0.3, True), (300, 3, 0.7, False), (1024, 4, 0.5, True)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_equals_alone(hh, prec):
+    P = hh.HH_FP64 if prec == "fp64" else hh.HH_MIXED
+    t1 = 2.0 ** -6
+    alone = []
+    for n, seed, th, sal in SPECS:
+        with _ctx(hh, P, n, seed, th, salpeter=sal) as c:
+            c.hh_advance(t1)
+            alone.append((c.hh_get_state(), c.hh_get_counters()))
+    ctxs = [_ctx(hh, P, n, seed, th, salpeter=sal) for n, seed, th, sal in SPECS]
+    with hh.Batch(P, max_sims=8, max_steps=4096) as b:
+        steps, tn, us = b.hh_batch_run(ctxs, [t1] * len(ctxs))
+    assert np.all(tn > t1) and steps > 0 and len(us) == steps and np.all(us > 0)
+    for c, (st, cnt) in zip(ctxs, alone):
+        got = c.hh_get_state()
+        gc = c.hh_get_counters()
+        for k in ("x", "v", "a", "jk", "t", "dt"):
+            assert np.array_equal(got[k], st[k]), k
+        assert gc["block_steps"] == cnt["block_steps"]
+        assert gc["particle_steps"] == cnt["particle_steps"]
+        assert gc["interactions"] == cnt["interactions"]
+        c.close()
+    assert steps == max(c[1]["block_steps"] for c in alone)
+
+
+def test_batch_in_short_launches_and_with_rebuilds(hh):
+    # continuous batching: the same simulations advanced in launches of 7
+    # global steps, rebuilt at each dt_tree, reach the same state as one
+    # simulation advanced alone with hh_advance + hh_rebuild
+    P = hh.HH_MIXED
+    dtt = 2.0 ** -6
+    ref = []
+    for n, seed, th, sal in SPECS[:3]:
+        with _ctx(hh, P, n, seed, th, salpeter=sal) as c:
+            for k in range(2):
+                c.hh_advance((k + 1) * dtt)
+                c.hh_rebuild((k + 1) * dtt)
+            ref.append(c.hh_get_state())
+    ctxs = [_ctx(hh, P, n, seed, th, salpeter=sal) for n, seed, th, sal in SPECS[:3]]
+    t_stop = np.full(3, dtt)
+    with hh.Batch(P, max_sims=4, max_steps=64) as b:
+        done = np.zeros(3, bool)
+        rounds = 0
+        while not done.all():
+            live = [i for i in range(3) if not done[i]]
+            steps, tn, _ = b.hh_batch_run([ctxs[i] for i in live], t_stop[live], max_steps=7)
+            for i, t in zip(live, tn):
+                if t > t_stop[i]:
+                    ctxs[i].hh_rebuild(t_stop[i])
+                    if t_stop[i] >= 2 * dtt:
+                        done[i] = True
+                    t_stop[i] += dtt
+            rounds += 1
+            assert rounds < 10000
+    for c, st in zip(ctxs, ref):
+        got = c.hh_get_state()
+        for k in ("x", "v", "t", "dt"):
+            assert np.array_equal(got[k], st[k]), k
+        c.close()
+
+
+def test_batch_rejects_bad_requests(hh):
+    with hh.Batch(hh.HH_FP64, max_sims=2, max_steps=16) as b:
+        c1 = _ctx(hh, hh.HH_FP64, 200, 5, 0.5)
+        c2 = _ctx(hh, hh.HH_MIXED, 200, 6, 0.5)
+        with pytest.raises(hh.HHError):
+            b.hh_batch_run([c1, c2], [0.01, 0.01])  # precision mismatch
+        with pytest.raises(hh.HHError):
+            b.hh_batch_run([c1, c1], [0.01, 0.01])  # same context twice
+        with pytest.raises(hh.HHError):
+            b.hh_batch_run([c1], [0.01], max_steps=17)  # above the batch's step capacity
+        steps, tn, _ = b.hh_batch_run([c1], [0.01], max_steps=16)
+        assert 0 < steps <= 16
+        c1.close()
+        c2.close()

@@ -1,0 +1,112 @@
+"""Host logic of the continuous-batching server, with fake GPU objects (no GPU).
+
+The fakes stand in for libhh's Context and Batch: each fake simulation needs a
+fixed number of block steps per tree interval.  The checks: admission never
+exceeds the memory budget, requests are admitted in arrival order as memory
+frees up, every request finishes exactly once at its end time, and batches
+mix simulations of different sizes.
+"""
+import numpy as np
+import pytest
+
+try:
+    import paper_1602_02832_gb300 as hh
+    from paper_1602_02832_gb300 import serve
+except ImportError:  # libhh not built in this checkout
+    hh = serve = None
+
+pytestmark = pytest.mark.skipif(serve is None, reason="libhh.so not built")
+
+
+class FakeCtx:
+    live = 0
+    peak = 0
+
+    def __init__(self, cfg, n_max=1, nj_max=1, list_max=1, groups_max=1, device=0):
+        self.n = n_max
+        self.device_bytes = 1000 * n_max
+        self.t = 0.0
+        self.steps_per_interval = 3 + n_max % 5
+        self.done_steps = 0
+        self.rebuilds = 0
+        FakeCtx.live += 1
+        FakeCtx.peak = max(FakeCtx.peak, FakeCtx.live)
+
+    def hh_load_particles(self, x, v, m):
+        self.x = x.copy()
+
+    def hh_run(self, t0, t1):
+        self.t = t0
+
+    def hh_rebuild(self, t):
+        assert abs(t - self.t) < 1e-15
+        self.rebuilds += 1
+
+    def hh_get_state(self):
+        return {"x": self.x, "v": self.x * 0}
+
+    def hh_get_ids(self):
+        return np.arange(self.n)
+
+    def hh_get_counters(self):
+        return {"block_steps": self.done_steps, "particle_steps": self.done_steps * self.n, "interactions": 7}
+
+    def close(self):
+        FakeCtx.live -= 1
+
+
+class FakeBatch:
+    def __init__(self, precision, max_sims, max_steps, device=0):
+        self.calls = []
+
+    def hh_batch_run(self, ctxs, t_stop, max_steps=None):
+        self.calls.append(len(ctxs))
+        tn = []
+        for c, ts in zip(ctxs, t_stop):
+            k = 0
+            while k < max_steps and c.t < ts:
+                c.done_steps += 1
+                k += 1
+                if c.done_steps % c.steps_per_interval == 0:
+                    c.t = ts
+            tn.append(ts + 1.0 / 128 if c.t >= ts else c.t + 1e-3)
+        return max_steps, np.array(tn), np.ones(max_steps)
+
+    def close(self):
+        pass
+
+
+def test_server_budget_order_and_completion(monkeypatch):
+    monkeypatch.setattr(serve, "Context", FakeCtx)
+    monkeypatch.setattr(serve, "Batch", FakeBatch)
+    monkeypatch.setattr(serve.Server, "estimate_bytes",
+                        lambda self, r: (1000 * len(r.m), dict(n_max=len(r.m), nj_max=1, list_max=1, groups_max=1)))
+    FakeCtx.live = FakeCtx.peak = 0
+    sizes = [100, 700, 300, 900, 200, 500, 800, 400]
+    reqs = [serve.SimRequest(i, np.zeros((n, 3)) + i, np.zeros((n, 3)), np.ones(n) / n,
+                             t_end=(1 + i % 3) / 64, arrival_s=0.0) for i, n in enumerate(sizes)]
+    srv = serve.Server(budget_bytes=1000 * 1500, max_sims=8, max_steps=2, rebuild_threads=2)
+    res, stats = srv.run(reqs, realtime=False)
+    srv.close()
+    assert sorted(r.rid for r in res) == list(range(len(sizes)))
+    for r in res:
+        assert np.all(r.x == r.rid)  # each result belongs to its own request
+        assert r.t_end == (1 + r.rid % 3) / 64
+    assert FakeCtx.live == 0
+    assert srv.used_bytes == 0
+    # never more resident than the budget allows (1500 units, sizes as above)
+    assert FakeCtx.peak <= 4
+    assert max(srv.batch.calls) >= 2  # simulations were batched together
+    assert stats.launches == len(srv.batch.calls)
+
+
+def test_server_rejects_a_request_above_the_budget(monkeypatch):
+    monkeypatch.setattr(serve, "Context", FakeCtx)
+    monkeypatch.setattr(serve, "Batch", FakeBatch)
+    monkeypatch.setattr(serve.Server, "estimate_bytes",
+                        lambda self, r: (1000 * len(r.m), dict(n_max=len(r.m), nj_max=1, list_max=1, groups_max=1)))
+    srv = serve.Server(budget_bytes=1000 * 10, max_sims=4, max_steps=2)
+    req = serve.SimRequest(0, np.zeros((50, 3)), np.zeros((50, 3)), np.ones(50) / 50, t_end=1 / 64)
+    with pytest.raises(MemoryError):
+        srv.run([req], realtime=False)
+    srv.close()
