@@ -51,12 +51,17 @@ def _args():
     p.add_argument("--n", type=int, default=65536)
     p.add_argument("--n-crit", type=int, default=64)
     p.add_argument("--theta", type=float, default=0.5)
+    p.add_argument("--tile-j", type=int, default=0, help="list part length of the plain FP64 form (0: tuned default)")
+    p.add_argument("--tile-j-mixed", type=int, default=0, help="list part length of the mixed form (0: tuned default)")
+    p.add_argument("--work-item", type=int, default=0, help="interactions per work item, plain form (0: default)")
+    p.add_argument("--work-item-mixed", type=int, default=0, help="interactions per work item, mixed form (0: default)")
     p.add_argument("--no-mixed", action="store_true")
     p.add_argument("--mixed-only", action="store_true", help="run only the mixed form (profiling aid)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--ensemble", type=int, default=256, help="clusters in the batched-ensemble measurement (0: skip)")
     p.add_argument("--ensemble-intervals", type=int, default=2)
     p.add_argument("--serve-seconds", type=float, default=20.0, help="wall time of the serving measurement (0: skip)")
+    p.add_argument("--no-autotune", action="store_true", help="skip the tile-shape autotuner (use the defaults)")
     p.add_argument("--loop", default="persistent", choices=["persistent", "graph"],
                    help="block-step loop: one persistent cooperative kernel per interval, or CUDA-graph replays")
     return p.parse_args()
@@ -81,6 +86,8 @@ def _cfg(hh, prec, a):
     c.leaf = 8
     c.n_crit = a.n_crit
     c.precision = prec
+    c.tile_j = (a.tile_j if prec == hh.HH_FP64 else a.tile_j_mixed) or 0
+    c.work_item = (a.work_item if prec == hh.HH_FP64 else a.work_item_mixed) or 0
     return c
 
 
@@ -209,12 +216,26 @@ class _Loop:
             self.batch.close()
 
 
-def _run_form(hh, torch, a, prec, seed, steps, warmup, flush, e2e_steps=0):
+def _tuned(hh, a, prec, seed):
+    """Tile shape for this workload from the autotuner (outside the timed region)."""
+    if a.no_autotune or a.tile_j or a.tile_j_mixed:
+        return {}, None
+    import synth
+    from paper_1602_02832_gb300 import autotune
+
+    x, v, m = synth.plummer(a.n, seed)
+    best, table = autotune.tune(x, v, m, _cfg(hh, prec, a), intervals=1, warm=1)
+    return best, [{"config": c, "interactions_per_s": r} for c, r in table]
+
+
+def _run_form(hh, torch, a, prec, seed, steps, warmup, flush, e2e_steps=0, over=None):
     import numpy as np
     import synth
 
     x, v, m = synth.plummer(a.n, seed)
     cfg = _cfg(hh, prec, a)
+    for k, val in (over or {}).items():
+        setattr(cfg, k, val)
     z = np.zeros((3, a.n))
     T0 = hh.hh_tree_build(x.T, v.T, z, z, m, leaf=8, n_crit=a.n_crit, theta=a.theta)
     nj_max = 2 * a.n
@@ -460,17 +481,19 @@ def main():
             print(json.dumps({"form": "mixed", "value": r["interactions"] / (r["ms"] * 1e-3), "ms": r["ms"],
                               "force_ms": r["force_ms"]}), flush=True)
         return 0
+    best64, table64 = _tuned(hh, a, hh.HH_FP64, rank)
+    bestmx, tablemx = _tuned(hh, a, hh.HH_MIXED, rank) if not a.no_mixed else ({}, None)
     with Clocks(local) as clk:
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        res = _run_form(hh, torch, a, hh.HH_FP64, rank, a.steps, a.warmup, flush, e2e_steps=a.steps)
+        res = _run_form(hh, torch, a, hh.HH_FP64, rank, a.steps, a.warmup, flush, e2e_steps=a.steps, over=best64)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
     mixed = None
     if not a.no_mixed:
-        mixed = _run_form(hh, torch, a, hh.HH_MIXED, rank, a.steps, a.warmup, flush)
+        mixed = _run_form(hh, torch, a, hh.HH_MIXED, rank, a.steps, a.warmup, flush, over=bestmx)
     tot = torch.tensor([res["interactions"], res["block_steps"], res["particle_steps"], res["gpu_launches"],
                         res["e2e"]["interactions"]], dtype=torch.float64, device="cuda")
     mx = torch.tensor([res["ms"], res["e2e"]["ms"]], dtype=torch.float64, device="cuda")
@@ -505,6 +528,9 @@ def main():
                     "h2d_bytes_per_step": res["e2e"]["bi"], "d2h_bytes_per_step": res["e2e"]["bo"]},
             "gpu_launches": int(tot[3]),
             "loop": a.loop,
+            "tuning": {"fp64": {"chosen": best64, "candidates": table64},
+                       "mixed": {"chosen": bestmx, "candidates": tablemx},
+                       "note": "autotuner runs before the timed region (paper_1602_02832_gb300/autotune.py)"},
             "time_split_ms_per_step": _split(res, a.steps),
             "block_step_latency_us": _lat(res["step_us"]),
             "force_kernel_share": res["force_ms"] / res["ms"],

@@ -69,8 +69,11 @@ typedef struct hh_config {
     int32_t n_crit; /* max particles per group for hh_rebuild (Section 2) */
     int32_t precision; /* HH_FP64 or HH_MIXED */
     int32_t tile_i;    /* particles per static i tile, 1..32; 0 = 32 */
-    int32_t tile_j;    /* list entries per work item (part of a list), multiple of 256; 0 = 512 */
-    int32_t reserved;
+    int32_t tile_j;    /* shortest list part per work item: a multiple of 128 (HH_FP64) or 256
+                          (HH_MIXED); 0 = 256 (HH_FP64), 512 (HH_MIXED) */
+    int32_t work_item; /* 0 (default): every list part is tile_j entries long.  > 0: a tile with
+                          n_a active particles takes parts of about work_item / n_a entries (at
+                          least tile_j), so that work items cost about the same */
 } hh_config;
 
 typedef struct hh_counters {
@@ -82,7 +85,7 @@ typedef struct hh_counters {
 
 /* Fills cfg with defaults: eps2 = 1e-8, eta = 0.02, eta_s = 0.01,
  * dt in [2^-30, 2^-6], dt_tree = 2^-6, theta = 0.5, leaf = 8, n_crit = 64,
- * HH_FP64, default tiles. */
+ * HH_FP64, default tiles and work items. */
 void hh_config_default(hh_config *cfg);
 
 /* Creates a context on CUDA device `device` with room for n_max particles,
@@ -217,7 +220,12 @@ const char *hh_last_error(const hh_ctx *ctx);
  *   each simulation's next block time (> t_end[s] when it reached t_end[s]);
  *   step_us_out[max_steps], the duration of each global step in
  *   microseconds (device timer); phase_us_out[3 max_steps], per step the
- *   durations of the predict/select, force and correct phases.  Synchronises.  Grid barriers give up after
+ *   durations of the predict/select, force and correct phases.  Synchronises.
+ *   Every particle must follow the block rule (dt a power of two in
+ *   [2^-31, 1], t a multiple of dt, t + dt after the latest t), as states
+ *   made by hh_init_dt, hh_step, hh_advance and hh_rebuild do; otherwise
+ *   HH_EINVAL.  The loop keeps a per-simulation histogram of step levels
+ *   and per-tile level masks, so a block step touches only the due tiles.  Grid barriers give up after
  *   about a second and return HH_ETIMEOUT. */
 typedef struct hh_batch hh_batch;
 int hh_batch_create(hh_batch **out, int device, int precision, int32_t max_sims, int32_t max_steps);

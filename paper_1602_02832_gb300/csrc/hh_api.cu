@@ -89,12 +89,14 @@ bool is_pow2(double x)
     return std::frexp(x, &e) == 0.5;
 }
 
-__global__ void k_set_sizes(DevScalars *ds, int64_t n, int64_t nj, int32_t n_tiles, int32_t part_len)
+__global__ void k_set_sizes(DevScalars *ds, int64_t n, int64_t nj, int32_t n_tiles, int32_t part_len,
+                            int32_t work_item)
 {
     ds->n = n;
     ds->nj = nj;
     ds->n_tiles = n_tiles;
     ds->part_len = part_len;
+    ds->work_item = work_item;
 }
 
 __global__ void k_begin_loop(DevScalars *ds, double t_end)
@@ -102,6 +104,7 @@ __global__ void k_begin_loop(DevScalars *ds, double t_end)
     ds->t_end = t_end;
     ds->done = 0;
     ds->n_items = 0u;
+    ds->slot_ctr = 0u;
     ds->work = 0u;
     ds->tmin[0] = 0x7FF0000000000000ull;
     ds->tmin[1] = 0x7FF0000000000000ull;
@@ -142,6 +145,7 @@ int launch_correct(hh_ctx *ctx, StepCtl c)
 int launch_select(hh_ctx *ctx, StepCtl c)
 {
     CK(cudaMemsetAsync(&ctx->ds->work, 0, 2 * sizeof(uint32_t), ctx->stream));  // work, n_items
+    CK(cudaMemsetAsync(&ctx->ds->slot_ctr, 0, sizeof(uint32_t), ctx->stream));
     k_select<<<ctx->elem_grid, 256, 0, ctx->stream>>>(ctx->st, lists_of(ctx), ctx->ds, c);
     CKL();
     return HH_OK;
@@ -357,7 +361,8 @@ int hh_destroy(hh_ctx *ctx)
     if (ctx->e1) cudaEventDestroy(ctx->e1);
     void *dev[] = {ctx->st.x, ctx->st.v, ctx->st.a, ctx->st.jk, ctx->st.m, ctx->st.t, ctx->st.dt, ctx->st.acc1,
                    ctx->st.jerk1, ctx->st.pot1, ctx->st.mark, ctx->rec, ctx->off, ctx->idx, ctx->group_of,
-                   ctx->tiles, ctx->ds, ctx->i_buf, ctx->out_buf, ctx->items, ctx->partials, ctx->tile_cnt};
+                   ctx->tiles, ctx->ds, ctx->i_buf, ctx->out_buf, ctx->items, ctx->partials, ctx->tile_cnt,
+                   ctx->tile_lv};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (ctx->h_ds) cudaFreeHost(ctx->h_ds);
@@ -388,9 +393,12 @@ int hh_create(hh_ctx **out, int device, const hh_config *cfg, int64_t n_max, int
                                               "dt_min <= dt_max <= dt_tree, eps2 >= 0, eta > 0)");
     if (c.tile_i == 0) c.tile_i = 32;
     if (c.tile_i < 1 || c.tile_i > kMaxTileI) return hh_set_global_error(HH_EINVAL, "hh_create: tile_i must be 1..32");
-    if (c.tile_j == 0) c.tile_j = 512;
-    if (c.tile_j < 256 || c.tile_j % 256 != 0 || c.tile_j > (1 << 20))
-        return hh_set_global_error(HH_EINVAL, "hh_create: tile_j (list part length) must be a multiple of 256");
+    const int chunk = c.precision == HH_MIXED ? kTjMix : kTjF64;
+    if (c.tile_j == 0) c.tile_j = c.precision == HH_MIXED ? 512 : 256;
+    if (c.work_item < 0) c.work_item = 0;
+    if (c.tile_j < chunk || c.tile_j % chunk != 0 || c.tile_j > (1 << 20))
+        return hh_set_global_error(HH_EINVAL, "hh_create: tile_j (list part length) must be a multiple of 128 "
+                                              "(HH_FP64) or 256 (HH_MIXED)");
     hh_ctx *ctx = new (std::nothrow) hh_ctx;
     if (!ctx) return hh_set_global_error(HH_ENOMEM, "hh_create: out of host memory");
     ctx->device = device;
@@ -439,6 +447,7 @@ int hh_create(hh_ctx **out, int device, const hh_config *cfg, int64_t n_max, int
         {(void **)&ctx->ds, sizeof(DevScalars)},                 {(void **)&ctx->i_buf, sizeof(int32_t) * n_max},
         {(void **)&ctx->out_buf, sizeof(double) * 7 * n_max},
         {(void **)&ctx->tile_cnt, sizeof(int32_t) * ctx->cap_tiles},
+        {(void **)&ctx->tile_lv, sizeof(uint32_t) * ctx->cap_tiles},
         {(void **)&ctx->items, sizeof(int4) * ctx->cap_parts},
         {(void **)&ctx->partials, sizeof(RedF64) * kMaxTileI * ctx->cap_parts},
     };
@@ -579,7 +588,8 @@ int set_lists_core(hh_ctx *ctx, int64_t n_particles, int64_t n_j, int32_t n_grou
     if (L) CK(cudaMemcpyAsync(ctx->idx, idx, sizeof(int32_t) * L, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->group_of, group_of, sizeof(int32_t) * n_particles, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, ctx->stream));
-    k_set_sizes<<<1, 1, 0, ctx->stream>>>(ctx->ds, n_particles, n_j, int32_t(tiles.size()), ctx->part_len);
+    k_set_sizes<<<1, 1, 0, ctx->stream>>>(ctx->ds, n_particles, n_j, int32_t(tiles.size()), ctx->part_len,
+                                           ctx->cfg.work_item);
     CKL();
     CK(cudaStreamSynchronize(ctx->stream));  // host arrays may be freed after return
     ctx->n = n_particles;

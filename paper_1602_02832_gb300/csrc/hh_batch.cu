@@ -36,14 +36,16 @@ namespace {
 constexpr long long kSpinLimit = 1ll << 25;  // ~ seconds of __nanosleep(64) polling
 constexpr int kGroups = 4;                   // 128-thread worker groups per CTA (one CTA per SM)
 constexpr int kBlock = kThreads * kGroups;
+constexpr int kSimCache = 256;               // simulations whose step data a CTA keeps in shared memory
 
 struct SimDesc {
     State st;
     const void *rec;
     Lists L;
+    uint32_t *tile_lv;  // levels present in each tile
     DevScalars *ds;
     int64_t n, nj;
-    int32_t n_tiles, pj;
+    int32_t n_tiles, pj, work;
     Params prm;
     double t_end;
 };
@@ -121,6 +123,71 @@ __device__ __forceinline__ int find_sim(const int64_t *base, int n_sims, int64_t
 __device__ __forceinline__ double sim_time(const SimDesc &sd, int par)
 {
     return __longlong_as_double((long long)__ldcg(&sd.ds->tmin[par]));
+}
+
+// Block-step levels: a step dt = 2^-k has level k.  Power-of-two steps that
+// start on multiples of themselves (the block rule) make every particle of
+// level k due at the same time, the first multiple of 2^-k after the latest
+// block time; at block time t the due particles are exactly those with
+// levels >= kmin(t), where 2^-kmin(t) is the largest power of two dividing t.
+__device__ __forceinline__ int level_of(double dt)
+{
+    return 1023 - (int)((__double_as_longlong(dt) >> 52) & 0x7ff);
+}
+
+__device__ __forceinline__ bool is_level_step(double dt)
+{
+    const long long b = __double_as_longlong(dt);
+    const int lv = 1023 - (int)((b >> 52) & 0x7ff);
+    return (b & ((1ll << 52) - 1)) == 0 && b > 0 && lv >= 0 && lv <= 31;
+}
+
+__device__ __forceinline__ double pow2i(int k)  // 2^k for |k| < 1000
+{
+    return __longlong_as_double((long long)(1023 + k) << 52);
+}
+
+__device__ __forceinline__ int kmin_of(double t)  // t > 0
+{
+    const long long b = __double_as_longlong(t);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    const long long mant = (b & ((1ll << 52) - 1)) | (1ll << 52);
+    const int z = __ffsll(mant) - 1;
+    const int k = 52 - z - e;
+    return k < 0 ? 0 : k;
+}
+
+// Earliest due time after block time t of the occupied levels below kmin(t)
+// (those particles are not corrected at t, so their due times stand).
+// Warp-collective: lane k looks at level k, all lanes return the minimum.
+__device__ __forceinline__ double due_below_warp(const int32_t *lvl_cnt, double t, int kmin)
+{
+    const int k = threadIdx.x & 31;
+    double m = __longlong_as_double(0x7FF0000000000000LL);
+    if (k < kmin && __ldcg(&lvl_cnt[k]) > 0) m = (floor(t * pow2i(k)) + 1.0) * pow2i(-k);
+    for (int off = 16; off > 0; off >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, off));
+    return m;
+}
+
+// Per-CTA copy of each simulation's block time for the current step
+// (read once per phase instead of once per element).
+struct StepCache {
+    double t[kSimCache];
+    double t_end[kSimCache];
+};
+
+__device__ __forceinline__ void cache_times(StepCache &c, const SimDesc *sims, int n_sims, int par)
+{
+    for (int s = threadIdx.x; s < n_sims && s < kSimCache; s += blockDim.x) {
+        c.t[s] = __longlong_as_double((long long)__ldcg(&sims[s].ds->tmin[par]));
+        c.t_end[s] = sims[s].t_end;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ double cached_time(const StepCache &c, const SimDesc *sims, int s, int par)
+{
+    return s < kSimCache ? c.t[s] : __longlong_as_double((long long)__ldcg(&sims[s].ds->tmin[par]));
 }
 
 // Running (simulation, min of t_i + dt_i, corrected count) of one thread;
@@ -204,6 +271,7 @@ template <typename Rec, int TJ>
 __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ StepCache sc;
     const int tid = threadIdx.x;
     const int group = tid / kThreads, gt = tid - group * kThreads;
     ForceSmem<Rec, TJ> &sm = reinterpret_cast<ForceSmem<Rec, TJ> *>(smem_raw)[group];
@@ -212,39 +280,95 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
     const int n_sims = B.n_sims;
     const int64_t NJ = B.jbase[n_sims], NP = B.pbase[n_sims], NT = B.tbase[n_sims];
 
-    // phase 0: every simulation's first block time
+    // phase 0: every simulation's first block time, latest time, level
+    // histogram and tile level masks; the block rule is checked here
     if (blockIdx.x == 0)
         for (int s = tid; s < n_sims; s += blockDim.x) {
-            B.sims[s].ds->tmin[0] = 0x7FF0000000000000ull;
-            B.sims[s].ds->tmin[1] = 0x7FF0000000000000ull;
+            DevScalars *ds = B.sims[s].ds;
+            ds->tmin[0] = 0x7FF0000000000000ull;
+            ds->tmin[1] = 0x7FF0000000000000ull;
+            ds->t_cur_bits = 0ull;
+            ds->slot_ctr = 0u;
+            for (int k = 0; k < 32; k++) ds->lvl_cnt[k] = 0;
         }
     if (blockIdx.x == 0 && tid == 0) B.step_ns[0] = globaltimer_ns();
     if (!grid_sync(B.bs)) return;
     {
         MinCnt acc{-1, 0.0, 0};
-        for (int64_t g = gtid; g < NP; g += nth) {
-            const int s = find_sim(B.pbase, n_sims, g);
-            const SimDesc &sd = B.sims[s];
-            const int64_t p = g - B.pbase[s];
-            mc_push(B.sims, acc, s, sd.st.t[p] + sd.st.dt[p], 0, 0);
+        const int lane = tid & 31;
+        for (int64_t g0 = gtid - lane; g0 < NP; g0 += nth) {  // warp-aligned so that lanes can aggregate
+            const int64_t g = g0 + lane;
+            const bool valid = g < NP;
+            int s = -1, lv = -1;
+            double t = 0.0, dt = 0.0;
+            if (valid) {
+                s = find_sim(B.pbase, n_sims, g);
+                const SimDesc &sd = B.sims[s];
+                const int64_t p = g - B.pbase[s];
+                t = sd.st.t[p];
+                dt = sd.st.dt[p];
+                if (!is_level_step(dt) || !(t >= 0.0)) {
+                    atomicExch(&B.bs->err, HH_EINVAL);
+                } else {
+                    lv = level_of(dt);
+                    const double u = t * pow2i(lv);
+                    if (u != floor(u)) atomicExch(&B.bs->err, HH_EINVAL);  // t_i not a multiple of dt_i
+                }
+                mc_push(B.sims, acc, s, t + dt, 0, 0);
+            }
+            // histogram and latest time: lanes of one simulation and level combine
+            const unsigned grp = __match_any_sync(0xffffffffu, valid ? s * 64 + (lv & 63) : -1);
+            const int leader = __ffs(grp) - 1;
+            double tmax = t;
+            for (unsigned m2 = grp; m2; m2 &= m2 - 1) tmax = fmax(tmax, __shfl_sync(grp, t, __ffs(m2) - 1));
+            if (valid && lane == leader && lv >= 0) {
+                DevScalars *ds = B.sims[s].ds;
+                atomicAdd(&ds->lvl_cnt[lv], __popc(grp));
+                atomicMax(&ds->t_cur_bits, (unsigned long long)__double_as_longlong(tmax));
+            }
         }
         mc_block_flush(B.sims, acc, 0);
+        const int64_t w0 = gtid >> 5, nw = nth >> 5;
+        for (int64_t wt = w0; wt < NT; wt += nw) {
+            const int s = find_sim(B.tbase, n_sims, wt);  // warp-uniform
+            const SimDesc &sd = B.sims[s];
+            const int tile = (int)(wt - B.tbase[s]);
+            const int4 td = sd.L.tiles[tile];
+            const int64_t p = td.x + lane;
+            const uint32_t bit = (p < td.y) ? (1u << (level_of(sd.st.dt[p]) & 31)) : 0u;
+            const uint32_t m = __reduce_or_sync(0xffffffffu, bit);
+            if (lane == 0) sd.tile_lv[tile] = m;
+        }
     }
     if (!grid_sync(B.bs)) return;
+    if (blockIdx.x == 0)
+        for (int s = tid; s < n_sims; s += blockDim.x) {
+            const DevScalars *ds = B.sims[s].ds;
+            const double tcur = __longlong_as_double((long long)__ldcg(&ds->t_cur_bits));
+            if (!(sim_time(B.sims[s], 0) > tcur)) atomicExch(&B.bs->err, HH_EINVAL);  // an overdue particle
+        }
 
     int step = 0;
     for (; step < B.max_steps; step++) {
         const int par = step & 1;
         // ---- phase 1: predict + select
+        cache_times(sc, B.sims, n_sims, par);
         if (blockIdx.x == 0)
-            for (int s = tid; s < n_sims; s += blockDim.x) {
-                B.sims[s].ds->tmin[par ^ 1] = 0x7FF0000000000000ull;
-                B.sims[s].ds->n_act_last = 0;
+            for (int s = tid >> 5; s < n_sims; s += blockDim.x >> 5) {
+                // the next block time starts from the due times of the levels
+                // not corrected now; phase 3 lowers it with the corrected ones
+                DevScalars *ds = B.sims[s].ds;
+                const double tnow = cached_time(sc, B.sims, s, par);
+                const double below = due_below_warp(ds->lvl_cnt, tnow, kmin_of(tnow));
+                if ((tid & 31) == 0) {
+                    ds->tmin[par ^ 1] = (unsigned long long)__double_as_longlong(below);
+                    ds->n_act_last = 0;
+                }
             }
         for (int64_t g = gtid; g < NJ; g += nth) {
             const int s = find_sim(B.jbase, n_sims, g);
             const SimDesc &sd = B.sims[s];
-            const double tnow = sim_time(sd, par);
+            const double tnow = cached_time(sc, B.sims, s, par);
             if (!(tnow <= sd.t_end)) continue;
             const int64_t e = g - B.jbase[s];
             double xp[3], vp[3];
@@ -257,14 +381,17 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
             for (int64_t wt = w0; wt < NT; wt += nw) {
                 const int s = find_sim(B.tbase, n_sims, wt);  // warp-uniform
                 const SimDesc &sd = B.sims[s];
-                const double tnow = sim_time(sd, par);
+                const double tnow = cached_time(sc, B.sims, s, par);
                 if (!(tnow <= sd.t_end)) continue;
                 const int tile = (int)(wt - B.tbase[s]);
+                if ((sd.tile_lv[tile] >> kmin_of(tnow)) == 0u) continue;  // no due level in this tile
                 const int4 td = sd.L.tiles[tile];
                 const int64_t p = td.x + lane;
                 const bool act = (p < td.y) && (sd.st.t[p] + sd.st.dt[p] == tnow);
                 const uint32_t mask = __ballot_sync(0xffffffffu, act);
-                if (mask) append_tile_items(sd.L, tile, td, mask, sd.pj, &B.bs->n_items, B.items, s);
+                if (mask)
+                    append_tile_items(sd.L, tile, td, mask, sd.pj, sd.work, &B.bs->n_items, &sd.ds->slot_ctr, B.items,
+                                      s);
             }
         }
         if (!grid_sync(B.bs)) return;
@@ -282,7 +409,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                 const int4 it = B.items[item];
                 const SimDesc &sd = B.sims[it.y >> 16];
                 unsigned long long n_int = 0;
-                force_item<Rec, TJ, false>(sd.st, (const Rec *)sd.rec, sd.L, sd.pj,
+                force_item<Rec, TJ, false>(sd.st, (const Rec *)sd.rec, sd.L, sd.pj, sd.work,
                                            (typename Traits<Rec>::Eps)sd.prm.eps2, it, sm, n_int, gt, bar);
                 if (gt == 0 && n_int) atomicAdd(&sd.ds->interactions, n_int);
                 group_sync(bar);
@@ -291,23 +418,45 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
         if (!grid_sync(B.bs)) return;
         if (blockIdx.x == 0 && tid == 0) B.step_ns[3 * step + 2] = globaltimer_ns();
 
-        // ---- phase 3: correct + next block times
+        // ---- phase 3: correct the due particles, tile by tile
         {
-            MinCnt acc{-1, 0.0, 0};
-            for (int64_t g = gtid; g < NP; g += nth) {
-                const int s = find_sim(B.pbase, n_sims, g);
+            // active tiles go round-robin over the CTAs (one SM each), so that
+            // the FP64 corrector work of neighbouring tiles lands on different SMs
+            const uint32_t n_items = __ldcg(&B.bs->n_items);
+            const int lane = tid & 31;
+            const int64_t w0 = blockIdx.x + (int64_t)gridDim.x * (tid >> 5), nw = nth >> 5;
+            for (int64_t wi = w0; wi < n_items; wi += nw) {
+                const int4 it = B.items[wi];
+                if ((it.y & 0xFFFF) != 0) continue;  // one item per active tile: its part 0
+                const int s = it.y >> 16;
                 const SimDesc &sd = B.sims[s];
-                const double tnow = sim_time(sd, par);
-                if (!(tnow <= sd.t_end)) continue;  // finished simulations keep their next time
-                const int64_t p = g - B.pbase[s];
-                int cnt = 0;
-                if (sd.st.t[p] + sd.st.dt[p] == tnow) {
+                const double tnow = cached_time(sc, B.sims, s, par);
+                const int4 td = sd.L.tiles[it.x];
+                const int64_t p = td.x + lane;
+                const bool act = ((uint32_t)it.z >> lane) & 1u;
+                double tn = __longlong_as_double(0x7FF0000000000000LL);
+                if (act) {
+                    const int lv_old = level_of(sd.st.dt[p]);
                     correct_particle(sd.st, p, tnow, sd.prm);
-                    cnt = 1;
+                    const double dtn = sd.st.dt[p];
+                    const int lv_new = level_of(dtn);
+                    tn = tnow + dtn;
+                    if (lv_new != lv_old) {
+                        atomicSub(&sd.ds->lvl_cnt[lv_old], 1);
+                        atomicAdd(&sd.ds->lvl_cnt[lv_new & 31], 1);
+                    }
                 }
-                mc_push(B.sims, acc, s, sd.st.t[p] + sd.st.dt[p], cnt, par ^ 1);
+                for (int off = 16; off > 0; off >>= 1) tn = fmin(tn, __shfl_xor_sync(0xffffffffu, tn, off));
+                const uint32_t bit = (p < td.y) ? (1u << (level_of(sd.st.dt[p]) & 31)) : 0u;
+                const uint32_t lvm = __reduce_or_sync(0xffffffffu, bit);
+                if (lane == 0) {
+                    const int c = __popc((uint32_t)it.z);
+                    sd.tile_lv[it.x] = lvm;
+                    atomicMin(&sd.ds->tmin[par ^ 1], (unsigned long long)__double_as_longlong(tn));
+                    atomicAdd(&sd.ds->particle_steps, (unsigned long long)c);
+                    atomicAdd(&sd.ds->n_act_last, c);
+                }
             }
-            mc_block_flush(B.sims, acc, par ^ 1);
         }
         if (blockIdx.x == 0) {
             if (tid == 0) {
@@ -316,7 +465,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
             }
             for (int s = tid; s < n_sims; s += blockDim.x) {
                 const SimDesc &sd = B.sims[s];
-                if (sim_time(sd, par) <= sd.t_end) {
+                sd.ds->slot_ctr = 0u;  // this step's forces are done
+                if (cached_time(sc, B.sims, s, par) <= sd.t_end) {
                     sd.ds->block_steps += 1ull;
                 } else {
                     sd.ds->tmin[par ^ 1] = sd.ds->tmin[par];  // carry a finished simulation's time
@@ -464,11 +614,13 @@ extern "C" int hh_batch_run(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const d
         d.L.partials = c->partials;
         d.L.tile_cnt = c->tile_cnt;
         d.L.i_map = nullptr;
+        d.tile_lv = c->tile_lv;
         d.ds = c->ds;
         d.n = c->n;
         d.nj = c->nj;
         d.n_tiles = c->n_tiles;
         d.pj = c->part_len;
+        d.work = c->cfg.work_item;
         d.prm.eps2 = c->cfg.eps2;
         d.prm.eta = c->cfg.eta;
         d.prm.eta_s = c->cfg.eta_s;
@@ -528,7 +680,10 @@ extern "C" int hh_batch_run(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const d
                         cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return bfail(b, HH_ECUDA, "hh_batch_run: kernel execution failed");
-    if (hbs.err) return bfail(b, hbs.err, "hh_batch_run: grid barrier timed out");
+    if (hbs.err == HH_ETIMEOUT) return bfail(b, hbs.err, "hh_batch_run: grid barrier timed out");
+    if (hbs.err)
+        return bfail(b, hbs.err, "hh_batch_run: block-step state breaks the block rule (a step that is not a power "
+                                 "of two in [2^-31, 1], a time not a multiple of its step, or an overdue particle)");
     for (int32_t s = 0; s < n; s++) {
         ctxs[s]->predicted = false;
         ctxs[s]->have_forces = true;

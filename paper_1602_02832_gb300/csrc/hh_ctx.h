@@ -34,6 +34,7 @@ struct hh_ctx {
     int4 *items = nullptr;      // [cap_parts]
     void *partials = nullptr;   // [cap_parts][32] partial sums (scratch)
     int32_t *tile_cnt = nullptr;  // [cap_tiles]
+    uint32_t *tile_lv = nullptr;  // [cap_tiles] levels present in each tile (batched loop)
     int64_t cap_parts = 0;
     int64_t total_parts = 0;    // work items of a step with every tile active
     int64_t device_bytes = 0;   // device memory allocated for this context

@@ -30,13 +30,18 @@ struct DevScalars {
     int32_t err;                 // device-detected error (HH_* code), 0 = none
     uint32_t work;               // force work-queue head
     uint32_t n_items;            // work items of this step
-    int32_t part_len;            // list entries per part (a multiple of the staging chunk)
+    int32_t part_len;            // shortest list part (a multiple of the staging chunk)
+    int32_t work_item;           // target interactions per work item (0: every part is part_len long)
+    uint32_t slot_ctr;           // partial-sum slots handed out this step
     int32_t n_act_last;          // active particles of the last corrected step
     int64_t n;                   // particles
     int64_t nj;                  // j entries
     int32_t n_tiles;             // static i tiles
     int32_t pad0;
     unsigned long long block_steps, particle_steps, interactions;
+    // block-step levels (level k <=> dt = 2^-k), kept by the batched loop
+    int32_t lvl_cnt[32];          // particles per level
+    unsigned long long t_cur_bits;  // latest block time (max t_i), positive-double bits
 };
 
 // Block-step control passed by value to every kernel of a step.
@@ -120,16 +125,36 @@ __device__ __forceinline__ double pow2_floor(double x)
 // any active particle appends one work item per part of its group's list.
 // Item order may vary between runs; results do not depend on it.
 // Warp-collective: appends one work item per part of tile `tile`'s list.
-__device__ __forceinline__ void append_tile_items(const Lists &L, int tile, const int4 td, uint32_t mask, int pj,
-                                                  uint32_t *n_items, int4 *items, int sim)
+// List entries per work item for a tile with n_a active particles: about
+// `work` interactions per item (n_a x part length), never shorter than
+// pj_min, a multiple of pj_min.  Items of equal cost keep the SMs evenly
+// loaded; the length depends only on n_a, so results stay deterministic.
+__device__ __forceinline__ int part_len_for(int n_a, int pj_min, int work)
+{
+    if (work <= 0) return pj_min;
+    const int want = (work + n_a - 1) / n_a;
+    const int k = (want + pj_min - 1) / pj_min;
+    return (k < 1 ? 1 : k) * pj_min;
+}
+
+__device__ __forceinline__ int parts_of(int64_t len, int pj) { return len > 0 ? (int)((len + pj - 1) / pj) : 1; }
+
+// Warp-collective: appends one work item per part of tile `tile`'s list;
+// item = (tile, part | sim << 16, active mask, first partial-sum slot).
+__device__ __forceinline__ void append_tile_items(const Lists &L, int tile, const int4 td, uint32_t mask, int pj_min,
+                                                  int work, uint32_t *n_items, uint32_t *slot_ctr, int4 *items, int sim)
 {
     const int lane = threadIdx.x & 31;
     const int64_t len = L.off[td.z + 1] - L.off[td.z];
-    const int n_parts = len > 0 ? (int)((len + pj - 1) / pj) : 1;
-    int base = 0;
-    if (lane == 0) base = (int)atomicAdd(n_items, (uint32_t)n_parts);
+    const int n_parts = parts_of(len, part_len_for(__popc(mask), pj_min, work));
+    int base = 0, slot = 0;
+    if (lane == 0) {
+        base = (int)atomicAdd(n_items, (uint32_t)n_parts);
+        slot = n_parts > 1 ? (int)atomicAdd(slot_ctr, (uint32_t)n_parts) : 0;
+    }
     base = __shfl_sync(0xffffffffu, base, 0);
-    for (int q = lane; q < n_parts; q += 32) items[base + q] = make_int4(tile, q | (sim << 16), (int)mask, n_parts);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    for (int q = lane; q < n_parts; q += 32) items[base + q] = make_int4(tile, q | (sim << 16), (int)mask, slot);
 }
 
 __device__ __forceinline__ void select_tiles(const State &s, const Lists &L, DevScalars *ds, const StepCtl &c,
@@ -139,14 +164,14 @@ __device__ __forceinline__ void select_tiles(const State &s, const Lists &L, Dev
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int n_tiles = ds->n_tiles;
-    const int pj = ds->part_len;
+    const int pj = ds->part_len, work = ds->work_item;
     for (int64_t tile = warp0; tile < n_tiles; tile += nwarps) {
         const int4 td = L.tiles[tile];
         const int64_t p = td.x + lane;
         const bool act = (p < td.y) && is_active(s, c, p, tnow);
         const uint32_t mask = __ballot_sync(0xffffffffu, act);
         if (mask == 0u) continue;
-        append_tile_items(L, (int)tile, td, mask, pj, &ds->n_items, L.items, 0);
+        append_tile_items(L, (int)tile, td, mask, pj, work, &ds->n_items, &ds->slot_ctr, L.items, 0);
     }
 }
 
@@ -485,18 +510,20 @@ __device__ __forceinline__ void group_sync(int bar_id)
 // item = (tile, part | sim << 16, active mask, parts of the tile); tid is
 // the thread's index in its 128-thread group.
 template <typename Rec, int TJ, bool kMapI>
-__device__ __forceinline__ void force_item(const State &s, const Rec *__restrict__ rec, const Lists &L, int pj,
-                                           typename Traits<Rec>::Eps eps2, const int4 it, ForceSmem<Rec, TJ> &sm,
-                                           unsigned long long &n_int, const int tid, const int bar_id)
+__device__ __forceinline__ void force_item(const State &s, const Rec *__restrict__ rec, const Lists &L, int pj_min,
+                                           int work, typename Traits<Rec>::Eps eps2, const int4 it,
+                                           ForceSmem<Rec, TJ> &sm, unsigned long long &n_int, const int tid,
+                                           const int bar_id)
 {
     using T = Traits<Rec>;
     using Red = typename T::Red;
     const int lane = tid & 31, warp = tid >> 5;
     Red *partials = reinterpret_cast<Red *>(L.partials);
     const int4 td = L.tiles[it.x];
-    const int part = it.y & 0xFFFF, n_parts = it.w;
     const uint32_t mask = (uint32_t)it.z;
     const int n_a = __popc(mask);
+    const int pj = part_len_for(n_a, pj_min, work);
+    const int part = it.y & 0xFFFF, slot0 = it.w;
 
     int I = 1;
     while (I < n_a) I <<= 1;
@@ -522,6 +549,7 @@ __device__ __forceinline__ void force_item(const State &s, const Rec *__restrict
     A.zero();
 
     const int64_t gb = L.off[td.z], ge = L.off[td.z + 1];
+    const int n_parts = parts_of(ge - gb, pj);
     const int64_t lb = gb + (int64_t)part * pj;
     const int64_t le = min(ge, lb + (int64_t)pj);
     const int64_t len = le - lb;
@@ -562,7 +590,7 @@ __device__ __forceinline__ void force_item(const State &s, const Rec *__restrict
     }
     bool write_out = n_parts == 1;
     if (n_parts > 1) {
-        Red *mine = partials + ((int64_t)td.w + part) * kMaxTileI;
+        Red *mine = partials + ((int64_t)slot0 + part) * kMaxTileI;
         if (tid < n_a) mine[tid] = r;
         __threadfence();
         group_sync(bar_id);
@@ -575,7 +603,7 @@ __device__ __forceinline__ void force_item(const State &s, const Rec *__restrict
         if (write_out) {
             __threadfence();
             if (tid < n_a) {
-                const Red *base = partials + (int64_t)td.w * kMaxTileI;
+                const Red *base = partials + (int64_t)slot0 * kMaxTileI;
                 r = ld_red_cg(base + tid);
                 for (int q = 1; q < n_parts; q++) red_add(r, ld_red_cg(base + (int64_t)q * kMaxTileI + tid));
             }
@@ -605,7 +633,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_force(State s, const Rec *__res
     if (!step_time(ds, c, &tnow)) return;
     __shared__ ForceSmem<Rec, TJ> sm;
     const int n_items = (int)ds->n_items;
-    const int pj = ds->part_len;
+    const int pj = ds->part_len, work = ds->work_item;
     const typename Traits<Rec>::Eps eps2 = (typename Traits<Rec>::Eps)prm.eps2;
     unsigned long long n_int = 0;
     for (;;) {
@@ -613,7 +641,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_force(State s, const Rec *__res
         __syncthreads();
         const int item = sm.item;
         if (item >= n_items) break;
-        force_item<Rec, TJ, kMapI>(s, rec, L, pj, eps2, L.items[item], sm, n_int, threadIdx.x, 0);
+        force_item<Rec, TJ, kMapI>(s, rec, L, pj, work, eps2, L.items[item], sm, n_int, threadIdx.x, 0);
         // the next iteration's first barrier protects sm reuse
     }
     if (threadIdx.x == 0 && n_int) atomicAdd(&ds->interactions, n_int);
@@ -721,7 +749,10 @@ static __global__ void k_correct(State s, DevScalars *ds, StepCtl c, Params prm)
             cn += s_cnt[w];
         }
         atomic_min_time(&ds->tmin[c.slot_next], mn);
-        if (blockIdx.x == 0) ds->n_items = 0u;  // the force kernel of this step has finished
+        if (blockIdx.x == 0) {  // the force kernel of this step has finished
+            ds->n_items = 0u;
+            ds->slot_ctr = 0u;
+        }
         if (cn) {
             atomicAdd(&ds->n_act_last, cn);
             atomicAdd(&ds->particle_steps, (unsigned long long)cn);
