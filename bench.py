@@ -49,7 +49,7 @@ def _args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="hh", choices=["hh", "reference"])
     p.add_argument("--n", type=int, default=65536)
-    p.add_argument("--n-crit", type=int, default=64)
+    p.add_argument("--n-crit", type=int, default=64, help="group size when the autotuner is off")
     p.add_argument("--theta", type=float, default=0.5)
     p.add_argument("--tile-j", type=int, default=0, help="list part length of the plain FP64 form (0: tuned default)")
     p.add_argument("--tile-j-mixed", type=int, default=0, help="list part length of the mixed form (0: tuned default)")
@@ -93,7 +93,8 @@ def _cfg(hh, prec, a):
 
 def _workload(a):
     return (f"Plummer N={a.n}, 4th-order Hermite, power-of-two block steps (eta=0.02, dt in [2^-30, 2^-6]), "
-            f"tree/lists rebuilt every dt_tree=1/64, theta={a.theta}, leaf 8, n_crit={a.n_crit}, eps=1e-4; "
+            f"tree/lists rebuilt every dt_tree=1/64, theta={a.theta}, leaf 8, n_crit from the autotuner "
+            f"(time to solution; {a.n_crit} without it), eps=1e-4; "
             f"one step = one dt_tree interval")
 
 
@@ -225,7 +226,7 @@ def _tuned(hh, a, prec, seed):
 
     x, v, m = synth.plummer(a.n, seed)
     best, table = autotune.tune(x, v, m, _cfg(hh, prec, a), intervals=1, warm=1)
-    return best, [{"config": c, "interactions_per_s": r} for c, r in table]
+    return best, [{"config": c, "particle_steps_per_s": ps, "interactions_per_s": r} for c, ps, r in table]
 
 
 def _run_form(hh, torch, a, prec, seed, steps, warmup, flush, e2e_steps=0, over=None):
@@ -237,7 +238,7 @@ def _run_form(hh, torch, a, prec, seed, steps, warmup, flush, e2e_steps=0, over=
     for k, val in (over or {}).items():
         setattr(cfg, k, val)
     z = np.zeros((3, a.n))
-    T0 = hh.hh_tree_build(x.T, v.T, z, z, m, leaf=8, n_crit=a.n_crit, theta=a.theta)
+    T0 = hh.hh_tree_build(x.T, v.T, z, z, m, leaf=8, n_crit=cfg.n_crit, theta=a.theta)
     nj_max = 2 * a.n
     list_max = int(len(T0.idx) * 2) + 1024
     groups_max = int(T0.n_groups * 2) + 64
@@ -510,7 +511,8 @@ def main():
             "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": mx[0] / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Plummer spheres, seed = rank)",
-            "config": {"workload": _workload(a), "n": a.n, "theta": a.theta, "n_crit": a.n_crit,
+            "config": {"workload": _workload(a), "n": a.n, "theta": a.theta,
+                       "n_crit": best64.get("n_crit", a.n_crit),
                        "form": "plain FP64", "replicas": world,
                        "l2": "flushed (256 MB write) before every timed step"},
             "equiv_tflops": FLOP_PER_INT * value / 1e12,

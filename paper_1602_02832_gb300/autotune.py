@@ -1,14 +1,17 @@
-"""Autotuner for the force work decomposition: i tile size (tile_i, particles
-per static tile), list part length (tile_j) and work-item cost target
-(work_item).
+"""Autotuner for the group size and the force work decomposition: n_crit
+(particles per group sharing one list: the paper sets it to the value that
+minimises the total computing time, Section 2), i tile size (tile_i,
+particles per static tile), list part length (tile_j) and work-item cost
+target (work_item).
 
 For a given workload (a particle set and its tree settings) every candidate
 runs the same short stretch of the real tree loop — start-up, a warm-up tree
 interval, then timed intervals of block steps plus rebuilds through the
-persistent batched loop — and the candidate with the most interactions per
-second wins.  Results are kept in a JSON cache keyed by device, precision,
-N (rounded to a power of two), theta and n_crit.  Tuning runs outside any
-timed region.
+persistent batched loop — and the candidate that advances the simulation
+fastest (particle steps per second, i.e. shortest time to solution; the
+interaction count itself grows with n_crit) wins.  Results are kept in a JSON
+cache keyed by device, precision, N (rounded to a power of two) and theta.
+Tuning runs outside any timed region.
 """
 from __future__ import annotations
 
@@ -22,16 +25,20 @@ import numpy as np
 from . import HH_FP64, HH_MIXED, Batch, Context, hh_config_default, hh_tree_build
 
 CANDIDATES = {
-    HH_FP64: [dict(tile_i=ti, tile_j=tj, work_item=0) for ti in (32, 16) for tj in (128, 256, 512)],
-    HH_MIXED: [dict(tile_i=ti, tile_j=tj, work_item=0) for ti in (32, 16) for tj in (256, 512, 1024)],
+    HH_FP64: [dict(n_crit=nc, tile_i=ti, tile_j=tj, work_item=0)
+              for nc in (64, 256) for ti in (32, 16) for tj in (128, 256, 512)]
+             + [dict(n_crit=nc, tile_i=16, tile_j=256, work_item=0) for nc in (128, 1024)],
+    HH_MIXED: [dict(n_crit=nc, tile_i=ti, tile_j=tj, work_item=0)
+               for nc in (64, 256) for ti in (32, 16) for tj in (256, 512, 1024)]
+              + [dict(n_crit=nc, tile_i=32, tile_j=512, work_item=0) for nc in (128, 1024)],
 }
 
 _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 
-def _key(device_name, precision, n, theta, n_crit):
+def _key(device_name, precision, n, theta):
     return f"{device_name}|{'mixed' if precision == HH_MIXED else 'fp64'}|n2^{round(math.log2(max(n, 2)))}|" \
-           f"theta{theta}|ncrit{n_crit}"
+           f"theta{theta}"
 
 
 def _run_candidate(x, v, m, base, cand, intervals, warm):
@@ -61,23 +68,24 @@ def _run_candidate(x, v, m, base, cand, intervals, warm):
 
         for _ in range(warm):
             interval()
-        c0 = ctx.hh_get_counters()["interactions"]
+        c0 = ctx.hh_get_counters()
         w0 = time.perf_counter()
         for _ in range(intervals):
             interval()
         dt = time.perf_counter() - w0
-        return (ctx.hh_get_counters()["interactions"] - c0) / dt
+        c1 = ctx.hh_get_counters()
+        return (c1["particle_steps"] - c0["particle_steps"]) / dt, (c1["interactions"] - c0["interactions"]) / dt
 
 
 def tune(x, v, m, base_cfg, intervals=1, warm=1, use_cache=True, device_name=None):
-    """Returns (best candidate dict, table of (candidate, interactions/s))."""
+    """Returns (best candidate dict, table of (candidate, particle steps/s, interactions/s))."""
     if device_name is None:
         try:
             import torch
             device_name = torch.cuda.get_device_name(0)
         except Exception:
             device_name = "cuda"
-    key = _key(device_name, base_cfg.precision, len(m), round(base_cfg.theta, 3), base_cfg.n_crit)
+    key = _key(device_name, base_cfg.precision, len(m), round(base_cfg.theta, 3))
     cache = {}
     if use_cache and os.path.exists(_CACHE):
         try:
@@ -88,8 +96,8 @@ def tune(x, v, m, base_cfg, intervals=1, warm=1, use_cache=True, device_name=Non
             return cache[key]["best"], cache[key]["table"]
     table = []
     for cand in CANDIDATES[base_cfg.precision]:
-        rate = _run_candidate(x, v, m, base_cfg, cand, intervals, warm)
-        table.append((cand, rate))
+        steps_rate, int_rate = _run_candidate(x, v, m, base_cfg, cand, intervals, warm)
+        table.append((cand, steps_rate, int_rate))
     best = max(table, key=lambda r: r[1])[0]
     if use_cache:
         cache[key] = {"best": best, "table": table}

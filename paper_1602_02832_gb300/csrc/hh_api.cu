@@ -210,6 +210,10 @@ int set_j_impl(hh_ctx *ctx, int64_t first, int64_t n, const double *x, const dou
         k_check_j<<<ctx->elem_grid, 256, 0, ctx->stream>>>(ctx->st, first, n, ctx->ds);
         CKL();
     }
+    if (ctx->st.base) {
+        k_refresh_base<<<ctx->elem_grid, 256, 0, ctx->stream>>>(ctx->st, first, n);
+        CKL();
+    }
     ctx->have_j = true;
     ctx->predicted = false;
     return sync_and_check(ctx);
@@ -359,7 +363,7 @@ int hh_destroy(hh_ctx *ctx)
     for (auto e : ctx->ev) cudaEventDestroy(e);
     if (ctx->e0) cudaEventDestroy(ctx->e0);
     if (ctx->e1) cudaEventDestroy(ctx->e1);
-    void *dev[] = {ctx->st.x, ctx->st.v, ctx->st.a, ctx->st.jk, ctx->st.m, ctx->st.t, ctx->st.dt, ctx->st.acc1,
+    void *dev[] = {ctx->st.base, ctx->st.x, ctx->st.v, ctx->st.a, ctx->st.jk, ctx->st.m, ctx->st.t, ctx->st.dt, ctx->st.acc1,
                    ctx->st.jerk1, ctx->st.pot1, ctx->st.mark, ctx->rec, ctx->off, ctx->idx, ctx->group_of,
                    ctx->tiles, ctx->ds, ctx->i_buf, ctx->out_buf, ctx->items, ctx->partials, ctx->tile_cnt,
                    ctx->tile_lv};
@@ -448,10 +452,15 @@ int hh_create(hh_ctx **out, int device, const hh_config *cfg, int64_t n_max, int
         {(void **)&ctx->out_buf, sizeof(double) * 7 * n_max},
         {(void **)&ctx->tile_cnt, sizeof(int32_t) * ctx->cap_tiles},
         {(void **)&ctx->tile_lv, sizeof(uint32_t) * ctx->cap_tiles},
+        {(void **)&ctx->st.base, c.precision == HH_MIXED ? sizeof(BaseMix) * nj_max : 0},
         {(void **)&ctx->items, sizeof(int4) * ctx->cap_parts},
         {(void **)&ctx->partials, sizeof(RedF64) * kMaxTileI * ctx->cap_parts},
     };
     for (auto &al : allocs) {
+        if (al.bytes == 0) {
+            *al.p = nullptr;
+            continue;
+        }
         if (cudaMalloc(al.p, al.bytes) != cudaSuccess) {
             cudaGetLastError();
             return bail(HH_ENOMEM, "device allocation failed (capacities too large)");

@@ -370,10 +370,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
             const SimDesc &sd = B.sims[s];
             const double tnow = cached_time(sc, B.sims, s, par);
             if (!(tnow <= sd.t_end)) continue;
-            const int64_t e = g - B.jbase[s];
-            double xp[3], vp[3];
-            predict_one(sd.st, e, tnow, xp, vp);
-            store_rec<Rec>((Rec *)sd.rec, e, xp, vp, sd.st.m[e]);
+            predict_entry<Rec>(sd.st, (Rec *)sd.rec, g - B.jbase[s], tnow);
         }
         {
             const int lane = tid & 31;

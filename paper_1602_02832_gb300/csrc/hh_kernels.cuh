@@ -67,8 +67,20 @@ struct __align__(16) RecMix {
     float4 v;   // (vx, vy, vz, 0)
 };
 
+// Mixed form: per j entry, the FP32 quantities the predictor needs,
+// refreshed whenever the entry's FP64 state changes (upload, correction):
+// position as a float pair, velocity, a/2 and jerk/6.
+struct __align__(16) BaseMix {
+    float4 hm;  // (x_hi, y_hi, z_hi, m)
+    float4 lo;  // (x_lo, y_lo, z_lo, 0)
+    float4 v;   // (vx, vy, vz, 0)
+    float4 a2;  // a / 2
+    float4 j6;  // jerk / 6
+};
+
 struct State {
     double *x, *v, *a, *jk;  // [3][cap_j]
+    BaseMix *base;           // [cap_j] mixed form only (else nullptr)
     double *m, *t;           // [cap_j]
     double *dt;              // [cap_n]
     double *acc1, *jerk1, *pot1;  // [3][cap_n], [cap_n]: last force results
@@ -227,6 +239,71 @@ __device__ __forceinline__ void store_rec<RecMix>(RecMix *out, int64_t e, const 
     out[e] = r;
 }
 
+// FP32 copy of entry e's FP64 state for the mixed predictor.
+__device__ __forceinline__ void refresh_base(const State &s, int64_t e)
+{
+    float hi[3], lo[3], v[3], a2[3], j6[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const double x = s.x[d * s.cap_j + e];
+        hi[d] = __double2float_rn(x);
+        lo[d] = __double2float_rn(x - (double)hi[d]);
+        v[d] = __double2float_rn(s.v[d * s.cap_j + e]);
+        a2[d] = 0.5f * __double2float_rn(s.a[d * s.cap_j + e]);
+        j6[d] = __double2float_rn(s.jk[d * s.cap_j + e]) * (1.0f / 6.0f);
+    }
+    BaseMix b;
+    b.hm = make_float4(hi[0], hi[1], hi[2], __double2float_rn(s.m[e]));
+    b.lo = make_float4(lo[0], lo[1], lo[2], 0.f);
+    b.v = make_float4(v[0], v[1], v[2], 0.f);
+    b.a2 = make_float4(a2[0], a2[1], a2[2], 0.f);
+    b.j6 = make_float4(j6[0], j6[1], j6[2], 0.f);
+    s.base[e] = b;
+}
+
+// Mixed predictor: the FP64 base position (as a float pair) plus an FP32
+// increment D (v + D (a/2 + D jerk/6)), added with TwoSum; v + D (a + D jerk/2)
+// in FP32.  D = t - t_e is exact in FP32 (a multiple of dt_min below dt_tree).
+__device__ __forceinline__ void predict_mix(const State &s, RecMix *rec, int64_t e, double tnow)
+{
+    const float D = __double2float_rn(tnow - s.t[e]);
+    const BaseMix b = s.base[e];
+    const float hx[3] = {b.hm.x, b.hm.y, b.hm.z}, lx[3] = {b.lo.x, b.lo.y, b.lo.z};
+    const float vv[3] = {b.v.x, b.v.y, b.v.z}, aa[3] = {b.a2.x, b.a2.y, b.a2.z}, jj[3] = {b.j6.x, b.j6.y, b.j6.z};
+    float ho[3], lo[3], vo[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const float dx = D * fmaf(D, fmaf(D, jj[d], aa[d]), vv[d]);
+        const float sum = __fadd_rn(hx[d], dx);
+        const float bb = __fsub_rn(sum, hx[d]);
+        const float err = __fadd_rn(__fsub_rn(hx[d], __fsub_rn(sum, bb)), __fsub_rn(dx, bb));
+        ho[d] = sum;
+        lo[d] = __fadd_rn(lx[d], err);
+        vo[d] = fmaf(D, fmaf(D, 3.f * jj[d], 2.f * aa[d]), vv[d]);
+    }
+    RecMix r;
+    r.hm = make_float4(ho[0], ho[1], ho[2], b.hm.w);
+    r.lo = make_float4(lo[0], lo[1], lo[2], 0.f);
+    r.v = make_float4(vo[0], vo[1], vo[2], 0.f);
+    rec[e] = r;
+}
+
+// Predicted record of entry e at tnow, in the form's own arithmetic.
+template <typename Rec>
+__device__ __forceinline__ void predict_entry(const State &s, Rec *rec, int64_t e, double tnow);
+template <>
+__device__ __forceinline__ void predict_entry<RecF64>(const State &s, RecF64 *rec, int64_t e, double tnow)
+{
+    double xp[3], vp[3];
+    predict_one(s, e, tnow, xp, vp);
+    store_rec<RecF64>(rec, e, xp, vp, s.m[e]);
+}
+template <>
+__device__ __forceinline__ void predict_entry<RecMix>(const State &s, RecMix *rec, int64_t e, double tnow)
+{
+    predict_mix(s, rec, e, tnow);
+}
+
 template <typename Rec>
 __global__ void k_predict(State s, Rec *rec, Lists L, DevScalars *ds, StepCtl c)
 {
@@ -243,11 +320,8 @@ __global__ void k_predict(State s, Rec *rec, Lists L, DevScalars *ds, StepCtl c)
     }
 
     const int64_t nj = ds->nj;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nj; e += (int64_t)gridDim.x * blockDim.x) {
-        double xp[3], vp[3];
-        predict_one(s, e, tnow, xp, vp);
-        store_rec<Rec>(rec, e, xp, vp, s.m[e]);
-    }
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nj; e += (int64_t)gridDim.x * blockDim.x)
+        predict_entry<Rec>(s, rec, e, tnow);
     if (c.mode == 0) select_tiles(s, L, ds, c, tnow);
 }
 
@@ -489,10 +563,30 @@ __device__ __forceinline__ void fold_chunk(AccMix &A) { A.fold(); }
 // tile's last part (arrival counter, threadfence pattern: no waiting) adds
 // the parts in part order.  So each particle's result depends only on its
 // list, its tile's active count and the part length, never on scheduling.
+// Asynchronous global -> shared copies (16 B each, through L2 only: the
+// records are rewritten every block step) for chunk staging.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <typename Rec>
+__device__ __forceinline__ void cp_async_rec(Rec *dst, const Rec *src)
+{
+    static_assert(sizeof(Rec) % 16 == 0, "records are whole 16-byte pieces");
+#pragma unroll
+    for (int q = 0; q < (int)(sizeof(Rec) / 16); q++)
+        cp_async16(reinterpret_cast<char *>(dst) + 16 * q, reinterpret_cast<const char *>(src) + 16 * q);
+}
+
 template <typename Rec, int TJ>
 struct ForceSmem {
-    Rec rec[TJ];
-    int32_t idx[TJ];
+    Rec rec[2][TJ];      // double-buffered staging of list chunks
+    int32_t idx[2][TJ];
     typename Traits<Rec>::Red red[kThreads / 32][kMaxTileI];
     int item;
     int last;
@@ -554,12 +648,43 @@ __device__ __forceinline__ void force_item(const State &s, const Rec *__restrict
     const int64_t le = min(ge, lb + (int64_t)pj);
     const int64_t len = le - lb;
     if (tid == 0 && part == 0) n_int += (unsigned long long)n_a * (unsigned long long)(ge - gb - 1);
-    for (int64_t c0 = 0; c0 < len; c0 += TJ) {
-        const int nc = (len - c0 < (int64_t)TJ) ? (int)(len - c0) : TJ;
-        for (int e = tid; e < nc; e += kThreads) {
-            const int32_t j = L.idx[lb + c0 + e];
-            sm.idx[e] = j;
-            sm.rec[e] = rec[j];
+    // Chunks of TJ list entries are staged in two shared buffers: while one
+    // is summed, cp.async fills the other; the list indices of the chunk
+    // after that are already loading into registers.
+    constexpr int EPT = TJ / kThreads;  // staged entries per thread and chunk
+    const int n_chunks = (int)((len + TJ - 1) / TJ);
+    int32_t nxt[EPT];
+    auto load_idx = [&](int c) {
+#pragma unroll
+        for (int q = 0; q < EPT; q++) {
+            const int64_t e = (int64_t)c * TJ + q * kThreads + tid;
+            nxt[q] = (c < n_chunks && e < len) ? L.idx[lb + e] : -1;
+        }
+    };
+    auto issue = [&](int c) {  // chunk c's records into buffer c & 1, indices from nxt
+        const int b = c & 1;
+#pragma unroll
+        for (int q = 0; q < EPT; q++) {
+            const int e = q * kThreads + tid;
+            sm.idx[b][e] = nxt[q];
+            if (nxt[q] >= 0) cp_async_rec(&sm.rec[b][e], &rec[nxt[q]]);
+        }
+        cp_async_commit();
+    };
+    if (n_chunks > 0) {
+        load_idx(0);
+        issue(0);
+        load_idx(1);
+    }
+    for (int c = 0; c < n_chunks; c++) {
+        const int b = c & 1;
+        const int nc = (len - (int64_t)c * TJ < (int64_t)TJ) ? (int)(len - (int64_t)c * TJ) : TJ;
+        if (c + 1 < n_chunks) {
+            issue(c + 1);
+            load_idx(c + 2);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         group_sync(bar_id);
         // FP32 partials are folded into the compensated sums every
@@ -568,12 +693,12 @@ __device__ __forceinline__ void force_item(const State &s, const Rec *__restrict
         for (int e = jslice; e < nc;) {
             const int e_end = min(nc, e + kFold * S);
             for (; e < e_end; e += S) {
-                const int32_t j = sm.idx[e];
-                interact(Iv, sm.rec[e], (int64_t)j == pi, eps2, A);
+                const int32_t j = sm.idx[b][e];
+                interact(Iv, sm.rec[b][e], (int64_t)j == pi, eps2, A);
             }
             fold_chunk(A);
         }
-        group_sync(bar_id);
+        group_sync(bar_id);  // buffer b is refilled two chunks later
     }
     // reduce the S slices of each i slot: lanes l, l+I, ... then warps
     for (int off = I; off < 32; off <<= 1) acc_shfl_add(A, off);
@@ -661,7 +786,9 @@ __device__ __forceinline__ double block_dt(double want, double dt_old, double t_
     else q = pow2_floor(want);
     if (q > 2.0 * dt_old) q = 2.0 * dt_old;
     if (q > dt_old) {
-        const double r = t_new / q;
+        // t_new / q for a power of two q, as an exact product with 1 / q
+        const double inv = __longlong_as_double((long long)(2046 - ((__double_as_longlong(q) >> 52) & 0x7ff)) << 52);
+        const double r = t_new * inv;
         if (r != floor(r)) q = dt_old;
     }
     if (q > dt_max) q = dt_max;
@@ -680,31 +807,38 @@ __device__ __forceinline__ void atomic_min_time(unsigned long long *slot, double
 // new step from Aarseth's criterion at the end of the step.
 __device__ __forceinline__ void correct_particle(const State &s, int64_t p, double tnow, const Params &prm)
 {
-            const double D = tnow - s.t[p];
-            double xp[3], vp[3];
-            predict_one(s, p, tnow, xp, vp);
-            double a1[3], j1[3], a2e[3], a3v[3];
-            const double D2 = D * D, D3 = D2 * D;
+    // The FP64 pipe is narrow on this GPU, so divisions and square roots are
+    // kept few: one reciprocal of D, products of squared norms under one root.
+    const double D = tnow - s.t[p];
+    double xp[3], vp[3];
+    predict_one(s, p, tnow, xp, vp);
+    const double iD = 1.0 / D;
+    const double iD2 = iD * iD, iD3 = iD2 * iD;
+    const double D2 = D * D, D3 = D2 * D;
+    double A = 0.0, J = 0.0, S = 0.0, T = 0.0;  // |a1|^2, |j1|^2, |a^(2)(t1)|^2, |a^(3)|^2
 #pragma unroll
-            for (int d = 0; d < 3; d++) {
-                const double a0 = s.a[d * s.cap_j + p], j0 = s.jk[d * s.cap_j + p];
-                a1[d] = s.acc1[d * s.cap_n + p];
-                j1[d] = s.jerk1[d * s.cap_n + p];
-                const double a2 = (-6.0 * (a0 - a1[d]) - D * (4.0 * j0 + 2.0 * j1[d])) / D2;
-                const double a3 = (12.0 * (a0 - a1[d]) + 6.0 * D * (j0 + j1[d])) / D3;
-                s.x[d * s.cap_j + p] = xp[d] + D2 * D2 * (a2 * (1.0 / 24.0) + a3 * D * (1.0 / 120.0));
-                s.v[d * s.cap_j + p] = vp[d] + D3 * (a2 * (1.0 / 6.0) + a3 * D * (1.0 / 24.0));
-                s.a[d * s.cap_j + p] = a1[d];
-                s.jk[d * s.cap_j + p] = j1[d];
-                a2e[d] = a2 + a3 * D;
-                a3v[d] = a3;
-            }
-            const double na = norm3(a1[0], a1[1], a1[2]), nj = norm3(j1[0], j1[1], j1[2]);
-            const double n2 = norm3(a2e[0], a2e[1], a2e[2]), n3 = norm3(a3v[0], a3v[1], a3v[2]);
-            const double want = sqrt(prm.eta * (na * n2 + nj * nj) / (nj * n3 + n2 * n2));
-            const double dtn = block_dt(want, s.dt[p], tnow, prm.dt_min, prm.dt_max);
-            s.t[p] = tnow;
-            s.dt[p] = dtn;
+    for (int d = 0; d < 3; d++) {
+        const double a0 = s.a[d * s.cap_j + p], j0 = s.jk[d * s.cap_j + p];
+        const double a1 = s.acc1[d * s.cap_n + p];
+        const double j1 = s.jerk1[d * s.cap_n + p];
+        const double a2 = (-6.0 * (a0 - a1) - D * (4.0 * j0 + 2.0 * j1)) * iD2;
+        const double a3 = (12.0 * (a0 - a1) + 6.0 * D * (j0 + j1)) * iD3;
+        s.x[d * s.cap_j + p] = xp[d] + D2 * D2 * (a2 * (1.0 / 24.0) + a3 * D * (1.0 / 120.0));
+        s.v[d * s.cap_j + p] = vp[d] + D3 * (a2 * (1.0 / 6.0) + a3 * D * (1.0 / 24.0));
+        s.a[d * s.cap_j + p] = a1;
+        s.jk[d * s.cap_j + p] = j1;
+        const double a2e = a2 + a3 * D;
+        A += a1 * a1;
+        J += j1 * j1;
+        S += a2e * a2e;
+        T += a3 * a3;
+    }
+    // Aarseth: dt^2 = eta (|a||a2| + |j|^2) / (|j||a3| + |a2|^2)
+    const double want = sqrt(prm.eta * (sqrt(A * S) + J) / (sqrt(J * T) + S));
+    const double dtn = block_dt(want, s.dt[p], tnow, prm.dt_min, prm.dt_max);
+    s.t[p] = tnow;
+    s.dt[p] = dtn;
+    if (s.base) refresh_base(s, p);
 }
 
 static __global__ void k_correct(State s, DevScalars *ds, StepCtl c, Params prm)
@@ -802,7 +936,14 @@ static __global__ void k_adopt_forces(State s, DevScalars *ds)
             s.a[d * s.cap_j + p] = s.acc1[d * s.cap_n + p];
             s.jk[d * s.cap_j + p] = s.jerk1[d * s.cap_n + p];
         }
+        if (s.base) refresh_base(s, p);
     }
+}
+
+static __global__ void k_refresh_base(State s, int64_t first, int64_t n)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        refresh_base(s, first + q);
 }
 
 static __global__ void k_set_marks(int32_t *mark, const int32_t *idx, int32_t n, int32_t value)
