@@ -51,6 +51,7 @@ def _args():
     p.add_argument("--n", type=int, default=65536)
     p.add_argument("--n-crit", type=int, default=64, help="group size when the autotuner is off")
     p.add_argument("--theta", type=float, default=0.5)
+    p.add_argument("--tile-i", type=int, default=0, help="particles per i tile, both forms (0: tuned default)")
     p.add_argument("--tile-j", type=int, default=0, help="list part length of the plain FP64 form (0: tuned default)")
     p.add_argument("--tile-j-mixed", type=int, default=0, help="list part length of the mixed form (0: tuned default)")
     p.add_argument("--work-item", type=int, default=0, help="interactions per work item, plain form (0: default)")
@@ -86,6 +87,7 @@ def _cfg(hh, prec, a):
     c.leaf = 8
     c.n_crit = a.n_crit
     c.precision = prec
+    c.tile_i = a.tile_i or 0
     c.tile_j = (a.tile_j if prec == hh.HH_FP64 else a.tile_j_mixed) or 0
     c.work_item = (a.work_item if prec == hh.HH_FP64 else a.work_item_mixed) or 0
     return c
@@ -217,9 +219,24 @@ class _Loop:
             self.batch.close()
 
 
+def reduce_over_ranks(sums, maxes, device, world):
+    """Whole-job aggregation of independent replicas: work counts are summed
+    and times take the maximum over ranks (the slowest rank bounds the job).
+    No data-path collective: only these scalars cross ranks."""
+    import torch
+
+    t_sum = torch.tensor(sums, dtype=torch.float64, device=device)
+    t_max = torch.tensor(maxes, dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t_sum, op=dist.ReduceOp.SUM)
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    return t_sum.tolist(), t_max.tolist()
+
+
 def _tuned(hh, a, prec, seed):
     """Tile shape for this workload from the autotuner (outside the timed region)."""
-    if a.no_autotune or a.tile_j or a.tile_j_mixed:
+    if a.no_autotune or a.tile_j or a.tile_j_mixed or a.tile_i:
         return {}, None
     import synth
     from paper_1602_02832_gb300 import autotune
@@ -495,14 +512,9 @@ def main():
     mixed = None
     if not a.no_mixed:
         mixed = _run_form(hh, torch, a, hh.HH_MIXED, rank, a.steps, a.warmup, flush, over=bestmx)
-    tot = torch.tensor([res["interactions"], res["block_steps"], res["particle_steps"], res["gpu_launches"],
-                        res["e2e"]["interactions"]], dtype=torch.float64, device="cuda")
-    mx = torch.tensor([res["ms"], res["e2e"]["ms"]], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-    tot = tot.tolist()
-    mx = mx.tolist()
+    tot, mx = reduce_over_ranks(
+        [res["interactions"], res["block_steps"], res["particle_steps"], res["gpu_launches"], res["e2e"]["interactions"]],
+        [res["ms"], res["e2e"]["ms"]], torch.device("cuda", local), world)
     if rank == 0:
         value = tot[0] / (mx[0] * 1e-3)
         achieved = FLOP_PER_INT * res["interactions"] / (res["force_ms"] * 1e-3) / 1e12

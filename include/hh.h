@@ -221,18 +221,26 @@ const char *hh_last_error(const hh_ctx *ctx);
  *   step_us_out[max_steps], the duration of each global step in
  *   microseconds (device timer); phase_us_out[3 max_steps], per step the
  *   durations of the predict/select, force and correct phases.  Synchronises.
+ *   A grid-barrier wait gives up after 2 s (HH_ETIMEOUT).
  *   Every particle must follow the block rule (dt a power of two in
  *   [2^-31, 1], t a multiple of dt, t + dt after the latest t), as states
  *   made by hh_init_dt, hh_step, hh_advance and hh_rebuild do; otherwise
  *   HH_EINVAL.  The loop keeps a per-simulation histogram of step levels
- *   and per-tile level masks, so a block step touches only the due tiles.  Grid barriers give up after
- *   about a second and return HH_ETIMEOUT. */
+ *   and per-tile level masks, so a block step touches only the due tiles. */
 typedef struct hh_batch hh_batch;
 int hh_batch_create(hh_batch **out, int device, int precision, int32_t max_sims, int32_t max_steps);
 int hh_batch_destroy(hh_batch *b);
 int hh_batch_run(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const double *t_end, int32_t max_steps,
                  int32_t *steps_out, double *t_next_out, double *step_us_out, double *phase_us_out);
 const char *hh_batch_last_error(const hh_batch *b);
+
+/* Self-test of the bounded grid barrier of the batched kernel: a
+ * cooperative launch of one CTA per SM runs 64 barriers; with skip_cta >= 0
+ * that CTA never arrives, so every other CTA's wait must give up after its
+ * limit (2 s) and the call returns HH_ETIMEOUT with the
+ * GPU still usable; skip_cta < 0 must return HH_OK.  *elapsed_s (may be
+ * NULL) receives the kernel's duration. */
+int hh_barrier_selftest(int device, int skip_cta, double *elapsed_s);
 
 /* Device memory held by a context (bytes), for admission by memory budget. */
 int64_t hh_ctx_device_bytes(const hh_ctx *ctx);

@@ -95,6 +95,7 @@ _SIGS = {
     "hh_batch_run": (C.c_int, [_P, C.c_int32, C.POINTER(_P), _D, C.c_int32, _I32, _D, _D, _D]),
     "hh_batch_last_error": (C.c_char_p, [_P]),
     "hh_ctx_device_bytes": (C.c_int64, [_P]),
+    "hh_barrier_selftest": (C.c_int, [C.c_int, C.c_int, _D]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -405,3 +406,10 @@ class Batch:
             raise HHError(rc, (_lib.hh_batch_last_error(self.h) or b"").decode())
         self.last_phase_us = ph[:steps.value]
         return steps.value, tn, us[:steps.value]
+
+
+def hh_barrier_selftest(skip_cta=-1, device=0):
+    """Returns (status code, seconds): HH_ETIMEOUT expected when skip_cta >= 0."""
+    t = C.c_double()
+    rc = _lib.hh_barrier_selftest(int(device), int(skip_cta), C.byref(t))
+    return rc, t.value

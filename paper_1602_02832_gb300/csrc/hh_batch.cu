@@ -33,7 +33,8 @@ using namespace hh;
 
 namespace {
 
-constexpr long long kSpinLimit = 1ll << 25;  // ~ seconds of __nanosleep(64) polling
+constexpr unsigned long long kWaitNs = 2000000000ull;  // a barrier wait gives up after 2 s
+constexpr long long kSpinLimit = 1ll << 28;            // iteration backstop for the same wait
 constexpr int kGroups = 4;                   // 128-thread worker groups per CTA (one CTA per SM)
 constexpr int kBlock = kThreads * kGroups;
 constexpr int kSimCache = 256;               // simulations whose step data a CTA keeps in shared memory
@@ -94,11 +95,13 @@ __device__ __forceinline__ bool grid_sync(BatchScalars *bs)
             atomicAdd(&bs->bar_gen, 1u);
         } else {
             long long it = 0;
+            const unsigned long long t0 = globaltimer_ns();
             while (*gen == g) {
-                if (++it > kSpinLimit) {
+                if (++it > kSpinLimit || globaltimer_ns() - t0 > kWaitNs) {
                     atomicExch(&bs->err, HH_ETIMEOUT);
                     break;
                 }
+                if ((it & 255) == 0 && *(volatile int32_t *)&bs->err) break;  // another CTA gave up
                 __nanosleep(64);
             }
         }
@@ -698,3 +701,54 @@ extern "C" int hh_batch_run(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const d
 }
 
 extern "C" const char *hh_batch_last_error(const hh_batch *b) { return b ? b->err.c_str() : hh_last_error(nullptr); }
+
+namespace {
+
+// Runs `rounds` grid barriers; CTA `skip` (if >= 0) never arrives, so the
+// others' bounded waits must give up and report HH_ETIMEOUT.
+__global__ void k_barrier_selftest(BatchScalars *bs, int rounds, int skip)
+{
+    if ((int)blockIdx.x == skip) return;
+    for (int r = 0; r < rounds; r++)
+        if (!grid_sync(bs)) return;
+}
+
+}  // namespace
+
+extern "C" int hh_barrier_selftest(int device, int skip_cta, double *elapsed_s)
+{
+    if (cudaSetDevice(device) != cudaSuccess) return hh_set_global_error(HH_ECUDA, "hh_barrier_selftest: bad device");
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess)
+        return hh_set_global_error(HH_ECUDA, "hh_barrier_selftest: device query failed");
+    const int grid = prop.multiProcessorCount;
+    if (skip_cta >= grid) return hh_set_global_error(HH_EINVAL, "hh_barrier_selftest: skip_cta >= number of CTAs");
+    BatchScalars *bs = nullptr;
+    if (cudaMalloc(&bs, sizeof(BatchScalars)) != cudaSuccess || cudaMemset(bs, 0, sizeof(BatchScalars)) != cudaSuccess) {
+        cudaGetLastError();
+        if (bs) cudaFree(bs);
+        return hh_set_global_error(HH_ENOMEM, "hh_barrier_selftest: allocation failed");
+    }
+    int rounds = 64;
+    void *args[] = {&bs, &rounds, &skip_cta};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_barrier_selftest, dim3(grid), dim3(kThreads), args, 0, 0);
+    cudaEventRecord(e1);
+    BatchScalars h;
+    std::memset(&h, 0, sizeof(h));
+    if (e == cudaSuccess) e = cudaMemcpy(&h, bs, sizeof(h), cudaMemcpyDeviceToHost);
+    float ms = 0.f;
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(bs);
+    if (elapsed_s) *elapsed_s = ms * 1e-3;
+    if (e != cudaSuccess) return hh_set_global_error(HH_ECUDA, cudaGetErrorString(e));
+    hh_count_launches(1);
+    if (h.err) return hh_set_global_error(h.err, "hh_barrier_selftest: a grid barrier timed out");
+    return HH_OK;
+}

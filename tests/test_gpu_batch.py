@@ -112,3 +112,15 @@ def test_batch_rejects_bad_requests(hh):
         assert 0 < steps <= 16
         c1.close()
         c2.close()
+
+
+def test_bounded_barrier_reports_timeout(hh):
+    # Failure detection without a GPU fault: a CTA that never arrives makes
+    # the others' bounded waits give up; the call reports HH_ETIMEOUT and the
+    # context stays usable (the normal barrier run afterwards succeeds).
+    rc, t = hh.hh_barrier_selftest(skip_cta=-1)
+    assert rc == hh.HH_OK and t < 1.0
+    rc, t = hh.hh_barrier_selftest(skip_cta=3)
+    assert rc == hh.HH_ETIMEOUT and 0.05 < t < 30.0
+    rc, t = hh.hh_barrier_selftest(skip_cta=-1)
+    assert rc == hh.HH_OK
