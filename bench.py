@@ -39,6 +39,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FLOP_PER_INT = 60
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_batch launch (plain FP64,
+# one tree interval of the N = 65536 run), from profiles/batch_kernel_plummer65536.md
+TRAFFIC_FP64_PER_LAUNCH = 100.23168e6 + 81.654528e6
 METRIC = "interactions/s & equiv. Tflops (60 flop/int); block-steps/s, p50/p99 latency vs plain"
 
 
@@ -531,13 +534,18 @@ def main():
             "equiv_tflops_57": 57 * value / 1e12,
             "block_steps_per_s": tot[1] / (mx[0] * 1e-3),
             "particle_steps_per_s": tot[2] / (mx[0] * 1e-3),
-            "roofline": {"kernel": "k_force<RecF64> (plain FP64 list force)", "bound": "alu",
+            "roofline": {"kernel": ("k_batch force phase, plain FP64" if a.loop == "persistent"
+                                    else "k_force<RecF64> (plain FP64 list force)"),
+                         "bound": "alu",
                          "achieved": achieved, "peak": peaks.get("fp64_tflops"), "unit": "TFLOP/s",
                          "frac": achieved / peaks["fp64_tflops"] if peaks.get("fp64_tflops") else None,
-                         "traffic": None,
-                         "note": "60 algorithmic flop per interaction / mean CUDA-event time of the force "
-                                 "kernel launches in the timed region; peak = measured FP64 FMA throughput "
-                                 "(of measured)"},
+                         "traffic": TRAFFIC_FP64_PER_LAUNCH if a.loop == "persistent" else None,
+                         "note": "achieved = 60 algorithmic flop per interaction / device time of the force "
+                                 "phases (persistent loop: %globaltimer stamps at the phase barriers; graph loop: "
+                                 "CUDA events around the force kernel); peak = measured FP64 FMA throughput "
+                                 "(of measured, libhh_peaks.so); traffic = DRAM bytes of one k_batch launch "
+                                 "(one interval, all phases) from the ncu capture summarised in "
+                                 "profiles/batch_kernel_plummer65536.md"},
             "e2e": {"value": tot[4] / (mx[1] * 1e-3), "unit": "interactions/s",
                     "h2d_bytes_per_step": res["e2e"]["bi"], "d2h_bytes_per_step": res["e2e"]["bo"]},
             "gpu_launches": int(tot[3]),
