@@ -8,9 +8,12 @@ to dt_tree because the tree loop caps every step at the rebuild interval),
 tree and lists rebuilt every dt_tree = 1/64, theta = 0.5, eps = 1e-4, FP64.
 
 One step = one tree interval dt_tree: all block steps of the interval on the
-device (CUDA graph replays of predict / force / correct) followed by the tree
-rebuild (state to host, the library's host tree builder, upload of
-particles, nodes and lists).  Warm-up intervals start at t = 0; the timed
+device (persistent batched loop, or CUDA graph replays of predict / force /
+correct with --loop graph) followed by the tree rebuild: on the device by
+default (Morton keys, radix sort, cells, node records, groups and lists built
+by the library's kernels without the state leaving the GPU); --rebuild host
+takes the state to the host, runs the library's host tree builder and
+uploads particles, nodes and lists.  Warm-up intervals start at t = 0; the timed
 intervals follow.  L2 is flushed (256 MB write) before each timed interval.
 
 value = interactions / time (interactions = sum over particle steps of the
@@ -66,6 +69,8 @@ def _args():
     p.add_argument("--ensemble-intervals", type=int, default=2)
     p.add_argument("--serve-seconds", type=float, default=20.0, help="wall time of the serving measurement (0: skip)")
     p.add_argument("--no-autotune", action="store_true", help="skip the tile-shape autotuner (use the defaults)")
+    p.add_argument("--rebuild", default="device", choices=["device", "host"],
+                   help="where the tree, groups and lists are rebuilt every dt_tree")
     p.add_argument("--loop", default="persistent", choices=["persistent", "graph"],
                    help="block-step loop: one persistent cooperative kernel per interval, or CUDA-graph replays")
     return p.parse_args()
@@ -245,7 +250,8 @@ def _tuned(hh, a, prec, seed):
     from paper_1602_02832_gb300 import autotune
 
     x, v, m = synth.plummer(a.n, seed)
-    best, table = autotune.tune(x, v, m, _cfg(hh, prec, a), intervals=1, warm=1)
+    best, table = autotune.tune(x, v, m, _cfg(hh, prec, a), intervals=1, warm=1,
+                                rebuild_device=a.rebuild == "device")
     return best, [{"config": c, "particle_steps_per_s": ps, "interactions_per_s": r} for c, ps, r in table]
 
 
@@ -267,6 +273,7 @@ def _run_form(hh, torch, a, prec, seed, steps, warmup, flush, e2e_steps=0, over=
     ctx.hh_set_stream(stream.cuda_stream)
     dtt = cfg.dt_tree
     ctx.hh_load_particles(x.T, v.T, m)
+    ctx.hh_set_rebuild_device(a.rebuild == "device")
     ctx.hh_run(0.0, 0.0)  # rebuild, initial forces, rebuild with node derivatives, initial steps
     loop = _Loop(hh, ctx, prec, a.loop)
     t = 0.0
@@ -356,7 +363,8 @@ def _ensemble(hh, a):
     for th in sorted({mb.theta for mb in members}):
         sub = [r for r, mb in zip(reqs, members) if mb.theta == th]
         srv = serve.Server(precision=hh.HH_MIXED, budget_bytes=150 * 10 ** 9, max_sims=256, max_steps=64,
-                           theta=th, n_crit=a.n_crit, rebuild_threads=8)
+                           theta=th, n_crit=a.n_crit, rebuild_threads=8,
+                           rebuild_device=a.rebuild == "device")
         res, st = srv.run(sub, realtime=False)
         srv.close()
         results += res
@@ -374,7 +382,8 @@ def _ensemble(hh, a):
             "equiv_tflops": FLOP_PER_INT * tot["interactions"] / wall / 1e12,
             "mean_live_sims_per_step": float(np.mean(tot["live"])) if tot["live"] else None,
             "block_step_latency_us": lat,
-            "note": "wall time includes admission (host tree builds, initial forces) and host rebuilds; "
+            "note": "wall time includes admission (host tree build for the memory estimate, initial forces) "
+                    "and the rebuilds; "
                     "block steps are summed over clusters; latency = device time of one global block step"}
 
 
@@ -390,7 +399,7 @@ def _serving(hh, a):
     reqs = [serve.SimRequest(r.rid, None, None, None, r.t_end, arrival_s=r.arrival_s,
                              make=(lambda n=r.n, sd=r.seed: synth.plummer_salpeter(n, sd))) for r in stream]
     srv = serve.Server(precision=hh.HH_MIXED, budget_bytes=150 * 10 ** 9, max_sims=256, max_steps=32,
-                       n_crit=a.n_crit, rebuild_threads=8)
+                       n_crit=a.n_crit, rebuild_threads=8, rebuild_device=a.rebuild == "device")
     res, st = srv.run(reqs, realtime=True, max_wall_s=a.serve_seconds)
     srv.close()
     return {"requests_arrived": sum(1 for r in stream if r.arrival_s <= st.wall_s), "completed": len(res),
@@ -416,7 +425,7 @@ def _split(r, steps):
     if not any(ph):
         return {"force_kernel": r["force_ms"] / steps, "other": (r["ms"] - r["force_ms"]) / steps}
     return {"predict_select": ph[0] / steps, "force": ph[1] / steps, "correct": ph[2] / steps,
-            "host_rebuild_and_launch": (r["ms"] - sum(ph)) / steps}
+            "rebuild_and_launch": (r["ms"] - sum(ph)) / steps}
 
 
 def _cpu_baseline(a, seed):
@@ -550,6 +559,7 @@ def main():
                     "h2d_bytes_per_step": res["e2e"]["bi"], "d2h_bytes_per_step": res["e2e"]["bo"]},
             "gpu_launches": int(tot[3]),
             "loop": a.loop,
+            "rebuild": a.rebuild,
             "tuning": {"fp64": {"chosen": best64, "candidates": table64},
                        "mixed": {"chosen": bestmx, "candidates": tablemx},
                        "note": "autotuner runs before the timed region (paper_1602_02832_gb300/autotune.py)"},

@@ -169,6 +169,14 @@ int hh_advance(hh_ctx *ctx, double t_end, int64_t *n_steps_out);
  * particles must be at time t. */
 int hh_rebuild(hh_ctx *ctx, double t);
 
+/* Selects where hh_rebuild builds the tree and lists: on_device = 0 (the
+ * default) uses the host builder (hh_tree_build, with host copies of the
+ * state); 1 builds them on the GPU with the same rules (Morton keys, pre-order
+ * cells, maximal groups, the same opening walk) without leaving the device.
+ * The device builder sums node moments in a different order than the host
+ * builder, so a node's centre of mass can differ in the last bits. */
+int hh_set_rebuild_device(hh_ctx *ctx, int on_device);
+
 /* Loads n particles (host SoA, any order) at time t with a = jk = 0 and
  * assigns them ids 0..n-1; hh_get_ids reports each slot's id after Morton
  * reordering. */
@@ -184,6 +192,14 @@ int hh_run(hh_ctx *ctx, double t0, double t_end);
 /* Copies particle state [0, n_particles) to host SoA arrays (any may be NULL). */
 int hh_get_state(hh_ctx *ctx, double *x, double *v, double *a, double *jk, double *t, double *dt);
 int hh_get_ids(hh_ctx *ctx, int64_t *ids);
+/* The current lists (step 1 output): group count, list length, and host
+ * copies of off[n_groups + 1], idx[list_len], group_of[n_particles] (any
+ * array may be NULL; call with NULL arrays first to size them). */
+int hh_get_lists(hh_ctx *ctx, int32_t *n_groups, int64_t *list_len, int64_t *off, int32_t *idx, int32_t *group_of);
+/* Host SoA copies of j entries [first, first + count): x, v, a, jk [3][count],
+ * m, t [count] (any may be NULL), e.g. the node records after a rebuild. */
+int hh_get_j(hh_ctx *ctx, int64_t first, int64_t count, double *x, double *v, double *a, double *jk, double *m,
+             double *t);
 int64_t hh_n_particles(const hh_ctx *ctx);
 int64_t hh_n_j(const hh_ctx *ctx);
 int hh_get_counters(hh_ctx *ctx, hh_counters *out);

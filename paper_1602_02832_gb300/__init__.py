@@ -96,6 +96,9 @@ _SIGS = {
     "hh_batch_last_error": (C.c_char_p, [_P]),
     "hh_ctx_device_bytes": (C.c_int64, [_P]),
     "hh_barrier_selftest": (C.c_int, [C.c_int, C.c_int, _D]),
+    "hh_set_rebuild_device": (C.c_int, [_P, C.c_int]),
+    "hh_get_lists": (C.c_int, [_P, _I32, _I64, _I64, _I32, _I32]),
+    "hh_get_j": (C.c_int, [_P, C.c_int64, C.c_int64, _D, _D, _D, _D, _D, _D]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -253,6 +256,9 @@ class Context:
     def hh_rebuild(self, t):
         self._c(_lib.hh_rebuild(self.h, float(t)))
 
+    def hh_set_rebuild_device(self, on=True):
+        self._c(_lib.hh_set_rebuild_device(self.h, int(bool(on))))
+
     def hh_load_particles(self, x, v, m, t=0.0):
         n = len(m)
         self._c(_lib.hh_load_particles(self.h, n, _ptr(_f64(x, (3, n))), _ptr(_f64(v, (3, n))),
@@ -276,6 +282,22 @@ class Context:
         t, dt = np.zeros(n), np.zeros(n)
         self._c(_lib.hh_get_state(self.h, *[_ptr(u) for u in (x, v, a, jk, t, dt)]))
         return dict(x=x, v=v, a=a, jk=jk, t=t, dt=dt)
+
+    def hh_get_lists(self):
+        g, L = C.c_int32(), C.c_int64()
+        self._c(_lib.hh_get_lists(self.h, C.byref(g), C.byref(L), None, None, None))
+        off = np.zeros(g.value + 1, np.int64)
+        idx = np.zeros(max(L.value, 1), np.int32)
+        gof = np.zeros(self.n, np.int32)
+        self._c(_lib.hh_get_lists(self.h, None, None, _ptr(off, C.c_int64), _ptr(idx, C.c_int32),
+                                  _ptr(gof, C.c_int32)))
+        return off, idx[:L.value], gof
+
+    def hh_get_j(self, first, count):
+        x, v, a, jk = (np.zeros((3, count)) for _ in range(4))
+        m, t = np.zeros(count), np.zeros(count)
+        self._c(_lib.hh_get_j(self.h, int(first), int(count), *[_ptr(u) for u in (x, v, a, jk, m, t)]))
+        return dict(x=x, v=v, a=a, jk=jk, m=m, t=t)
 
     def hh_get_ids(self):
         ids = np.zeros(self.n, np.int64)

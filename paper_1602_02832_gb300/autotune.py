@@ -36,12 +36,12 @@ CANDIDATES = {
 _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 
-def _key(device_name, precision, n, theta):
+def _key(device_name, precision, n, theta, rebuild_device):
     return f"{device_name}|{'mixed' if precision == HH_MIXED else 'fp64'}|n2^{round(math.log2(max(n, 2)))}|" \
-           f"theta{theta}"
+           f"theta{theta}|{'dev' if rebuild_device else 'host'}"
 
 
-def _run_candidate(x, v, m, base, cand, intervals, warm):
+def _run_candidate(x, v, m, base, cand, intervals, warm, rebuild_device):
     n = len(m)
     cfg = hh_config_default()
     for f, _ in base._fields_:
@@ -54,6 +54,7 @@ def _run_candidate(x, v, m, base, cand, intervals, warm):
     with Context(cfg, n, 2 * n, int(2 * len(T.idx)) + 1024, 2 * T.n_groups + 64) as ctx, \
             Batch(cfg.precision, max_sims=1, max_steps=4096) as b:
         ctx.hh_load_particles(np.ascontiguousarray(x.T), np.ascontiguousarray(v.T), m)
+        ctx.hh_set_rebuild_device(rebuild_device)
         ctx.hh_run(0.0, 0.0)
         t = 0.0
 
@@ -77,15 +78,17 @@ def _run_candidate(x, v, m, base, cand, intervals, warm):
         return (c1["particle_steps"] - c0["particle_steps"]) / dt, (c1["interactions"] - c0["interactions"]) / dt
 
 
-def tune(x, v, m, base_cfg, intervals=1, warm=1, use_cache=True, device_name=None):
-    """Returns (best candidate dict, table of (candidate, particle steps/s, interactions/s))."""
+def tune(x, v, m, base_cfg, intervals=1, warm=1, use_cache=True, device_name=None, rebuild_device=False):
+    """Returns (best candidate dict, table of (candidate, particle steps/s, interactions/s)).
+    rebuild_device selects where the tuning runs rebuild the tree (the cost of
+    a rebuild depends on n_crit, so the choice is part of the cache key)."""
     if device_name is None:
         try:
             import torch
             device_name = torch.cuda.get_device_name(0)
         except Exception:
             device_name = "cuda"
-    key = _key(device_name, base_cfg.precision, len(m), round(base_cfg.theta, 3))
+    key = _key(device_name, base_cfg.precision, len(m), round(base_cfg.theta, 3), rebuild_device)
     cache = {}
     if use_cache and os.path.exists(_CACHE):
         try:
@@ -96,7 +99,7 @@ def tune(x, v, m, base_cfg, intervals=1, warm=1, use_cache=True, device_name=Non
             return cache[key]["best"], cache[key]["table"]
     table = []
     for cand in CANDIDATES[base_cfg.precision]:
-        steps_rate, int_rate = _run_candidate(x, v, m, base_cfg, cand, intervals, warm)
+        steps_rate, int_rate = _run_candidate(x, v, m, base_cfg, cand, intervals, warm, rebuild_device)
         table.append((cand, steps_rate, int_rate))
     best = max(table, key=lambda r: r[1])[0]
     if use_cache:

@@ -13,7 +13,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhh.so")
 PEAKS_LIB = os.path.join(HERE, "libhh_peaks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU = ["hh_api.cu", "hh_static.cu", "hh_batch.cu"]
+CU = ["hh_api.cu", "hh_static.cu", "hh_batch.cu", "hh_gtree.cu"]
 CPP = ["hh_tree.cpp"]
 HEADERS = ["hh_internal.h", "hh_kernels.cuh", "hh_ctx.h"]
 

@@ -165,6 +165,17 @@ int sync_and_check(hh_ctx *ctx)
     return HH_OK;
 }
 
+// Particle ids follow the slots; after device rebuilds they live on the device.
+int sync_ids_to_host(hh_ctx *ctx)
+{
+    if (!ctx->ids_on_device || !ctx->gtree) return HH_OK;
+    CK(cudaMemcpyAsync(ctx->ids.data(), hh_gtree_ids(ctx->gtree), sizeof(int64_t) * ctx->n, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->ids_on_device = false;
+    return HH_OK;
+}
+
 int check_ctx(hh_ctx *ctx)
 {
     if (!ctx) return hh_set_global_error(HH_EINVAL, "NULL context");
@@ -374,6 +385,7 @@ int hh_destroy(hh_ctx *ctx)
     if (ctx->h_ibuf) cudaFreeHost(ctx->h_ibuf);
     if (ctx->h_jbuf) cudaFreeHost(ctx->h_jbuf);
     if (ctx->tree) hh_tree_free(ctx->tree);
+    if (ctx->gtree) hh_gtree_free(ctx->gtree);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
     return HH_OK;
@@ -533,9 +545,38 @@ int hh_set_lists(hh_ctx *ctx, int64_t n_particles, int64_t n_j, int32_t n_groups
 namespace {
 // `trusted`: lists made by this library's own builder skip the per-entry
 // index scan (they are valid by construction); everything else is checked.
+// Work items and partial sums grow with the lists; kernels captured in the
+// loop graph hold the old pointers, so the graph is rebuilt.
+int ensure_parts(hh_ctx *ctx, int64_t total_parts)
+{
+    if (total_parts <= ctx->cap_parts) return HH_OK;
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int64_t cap = total_parts + total_parts / 4 + 64;
+    int4 *items = nullptr;
+    void *partials = nullptr;
+    if (cudaMalloc(&items, sizeof(int4) * cap) != cudaSuccess ||
+        cudaMalloc(&partials, sizeof(RedF64) * kMaxTileI * cap) != cudaSuccess) {
+        cudaGetLastError();
+        if (items) cudaFree(items);
+        return fail(ctx, HH_ENOMEM, "cannot grow the work-item buffers");
+    }
+    cudaFree(ctx->items);
+    cudaFree(ctx->partials);
+    ctx->device_bytes += (cap - ctx->cap_parts) * int64_t(sizeof(int4) + sizeof(RedF64) * kMaxTileI);
+    ctx->items = items;
+    ctx->partials = partials;
+    ctx->cap_parts = cap;
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    return HH_OK;
+}
+
 int set_lists_core(hh_ctx *ctx, int64_t n_particles, int64_t n_j, int32_t n_groups, const int64_t *off,
                    const int32_t *idx, const int32_t *group_of, bool trusted)
 {
+    int rc = HH_OK;
     if (n_particles < 1 || n_particles > ctx->cap_n || n_j < n_particles || n_j > ctx->cap_j)
         return fail(ctx, HH_EINVAL, "hh_set_lists: n_particles / n_j out of capacity");
     if (n_groups < 1 || n_groups > ctx->cap_g || !off || !idx || !group_of)
@@ -569,30 +610,7 @@ int set_lists_core(hh_ctx *ctx, int64_t n_particles, int64_t n_j, int32_t n_grou
     }
     if (int64_t(tiles.size()) > ctx->cap_tiles) return fail(ctx, HH_ENOMEM, "hh_set_lists: too many tiles");
     if (total_parts > INT32_MAX / 2) return fail(ctx, HH_ENOMEM, "hh_set_lists: too many list parts");
-    if (total_parts > ctx->cap_parts) {
-        // work items and partial sums grow with the lists; kernels captured in
-        // the loop graph hold the old pointers, so the graph is rebuilt
-        CK(cudaStreamSynchronize(ctx->stream));
-        const int64_t cap = total_parts + total_parts / 4 + 64;
-        int4 *items = nullptr;
-        void *partials = nullptr;
-        if (cudaMalloc(&items, sizeof(int4) * cap) != cudaSuccess ||
-            cudaMalloc(&partials, sizeof(RedF64) * kMaxTileI * cap) != cudaSuccess) {
-            cudaGetLastError();
-            if (items) cudaFree(items);
-            return fail(ctx, HH_ENOMEM, "hh_set_lists: cannot grow the work-item buffers");
-        }
-        cudaFree(ctx->items);
-        cudaFree(ctx->partials);
-        ctx->device_bytes += (cap - ctx->cap_parts) * int64_t(sizeof(int4) + sizeof(RedF64) * kMaxTileI);
-        ctx->items = items;
-        ctx->partials = partials;
-        ctx->cap_parts = cap;
-        if (ctx->graph) {
-            cudaGraphExecDestroy(ctx->graph);
-            ctx->graph = nullptr;
-        }
-    }
+    if ((rc = ensure_parts(ctx, total_parts))) return rc;
     CK(cudaMemcpyAsync(ctx->off, off, sizeof(int64_t) * (n_groups + 1), cudaMemcpyHostToDevice, ctx->stream));
     if (L) CK(cudaMemcpyAsync(ctx->idx, idx, sizeof(int32_t) * L, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->group_of, group_of, sizeof(int32_t) * n_particles, cudaMemcpyHostToDevice, ctx->stream));
@@ -766,7 +784,7 @@ int hh_get_state(hh_ctx *ctx, double *x, double *v, double *a, double *jk, doubl
 {
     int rc = check_ctx(ctx);
     if (rc) return rc;
-    if (!ctx->have_lists) return fail(ctx, HH_ESTATE, "hh_get_state: no particles");
+    if (!ctx->have_lists) return fail(ctx, HH_ESTATE, "hh_get_state: no tree yet (call hh_rebuild, hh_set_lists or hh_run)");
     const int64_t n = ctx->n;
     double *src[4] = {ctx->st.x, ctx->st.v, ctx->st.a, ctx->st.jk};
     double *dst[4] = {x, v, a, jk};
@@ -784,7 +802,43 @@ int hh_get_state(hh_ctx *ctx, double *x, double *v, double *a, double *jk, doubl
 int hh_get_ids(hh_ctx *ctx, int64_t *ids)
 {
     if (!ctx || !ids) return hh_set_global_error(HH_EINVAL, "hh_get_ids: NULL");
+    int rc = sync_ids_to_host(ctx);
+    if (rc) return rc;
     std::copy(ctx->ids.begin(), ctx->ids.end(), ids);
+    return HH_OK;
+}
+
+int hh_get_lists(hh_ctx *ctx, int32_t *n_groups, int64_t *list_len, int64_t *off, int32_t *idx, int32_t *group_of)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (!ctx->have_lists) return fail(ctx, HH_ESTATE, "hh_get_lists: no lists");
+    if (n_groups) *n_groups = ctx->n_groups;
+    if (list_len) *list_len = ctx->list_len;
+    if (off) CK(cudaMemcpyAsync(off, ctx->off, sizeof(int64_t) * (ctx->n_groups + 1), cudaMemcpyDeviceToHost, ctx->stream));
+    if (idx && ctx->list_len)
+        CK(cudaMemcpyAsync(idx, ctx->idx, sizeof(int32_t) * ctx->list_len, cudaMemcpyDeviceToHost, ctx->stream));
+    if (group_of) CK(cudaMemcpyAsync(group_of, ctx->group_of, sizeof(int32_t) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return HH_OK;
+}
+
+int hh_get_j(hh_ctx *ctx, int64_t first, int64_t count, double *x, double *v, double *a, double *jk, double *m,
+             double *t)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (first < 0 || count < 0 || first + count > ctx->nj) return fail(ctx, HH_EINVAL, "hh_get_j: range outside [0, n_j)");
+    double *src[4] = {ctx->st.x, ctx->st.v, ctx->st.a, ctx->st.jk};
+    double *dst[4] = {x, v, a, jk};
+    for (int f = 0; f < 4; f++)
+        if (dst[f])
+            for (int d = 0; d < 3; d++)
+                CK(cudaMemcpyAsync(dst[f] + d * count, src[f] + d * ctx->cap_j + first, sizeof(double) * count,
+                                   cudaMemcpyDeviceToHost, ctx->stream));
+    if (m) CK(cudaMemcpyAsync(m, ctx->st.m + first, sizeof(double) * count, cudaMemcpyDeviceToHost, ctx->stream));
+    if (t) CK(cudaMemcpyAsync(t, ctx->st.t + first, sizeof(double) * count, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     return HH_OK;
 }
 
@@ -840,8 +894,48 @@ int hh_load_particles(hh_ctx *ctx, int64_t n, const double *x, const double *v, 
     ctx->nj = n;
     ctx->ids.resize(size_t(n));
     for (int64_t q = 0; q < n; q++) ctx->ids[size_t(q)] = q;
+    ctx->ids_on_device = false;
     ctx->have_lists = false;
     ctx->have_dt = false;
+    return HH_OK;
+}
+
+}  // extern "C"
+
+
+// Completes a device rebuild (hh_gtree.cu): work-item capacity, sizes,
+// mixed-form base records; the state buffers were swapped, so the loop graph
+// is rebuilt on the next hh_advance.
+int hh_finish_device_rebuild(hh_ctx *ctx, int64_t total_parts)
+{
+    int rc = ensure_parts(ctx, total_parts);
+    if (rc) return rc;
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    k_set_sizes<<<1, 1, 0, ctx->stream>>>(ctx->ds, ctx->n, ctx->nj, ctx->n_tiles, ctx->part_len, ctx->cfg.work_item);
+    CKL();
+    if (ctx->st.base) {
+        k_refresh_base<<<ctx->elem_grid, 256, 0, ctx->stream>>>(ctx->st, 0, ctx->nj);
+        CKL();
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->total_parts = total_parts;
+    ctx->have_j = true;
+    ctx->have_lists = true;
+    ctx->predicted = false;
+    ctx->rebuilds++;
+    return HH_OK;
+}
+
+extern "C" {
+
+int hh_set_rebuild_device(hh_ctx *ctx, int on_device)
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    ctx->rebuild_device = on_device != 0;
     return HH_OK;
 }
 
@@ -850,6 +944,13 @@ int hh_rebuild(hh_ctx *ctx, double t)
     int rc = check_ctx(ctx);
     if (rc) return rc;
     if (!ctx->have_j || ctx->n < 2) return fail(ctx, HH_ESTATE, "hh_rebuild: no particles loaded");
+    if (ctx->rebuild_device) {
+        if (ctx->gtree && !ctx->ids_on_device &&
+            hh_gtree_set_ids(ctx->gtree, ctx->ids.data(), ctx->n, ctx->stream) != HH_OK)
+            return fail(ctx, HH_ECUDA, "hh_rebuild: id upload failed");
+        return hh_rebuild_device(ctx, t);
+    }
+    if ((rc = sync_ids_to_host(ctx))) return rc;
     const int64_t n = ctx->n;
     double *H = ctx->h_buf;  // pinned: x v a jk [3][n] each, then m, t, dt
     double *hx = H, *hv = H + 3 * n, *ha = H + 6 * n, *hj = H + 9 * n, *hm = H + 12 * n, *ht = H + 13 * n;

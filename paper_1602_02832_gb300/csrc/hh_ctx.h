@@ -16,6 +16,14 @@ constexpr int kTjMix = 256;  // list entries staged per chunk, mixed form
 // Adds n to the process-wide count of kernels launched by libhh.
 void hh_count_launches(int64_t n);
 
+struct GTreeBuf;  // device tree-builder buffers (hh_gtree.cu)
+void hh_gtree_free(GTreeBuf *g);
+int64_t *hh_gtree_ids(GTreeBuf *g);
+int hh_gtree_set_ids(GTreeBuf *g, const int64_t *ids, int64_t n, cudaStream_t st);
+struct hh_ctx;
+int hh_rebuild_device(hh_ctx *ctx, double t);        // hh_gtree.cu
+int hh_finish_device_rebuild(hh_ctx *ctx, int64_t total_parts);  // hh_api.cu
+
 struct hh_ctx {
     int device = 0;
     hh_config cfg{};
@@ -48,6 +56,9 @@ struct hh_ctx {
     int32_t *h_ibuf = nullptr; // [cap_n]
     double *h_jbuf = nullptr;  // [14 * cap_j] staging of the rebuilt j entries
     hh_tree *tree = nullptr;   // host tree reused by hh_rebuild
+    GTreeBuf *gtree = nullptr; // device tree builder (rebuild_device)
+    bool rebuild_device = false;
+    bool ids_on_device = false;  // particle ids kept by the device builder
     std::vector<int64_t> ids;  // slot -> particle id
     std::vector<int32_t> h_group_of;
     // grid shapes

@@ -1,0 +1,931 @@
+// Tree-loop step 1 on the device (Section 2): Morton octree, Barnes groups
+// and interaction lists built from the synchronised particle state without
+// leaving the GPU, then the particles reordered into Morton order and the
+// node records written behind them.  The rules are those of the host builder
+// (include/hh.h, hh_tree_build): root cube from the bounding box, 21-bit
+// Morton keys, cells split while they hold more than `leaf` particles,
+// pre-order cell numbering, groups = maximal cells with <= n_crit particles,
+// the same opening walk.  Node moments are warp sums (the host sums in
+// index order), so a node's centre of mass may differ in the last bits.
+//
+// CUB (shipped with the CUDA toolkit) provides the radix sort of the keys and
+// the prefix sums; every other step is a kernel of this file.
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+
+#include "hh_ctx.h"
+
+using namespace hh;
+
+namespace {
+
+constexpr int kBits = 21;
+constexpr int kMaxDepth = 21;
+
+// ------------------------------------------------------------ small helpers
+__device__ __forceinline__ unsigned long long order_bits(double v)  // monotone map double -> u64
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double from_order_bits(unsigned long long o)
+{
+    const unsigned long long b = (o >> 63) ? (o & 0x7fffffffffffffffull) : ~o;
+    return __longlong_as_double((long long)b);
+}
+
+__device__ __forceinline__ uint64_t spread_bits(uint32_t v)
+{
+    uint64_t x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x001f00000000ffffull;
+    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__device__ __forceinline__ int digit_at(uint64_t key, int depth) { return int((key >> (3 * (kBits - 1 - depth))) & 7u); }
+
+struct Box {
+    unsigned long long lo[3], hi[3];  // order bits
+    int32_t bad;                      // a particle not at the tree time
+};
+
+// ------------------------------------------------------------ kernels
+__global__ void k_box_init(Box *b)
+{
+    for (int d = 0; d < 3; d++) {
+        b->lo[d] = ~0ull;
+        b->hi[d] = 0ull;
+    }
+    b->bad = 0;
+}
+
+__global__ void k_box(const State s, int64_t n, double t_tree, Box *b)
+{
+    unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int d = 0; d < 3; d++) {
+            const unsigned long long o = order_bits(s.x[d * s.cap_j + i]);
+            lo[d] = o < lo[d] ? o : lo[d];
+            hi[d] = o > hi[d] ? o : hi[d];
+        }
+        bad |= s.t[i] != t_tree;
+    }
+    for (int d = 0; d < 3; d++) {
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo[d], off);
+            const unsigned long long h2 = __shfl_xor_sync(0xffffffffu, hi[d], off);
+            lo[d] = l2 < lo[d] ? l2 : lo[d];
+            hi[d] = h2 > hi[d] ? h2 : hi[d];
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&b->lo[d], lo[d]);
+            atomicMax(&b->hi[d], hi[d]);
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(&b->bad, 1);
+}
+
+__global__ void k_keys(const State s, int64_t n, const Box *b, uint64_t *key, int32_t *idx, double *root_side,
+                       float *xmax)
+{
+    double lo[3], side = 0.0;
+    for (int d = 0; d < 3; d++) {
+        lo[d] = from_order_bits(b->lo[d]);
+        const double ext = from_order_bits(b->hi[d]) - lo[d];
+        if (ext > side) side = ext;
+    }
+    if (side == 0.0) side = 1.0;
+    const double scale = double(1u << kBits) / side;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *root_side = side;
+        double xm = 0.0;  // bound on |coordinate| of every particle, node and group box
+        for (int d = 0; d < 3; d++) xm = fmax(xm, fmax(fabs(lo[d]), fabs(from_order_bits(b->hi[d]))));
+        *xmax = float(xm) * 1.0001f;
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k = 0;
+        for (int d = 0; d < 3; d++) {
+            double f = floor((s.x[d * s.cap_j + i] - lo[d]) * scale);
+            f = f < 0.0 ? 0.0 : f;
+            f = f > double((1u << kBits) - 1u) ? double((1u << kBits) - 1u) : f;
+            k |= spread_bits(uint32_t(f)) << (2 - d);
+        }
+        key[i] = k;
+        idx[i] = int32_t(i);
+    }
+}
+
+// BFS level arrays: cells of one level are contiguous; children of a cell are
+// contiguous in the next level.
+struct Cells {
+    int32_t *begin, *end, *depth, *nchild, *first;  // first: BFS index of the first child
+    int32_t *parent;                                 // BFS index of the parent (-1 root)
+    int32_t *size;                                   // cells in the subtree
+    int32_t *pre;                                    // pre-order number
+};
+
+// counts the children of each cell of a level (binary search per octant)
+__global__ void k_count_children(Cells C, const uint64_t *key, int32_t c0, int32_t nc, int leaf, int32_t *cnt)
+{
+    for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
+        const int32_t c = c0 + q;
+        const int32_t b = C.begin[c], e = C.end[c], d = C.depth[c];
+        int nch = 0;
+        if (e - b > leaf && d < kMaxDepth) {
+            int32_t lo = b;
+            for (int o = 0; o < 8 && lo < e; o++) {
+                int32_t l = lo, h = e;  // first index with digit > o
+                while (l < h) {
+                    const int32_t mid = (l + h) >> 1;
+                    if (digit_at(key[mid], d) <= o) l = mid + 1;
+                    else h = mid;
+                }
+                if (l > lo) nch++;
+                lo = l;
+            }
+        }
+        C.nchild[c] = nch;
+        cnt[q] = nch;
+    }
+}
+
+__global__ void k_write_children(Cells C, const uint64_t *key, int32_t c0, int32_t nc, int leaf, const int32_t *offs,
+                                 int32_t next0)
+{
+    for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
+        const int32_t c = c0 + q;
+        const int32_t b = C.begin[c], e = C.end[c], d = C.depth[c];
+        int32_t w = next0 + offs[q];
+        C.first[c] = w;
+        if (C.nchild[c] == 0) continue;
+        int32_t lo = b;
+        for (int o = 0; o < 8 && lo < e; o++) {
+            int32_t l = lo, h = e;
+            while (l < h) {
+                const int32_t mid = (l + h) >> 1;
+                if (digit_at(key[mid], d) <= o) l = mid + 1;
+                else h = mid;
+            }
+            if (l > lo) {
+                C.begin[w] = lo;
+                C.end[w] = l;
+                C.depth[w] = d + 1;
+                C.parent[w] = c;
+                w++;
+            }
+            lo = l;
+        }
+        (void)leaf;
+    }
+}
+
+__global__ void k_subtree_size(Cells C, int32_t c0, int32_t nc)
+{
+    for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
+        const int32_t c = c0 + q;
+        int32_t sz = 1;
+        for (int k = 0; k < C.nchild[c]; k++) sz += C.size[C.first[c] + k];
+        C.size[c] = sz;
+    }
+}
+
+__global__ void k_preorder(Cells C, int32_t c0, int32_t nc)
+{
+    for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
+        const int32_t c = c0 + q;
+        int32_t run = C.pre[c] + 1;
+        for (int k = 0; k < C.nchild[c]; k++) {
+            const int32_t ch = C.first[c] + k;
+            C.pre[ch] = run;
+            run += C.size[ch];
+        }
+    }
+}
+
+// Pre-order cell table used by the group and list kernels.
+struct PCells {
+    int32_t *begin, *end, *nchild, *parent;
+    int32_t *size;   // cells in the subtree: the subtree of p is [p, p + size)
+    int4 *pack;      // {begin, end, nchild, size}: what the list walk reads per cell
+    float4 *cf;      // {centre of mass x, y, z, side} rounded to FP32 (screening)
+    int32_t *child;  // [8 * n]
+    double *side;
+};
+
+__global__ void k_to_preorder(Cells C, int32_t ncells, PCells P, const double *root_side)
+{
+    const double s0 = *root_side;
+    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+        const int32_t p = C.pre[c];
+        P.begin[p] = C.begin[c];
+        P.end[p] = C.end[c];
+        P.nchild[p] = C.nchild[c];
+        P.size[p] = C.size[c];
+        P.pack[p] = make_int4(C.begin[c], C.end[c], C.nchild[c], C.size[c]);
+        P.parent[p] = C.parent[c] >= 0 ? C.pre[C.parent[c]] : -1;
+        double side = s0;
+        for (int d = 0; d < C.depth[c]; d++) side *= 0.5;
+        P.side[p] = side;
+        for (int k = 0; k < C.nchild[c]; k++) P.child[8 * p + k] = C.pre[C.first[c] + k];
+    }
+}
+
+// State of the reordered particles: new[k] = old[perm[k]] (Morton order).
+__global__ void k_permute(const State src, State dst, const int32_t *perm, int64_t n, const int64_t *ids_src,
+                          int64_t *ids_dst)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = perm[k];
+        for (int d = 0; d < 3; d++) {
+            dst.x[d * dst.cap_j + k] = src.x[d * src.cap_j + i];
+            dst.v[d * dst.cap_j + k] = src.v[d * src.cap_j + i];
+            dst.a[d * dst.cap_j + k] = src.a[d * src.cap_j + i];
+            dst.jk[d * dst.cap_j + k] = src.jk[d * src.cap_j + i];
+        }
+        dst.m[k] = src.m[i];
+        dst.t[k] = src.t[i];
+        dst.dt[k] = src.dt[i];
+        ids_dst[k] = ids_src[i];
+    }
+}
+
+// Node records (pseudo-particles): mass and mass-weighted sums of x, v, a, jk
+// of the members, bottom-up one tree level per launch: a leaf sums its
+// particles, an inner cell the sums of its children.  mom is [13][cap] in BFS
+// cell order.
+__global__ void k_moments_level(const State s, Cells C, int32_t c0, int32_t nc, int64_t cap, double *mom)
+{
+    for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
+        const int32_t c = c0 + q;
+        double acc[13];
+        for (int k = 0; k < 13; k++) acc[k] = 0.0;
+        const int nch = C.nchild[c];
+        if (nch == 0) {
+            for (int32_t p = C.begin[c]; p < C.end[c]; p++) {
+                const double mi = s.m[p];
+                acc[0] += mi;
+                for (int d = 0; d < 3; d++) {
+                    acc[1 + d] += mi * s.x[d * s.cap_j + p];
+                    acc[4 + d] += mi * s.v[d * s.cap_j + p];
+                    acc[7 + d] += mi * s.a[d * s.cap_j + p];
+                    acc[10 + d] += mi * s.jk[d * s.cap_j + p];
+                }
+            }
+        } else {
+            const int32_t f = C.first[c];
+            for (int k = 0; k < nch; k++)
+                for (int w = 0; w < 13; w++) acc[w] += mom[w * cap + f + k];
+        }
+        for (int w = 0; w < 13; w++) mom[w * cap + c] = acc[w];
+    }
+}
+
+// j entry n + (pre-order number) of every cell: centre of mass and
+// mass-weighted mean velocity, acceleration and jerk at the tree time.
+__global__ void k_node_records(State s, Cells C, PCells P, int32_t ncells, int64_t cap, const double *mom, int64_t n,
+                               double t_tree)
+{
+    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+        const int32_t p = C.pre[c];
+        const int64_t j = n + p;
+        const double M = mom[c];
+        s.m[j] = M;
+        s.t[j] = t_tree;
+        double x[3];
+        for (int d = 0; d < 3; d++) {
+            x[d] = mom[(1 + d) * cap + c] / M;
+            s.x[d * s.cap_j + j] = x[d];
+            s.v[d * s.cap_j + j] = mom[(4 + d) * cap + c] / M;
+            s.a[d * s.cap_j + j] = mom[(7 + d) * cap + c] / M;
+            s.jk[d * s.cap_j + j] = mom[(10 + d) * cap + c] / M;
+        }
+        P.cf[p] = make_float4(float(x[0]), float(x[1]), float(x[2]), float(P.side[p]));
+    }
+}
+
+// Groups (Barnes 1990): maximal cells with <= n_crit particles (or leaves).
+__global__ void k_group_flags(PCells P, int32_t ncells, int n_crit, int32_t *flag)
+{
+    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+        const int32_t cnt = P.end[c] - P.begin[c];
+        const bool small = cnt <= n_crit || P.nchild[c] == 0;
+        const int32_t par = P.parent[c];
+        const bool parent_big = par < 0 || !((P.end[par] - P.begin[par]) <= n_crit || P.nchild[par] == 0);
+        flag[c] = (small && parent_big) ? 1 : 0;
+    }
+}
+
+__global__ void k_groups(PCells P, int32_t ncells, const int32_t *flag, const int32_t *gpos, int32_t *g_cell,
+                         int32_t *group_of)
+{
+    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+        if (!flag[c]) continue;
+        const int32_t g = gpos[c];
+        g_cell[g] = c;
+        for (int32_t p = P.begin[c]; p < P.end[c]; p++) group_of[p] = g;
+    }
+}
+
+// Bounding box of each group's particles ([3][G] lo and hi), one warp per group.
+__global__ void k_group_box(const State s, PCells P, int32_t G, const int32_t *g_cell, double *box_lo, double *box_hi,
+                            float4 *box_f)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t g = w0; g < G; g += nw) {
+        const int32_t c = g_cell[g], b = P.begin[c], e = P.end[c];
+        for (int d = 0; d < 3; d++) {
+            double lo = s.x[d * s.cap_j + b], hi = lo;
+            for (int32_t p = b + lane; p < e; p += 32) {
+                const double u = s.x[d * s.cap_j + p];
+                lo = u < lo ? u : lo;
+                hi = u > hi ? u : hi;
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                const double l2 = __shfl_xor_sync(0xffffffffu, lo, off), h2 = __shfl_xor_sync(0xffffffffu, hi, off);
+                lo = l2 < lo ? l2 : lo;
+                hi = h2 > hi ? h2 : hi;
+            }
+            if (lane == 0) {
+                box_lo[d * G + g] = lo;
+                box_hi[d * G + g] = hi;
+            }
+        }
+        if (lane == 0) {
+            box_f[2 * g] = make_float4(float(box_lo[g]), float(box_lo[G + g]), float(box_lo[2 * G + g]), 0.f);
+            box_f[2 * g + 1] = make_float4(float(box_hi[g]), float(box_hi[G + g]), float(box_hi[2 * G + g]), 0.f);
+        }
+    }
+}
+
+// Cut through the tree: the maximal cells whose subtree holds <= S cells.
+// They partition the cells at or below the cut; every cell above it is an
+// ancestor of some cut cell.  Flags in pre-order, compacted by a scan.
+__global__ void k_cut_flags(PCells P, int32_t ncells, int32_t S, int32_t *flag)
+{
+    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+        const int32_t par = P.parent[c];
+        flag[c] = (P.size[c] <= S && (par < 0 || P.size[par] > S)) ? 1 : 0;
+    }
+}
+
+__global__ void k_above_flags(PCells P, int32_t ncells, int32_t S, int32_t *flag)
+{
+    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x)
+        flag[c] = P.size[c] > S ? 1 : 0;
+}
+
+__global__ void k_cut_write(int32_t ncells, const int32_t *flag, const int32_t *pos, int32_t *cut)
+{
+    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x)
+        if (flag[c]) cut[pos[c]] = c;
+}
+
+enum : int { kOpen = 0, kEmitParticles = 1, kEmitNode = 2 };
+
+// The opening decision of cell c for group g (rules of hh_tree_build): the
+// group's own cell and single particles go in as particles; a cell that does
+// not contain the group goes in as a node when side < theta * (distance of its
+// centre of mass to the group's box), else as particles when it is a leaf;
+// everything else is opened.
+//
+// The distance test is screened in FP32 (FP64 throughput is low on this part).
+// With X a bound on |coordinates|, rounding centre, box and side to FP32 and
+// evaluating gaps, squares, sum, sqrtf and the product with theta in FP32
+// moves side - theta * distance by less than
+// 2^-21 (side + theta * distance) + 2^-21 theta X; the screen's margin is
+// 2^-18 (side + theta * distance) + 2^-19 theta X.  Inside the margin the test
+// is redone in FP64 with the roundings of the sequential builder (no
+// contraction), so the decision is always the FP64 one.
+struct GroupView {
+    int32_t gc, gb, ge;
+    double lo[3], hi[3];
+    float3 lof, hif;
+};
+
+__device__ __forceinline__ int decide(const State &s, const PCells &P, int64_t n, double theta, float theta_f,
+                                      float tol_abs, const GroupView &G, int32_t c, int4 &pk)
+{
+    pk = P.pack[c];
+    if (c == G.gc) return kEmitParticles;
+    if (pk.x <= G.gb && G.ge <= pk.y) return kOpen;
+    if (pk.y - pk.x == 1) return kEmitParticles;
+    const float4 cf = P.cf[c];
+    const float gx = fmaxf(fmaxf(G.lof.x - cf.x, cf.x - G.hif.x), 0.f);
+    const float gy = fmaxf(fmaxf(G.lof.y - cf.y, cf.y - G.hif.y), 0.f);
+    const float gz = fmaxf(fmaxf(G.lof.z - cf.z, cf.z - G.hif.z), 0.f);
+    const float rhs = theta_f * sqrtf(gx * gx + gy * gy + gz * gz);
+    const float tol = 0x1p-18f * (cf.w + rhs) + tol_abs;
+    bool accept;
+    if (cf.w < rhs - tol) {
+        accept = true;
+    } else if (cf.w > rhs + tol) {
+        accept = false;
+    } else {
+        double d2 = 0.0;
+        for (int d = 0; d < 3; d++) {
+            const double cm = s.x[d * s.cap_j + n + c];
+            double gap = 0.0;
+            if (cm < G.lo[d]) gap = __dsub_rn(G.lo[d], cm);
+            else if (cm > G.hi[d]) gap = __dsub_rn(cm, G.hi[d]);
+            d2 = __dadd_rn(d2, __dmul_rn(gap, gap));
+        }
+        accept = P.side[c] < __dmul_rn(theta, __dsqrt_rn(d2));
+    }
+    if (accept) return kEmitNode;
+    return pk.z == 0 ? kEmitParticles : kOpen;
+}
+
+// What the list walk kernels read: the pre-order cells, the node records,
+// the groups and their boxes, the opening angle and the FP32 screen's
+// absolute margin (2^-19 theta X).
+struct WalkArgs {
+    State s;
+    PCells P;
+    int64_t n;
+    int32_t G;
+    const int32_t *g_cell;
+    const double *box_lo, *box_hi;
+    const float4 *box_f;
+    double theta;
+    float theta_f;
+    const float *xmax;
+};
+
+__device__ __forceinline__ GroupView group_view(const WalkArgs &W, int32_t g)
+{
+    GroupView V;
+    V.gc = W.g_cell[g];
+    V.gb = W.P.begin[V.gc];
+    V.ge = W.P.end[V.gc];
+    for (int d = 0; d < 3; d++) {
+        V.lo[d] = W.box_lo[d * W.G + g];
+        V.hi[d] = W.box_hi[d * W.G + g];
+    }
+    const float4 l = W.box_f[2 * g], h = W.box_f[2 * g + 1];
+    V.lof = make_float3(l.x, l.y, l.z);
+    V.hif = make_float3(h.x, h.y, h.z);
+    return V;
+}
+
+__device__ __forceinline__ float walk_tol(const WalkArgs &W) { return 0x1p-19f * W.theta_f * *W.xmax; }
+
+// For every (group g, cell above the cut a = above[i]): the topmost cell on
+// the path root -> a that the walk of g does not open (-1: all opened).
+// Cells above the cut are few; this replaces a walk up the tree per
+// (group, cut cell) pair by one table lookup.
+__global__ void k_top_above(const WalkArgs W, const int32_t *above, int32_t A, int32_t *top_above)
+{
+    const float tol = walk_tol(W);
+    const int64_t total = int64_t(W.G) * A;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = int32_t(q / A), i = int32_t(q - int64_t(g) * A);
+        const GroupView V = group_view(W, g);
+        int32_t top = -1;
+        int4 pk;
+        for (int32_t a = above[i]; a >= 0; a = W.P.parent[a])
+            if (decide(W.s, W.P, W.n, W.theta, W.theta_f, tol, V, a, pk) != kOpen) top = a;
+        top_above[q] = top;
+    }
+}
+
+// One thread per (group g, cut cell k).  The topmost cell on the path
+// root -> cut[k] that the walk does not open comes from the table of the
+// parent (above the cut) and the decision on cut[k] itself; if there is one,
+// the leftmost cut cell below it emits it (once); otherwise the thread walks
+// the subtree of cut[k] in pre-order, skipping every emitted cell's subtree.
+// The list of a group is then the concatenation over k in pre-order:
+// particles ascending, then nodes ascending, as in the sequential walk.
+// Pass 0 counts into cnt_p/cnt_n[g * R + k]; pass 1 writes at the scanned
+// offsets.
+template <bool kWrite>
+__global__ void k_lists_cut(const WalkArgs W, const int32_t *cut, int32_t R, const int32_t *above_pos,
+                            const int32_t *top_above, int32_t A, int64_t *cnt_p, int64_t *cnt_n,
+                            const int64_t *scan_p, const int64_t *scan_n, int32_t *idx)
+{
+    const float tol = walk_tol(W);
+    const int64_t total = int64_t(W.G) * R;
+    const int64_t n = W.n;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = int32_t(q / R), k = int32_t(q - int64_t(g) * R);
+        const int32_t r = cut[k], par = W.P.parent[r];
+        int32_t top = par >= 0 ? top_above[int64_t(g) * A + above_pos[par]] : -1;
+        if (top >= 0 && k > 0 && cut[k - 1] >= top) {  // emitted by an earlier cut cell
+            if (!kWrite) cnt_p[q] = cnt_n[q] = 0;
+            continue;
+        }
+        const GroupView V = group_view(W, g);
+        int64_t wp = 0, wn = 0;
+        if (kWrite) {
+            wp = scan_p[q] + scan_n[int64_t(g) * R];
+            wn = scan_p[int64_t(g + 1) * R] + scan_n[q];
+        }
+        int64_t np = 0, nn = 0;
+        int4 pk;
+        int top_dec;
+        if (top >= 0) {
+            top_dec = decide(W.s, W.P, n, W.theta, W.theta_f, tol, V, top, pk);
+        } else {
+            top_dec = decide(W.s, W.P, n, W.theta, W.theta_f, tol, V, r, pk);
+            if (top_dec != kOpen) top = r;
+        }
+        if (top >= 0) {
+            if (top_dec == kEmitNode) {
+                if (kWrite) idx[wn] = int32_t(n + top);
+                nn = 1;
+            } else {
+                if (kWrite)
+                    for (int32_t p = pk.x; p < pk.y; p++) idx[wp++] = p;
+                np = pk.y - pk.x;
+            }
+        } else {
+            const int32_t end = r + pk.w;
+            int32_t c = r + 1;
+            while (c < end) {
+                const int dec = decide(W.s, W.P, n, W.theta, W.theta_f, tol, V, c, pk);
+                if (dec == kOpen) {
+                    c++;
+                    continue;
+                }
+                if (dec == kEmitNode) {
+                    if (kWrite) idx[wn++] = int32_t(n + c);
+                    nn++;
+                } else {
+                    if (kWrite)
+                        for (int32_t p = pk.x; p < pk.y; p++) idx[wp++] = p;
+                    np += pk.y - pk.x;
+                }
+                c += pk.w;
+            }
+        }
+        if (!kWrite) {
+            cnt_p[q] = np;
+            cnt_n[q] = nn;
+        }
+    }
+}
+
+// off[g] = entries of all lists before group g (g = 0..G)
+__global__ void k_list_off(int32_t G, int32_t R, const int64_t *scan_p, const int64_t *scan_n, int64_t *off)
+{
+    for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g <= G; g += gridDim.x * blockDim.x)
+        off[g] = scan_p[int64_t(g) * R] + scan_n[int64_t(g) * R];
+}
+
+// tiles of <= tile_i particles per group, written at tile_off[g]
+__global__ void k_tile_counts(const int32_t *g_cell, PCells P, int32_t G, int tile_i, const int64_t *off, int pj,
+                              int64_t *ntile, int64_t *nparts)
+{
+    for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        const int32_t c = g_cell[g];
+        const int64_t cnt = P.end[c] - P.begin[c];
+        const int64_t nt = (cnt + tile_i - 1) / tile_i;
+        const int64_t L = off[g + 1] - off[g];
+        const int64_t parts = L > 0 ? (L + pj - 1) / pj : 1;
+        ntile[g] = nt;
+        nparts[g] = nt * parts;
+    }
+}
+
+__global__ void k_tiles(const int32_t *g_cell, PCells P, int32_t G, int tile_i, const int64_t *tile_off, int4 *tiles)
+{
+    for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        const int32_t c = g_cell[g];
+        const int32_t b = P.begin[c], e = P.end[c];
+        int64_t t = tile_off[g];
+        for (int32_t p = b; p < e; p += tile_i) tiles[t++] = make_int4(p, min(p + tile_i, e), g, 0);
+    }
+}
+
+template <typename T>
+int cub_exclusive_sum(void *&tmp, size_t &tmp_bytes, const T *in, T *out, int64_t n, cudaStream_t st)
+{
+    size_t need = 0;
+    if (cub::DeviceScan::ExclusiveSum(nullptr, need, in, out, (int)n, st) != cudaSuccess || need == 0) return HH_ECUDA;
+    if (need > tmp_bytes) {
+        if (tmp) cudaFree(tmp);
+        tmp = nullptr;
+        tmp_bytes = 0;
+        if (cudaMalloc(&tmp, need) != cudaSuccess) return HH_ENOMEM;
+        tmp_bytes = need;
+    }
+    return cub::DeviceScan::ExclusiveSum(tmp, need, in, out, (int)n, st) == cudaSuccess ? HH_OK : HH_ECUDA;
+}
+
+}  // namespace
+
+// Buffers of the device builder, owned by the context (allocated on first use).
+struct GTreeBuf {
+    int64_t cap_n = 0, cap_c = 0;
+    uint64_t *key = nullptr, *key2 = nullptr;
+    int32_t *idx = nullptr, *perm = nullptr;
+    Box *box = nullptr;
+    double *root_side = nullptr;
+    float *xmax = nullptr;
+    float4 *box_f = nullptr;
+    Cells C{};
+    PCells P{};
+    int32_t *cnt = nullptr, *offs = nullptr, *gflag = nullptr, *gpos = nullptr, *g_cell = nullptr, *cut = nullptr,
+            *above = nullptr;
+    int64_t *ntile = nullptr, *nparts = nullptr, *tile_off = nullptr, *parts_off = nullptr;
+    double *mom = nullptr;                    // [13][cap_c] cell sums (BFS order)
+    double *box_lo = nullptr, *box_hi = nullptr;  // [3][cap_g] group boxes
+    State alt{};                 // second particle-state buffer for the reordering
+    int64_t *ids = nullptr, *ids2 = nullptr;
+    // (group, cut cell) counts and their scans, grown on demand
+    int64_t *pair_buf = nullptr;
+    int64_t pair_cap = 0;
+    int32_t *top_buf = nullptr;  // [G][A] topmost unopened cell above the cut
+    int64_t top_cap = 0;
+    void *tmp = nullptr;
+    size_t tmp_bytes = 0;
+    std::vector<void *> all;
+};
+
+int64_t *hh_gtree_ids(GTreeBuf *g) { return g->ids; }
+
+// Ordered on the context's stream: the copy lands before the next rebuild's
+// reordering kernel reads the ids (a copy on the legacy stream would not be
+// ordered with a non-blocking stream).
+int hh_gtree_set_ids(GTreeBuf *g, const int64_t *ids, int64_t n, cudaStream_t st)
+{
+    if (cudaMemcpyAsync(g->ids, ids, sizeof(int64_t) * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return HH_ECUDA;
+    return HH_OK;
+}
+
+// The second state set is swapped with the context's at every rebuild, so it
+// is freed through its current pointers (the context frees the other set).
+void hh_gtree_free(GTreeBuf *g)
+{
+    if (!g) return;
+    for (void *p : g->all)
+        if (p) cudaFree(p);
+    for (double *p : {g->alt.x, g->alt.v, g->alt.a, g->alt.jk, g->alt.m, g->alt.t, g->alt.dt})
+        if (p) cudaFree(p);
+    if (g->tmp) cudaFree(g->tmp);
+    if (g->pair_buf) cudaFree(g->pair_buf);
+    if (g->top_buf) cudaFree(g->top_buf);
+    delete g;
+}
+
+namespace {
+
+int gfail(hh_ctx *ctx, int code, const char *m)
+{
+    ctx->err = m;
+    return hh_set_global_error(code, m);
+}
+
+template <typename T>
+bool galloc(GTreeBuf *g, T **p, size_t count, bool track = true)
+{
+    if (cudaMalloc((void **)p, sizeof(T) * (count ? count : 1)) != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return false;
+    }
+    if (track) g->all.push_back(*p);
+    return true;
+}
+
+GTreeBuf *gtree_alloc(hh_ctx *ctx)
+{
+    GTreeBuf *g = new GTreeBuf;
+    const int64_t n = ctx->cap_n, cc = ctx->cap_j;  // cells <= cap_j - n, capped by cap_j
+    g->cap_n = n;
+    g->cap_c = cc;
+    bool ok = galloc(g, &g->key, n) && galloc(g, &g->key2, n) && galloc(g, &g->idx, n) && galloc(g, &g->perm, n) &&
+              galloc(g, &g->box, 1) && galloc(g, &g->root_side, 1) && galloc(g, &g->C.begin, cc) &&
+              galloc(g, &g->C.end, cc) && galloc(g, &g->C.depth, cc) && galloc(g, &g->C.nchild, cc) &&
+              galloc(g, &g->C.first, cc) && galloc(g, &g->C.parent, cc) && galloc(g, &g->C.size, cc) &&
+              galloc(g, &g->C.pre, cc) && galloc(g, &g->P.begin, cc) && galloc(g, &g->P.end, cc) &&
+              galloc(g, &g->P.nchild, cc) && galloc(g, &g->P.parent, cc) && galloc(g, &g->P.child, 8 * cc) &&
+              galloc(g, &g->P.side, cc) && galloc(g, &g->P.size, cc) && galloc(g, &g->P.pack, cc) &&
+              galloc(g, &g->P.cf, cc) && galloc(g, &g->xmax, 1) && galloc(g, &g->box_f, 2 * ctx->cap_g) && galloc(g, &g->cnt, cc) &&
+              galloc(g, &g->offs, cc) && galloc(g, &g->gflag, cc) && galloc(g, &g->gpos, cc) &&
+              galloc(g, &g->g_cell, ctx->cap_g) && galloc(g, &g->cut, cc) && galloc(g, &g->above, cc) && galloc(g, &g->mom, 13 * cc) &&
+              galloc(g, &g->box_lo, 3 * ctx->cap_g) && galloc(g, &g->box_hi, 3 * ctx->cap_g) &&
+              galloc(g, &g->ntile, ctx->cap_g + 1) && galloc(g, &g->nparts, ctx->cap_g + 1) &&
+              galloc(g, &g->tile_off, ctx->cap_g + 1) && galloc(g, &g->parts_off, ctx->cap_g + 1) &&
+              galloc(g, &g->ids, n) && galloc(g, &g->ids2, n);
+    // the second state buffer mirrors the context's (same capacities)
+    g->alt = ctx->st;
+    g->alt.x = g->alt.v = g->alt.a = g->alt.jk = g->alt.m = g->alt.t = g->alt.dt = nullptr;
+    ok = ok && galloc(g, &g->alt.x, 3 * ctx->cap_j, false) && galloc(g, &g->alt.v, 3 * ctx->cap_j, false) &&
+         galloc(g, &g->alt.a, 3 * ctx->cap_j, false) && galloc(g, &g->alt.jk, 3 * ctx->cap_j, false) &&
+         galloc(g, &g->alt.m, ctx->cap_j, false) && galloc(g, &g->alt.t, ctx->cap_j, false) &&
+         galloc(g, &g->alt.dt, n, false);
+    if (!ok) {
+        hh_gtree_free(g);
+        return nullptr;
+    }
+    return g;
+}
+
+int64_t gtree_bytes(const hh_ctx *ctx)
+{
+    const int64_t n = ctx->cap_n, cc = ctx->cap_j, G = ctx->cap_g + 1;
+    return n * (8 * 2 + 4 * 2 + 8 * 2) + cc * (4 * 8 + 4 * 5 + 32 + 8 + 4 * 6 + 13 * 8 + 32) + G * (4 + 8 * 4 + 6 * 8 + 32) +
+           ctx->cap_j * 8 * (12 + 2) + n * 8;
+}
+
+template <typename T>
+T d2h(const T *p, cudaStream_t st)
+{
+    T v{};
+    cudaMemcpyAsync(&v, p, sizeof(T), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    return v;
+}
+
+}  // namespace
+
+// Called by hh_rebuild when the context builds on the device.
+int hh_rebuild_device(hh_ctx *ctx, double t)
+{
+    cudaStream_t st = ctx->stream;
+    const int64_t n = ctx->n;
+    // A non-sticky error left pending by earlier runtime calls would make the
+    // library calls below report failure; every call here is checked itself.
+    cudaGetLastError();
+    if (!ctx->gtree) {
+        ctx->gtree = gtree_alloc(ctx);
+        if (!ctx->gtree) return gfail(ctx, HH_ENOMEM, "hh_rebuild: device tree buffers do not fit");
+        ctx->device_bytes += gtree_bytes(ctx);
+        // particle ids live on the device from now on
+        if (hh_gtree_set_ids(ctx->gtree, ctx->ids.data(), n, st) != HH_OK)
+            return gfail(ctx, HH_ECUDA, "hh_rebuild: id upload failed");
+    }
+    GTreeBuf *g = ctx->gtree;
+    const int grid = ctx->elem_grid;
+    // 1. bounding box, synchronisation check, keys, sort
+    k_box_init<<<1, 1, 0, st>>>(g->box);
+    k_box<<<grid, 256, 0, st>>>(ctx->st, n, t, g->box);
+    k_keys<<<grid, 256, 0, st>>>(ctx->st, n, g->box, g->key, g->idx, g->root_side, g->xmax);
+    if (d2h(&g->box->bad, st)) return gfail(ctx, HH_ESTATE, "hh_rebuild: particles are not synchronised at t");
+    {
+        size_t need = 0;
+        if (cub::DeviceRadixSort::SortPairs(nullptr, need, g->key, g->key2, g->idx, g->perm, (int)n, 0, 63, st) !=
+                cudaSuccess ||
+            need == 0)
+            return gfail(ctx, HH_ECUDA, "hh_rebuild: key sort size query failed");
+        if (need > g->tmp_bytes) {
+            if (g->tmp) cudaFree(g->tmp);
+            g->tmp = nullptr;
+            if (cudaMalloc(&g->tmp, need) != cudaSuccess) return gfail(ctx, HH_ENOMEM, "hh_rebuild: sort buffer");
+            g->tmp_bytes = need;
+        }
+        if (cub::DeviceRadixSort::SortPairs(g->tmp, need, g->key, g->key2, g->idx, g->perm, (int)n, 0, 63, st) !=
+            cudaSuccess)
+            return gfail(ctx, HH_ECUDA, "hh_rebuild: key sort failed");
+    }
+    // 2. cells level by level (BFS), subtree sizes, pre-order numbers
+    const int32_t root_b = 0, root_e = int32_t(n), zero = 0, m1 = -1;
+    cudaMemcpyAsync(g->C.begin, &root_b, 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(g->C.end, &root_e, 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(g->C.depth, &zero, 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(g->C.parent, &m1, 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(g->C.pre, &zero, 4, cudaMemcpyHostToDevice, st);
+    std::vector<int32_t> lvl0{0}, lvln{1};
+    const int64_t cap_cells = ctx->cap_j - n;
+    for (int d = 0; d <= kMaxDepth; d++) {
+        const int32_t c0 = lvl0.back(), nc = lvln.back();
+        k_count_children<<<grid, 256, 0, st>>>(g->C, g->key2, c0, nc, ctx->cfg.leaf, g->cnt);
+        int rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->cnt, g->offs, nc, st);
+        if (rc) return gfail(ctx, rc, "hh_rebuild: scan failed");
+        const int32_t last_off = d2h(g->offs + nc - 1, st), last_cnt = d2h(g->cnt + nc - 1, st);
+        const int32_t next = last_off + last_cnt;
+        if (int64_t(c0) + nc + next > cap_cells)
+            return gfail(ctx, HH_ENOMEM, "hh_rebuild: tree exceeds nj_max (more cells than room for nodes)");
+        k_write_children<<<grid, 256, 0, st>>>(g->C, g->key2, c0, nc, ctx->cfg.leaf, g->offs, c0 + nc);
+        if (next == 0) break;
+        lvl0.push_back(c0 + nc);
+        lvln.push_back(next);
+    }
+    const int32_t ncells = lvl0.back() + lvln.back();
+    for (int l = int(lvl0.size()) - 1; l >= 0; l--)
+        k_subtree_size<<<grid, 256, 0, st>>>(g->C, lvl0[size_t(l)], lvln[size_t(l)]);
+    for (size_t l = 0; l < lvl0.size(); l++) k_preorder<<<grid, 256, 0, st>>>(g->C, lvl0[l], lvln[l]);
+    k_to_preorder<<<grid, 256, 0, st>>>(g->C, ncells, g->P, g->root_side);
+    // 3. particles into Morton order (into the second buffer), then swap
+    k_permute<<<grid, 256, 0, st>>>(ctx->st, g->alt, g->perm, n, g->ids, g->ids2);
+    std::swap(ctx->st.x, g->alt.x);
+    std::swap(ctx->st.v, g->alt.v);
+    std::swap(ctx->st.a, g->alt.a);
+    std::swap(ctx->st.jk, g->alt.jk);
+    std::swap(ctx->st.m, g->alt.m);
+    std::swap(ctx->st.t, g->alt.t);
+    std::swap(ctx->st.dt, g->alt.dt);
+    std::swap(g->ids, g->ids2);
+    // 4. node records (bottom-up moments), groups and their boxes
+    const int64_t cap_c = g->cap_c;
+    for (int l = int(lvl0.size()) - 1; l >= 0; l--)
+        k_moments_level<<<grid, 256, 0, st>>>(ctx->st, g->C, lvl0[size_t(l)], lvln[size_t(l)], cap_c, g->mom);
+    k_node_records<<<grid, 256, 0, st>>>(ctx->st, g->C, g->P, ncells, cap_c, g->mom, n, t);
+    k_group_flags<<<grid, 256, 0, st>>>(g->P, ncells, ctx->cfg.n_crit, g->gflag);
+    int rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->gflag, g->gpos, ncells, st);
+    if (rc) return gfail(ctx, rc, "hh_rebuild: scan failed");
+    const int32_t G = d2h(g->gpos + ncells - 1, st) + d2h(g->gflag + ncells - 1, st);
+    if (G > ctx->cap_g) return gfail(ctx, HH_ENOMEM, "hh_rebuild: more groups than groups_max");
+    k_groups<<<grid, 256, 0, st>>>(g->P, ncells, g->gflag, g->gpos, g->g_cell, ctx->group_of);
+    k_group_box<<<grid, 256, 0, st>>>(ctx->st, g->P, G, g->g_cell, g->box_lo, g->box_hi, g->box_f);
+    WalkArgs W;
+    W.s = ctx->st;
+    W.P = g->P;
+    W.n = n;
+    W.G = G;
+    W.g_cell = g->g_cell;
+    W.box_lo = g->box_lo;
+    W.box_hi = g->box_hi;
+    W.box_f = g->box_f;
+    W.theta = ctx->cfg.theta;
+    W.theta_f = float(ctx->cfg.theta);
+    W.xmax = g->xmax;
+    // 5. lists: cut of subtrees of <= S cells, per-(group, cut cell) counts,
+    //    scans, offsets, write
+    const int32_t S = std::max<int32_t>(32, ncells / 256);
+    k_cut_flags<<<grid, 256, 0, st>>>(g->P, ncells, S, g->cnt);
+    if ((rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->cnt, g->offs, ncells, st)))
+        return gfail(ctx, rc, "hh_rebuild: scan failed");
+    const int32_t R = d2h(g->offs + ncells - 1, st) + d2h(g->cnt + ncells - 1, st);
+    k_cut_write<<<grid, 256, 0, st>>>(ncells, g->cnt, g->offs, g->cut);
+    // cells above the cut (the group flags are free again) and, per group,
+    // the topmost unopened cell on the path to each of them
+    k_above_flags<<<grid, 256, 0, st>>>(g->P, ncells, S, g->gflag);
+    if ((rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->gflag, g->gpos, ncells, st)))
+        return gfail(ctx, rc, "hh_rebuild: scan failed");
+    const int32_t A = d2h(g->gpos + ncells - 1, st) + d2h(g->gflag + ncells - 1, st);
+    k_cut_write<<<grid, 256, 0, st>>>(ncells, g->gflag, g->gpos, g->above);
+    const int64_t top_n = std::max<int64_t>(1, int64_t(G) * A);
+    if (top_n > g->top_cap) {
+        if (g->top_buf) cudaFree(g->top_buf);
+        g->top_buf = nullptr;
+        g->top_cap = 0;
+        if (cudaMalloc(&g->top_buf, sizeof(int32_t) * top_n) != cudaSuccess) {
+            cudaGetLastError();
+            return gfail(ctx, HH_ENOMEM, "hh_rebuild: list walk table does not fit");
+        }
+        g->top_cap = top_n;
+    }
+    if (A > 0)
+        k_top_above<<<unsigned((int64_t(G) * A + 127) / 128), 128, 0, st>>>(W, g->above, A, g->top_buf);
+    const int64_t pairs = int64_t(G) * R;
+    if (pairs + 1 >= int64_t(INT32_MAX)) return gfail(ctx, HH_ENOMEM, "hh_rebuild: too many (group, subtree) pairs");
+    if (4 * (pairs + 1) > g->pair_cap) {
+        if (g->pair_buf) cudaFree(g->pair_buf);
+        g->pair_buf = nullptr;
+        g->pair_cap = 0;
+        if (cudaMalloc(&g->pair_buf, sizeof(int64_t) * 4 * (pairs + 1)) != cudaSuccess) {
+            cudaGetLastError();
+            return gfail(ctx, HH_ENOMEM, "hh_rebuild: list count buffers do not fit");
+        }
+        g->pair_cap = 4 * (pairs + 1);
+    }
+    int64_t *cnt_p = g->pair_buf, *cnt_n = cnt_p + pairs + 1, *scan_p = cnt_n + pairs + 1, *scan_n = scan_p + pairs + 1;
+    const int64_t lgrid = std::min<int64_t>((pairs + 127) / 128, int64_t(1) << 30);
+    k_lists_cut<false><<<unsigned(lgrid), 128, 0, st>>>(W, g->cut, R, g->gpos, g->top_buf, A, cnt_p, cnt_n, nullptr,
+                                                        nullptr, nullptr);
+    cudaMemsetAsync(cnt_p + pairs, 0, sizeof(int64_t), st);
+    cudaMemsetAsync(cnt_n + pairs, 0, sizeof(int64_t), st);
+    if ((rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, cnt_p, scan_p, pairs + 1, st)) ||
+        (rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, cnt_n, scan_n, pairs + 1, st)))
+        return gfail(ctx, rc, "hh_rebuild: scan failed");
+    k_list_off<<<grid, 256, 0, st>>>(G, R, scan_p, scan_n, ctx->off);
+    const int64_t L = d2h(ctx->off + G, st);
+    if (L > ctx->cap_list) return gfail(ctx, HH_ENOMEM, "hh_rebuild: lists exceed list_max");
+    k_lists_cut<true><<<unsigned(lgrid), 128, 0, st>>>(W, g->cut, R, g->gpos, g->top_buf, A, nullptr, nullptr, scan_p,
+                                                       scan_n, ctx->idx);
+    // 6. tiles and their work-item capacity
+    k_tile_counts<<<grid, 256, 0, st>>>(g->g_cell, g->P, G, ctx->tile_i, ctx->off, ctx->part_len, g->ntile, g->nparts);
+    cudaMemsetAsync(g->ntile + G, 0, sizeof(int64_t), st);
+    cudaMemsetAsync(g->nparts + G, 0, sizeof(int64_t), st);
+    if ((rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->ntile, g->tile_off, G + 1, st)) ||
+        (rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->nparts, g->parts_off, G + 1, st)))
+        return gfail(ctx, rc, "hh_rebuild: scan failed");
+    const int64_t n_tiles = d2h(g->tile_off + G, st), total_parts = d2h(g->parts_off + G, st);
+    if (n_tiles > ctx->cap_tiles) return gfail(ctx, HH_ENOMEM, "hh_rebuild: too many tiles");
+    k_tiles<<<grid, 256, 0, st>>>(g->g_cell, g->P, G, ctx->tile_i, g->tile_off, ctx->tiles);
+    const cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) return gfail(ctx, HH_ECUDA, cudaGetErrorString(ce));
+    // kernels of this file: 18 fixed (19 with the table above the cut) plus 5
+    // per tree level (count, write,
+    // subtree size, pre-order, moments); the radix sort and scans are CUB's
+    hh_count_launches(18 + (A > 0 ? 1 : 0) + 5 * int64_t(lvl0.size()));
+    ctx->nj = n + ncells;
+    ctx->n_groups = G;
+    ctx->list_len = L;
+    ctx->n_tiles = int32_t(n_tiles);
+    ctx->ids_on_device = true;
+    return hh_finish_device_rebuild(ctx, total_parts);
+}

@@ -7,7 +7,9 @@ launch (hh_batch_run) that gives each resident simulation up to `max_steps`
 block steps, stopping each at its next tree rebuild time (Section 2: lists are
 rebuilt every dt_tree).  Simulations that reached a rebuild time are rebuilt on
 host threads while the next launch runs the others; finished ones release
-their memory and waiting requests take their place.  A simulation's result
+their memory and waiting requests take their place.  With rebuild_device the
+rebuilds run on the device (on the simulation's own stream) instead of the
+host tree builder.  A simulation's result
 does not depend on what else shares the launches (see hh_batch_run).
 
 The loop itself is thin Python; every step of the path runs in libhh.
@@ -79,8 +81,10 @@ class Server:
     """Continuous batching of block steps across resident simulations."""
 
     def __init__(self, precision=HH_MIXED, budget_bytes=150 * 10 ** 9, max_sims=256, max_steps=64,
-                 eps2=1e-8, eta=0.02, theta=0.5, n_crit=64, dt_tree=2.0 ** -6, rebuild_threads=4, device=0):
+                 eps2=1e-8, eta=0.02, theta=0.5, n_crit=64, dt_tree=2.0 ** -6, rebuild_threads=4, device=0,
+                 rebuild_device=False):
         self.precision = precision
+        self.rebuild_device = bool(rebuild_device)
         self.budget = int(budget_bytes)
         self.max_sims = int(max_sims)
         self.max_steps = int(max_steps)
@@ -116,6 +120,7 @@ class Server:
     def _admit(self, req: SimRequest, caps: dict, now_s: float) -> _Live:
         ctx = Context(self.cfg, device=self.device, **caps)
         ctx.hh_load_particles(np.ascontiguousarray(req.x.T), np.ascontiguousarray(req.v.T), req.m)
+        ctx.hh_set_rebuild_device(self.rebuild_device)
         ctx.hh_run(0.0, 0.0)  # tree, initial forces, node derivatives, initial steps
         return _Live(req, ctx, ctx.device_bytes, min(self.cfg.dt_tree, req.t_end), now_s)
 

@@ -1,0 +1,80 @@
+"""Tree, groups and lists built on the device (hh_set_rebuild_device) against
+the oracle's builder on the same positions.  Both follow the same rules; the
+device sums node moments in another order, so a node's centre of mass may
+differ in the last bits and, very rarely, flip an opening decision at a tie."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hh():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1602_02832_gb300 as hh
+    return hh
+
+
+@pytest.mark.parametrize("n,theta,n_crit,salp", [(3000, 0.5, 64, False), (20000, 0.3, 256, True),
+                                                 (777, 0.0, 32, False), (65536, 0.5, 64, False)])
+def test_device_tree_matches_oracle(hh, orc, n, theta, n_crit, salp):
+    x, v, m = (synth.plummer_salpeter if salp else synth.plummer)(n, 41)
+    cfg = hh.hh_config_default()
+    cfg.theta, cfg.n_crit = theta, n_crit
+    z = np.zeros_like(x)
+    T = orc.tree_build(x, v, z, z, m, leaf=8, n_crit=n_crit, theta=theta)
+    with hh.Context(cfg, n, n + 2 * T.n_cells + 64, 2 * len(T.list_idx) + 1024, 2 * T.n_groups + 64) as ctx:
+        ctx.hh_load_particles(x.T, v.T, m)
+        ctx.hh_set_rebuild_device(True)
+        ctx.hh_rebuild(0.0)
+        ids = ctx.hh_get_ids()
+        off, idx, gof = ctx.hh_get_lists()
+        nodes = ctx.hh_get_j(n, ctx.nj - n)
+    assert np.array_equal(ids, T.perm)                 # Morton order (keys and tie order)
+    assert ctx is not None and len(off) - 1 == T.n_groups
+    assert np.array_equal(gof, T.group_of)
+    np.testing.assert_allclose(nodes["m"], T.node_m, rtol=1e-13)
+    np.testing.assert_allclose(nodes["x"].T, T.node_x, rtol=1e-12, atol=1e-14)
+    same = np.array_equal(off, T.list_off) and np.array_equal(idx, T.list_idx)
+    if not same:  # only rare tie flips are acceptable
+        diff = sum(1 for g in range(T.n_groups)
+                   if not np.array_equal(idx[off[g]:off[g + 1]], T.list_idx[T.list_off[g]:T.list_off[g + 1]]))
+        assert diff <= max(1, T.n_groups // 1000), diff
+    # every list covers all mass exactly once
+    mj = np.concatenate([m[ids], nodes["m"]])
+    sums = np.add.reduceat(mj[idx], off[:-1])
+    np.testing.assert_allclose(sums, 1.0, rtol=1e-12)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_device_rebuild_run_matches_host_rebuild_run(hh, orc, prec):
+    # the whole tree loop with device rebuilds against the same loop with host
+    # rebuilds: identical step counts and energies within roundoff
+    n = 2048
+    x, v, m = synth.plummer(n, 42)
+    eps2 = 1e-6
+    P = hh.HH_FP64 if prec == "fp64" else hh.HH_MIXED
+    out = {}
+    for dev in (False, True):
+        cfg = hh.hh_config_default()
+        cfg.eps2, cfg.precision, cfg.n_crit = eps2, P, 64
+        with hh.Context(cfg, n, 2 * n, 4000 * n // 8, n) as ctx:
+            ctx.hh_load_particles(x.T, v.T, m)
+            ctx.hh_set_rebuild_device(dev)
+            ctx.hh_run(0.0, 3 / 64)
+            st = ctx.hh_get_state()
+            ids = ctx.hh_get_ids()
+            c = ctx.hh_get_counters()
+        xx = np.zeros((n, 3))
+        vv = np.zeros((n, 3))
+        xx[ids] = st["x"].T
+        vv[ids] = st["v"].T
+        out[dev] = (orc.energy(xx, vv, m, eps2), c, xx)
+    E0 = orc.energy(x, v, m, eps2)
+    assert out[True][1]["rebuilds"] == out[False][1]["rebuilds"] == 4
+    assert abs(out[True][1]["particle_steps"] / out[False][1]["particle_steps"] - 1) < 0.01
+    assert abs(out[True][0] - out[False][0]) / abs(E0) < 1e-8
+    assert np.abs(out[True][2] - out[False][2]).max() < 1e-6

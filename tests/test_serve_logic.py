@@ -35,6 +35,9 @@ class FakeCtx:
     def hh_load_particles(self, x, v, m):
         self.x = x.copy()
 
+    def hh_set_rebuild_device(self, on):
+        self.rebuild_device = bool(on)
+
     def hh_run(self, t0, t1):
         self.t = t0
 
