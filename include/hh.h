@@ -169,12 +169,19 @@ int hh_advance(hh_ctx *ctx, double t_end, int64_t *n_steps_out);
  * particles must be at time t. */
 int hh_rebuild(hh_ctx *ctx, double t);
 
-/* Selects where hh_rebuild builds the tree and lists: on_device = 0 (the
- * default) uses the host builder (hh_tree_build, with host copies of the
- * state); 1 builds them on the GPU with the same rules (Morton keys, pre-order
- * cells, maximal groups, the same opening walk) without leaving the device.
- * The device builder sums node moments in a different order than the host
- * builder, so a node's centre of mass can differ in the last bits. */
+/* Selects where hh_rebuild does step 1 of the tree loop (Section 2: tree,
+ * groups of up to n_crit particles, one interaction list per group):
+ * on_device = 0 (the default) uses the host builder (hh_tree_build, with
+ * host copies of the state); 1 builds them on the GPU with the same rules
+ * (21-bit Morton keys, pre-order cells split above `leaf` particles, maximal
+ * groups, the same opening walk and list order) without the state leaving
+ * the device.  The device builder sums node moments bottom-up (children's
+ * sums), so a node's centre of mass can differ from the host builder's in
+ * the last bits; the lists are the same unless an opening test sits exactly
+ * on that difference.  Its buffers (about 300 bytes per j entry plus 150 per
+ * group) are allocated by the first device rebuild and counted in
+ * hh_ctx_device_bytes; that rebuild returns HH_ENOMEM if they do not fit.
+ * Errors: HH_EINVAL for a NULL context. */
 int hh_set_rebuild_device(hh_ctx *ctx, int on_device);
 
 /* Loads n particles (host SoA, any order) at time t with a = jk = 0 and
