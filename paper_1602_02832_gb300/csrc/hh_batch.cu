@@ -2,15 +2,18 @@
 // advances many independent simulations, each by its own block steps (Section 2,
 // tree-loop steps 2-7), until each reaches its stop time or the step budget.
 //
-// A "global step" gives every live simulation one block step, in three
+// A "global step" gives every live simulation one block step, in two
 // phases separated by grid barriers:
 //   1. predict every j entry of every live simulation to its own block time
 //      and append the work items of tiles with active particles (one shared
 //      queue for all simulations);
 //   2. CTAs pull (simulation, tile, list part) items and run the same
-//      force_item body as the single-simulation kernel;
-//   3. correct the active particles and take, per simulation, the min of
-//      t_i + dt_i that starts its next block step.
+//      force_item body as the single-simulation kernel; the worker group
+//      that completes a tile's forces corrects its particles at once and
+//      lowers, per simulation, the min of t_i + dt_i that starts its next
+//      block step.
+// Per-step counters alternate between two copies by step parity, so the
+// copy of the previous step is cleared while this step fills the other.
 // Uneven active sets and list lengths of different simulations share one
 // queue, so small block steps of many simulations fill the GPU together.
 // Results of a simulation do not depend on what else is in the batch: its
@@ -55,8 +58,8 @@ struct BatchScalars {
     unsigned int bar_count;
     unsigned int bar_gen;
     int32_t err;
-    uint32_t work;
-    uint32_t n_items;
+    uint32_t work[2];     // force queue head, by step parity
+    uint32_t n_items[2];  // work items, by step parity
     int32_t steps_done;
 };
 
@@ -170,6 +173,70 @@ __device__ __forceinline__ double due_below_warp(const int32_t *lvl_cnt, double 
     if (k < kmin && __ldcg(&lvl_cnt[k]) > 0) m = (floor(t * pow2i(k)) + 1.0) * pow2i(-k);
     for (int off = 16; off > 0; off >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, off));
     return m;
+}
+
+// Step 6 for the due particles of one tile (mask over its lanes), three
+// lanes per particle (one Cartesian component each), ten particles per warp
+// and round (particles k_first + 10 r' ... of the active list, rounds k_step
+// apart): a warp instruction costs the same on the FP64 pipe whether one lane
+// or 32 are active, so this cuts the corrector's FP64 issue per small step
+// about threefold.  Same arithmetic as correct_particle, component by
+// component.  Returns (in every lane) the minimum of t + dt over the tile's
+// corrected particles and updates the simulation's level histogram.
+__device__ __forceinline__ double correct_tile_3lane(const SimDesc &sd, const int4 td, uint32_t mask, double tnow,
+                                                     int lane, int k_first, int k_step)
+{
+    const unsigned full = 0xffffffffu;
+    const State &s = sd.st;
+    const int na = __popc(mask);
+    const int q = lane / 3, d = lane - 3 * q, g = 3 * q;
+    double tn_min = __longlong_as_double(0x7FF0000000000000LL);
+    for (int base = k_first; base < na; base += k_step) {
+        const int k = base + q;
+        const bool on = lane < 30 && k < na;
+        const int64_t p = on ? td.x + (__fns(mask, 0, k + 1)) : td.x;
+        double sa = 0.0, sj = 0.0, ss = 0.0, st = 0.0, a1 = 0.0, j1 = 0.0, dt_old = 1.0;
+        CorrComp c{};
+        if (on) {
+            dt_old = s.dt[p];
+            const StepPowers P = step_powers(tnow - s.t[p]);
+            const double a0 = s.a[d * s.cap_j + p], j0 = s.jk[d * s.cap_j + p];
+            a1 = s.acc1[d * s.cap_n + p];
+            j1 = s.jerk1[d * s.cap_n + p];
+            c = correct_component(s.x[d * s.cap_j + p], s.v[d * s.cap_j + p], a0, j0, a1, j1, P);
+            sa = sq(a1);
+            sj = sq(j1);
+            ss = sq(c.a2e);
+            st = sq(c.a3);
+        }
+        // the particle's three lanes: g, g + 1, g + 2 (lanes 30, 31 are idle)
+        const double A = norm2_of(__shfl_sync(full, sa, g), __shfl_sync(full, sa, g + 1), __shfl_sync(full, sa, g + 2));
+        const double J = norm2_of(__shfl_sync(full, sj, g), __shfl_sync(full, sj, g + 1), __shfl_sync(full, sj, g + 2));
+        const double S = norm2_of(__shfl_sync(full, ss, g), __shfl_sync(full, ss, g + 1), __shfl_sync(full, ss, g + 2));
+        const double T = norm2_of(__shfl_sync(full, st, g), __shfl_sync(full, st, g + 1), __shfl_sync(full, st, g + 2));
+        __syncwarp();  // every lane has read t and dt before any is rewritten
+        if (on) {
+            const double dtn = block_dt(aarseth_want(A, J, S, T, sd.prm.eta), dt_old, tnow, sd.prm.dt_min,
+                                        sd.prm.dt_max);
+            s.x[d * s.cap_j + p] = c.x;
+            s.v[d * s.cap_j + p] = c.v;
+            s.a[d * s.cap_j + p] = a1;
+            s.jk[d * s.cap_j + p] = j1;
+            if (s.base) refresh_base_component(s, p, d);
+            if (d == 0) {
+                s.t[p] = tnow;
+                s.dt[p] = dtn;
+                const int lv_old = level_of(dt_old), lv_new = level_of(dtn);
+                if (lv_new != lv_old) {
+                    atomicSub(&sd.ds->lvl_cnt[lv_old], 1);
+                    atomicAdd(&sd.ds->lvl_cnt[lv_new & 31], 1);
+                }
+                tn_min = fmin(tn_min, tnow + dtn);
+            }
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) tn_min = fmin(tn_min, __shfl_xor_sync(full, tn_min, off));
+    return tn_min;
 }
 
 // Per-CTA copy of each simulation's block time for the current step
@@ -291,7 +358,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
             ds->tmin[0] = 0x7FF0000000000000ull;
             ds->tmin[1] = 0x7FF0000000000000ull;
             ds->t_cur_bits = 0ull;
-            ds->slot_ctr = 0u;
+            ds->slot_par[0] = ds->slot_par[1] = 0u;
             for (int k = 0; k < 32; k++) ds->lvl_cnt[k] = 0;
         }
     if (blockIdx.x == 0 && tid == 0) B.step_ns[0] = globaltimer_ns();
@@ -356,18 +423,28 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
         const int par = step & 1;
         // ---- phase 1: predict + select
         cache_times(sc, B.sims, n_sims, par);
-        if (blockIdx.x == 0)
+        if (blockIdx.x == 0) {
+            // counters of the previous step (other parity) are free again
+            if (tid == 0) {
+                B.bs->work[par ^ 1] = 0u;
+                B.bs->n_items[par ^ 1] = 0u;
+            }
             for (int s = tid >> 5; s < n_sims; s += blockDim.x >> 5) {
                 // the next block time starts from the due times of the levels
-                // not corrected now; phase 3 lowers it with the corrected ones
+                // not corrected now; the corrector lowers it with the
+                // corrected ones.  A finished simulation keeps its time.
                 DevScalars *ds = B.sims[s].ds;
                 const double tnow = cached_time(sc, B.sims, s, par);
+                const bool live = tnow <= B.sims[s].t_end;
                 const double below = due_below_warp(ds->lvl_cnt, tnow, kmin_of(tnow));
                 if ((tid & 31) == 0) {
-                    ds->tmin[par ^ 1] = (unsigned long long)__double_as_longlong(below);
+                    ds->tmin[par ^ 1] = live ? (unsigned long long)__double_as_longlong(below) : ds->tmin[par];
                     ds->n_act_last = 0;
+                    ds->slot_par[par ^ 1] = 0u;
+                    if (live) ds->block_steps += 1ull;
                 }
             }
+        }
         for (int64_t g = gtid; g < NJ; g += nth) {
             const int s = find_sim(B.jbase, n_sims, g);
             const SimDesc &sd = B.sims[s];
@@ -390,91 +467,70 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                 const bool act = (p < td.y) && (sd.st.t[p] + sd.st.dt[p] == tnow);
                 const uint32_t mask = __ballot_sync(0xffffffffu, act);
                 if (mask)
-                    append_tile_items(sd.L, tile, td, mask, sd.pj, sd.work, &B.bs->n_items, &sd.ds->slot_ctr, B.items,
+                    append_tile_items(sd.L, tile, td, mask, sd.pj, sd.work, &B.bs->n_items[par], &sd.ds->slot_par[par], B.items,
                                       s);
             }
         }
         if (!grid_sync(B.bs)) return;
         if (blockIdx.x == 0 && tid == 0) B.step_ns[3 * step + 1] = globaltimer_ns();
 
-        // ---- phase 2: forces from the shared queue, one item per worker group
+        // ---- phase 2: forces from the shared queue, one item per worker
+        // group; the group that completes a tile corrects its particles
+        // right away (step 6 needs only the particle's own new force)
         {
-            const uint32_t n_items = __ldcg(&B.bs->n_items);
+            const uint32_t n_items = __ldcg(&B.bs->n_items[par]);
             const int bar = 1 + group;
+            const int gw = gt >> 5, glane = gt & 31;
+            // The first item of every group is fixed, round-robin over the
+            // SMs (item i -> SM i mod grid): the few items of a small step
+            // land on different SMs instead of sharing one SM's FP64 pipe.
+            // Later items come from the shared queue.
+            const int n_static = (int)gridDim.x * kGroups;
+            int item = group * (int)gridDim.x + (int)blockIdx.x;
             for (;;) {
-                if (gt == 0) sm.item = (int)atomicAdd(&B.bs->work, 1u);
-                group_sync(bar);
-                const int item = sm.item;
                 if (item >= (int)n_items) break;
                 const int4 it = B.items[item];
-                const SimDesc &sd = B.sims[it.y >> 16];
-                unsigned long long n_int = 0;
-                force_item<Rec, TJ, false>(sd.st, (const Rec *)sd.rec, sd.L, sd.pj, sd.work,
-                                           (typename Traits<Rec>::Eps)sd.prm.eps2, it, sm, n_int, gt, bar);
-                if (gt == 0 && n_int) atomicAdd(&sd.ds->interactions, n_int);
-                group_sync(bar);
-            }
-        }
-        if (!grid_sync(B.bs)) return;
-        if (blockIdx.x == 0 && tid == 0) B.step_ns[3 * step + 2] = globaltimer_ns();
-
-        // ---- phase 3: correct the due particles, tile by tile
-        {
-            // active tiles go round-robin over the CTAs (one SM each), so that
-            // the FP64 corrector work of neighbouring tiles lands on different SMs
-            const uint32_t n_items = __ldcg(&B.bs->n_items);
-            const int lane = tid & 31;
-            const int64_t w0 = blockIdx.x + (int64_t)gridDim.x * (tid >> 5), nw = nth >> 5;
-            for (int64_t wi = w0; wi < n_items; wi += nw) {
-                const int4 it = B.items[wi];
-                if ((it.y & 0xFFFF) != 0) continue;  // one item per active tile: its part 0
                 const int s = it.y >> 16;
                 const SimDesc &sd = B.sims[s];
-                const double tnow = cached_time(sc, B.sims, s, par);
-                const int4 td = sd.L.tiles[it.x];
-                const int64_t p = td.x + lane;
-                const bool act = ((uint32_t)it.z >> lane) & 1u;
-                double tn = __longlong_as_double(0x7FF0000000000000LL);
-                if (act) {
-                    const int lv_old = level_of(sd.st.dt[p]);
-                    correct_particle(sd.st, p, tnow, sd.prm);
-                    const double dtn = sd.st.dt[p];
-                    const int lv_new = level_of(dtn);
-                    tn = tnow + dtn;
-                    if (lv_new != lv_old) {
-                        atomicSub(&sd.ds->lvl_cnt[lv_old], 1);
-                        atomicAdd(&sd.ds->lvl_cnt[lv_new & 31], 1);
+                unsigned long long n_int = 0;
+                const bool done = force_item<Rec, TJ, false>(sd.st, (const Rec *)sd.rec, sd.L, sd.pj, sd.work,
+                                                             (typename Traits<Rec>::Eps)sd.prm.eps2, it, sm, n_int,
+                                                             gt, bar);
+                if (gt == 0 && n_int) atomicAdd(&sd.ds->interactions, n_int);
+                if (done) {
+                    group_sync(bar);  // the tile's new forces are visible to the group
+                    const double tnow = cached_time(sc, B.sims, s, par);
+                    const int4 td = sd.L.tiles[it.x];
+                    const uint32_t mask = (uint32_t)it.z;
+                    const double tn = correct_tile_3lane(sd, td, mask, tnow, glane, 10 * gw, 10 * (kThreads / 32));
+                    if (glane == 0) sm.tn[gw] = tn;
+                    group_sync(bar);  // new steps and times are visible to the group
+                    if (gw == 0) {
+                        const int64_t p = td.x + glane;
+                        const uint32_t bit = (p < td.y) ? (1u << (level_of(sd.st.dt[p]) & 31)) : 0u;
+                        const uint32_t lvm = __reduce_or_sync(0xffffffffu, bit);
+                        if (glane == 0) {
+                            double m = sm.tn[0];
+                            for (int w = 1; w < kThreads / 32; w++) m = fmin(m, sm.tn[w]);
+                            const int c = __popc(mask);
+                            sd.tile_lv[it.x] = lvm;
+                            atomicMin(&sd.ds->tmin[par ^ 1], (unsigned long long)__double_as_longlong(m));
+                            atomicAdd(&sd.ds->particle_steps, (unsigned long long)c);
+                            atomicAdd(&sd.ds->n_act_last, c);
+                        }
                     }
                 }
-                for (int off = 16; off > 0; off >>= 1) tn = fmin(tn, __shfl_xor_sync(0xffffffffu, tn, off));
-                const uint32_t bit = (p < td.y) ? (1u << (level_of(sd.st.dt[p]) & 31)) : 0u;
-                const uint32_t lvm = __reduce_or_sync(0xffffffffu, bit);
-                if (lane == 0) {
-                    const int c = __popc((uint32_t)it.z);
-                    sd.tile_lv[it.x] = lvm;
-                    atomicMin(&sd.ds->tmin[par ^ 1], (unsigned long long)__double_as_longlong(tn));
-                    atomicAdd(&sd.ds->particle_steps, (unsigned long long)c);
-                    atomicAdd(&sd.ds->n_act_last, c);
-                }
-            }
-        }
-        if (blockIdx.x == 0) {
-            if (tid == 0) {
-                B.bs->work = 0u;
-                B.bs->n_items = 0u;
-            }
-            for (int s = tid; s < n_sims; s += blockDim.x) {
-                const SimDesc &sd = B.sims[s];
-                sd.ds->slot_ctr = 0u;  // this step's forces are done
-                if (cached_time(sc, B.sims, s, par) <= sd.t_end) {
-                    sd.ds->block_steps += 1ull;
-                } else {
-                    sd.ds->tmin[par ^ 1] = sd.ds->tmin[par];  // carry a finished simulation's time
-                }
+                if (gt == 0) sm.item = n_static + (int)atomicAdd(&B.bs->work[par], 1u);
+                group_sync(bar);  // also ends the use of the shared buffers by this item
+                item = sm.item;   // rewritten only after the next item's group barriers
             }
         }
         if (!grid_sync(B.bs)) return;
-        if (blockIdx.x == 0 && tid == 0) B.step_ns[3 * step + 3] = globaltimer_ns();
+        if (blockIdx.x == 0 && tid == 0) {
+            const unsigned long long now = globaltimer_ns();
+            B.step_ns[3 * step + 2] = now;
+            B.step_ns[3 * step + 3] = now;  // the corrector ran inside the force phase
+        }
 
         // any simulation still live for the next step?
         int live = 0;

@@ -33,6 +33,7 @@ struct DevScalars {
     int32_t part_len;            // shortest list part (a multiple of the staging chunk)
     int32_t work_item;           // target interactions per work item (0: every part is part_len long)
     uint32_t slot_ctr;           // partial-sum slots handed out this step
+    uint32_t slot_par[2];        // the same for the batched loop, by step parity
     int32_t n_act_last;          // active particles of the last corrected step
     int64_t n;                   // particles
     int64_t nj;                  // j entries
@@ -239,26 +240,32 @@ __device__ __forceinline__ void store_rec<RecMix>(RecMix *out, int64_t e, const 
     out[e] = r;
 }
 
-// FP32 copy of entry e's FP64 state for the mixed predictor.
+// FP32 copy of entry e's FP64 state for the mixed predictor, one component
+// (d = 0, 1, 2); the mass goes with component 0.
+__device__ __forceinline__ void refresh_base_component(const State &s, int64_t e, int d)
+{
+    const double x = s.x[d * s.cap_j + e];
+    const float hi = __double2float_rn(x);
+    const float lo = __double2float_rn(x - (double)hi);
+    const float v = __double2float_rn(s.v[d * s.cap_j + e]);
+    const float a2 = 0.5f * __double2float_rn(s.a[d * s.cap_j + e]);
+    const float j6 = __double2float_rn(s.jk[d * s.cap_j + e]) * (1.0f / 6.0f);
+    float *b = reinterpret_cast<float *>(&s.base[e]);  // hm, lo, v, a2, j6: float4 each
+    b[0 + d] = hi;
+    b[4 + d] = lo;
+    b[8 + d] = v;
+    b[12 + d] = a2;
+    b[16 + d] = j6;
+    if (d == 0) {
+        b[3] = __double2float_rn(s.m[e]);
+        b[7] = b[11] = b[15] = b[19] = 0.f;
+    }
+}
+
 __device__ __forceinline__ void refresh_base(const State &s, int64_t e)
 {
-    float hi[3], lo[3], v[3], a2[3], j6[3];
 #pragma unroll
-    for (int d = 0; d < 3; d++) {
-        const double x = s.x[d * s.cap_j + e];
-        hi[d] = __double2float_rn(x);
-        lo[d] = __double2float_rn(x - (double)hi[d]);
-        v[d] = __double2float_rn(s.v[d * s.cap_j + e]);
-        a2[d] = 0.5f * __double2float_rn(s.a[d * s.cap_j + e]);
-        j6[d] = __double2float_rn(s.jk[d * s.cap_j + e]) * (1.0f / 6.0f);
-    }
-    BaseMix b;
-    b.hm = make_float4(hi[0], hi[1], hi[2], __double2float_rn(s.m[e]));
-    b.lo = make_float4(lo[0], lo[1], lo[2], 0.f);
-    b.v = make_float4(v[0], v[1], v[2], 0.f);
-    b.a2 = make_float4(a2[0], a2[1], a2[2], 0.f);
-    b.j6 = make_float4(j6[0], j6[1], j6[2], 0.f);
-    s.base[e] = b;
+    for (int d = 0; d < 3; d++) refresh_base_component(s, e, d);
 }
 
 // Mixed predictor: the FP64 base position (as a float pair) plus an FP32
@@ -590,6 +597,7 @@ struct ForceSmem {
     typename Traits<Rec>::Red red[kThreads / 32][kMaxTileI];
     int item;
     int last;
+    double tn[kThreads / 32];  // per-warp minimum of t + dt after the corrector
 };
 
 // Barrier over the 128 threads working on one item: the whole CTA
@@ -602,9 +610,10 @@ __device__ __forceinline__ void group_sync(int bar_id)
 }
 
 // item = (tile, part | sim << 16, active mask, parts of the tile); tid is
-// the thread's index in its 128-thread group.
+// the thread's index in its 128-thread group.  Returns true (in every thread
+// of the group) for the item that wrote the tile's final forces.
 template <typename Rec, int TJ, bool kMapI>
-__device__ __forceinline__ void force_item(const State &s, const Rec *__restrict__ rec, const Lists &L, int pj_min,
+__device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict__ rec, const Lists &L, int pj_min,
                                            int work, typename Traits<Rec>::Eps eps2, const int4 it,
                                            ForceSmem<Rec, TJ> &sm, unsigned long long &n_int, const int tid,
                                            const int bar_id)
@@ -748,6 +757,7 @@ __device__ __forceinline__ void force_item(const State &s, const Rec *__restrict
         s.pot1[p] = -red_get(r, 6);
     }
     // callers put a barrier before the shared buffers are reused
+    return write_out;
 }
 
 template <typename Rec, int TJ, bool kMapI = false>
@@ -805,36 +815,112 @@ __device__ __forceinline__ void atomic_min_time(unsigned long long *slot, double
 // a2 = (-6 (a0 - a1) - D (4 j0 + 2 j1)) / D^2, a3 = (12 (a0 - a1) + 6 D (j0 + j1)) / D^3,
 // x1 = x_p + a2 D^4/24 + a3 D^5/120, v1 = v_p + a2 D^3/6 + a3 D^4/24;
 // new step from Aarseth's criterion at the end of the step.
+//
+// The FP64 pipe is narrow on this GPU (a warp instruction issues in 64
+// cycles per SM sub-partition), so the corrector avoids FP64 divisions and
+// roots: D is the particle's power-of-two step, so 1/D^2 and 1/D^3 are exact
+// powers of two, and the timestep criterion is screened in FP32.  The
+// per-component arithmetic and the order of every sum are shared by the
+// one-thread-per-particle and the three-lanes-per-particle correctors, so
+// both give the same bits.
+
+// Powers of D (a power of two) needed by the corrector, exact.
+struct StepPowers {
+    double D, iD2, iD3, D3, D4;
+};
+
+__device__ __forceinline__ StepPowers step_powers(double D)
+{
+    StepPowers P;
+    P.D = D;
+    const long long b = __double_as_longlong(D);
+    if ((b & ((1ll << 52) - 1)) == 0 && b > 0) {
+        const int e = (int)((b >> 52) & 0x7ff) - 1023;  // D = 2^e
+        auto p2 = [](int k) { return __longlong_as_double((long long)(1023 + k) << 52); };
+        P.iD2 = p2(-2 * e);
+        P.iD3 = p2(-3 * e);
+        P.D3 = p2(3 * e);
+        P.D4 = p2(4 * e);
+    } else {  // not reached from the block-step loops (D is a level step)
+        const double iD = 1.0 / D;
+        P.iD2 = iD * iD;
+        P.iD3 = P.iD2 * iD;
+        P.D3 = D * D * D;
+        P.D4 = D * D * D * D;
+    }
+    return P;
+}
+
+// One Cartesian component: state (x, v, a0, j0) at t, new force (a1, j1) at
+// t + D.  Returns the corrected x, v and the a^(2) at t + D and a^(3).
+struct CorrComp {
+    double x, v, a2e, a3;
+};
+
+__device__ __forceinline__ CorrComp correct_component(double x, double v, double a0, double j0, double a1, double j1,
+                                                      const StepPowers &P)
+{
+    const double D = P.D;
+    const double h = 0.5 * D, th = D * (1.0 / 3.0);
+    const double xp = x + D * (v + h * (a0 + th * j0));
+    const double vp = v + D * (a0 + h * j0);
+    const double a2 = (-6.0 * (a0 - a1) - D * (4.0 * j0 + 2.0 * j1)) * P.iD2;
+    const double a3 = (12.0 * (a0 - a1) + 6.0 * D * (j0 + j1)) * P.iD3;
+    CorrComp c;
+    c.x = xp + P.D4 * (a2 * (1.0 / 24.0) + a3 * D * (1.0 / 120.0));
+    c.v = vp + P.D3 * (a2 * (1.0 / 6.0) + a3 * D * (1.0 / 24.0));
+    c.a2e = a2 + a3 * D;
+    c.a3 = a3;
+    return c;
+}
+
+// |u|^2 from the components' squares, summed x, y, z with single roundings.
+__device__ __forceinline__ double norm2_of(double sx, double sy, double sz) { return __dadd_rn(__dadd_rn(sx, sy), sz); }
+__device__ __forceinline__ double sq(double u) { return __dmul_rn(u, u); }
+
+// Aarseth's criterion dt^2 = eta (|a||a2| + |j|^2) / (|j||a3| + |a2|^2) from
+// A = |a|^2, J = |j|^2, S = |a2|^2, T = |a3|^2.  Only the largest power of
+// two below dt is used (block_dt), so it is evaluated in FP32: with A, J, S,
+// T in [1e-18, 1e18] the FP32 value is within 6 * 2^-24 (relative) of the
+// FP64 one, and when its mantissa is at least 2^-17 away from a power-of-two
+// boundary the exact power of two below it is returned.  Otherwise (near a
+// boundary, or out of that range) the FP64 expression decides.
+__device__ __forceinline__ double aarseth_want(double A, double J, double S, double T, double eta)
+{
+    const float Af = __double2float_rn(A), Jf = __double2float_rn(J), Sf = __double2float_rn(S),
+                Tf = __double2float_rn(T);
+    const float lo = 1e-18f, hi = 1e18f;
+    if (Af >= lo && Af <= hi && Jf >= lo && Jf <= hi && Sf >= lo && Sf <= hi && Tf >= lo && Tf <= hi) {
+        const float w = sqrtf(__double2float_rn(eta) * (sqrtf(Af * Sf) + Jf) / (sqrtf(Jf * Tf) + Sf));
+        const int wb = __float_as_int(w);
+        const int frac = wb & 0x7fffff, ex = (wb >> 23) & 0xff;
+        if (ex > 0 && ex < 255 && frac >= 64 && frac <= 0x7fffff - 64)
+            return __longlong_as_double((long long)(ex - 127 + 1023) << 52);
+    }
+    return sqrt(eta * (sqrt(A * S) + J) / (sqrt(J * T) + S));
+}
+
 __device__ __forceinline__ void correct_particle(const State &s, int64_t p, double tnow, const Params &prm)
 {
-    // The FP64 pipe is narrow on this GPU, so divisions and square roots are
-    // kept few: one reciprocal of D, products of squared norms under one root.
-    const double D = tnow - s.t[p];
-    double xp[3], vp[3];
-    predict_one(s, p, tnow, xp, vp);
-    const double iD = 1.0 / D;
-    const double iD2 = iD * iD, iD3 = iD2 * iD;
-    const double D2 = D * D, D3 = D2 * D;
-    double A = 0.0, J = 0.0, S = 0.0, T = 0.0;  // |a1|^2, |j1|^2, |a^(2)(t1)|^2, |a^(3)|^2
+    const StepPowers P = step_powers(tnow - s.t[p]);
+    double sa[3], sj[3], ss[3], st[3];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         const double a0 = s.a[d * s.cap_j + p], j0 = s.jk[d * s.cap_j + p];
         const double a1 = s.acc1[d * s.cap_n + p];
         const double j1 = s.jerk1[d * s.cap_n + p];
-        const double a2 = (-6.0 * (a0 - a1) - D * (4.0 * j0 + 2.0 * j1)) * iD2;
-        const double a3 = (12.0 * (a0 - a1) + 6.0 * D * (j0 + j1)) * iD3;
-        s.x[d * s.cap_j + p] = xp[d] + D2 * D2 * (a2 * (1.0 / 24.0) + a3 * D * (1.0 / 120.0));
-        s.v[d * s.cap_j + p] = vp[d] + D3 * (a2 * (1.0 / 6.0) + a3 * D * (1.0 / 24.0));
+        const CorrComp c = correct_component(s.x[d * s.cap_j + p], s.v[d * s.cap_j + p], a0, j0, a1, j1, P);
+        s.x[d * s.cap_j + p] = c.x;
+        s.v[d * s.cap_j + p] = c.v;
         s.a[d * s.cap_j + p] = a1;
         s.jk[d * s.cap_j + p] = j1;
-        const double a2e = a2 + a3 * D;
-        A += a1 * a1;
-        J += j1 * j1;
-        S += a2e * a2e;
-        T += a3 * a3;
+        sa[d] = sq(a1);
+        sj[d] = sq(j1);
+        ss[d] = sq(c.a2e);
+        st[d] = sq(c.a3);
     }
-    // Aarseth: dt^2 = eta (|a||a2| + |j|^2) / (|j||a3| + |a2|^2)
-    const double want = sqrt(prm.eta * (sqrt(A * S) + J) / (sqrt(J * T) + S));
+    const double want = aarseth_want(norm2_of(sa[0], sa[1], sa[2]), norm2_of(sj[0], sj[1], sj[2]),
+                                     norm2_of(ss[0], ss[1], ss[2]), norm2_of(st[0], st[1], st[2]), prm.eta);
     const double dtn = block_dt(want, s.dt[p], tnow, prm.dt_min, prm.dt_max);
     s.t[p] = tnow;
     s.dt[p] = dtn;
