@@ -43,8 +43,9 @@ sys.path.insert(0, ROOT)
 
 FLOP_PER_INT = 60
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_batch launch (plain FP64,
-# one tree interval of the N = 65536 run), from profiles/batch_kernel_plummer65536.md
-TRAFFIC_FP64_PER_LAUNCH = 100.23168e6 + 81.654528e6
+# one tree interval of the N = 65536 run), from profiles/batch_kernel_plummer65536.md;
+# None until the current kernel has been captured
+TRAFFIC_FP64_PER_LAUNCH = None
 METRIC = "interactions/s & equiv. Tflops (60 flop/int); block-steps/s, p50/p99 latency vs plain"
 
 
@@ -543,15 +544,17 @@ def main():
             "equiv_tflops_57": 57 * value / 1e12,
             "block_steps_per_s": tot[1] / (mx[0] * 1e-3),
             "particle_steps_per_s": tot[2] / (mx[0] * 1e-3),
-            "roofline": {"kernel": ("k_batch force phase, plain FP64" if a.loop == "persistent"
+            "roofline": {"kernel": ("k_batch force phase (list force + corrector), plain FP64"
+                                    if a.loop == "persistent"
                                     else "k_force<RecF64> (plain FP64 list force)"),
                          "bound": "alu",
                          "achieved": achieved, "peak": peaks.get("fp64_tflops"), "unit": "TFLOP/s",
                          "frac": achieved / peaks["fp64_tflops"] if peaks.get("fp64_tflops") else None,
                          "traffic": TRAFFIC_FP64_PER_LAUNCH if a.loop == "persistent" else None,
                          "note": "achieved = 60 algorithmic flop per interaction / device time of the force "
-                                 "phases (persistent loop: %globaltimer stamps at the phase barriers; graph loop: "
-                                 "CUDA events around the force kernel); peak = measured FP64 FMA throughput "
+                                 "phases (persistent loop: %globaltimer stamps at the phase barriers, the phase "
+                                 "includes the corrector of each completed tile; graph loop: CUDA events around "
+                                 "the force kernel); peak = measured FP64 FMA throughput "
                                  "(of measured, libhh_peaks.so); traffic = DRAM bytes of one k_batch launch "
                                  "(one interval, all phases) from the ncu capture summarised in "
                                  "profiles/batch_kernel_plummer65536.md"},
@@ -578,7 +581,9 @@ def main():
                 "speedup_vs_plain": mv / (res["interactions"] / (res["ms"] * 1e-3)),
                 "time_split_ms_per_step": _split(mixed, a.steps),
                 "block_step_latency_us": _lat(mixed["step_us"]),
-                "roofline": {"kernel": "k_force<RecMix> (mixed list force)", "bound": "alu", "achieved": mach,
+                "roofline": {"kernel": ("k_batch force phase (list force + corrector), mixed"
+                                        if a.loop == "persistent" else "k_force<RecMix> (mixed list force)"),
+                             "bound": "alu", "achieved": mach,
                              "peak": peaks.get("fp32_tflops"), "unit": "TFLOP/s",
                              "frac": mach / peaks["fp32_tflops"] if peaks.get("fp32_tflops") else None},
             }
