@@ -81,6 +81,9 @@ typedef struct hh_counters {
     int64_t particle_steps; /* corrected particle steps */
     int64_t interactions;   /* pairwise terms evaluated, self excluded */
     int64_t rebuilds;       /* tree/list rebuilds */
+    int64_t tile_steps;     /* static i tiles with active particles, summed over block steps:
+                               particle_steps / tile_steps is the mean number of particles that
+                               share one staged list chunk (the paper's n_i, Eq. 3) */
 } hh_counters;
 
 /* Fills cfg with defaults: eps2 = 1e-8, eta = 0.02, eta_s = 0.01,

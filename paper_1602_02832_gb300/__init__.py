@@ -46,7 +46,7 @@ class hh_config(C.Structure):
 
 class hh_counters(C.Structure):
     _fields_ = [("block_steps", C.c_int64), ("particle_steps", C.c_int64), ("interactions", C.c_int64),
-                ("rebuilds", C.c_int64)]
+                ("rebuilds", C.c_int64), ("tile_steps", C.c_int64)]
 
 
 _P = C.c_void_p
@@ -308,7 +308,7 @@ class Context:
         c = hh_counters()
         self._c(_lib.hh_get_counters(self.h, C.byref(c)))
         return dict(block_steps=c.block_steps, particle_steps=c.particle_steps, interactions=c.interactions,
-                    rebuilds=c.rebuilds)
+                    rebuilds=c.rebuilds, tile_steps=c.tile_steps)
 
     def hh_reset_counters(self):
         self._c(_lib.hh_reset_counters(self.h))

@@ -856,6 +856,7 @@ int hh_get_counters(hh_ctx *ctx, hh_counters *out)
     out->particle_steps = int64_t(ctx->h_ds->particle_steps);
     out->interactions = int64_t(ctx->h_ds->interactions);
     out->rebuilds = ctx->rebuilds;
+    out->tile_steps = int64_t(ctx->h_ds->tile_steps);
     return HH_OK;
 }
 
@@ -863,7 +864,7 @@ int hh_reset_counters(hh_ctx *ctx)
 {
     int rc = check_ctx(ctx);
     if (rc) return rc;
-    CK(cudaMemsetAsync(&ctx->ds->block_steps, 0, 3 * sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(&ctx->ds->block_steps, 0, 4 * sizeof(unsigned long long), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->rebuilds = 0;
     return HH_OK;

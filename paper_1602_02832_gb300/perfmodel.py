@@ -1,0 +1,264 @@
+"""GPU analogue of the paper's breakdown of the calculation time (Section 3,
+Table 1) and a fit of its force-time model (Eq. 3).
+
+The paper splits the time per particle step into T_grape (force and jerk on
+GRAPE-9), T_tree (tree and lists on the host, step 1), T_comm (host <->
+GRAPE transfers) and T_host (the rest of the host's integration), and models
+T_grape = N_int t_pipe (n_i / n_pipe)^-1, where N_int is the mean list length
+and n_i the mean number of particles that are evaluated together (one group's
+active particles in a block step).
+
+Here, with the tree loop running on the GPU (`hh_batch_run`, device rebuilds):
+- T_force: the force phase of each block step (list force and, for each tile
+  whose forces are complete, the corrector), device time;
+- T_predict: the predict + select phase, device time;
+- T_tree: the device rebuild every dt_tree, wall time of hh_rebuild;
+- T_host: wall time of the loop minus the device phases (launch and host
+  bookkeeping);
+- T_comm: the loop moves no particle data between host and GPU per step; the
+  column gives, for context, a full state round trip (hh_get_state + hh_set_j)
+  per tree interval spread over that interval's particle steps.
+N_int = interactions / particle steps.  n_i = particle steps / active tile
+steps: the particles that share one staged list chunk (at most tile_i).
+
+The force-time model T_force / N_int = t_int + t_stage / n_i (t_int: time
+per interaction when staging is fully shared; t_stage: time to stage one
+list entry for a tile; t_stage / t_int plays the role of the paper's n_pipe,
+the n_i below which sharing, not arithmetic, sets the rate) is fitted on a
+controlled sweep: one force evaluation (hh_force, the same list-force body)
+on active sets with exactly k active particles in every i tile, k = 1 ... 32,
+timed with CUDA events around the force kernel.  The tree-loop runs give
+n_i of only ~4-6, too narrow a range to separate the two terms.
+
+Usage (on a GPU): python -m paper_1602_02832_gb300.perfmodel --out DIR
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import time
+
+import numpy as np
+
+# The paper's Table 1 (GRAPE-9, n_crit = 4000, dt_tree = 1/64): N, theta,
+# N_int, n_i, T_grape, T_tree, T_comm, T_host (seconds per particle step).
+PAPER_TABLE1 = [
+    (65536, 0.75, 5740, 29.3, 8.5e-6, 1.5e-7, 9.8e-7, 1.6e-7),
+    (65536, 0.5, 11081, 28.8, 1.6e-5, 2.4e-7, 9.8e-7, 1.6e-7),
+    (65536, 0.3, 22351, 28.6, 3.3e-5, 4.0e-7, 9.8e-7, 1.5e-7),
+    (262144, 0.75, 6433, 29.8, 9.2e-6, 9.7e-8, 1.2e-6, 2.7e-7),
+    (262144, 0.5, 12644, 29.5, 1.8e-5, 1.5e-7, 1.2e-6, 2.7e-7),
+    (262144, 0.3, 28168, 29.4, 4.0e-5, 2.7e-7, 1.2e-6, 2.6e-7),
+]
+
+
+def measure(n, theta, n_crit, precision, intervals=2, warm=1, seed=0, tile_i=0, tile_j=0):
+    """Runs the tree loop of a seeded Plummer sphere (standard units, eps^2 =
+    1e-8, eta = 0.02, dt_tree = 1/64) for `warm` + `intervals` tree intervals
+    from t = 0 and returns the per-particle-step breakdown of the timed ones."""
+    import synth
+    from . import HH_FP64, Batch, Context, hh_config_default, hh_tree_build
+
+    x, v, m = synth.plummer(n, seed)
+    cfg = hh_config_default()
+    cfg.eps2, cfg.eta, cfg.theta, cfg.n_crit, cfg.precision = 1e-8, 0.02, theta, n_crit, precision
+    cfg.tile_i, cfg.tile_j = tile_i, tile_j
+    z = np.zeros((3, n))
+    T = hh_tree_build(x.T, v.T, z, z, m, leaf=cfg.leaf, n_crit=n_crit, theta=theta)
+    dtt = cfg.dt_tree
+    with Context(cfg, n, 2 * n, 2 * len(T.idx) + 4096, 2 * T.n_groups + 64) as ctx, \
+            Batch(precision, max_sims=1, max_steps=4096) as b:
+        ctx.hh_load_particles(np.ascontiguousarray(x.T), np.ascontiguousarray(v.T), m)
+        ctx.hh_set_rebuild_device(True)
+        ctx.hh_run(0.0, 0.0)
+        t = 0.0
+        acc = dict(wall=0.0, phase=np.zeros(3), rebuild=0.0, comm=0.0)
+        c0 = None
+        for k in range(warm + intervals):
+            timed = k >= warm
+            if timed and c0 is None:
+                c0 = ctx.hh_get_counters()
+            w = time.perf_counter()
+            while True:
+                _, tn, _ = b.hh_batch_run([ctx], [t + dtt])
+                if timed:
+                    acc["phase"] += b.last_phase_us.sum(0) * 1e-6
+                if tn[0] > t + dtt:
+                    break
+            if timed:
+                acc["wall"] += time.perf_counter() - w
+            w = time.perf_counter()
+            ctx.hh_rebuild(t + dtt)
+            if timed:
+                acc["rebuild"] += time.perf_counter() - w
+            t += dtt
+            if timed:  # context for T_comm: one state round trip per interval
+                w = time.perf_counter()
+                st = ctx.hh_get_state()
+                ids = ctx.hh_get_ids()
+                ctx.hh_set_j(0, st["x"], st["v"], st["a"], st["jk"], np.ascontiguousarray(m[ids]), st["t"])
+                acc["comm"] += time.perf_counter() - w
+        c1 = ctx.hh_get_counters()
+    ps = c1["particle_steps"] - c0["particle_steps"]
+    n_int = (c1["interactions"] - c0["interactions"]) / ps
+    n_i = ps / max(1, c1["tile_steps"] - c0["tile_steps"])
+    ph = acc["phase"]
+    return {
+        "n": n, "theta": theta, "n_crit": n_crit, "form": "fp64" if precision == HH_FP64 else "mixed",
+        "particle_steps": int(ps), "block_steps": int(c1["block_steps"] - c0["block_steps"]),
+        "N_int": n_int, "n_i": n_i,
+        "T_force": ph[1] / ps, "T_predict": ph[0] / ps, "T_tree": acc["rebuild"] / ps,
+        "T_host": max(0.0, acc["wall"] - ph.sum()) / ps, "T_comm_round_trip": acc["comm"] / ps,
+    }
+
+
+def _tiles(off, group_of, tile_i):
+    """Static i tiles (begin, end) as the library forms them: runs of at most
+    tile_i consecutive particles inside each group (groups are contiguous in
+    Morton order)."""
+    g = np.asarray(group_of)
+    starts = np.r_[0, np.nonzero(np.diff(g))[0] + 1]
+    ends = np.r_[starts[1:], len(g)]
+    out = []
+    for b, e in zip(starts, ends):
+        for q in range(b, e, tile_i):
+            out.append((q, min(q + tile_i, e)))
+    return out
+
+
+def sweep_n_i(n, theta, n_crit, precision, ks=(1, 2, 4, 8, 16, 32), reps=5, seed=0, tile_i=32):
+    """Force time per interaction against the number k of active particles
+    per i tile (the paper's n_i), from hh_force on a tree at t = 0."""
+    import synth
+    from . import HH_FP64, Context, hh_config_default, hh_tree_build
+
+    x, v, m = synth.plummer(n, seed)
+    cfg = hh_config_default()
+    cfg.eps2, cfg.theta, cfg.n_crit, cfg.precision, cfg.tile_i = 1e-8, theta, n_crit, precision, tile_i
+    z = np.zeros((3, n))
+    T = hh_tree_build(x.T, v.T, z, z, m, leaf=cfg.leaf, n_crit=n_crit, theta=theta)
+    rows = []
+    with Context(cfg, n, 2 * n, 2 * len(T.idx) + 4096, 2 * T.n_groups + 64) as ctx:
+        ctx.hh_load_particles(np.ascontiguousarray(x.T), np.ascontiguousarray(v.T), m)
+        ctx.hh_set_rebuild_device(True)
+        ctx.hh_run(0.0, 0.0)
+        off, idx, gof = ctx.hh_get_lists()
+        length = np.diff(off)[gof] - 1  # interactions of each particle (self excluded)
+        tiles = _tiles(off, gof, tile_i)
+        ctx.hh_predict(0.0)
+        for k in ks:
+            act = np.concatenate([np.arange(b, min(b + k, e)) for b, e in tiles]).astype(np.int32)
+            ctx.hh_force(act, want=(False, False, False))  # warm-up
+            best = math.inf
+            for _ in range(reps):
+                ctx.hh_force_timing(1)
+                ctx.hh_force(act, want=(False, False, False))
+                ms, _ = ctx.hh_force_timing(0)
+                best = min(best, ms * 1e-3)
+            n_int = float(length[act].sum())
+            rows.append({"form": "fp64" if precision == HH_FP64 else "mixed", "n": n, "theta": theta,
+                         "n_crit": n_crit, "k": k, "n_act": int(len(act)), "n_i": float(len(act)) / len(tiles),
+                         "N_int": n_int / len(act), "T_force": best / len(act), "time_s": best,
+                         "interactions_per_s": n_int / best})
+    return rows
+
+
+def fit_force_model(rows):
+    """Least-squares fit of T_force / N_int = t_int + t_stage / n_i over rows
+    of one form.  Returns t_int, t_stage, n_pipe = t_stage / t_int and the
+    coefficient of determination of the fit."""
+    y = np.array([r["T_force"] / r["N_int"] for r in rows], dtype=np.float64)
+    x = np.array([1.0 / r["n_i"] for r in rows], dtype=np.float64)
+    A = np.stack([np.ones_like(x), x], axis=1)
+    (t_int, t_stage), *_ = np.linalg.lstsq(A, y, rcond=None)
+    pred = A @ np.array([t_int, t_stage])
+    ss_res = float(((y - pred) ** 2).sum())
+    ss_tot = float(((y - y.mean()) ** 2).sum())
+    return {"t_int": float(t_int), "t_stage": float(t_stage),
+            "n_pipe": float(t_stage / t_int) if t_int > 0 else math.inf,
+            "r2": 1.0 - ss_res / ss_tot if ss_tot > 0 else 1.0, "points": len(rows)}
+
+
+def sweep_markdown(rows, fits):
+    lines = ["| form | N | theta | n_crit | k active per tile | n_i | N_int | force time (s) | T_force / N_int (s) | "
+             "interactions/s |", "|---|---:|---:|---:|---:|---:|---:|---:|---:|---:|"]
+    for r in rows:
+        lines.append(f"| {r['form']} | {r['n']} | {r['theta']} | {r['n_crit']} | {r['k']} | {r['n_i']:.2f} | "
+                     f"{r['N_int']:.0f} | {r['time_s']:.3e} | {r['T_force'] / r['N_int']:.3e} | "
+                     f"{r['interactions_per_s']:.3e} |")
+    lines += ["", "Fit T_force / N_int = t_int + t_stage / n_i over the sweep:", "",
+              "| form | t_int (s) | t_stage (s) | n_pipe = t_stage / t_int | R^2 | points |",
+              "|---|---:|---:|---:|---:|---:|"]
+    for form, f in fits.items():
+        lines.append(f"| {form} | {f['t_int']:.3e} | {f['t_stage']:.3e} | {f['n_pipe']:.1f} | {f['r2']:.3f} | "
+                     f"{f['points']} |")
+    return "\n".join(lines) + "\n"
+
+
+def table_markdown(rows, fits):
+    lines = ["| form | N | theta | n_crit | N_int | n_i | T_force | T_predict | T_tree | T_host | "
+             "T_comm (round trip) |", "|---|---:|---:|---:|---:|---:|---:|---:|---:|---:|---:|"]
+    for r in rows:
+        lines.append(f"| {r['form']} | {r['n']} | {r['theta']} | {r['n_crit']} | {r['N_int']:.0f} | {r['n_i']:.1f} | "
+                     f"{r['T_force']:.2e} | {r['T_predict']:.2e} | {r['T_tree']:.2e} | {r['T_host']:.2e} | "
+                     f"{r['T_comm_round_trip']:.2e} |")
+    if fits:
+        lines += ["", "Fit T_force / N_int = t_int + t_stage / n_i over these runs:", "",
+                  "| form | t_int (s) | t_stage (s) | n_pipe = t_stage / t_int | R^2 | points |",
+                  "|---|---:|---:|---:|---:|---:|"]
+        for form, f in fits.items():
+            lines.append(f"| {form} | {f['t_int']:.3e} | {f['t_stage']:.3e} | {f['n_pipe']:.1f} | {f['r2']:.3f} | "
+                         f"{f['points']} |")
+    lines += ["", "Paper, Table 1 (GRAPE-9, n_crit 4000; seconds per particle step):", "",
+              "| N | theta | N_int | n_i | T_grape | T_tree | T_comm | T_host |", "|---:|---:|---:|---:|---:|---:|---:|---:|"]
+    for row in PAPER_TABLE1:
+        lines.append("| " + " | ".join(str(u) for u in row) + " |")
+    return "\n".join(lines) + "\n"
+
+
+def main(argv=None):
+    from . import HH_FP64, HH_MIXED
+
+    p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    p.add_argument("--n", type=int, nargs="+", default=[65536, 262144])
+    p.add_argument("--theta", type=float, nargs="+", default=[0.75, 0.5, 0.3])
+    p.add_argument("--n-crit", type=int, nargs="+", default=[64, 4000])
+    p.add_argument("--forms", nargs="+", default=["fp64", "mixed"], choices=["fp64", "mixed"])
+    p.add_argument("--intervals", type=int, default=2)
+    p.add_argument("--warm", type=int, default=1)
+    p.add_argument("--out", default=".")
+    p.add_argument("--sweep-n", type=int, default=65536, help="N of the controlled n_i sweep (0: skip)")
+    a = p.parse_args(argv)
+    sweep, sweep_fits = [], {}
+    if a.sweep_n:
+        for form in a.forms:
+            P = HH_FP64 if form == "fp64" else HH_MIXED
+            part = sweep_n_i(a.sweep_n, 0.5, 4000, P)
+            sweep += part
+            sweep_fits[form] = fit_force_model(part)
+            for r in part:
+                print(json.dumps(r), flush=True)
+    rows = []
+    for form in a.forms:
+        for n in a.n:
+            for th in a.theta:
+                for nc in a.n_crit:
+                    r = measure(n, th, nc, HH_FP64 if form == "fp64" else HH_MIXED, a.intervals, a.warm)
+                    rows.append(r)
+                    print(json.dumps(r), flush=True)
+    fits = {form: fit_force_model([r for r in rows if r["form"] == form]) for form in a.forms if rows}
+    os.makedirs(a.out, exist_ok=True)
+    with open(os.path.join(a.out, "perfmodel.json"), "w") as f:
+        json.dump({"rows": rows, "fits": fits, "sweep": sweep, "sweep_fits": sweep_fits}, f, indent=1)
+    with open(os.path.join(a.out, "perfmodel.md"), "w") as f:
+        if sweep:
+            f.write(sweep_markdown(sweep, sweep_fits) + "\n")
+        f.write(table_markdown(rows, fits))
+    print(json.dumps({"fits": fits, "sweep_fits": sweep_fits}), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

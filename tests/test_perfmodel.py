@@ -1,0 +1,51 @@
+"""Host logic of the performance-model module (the GPU analogue of the
+paper's Table 1 and the Eq. 3 fit): the fit recovers known parameters and
+the report carries the paper's rows."""
+import numpy as np
+
+from paper_1602_02832_gb300 import perfmodel
+
+
+def _rows(t_int, t_stage, n_is, n_ints, noise=0.0, seed=0):
+    rng = np.random.default_rng(seed)
+    rows = []
+    for n_i, n_int in zip(n_is, n_ints):
+        per = (t_int + t_stage / n_i) * (1.0 + noise * rng.standard_normal())
+        rows.append({"form": "fp64", "n": 65536, "theta": 0.5, "n_crit": 64, "N_int": n_int, "n_i": n_i,
+                     "T_force": per * n_int, "T_predict": 1e-8, "T_tree": 1e-9, "T_host": 1e-9,
+                     "T_comm_round_trip": 1e-9})
+    return rows
+
+
+def test_fit_recovers_exact_parameters():
+    rows = _rows(2.5e-11, 4.0e-10, [1.5, 3.0, 7.0, 12.0, 25.0], [2000, 2500, 11000, 5000, 22000])
+    f = perfmodel.fit_force_model(rows)
+    assert abs(f["t_int"] / 2.5e-11 - 1) < 1e-9
+    assert abs(f["t_stage"] / 4.0e-10 - 1) < 1e-9
+    assert abs(f["n_pipe"] - 16.0) < 1e-6
+    assert f["r2"] > 0.999999 and f["points"] == 5
+
+
+def test_fit_with_noise_is_close():
+    rows = _rows(1e-10, 3e-9, np.linspace(1.2, 30, 40), np.full(40, 5000.0), noise=0.01, seed=3)
+    f = perfmodel.fit_force_model(rows)
+    assert abs(f["t_int"] / 1e-10 - 1) < 0.05
+    assert abs(f["t_stage"] / 3e-9 - 1) < 0.05
+
+
+def test_report_has_measured_fit_and_paper_rows():
+    rows = _rows(2.5e-11, 4.0e-10, [2.0, 8.0], [3000, 9000])
+    md = perfmodel.table_markdown(rows, {"fp64": perfmodel.fit_force_model(rows)})
+    assert "| fp64 | 65536 | 0.5 | 64 |" in md
+    for row in perfmodel.PAPER_TABLE1:
+        assert f"| {row[0]} | {row[1]} | {row[2]} | {row[3]} |" in md
+    # Table 1 values as printed in the paper (Section 3)
+    assert perfmodel.PAPER_TABLE1[1][:4] == (65536, 0.5, 11081, 28.8)
+    assert perfmodel.PAPER_TABLE1[5][:4] == (262144, 0.3, 28168, 29.4)
+
+
+def test_static_tiles_follow_groups():
+    # groups [0,5), [5,45), [45,46) with tile_i 16: runs of at most 16 inside each group
+    gof = np.array([0] * 5 + [1] * 40 + [2])
+    tiles = perfmodel._tiles(None, gof, 16)
+    assert tiles == [(0, 5), (5, 21), (21, 37), (37, 45), (45, 46)]
