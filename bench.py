@@ -66,7 +66,8 @@ def _args():
     p.add_argument("--mixed-only", action="store_true", help="run only the mixed form (profiling aid)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--ensemble", type=int, default=256, help="clusters in the batched-ensemble measurement (0: skip)")
-    p.add_argument("--ensemble-intervals", type=int, default=2)
+    p.add_argument("--ensemble-t-end", type=float, default=0.5,
+                   help="end time of every ensemble cluster (a multiple of dt_tree = 1/64)")
     p.add_argument("--serve-seconds", type=float, default=20.0, help="wall time of the serving measurement (0: skip)")
     p.add_argument("--no-autotune", action="store_true", help="skip the tile-shape autotuner (use the defaults)")
     p.add_argument("--rebuild", default="device", choices=["device", "host"],
@@ -340,17 +341,17 @@ def _run_form(hh, torch, a, prec, seed, steps, warmup, flush, e2e_steps=0, over=
 
 
 def _ensemble(hh, a):
-    """Batched form: a = 256 independent Plummer clusters, N log-uniform in
+    """Batched form: 256 independent Plummer clusters, N log-uniform in
     [1024, 32768], seeds 0..255, theta from {0.3, 0.5, 0.7}, mixed precision,
-    all admitted at once and advanced by the continuous-batching server over
-    the first `ensemble_intervals` tree intervals (rebuilds on host threads
-    overlap the batched launches of the other clusters)."""
+    each run to t_end = 0.5, all admitted at once and advanced by the
+    continuous-batching server (rebuilds on worker threads overlap the
+    batched launches of the other clusters)."""
     import numpy as np
     import synth
     from paper_1602_02832_gb300 import serve
 
     members = synth.ensemble(a.ensemble, 1024, 32768, seed=0)
-    t_end = a.ensemble_intervals / 64.0
+    t_end = a.ensemble_t_end
     reqs = []
     for k, mb in enumerate(members):
         x, v, m = synth.plummer(mb.n, mb.seed)

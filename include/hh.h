@@ -184,6 +184,8 @@ int hh_rebuild(hh_ctx *ctx, double t);
  * on that difference.  Its buffers (about 300 bytes per j entry plus 150 per
  * group) are allocated by the first device rebuild and counted in
  * hh_ctx_device_bytes; that rebuild returns HH_ENOMEM if they do not fit.
+ * A device rebuild whose lists exceed list_max grows the list buffer (to the
+ * need plus a quarter) instead of failing, so list_max may be a guess.
  * Errors: HH_EINVAL for a NULL context. */
 int hh_set_rebuild_device(hh_ctx *ctx, int on_device);
 

@@ -481,10 +481,10 @@ int hh_create(hh_ctx **out, int device, const hh_config *cfg, int64_t n_max, int
     }
     ctx->st.cap_j = nj_max;
     ctx->st.cap_n = n_max;
+    // the pinned staging of the host tree build (h_buf, h_jbuf) is allocated by
+    // the first host rebuild: contexts that rebuild on the device never need it
     if (cudaHostAlloc((void **)&ctx->h_ds, sizeof(DevScalars), cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc((void **)&ctx->h_buf, sizeof(double) * 14 * nj_max, cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc((void **)&ctx->h_ibuf, sizeof(int32_t) * n_max, cudaHostAllocDefault) != cudaSuccess ||
-        cudaHostAlloc((void **)&ctx->h_jbuf, sizeof(double) * 14 * nj_max, cudaHostAllocDefault) != cudaSuccess) {
+        cudaHostAlloc((void **)&ctx->h_ibuf, sizeof(int32_t) * n_max, cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();
         return bail(HH_ENOMEM, "pinned host allocation failed");
     }
@@ -952,6 +952,12 @@ int hh_rebuild(hh_ctx *ctx, double t)
         return hh_rebuild_device(ctx, t);
     }
     if ((rc = sync_ids_to_host(ctx))) return rc;
+    if (!ctx->h_buf &&
+        (cudaHostAlloc((void **)&ctx->h_buf, sizeof(double) * 14 * ctx->cap_j, cudaHostAllocDefault) != cudaSuccess ||
+         cudaHostAlloc((void **)&ctx->h_jbuf, sizeof(double) * 14 * ctx->cap_j, cudaHostAllocDefault) != cudaSuccess)) {
+        cudaGetLastError();
+        return fail(ctx, HH_ENOMEM, "hh_rebuild: pinned host staging does not fit");
+    }
     const int64_t n = ctx->n;
     double *H = ctx->h_buf;  // pinned: x v a jk [3][n] each, then m, t, dt
     double *hx = H, *hv = H + 3 * n, *ha = H + 6 * n, *hj = H + 9 * n, *hm = H + 12 * n, *ht = H + 13 * n;

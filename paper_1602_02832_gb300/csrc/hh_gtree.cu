@@ -903,7 +903,18 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
         return gfail(ctx, rc, "hh_rebuild: scan failed");
     k_list_off<<<grid, 256, 0, st>>>(G, R, scan_p, scan_n, ctx->off);
     const int64_t L = d2h(ctx->off + G, st);
-    if (L > ctx->cap_list) return gfail(ctx, HH_ENOMEM, "hh_rebuild: lists exceed list_max");
+    if (L > ctx->cap_list) {  // the list buffer grows (by a quarter beyond the need)
+        const int64_t cap = L + L / 4 + 1024;
+        int32_t *idx = nullptr;
+        if (cudaMalloc(&idx, sizeof(int32_t) * cap) != cudaSuccess) {
+            cudaGetLastError();
+            return gfail(ctx, HH_ENOMEM, "hh_rebuild: lists do not fit in device memory");
+        }
+        cudaFree(ctx->idx);
+        ctx->idx = idx;
+        ctx->device_bytes += (cap - ctx->cap_list) * int64_t(sizeof(int32_t));
+        ctx->cap_list = cap;
+    }
     k_lists_cut<true><<<unsigned(lgrid), 128, 0, st>>>(W, g->cut, R, g->gpos, g->top_buf, A, nullptr, nullptr, scan_p,
                                                        scan_n, ctx->idx);
     // 6. tiles and their work-item capacity

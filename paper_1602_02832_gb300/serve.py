@@ -23,7 +23,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import HH_MIXED, Batch, Context, hh_config_default, hh_tree_build
+from . import HH_ENOMEM, HH_MIXED, Batch, Context, HHError, hh_config_default, hh_tree_build
 
 
 @dataclass
@@ -105,23 +105,45 @@ class Server:
 
     # -- admission ---------------------------------------------------------
     def estimate_bytes(self, req: SimRequest) -> tuple[int, dict]:
-        """Device bytes a simulation needs, from a host build of its tree."""
+        """Device bytes a simulation needs and the capacities to create it with.
+        With device rebuilds no tree is built here: j entries get 2n, groups n/4
+        (admission retries with n if a rebuild finds more), the list buffer
+        starts small and the first device rebuild grows it to the need; the byte estimate (used only until the
+        context reports its own size) takes a list length above those measured
+        for Plummer spheres.  With host rebuilds the capacities come from a host
+        build of the tree."""
         n = len(req.m)
-        z = np.zeros((3, n))
-        T = hh_tree_build(req.x.T, req.v.T, z, z, req.m, leaf=8, n_crit=self.cfg.n_crit, theta=self.cfg.theta)
-        caps = dict(n_max=n, nj_max=n + 2 * T.n_nodes + 64, list_max=int(1.5 * len(T.idx)) + 4096,
-                    groups_max=2 * T.n_groups + 64)
-        nj, L, G = caps["nj_max"], caps["list_max"], caps["groups_max"]
+        if self.rebuild_device:
+            th = max(self.cfg.theta, 0.05)
+            per = min(2.0 * n, 400.0 * (0.5 / th) ** 2)  # list entries per particle, generous
+            caps = dict(n_max=n, nj_max=2 * n + 64, list_max=16 * n + 4096, groups_max=n // 4 + 64)
+            L_est = int(per * n) + 4096
+        else:
+            z = np.zeros((3, n))
+            T = hh_tree_build(req.x.T, req.v.T, z, z, req.m, leaf=8, n_crit=self.cfg.n_crit, theta=self.cfg.theta)
+            caps = dict(n_max=n, nj_max=n + 2 * T.n_nodes + 64, list_max=int(1.5 * len(T.idx)) + 4096,
+                        groups_max=2 * T.n_groups + 64)
+            L_est = caps["list_max"]
+        nj, L, G = caps["nj_max"], L_est, caps["groups_max"]
         rec = 48 if self.precision == HH_MIXED else 64
         est = (nj * (14 * 8 + rec) + n * (8 * 8 + 4 * 3 + 7 * 8) + L * 4 + G * 8
                + (n // 32 + G) * (16 + 4 + 16 + 32 * 56) * 2)
         return int(est), caps
 
     def _admit(self, req: SimRequest, caps: dict, now_s: float) -> _Live:
-        ctx = Context(self.cfg, device=self.device, **caps)
-        ctx.hh_load_particles(np.ascontiguousarray(req.x.T), np.ascontiguousarray(req.v.T), req.m)
-        ctx.hh_set_rebuild_device(self.rebuild_device)
-        ctx.hh_run(0.0, 0.0)  # tree, initial forces, node derivatives, initial steps
+        for attempt in range(2):
+            ctx = Context(self.cfg, device=self.device, **caps)
+            try:
+                ctx.hh_load_particles(np.ascontiguousarray(req.x.T), np.ascontiguousarray(req.v.T), req.m)
+                ctx.hh_set_rebuild_device(self.rebuild_device)
+                ctx.hh_run(0.0, 0.0)  # tree, initial forces, node derivatives, initial steps
+                break
+            except HHError as e:
+                ctx.close()
+                if e.code != HH_ENOMEM or attempt:
+                    raise
+                n = caps["n_max"]  # more groups or cells than guessed: the bounds themselves
+                caps = dict(caps, nj_max=3 * n + 64, groups_max=n)
         return _Live(req, ctx, ctx.device_bytes, min(self.cfg.dt_tree, req.t_end), now_s)
 
     def _finish(self, s: _Live, now_s: float) -> SimResult:
