@@ -124,8 +124,10 @@ __global__ void k_keys(const State s, int64_t n, const Box *b, uint64_t *key, in
     }
 }
 
-// BFS level arrays: cells of one level are contiguous; children of a cell are
-// contiguous in the next level.
+// BFS level arrays: cells of one level are contiguous; the children of a cell
+// are one contiguous block of the next level, in octant order (the blocks of
+// different cells are placed in whatever order the reservations happen, which
+// changes no pre-order number: those follow from the tree alone).
 struct Cells {
     int32_t *begin, *end, *depth, *nchild, *first;  // first: BFS index of the first child
     int32_t *parent;                                 // BFS index of the parent (-1 root)
@@ -133,12 +135,41 @@ struct Cells {
     int32_t *pre;                                    // pre-order number
 };
 
-// counts the children of each cell of a level (binary search per octant)
-__global__ void k_count_children(Cells C, const uint64_t *key, int32_t c0, int32_t nc, int leaf, int32_t *cnt)
+// Sizes the build keeps on the device, so that no step waits for the host:
+// level d holds cells [lvl_c0[d], lvl_c0[d] + lvl_n[d]).
+struct GCounts {
+    int32_t lvl_c0[kMaxDepth + 2];
+    int32_t lvl_n[kMaxDepth + 2];
+    int32_t ncells, overflow, bad, G, R, A, pad[2];
+    int64_t L, n_tiles, total_parts;
+};
+
+__global__ void k_root_init(Cells C, int32_t n, GCounts *gc)
 {
+    C.begin[0] = 0;
+    C.end[0] = n;
+    C.depth[0] = 0;
+    C.parent[0] = -1;
+    C.pre[0] = 0;
+    for (int d = 0; d < kMaxDepth + 2; d++) gc->lvl_c0[d] = gc->lvl_n[d] = 0;
+    gc->lvl_n[0] = 1;
+    gc->ncells = gc->overflow = gc->bad = gc->G = gc->R = gc->A = 0;
+}
+
+// Splits the cells of level d that hold more than `leaf` particles (and are
+// above the depth limit): the octant boundaries come from binary searches of
+// the sorted keys, and each cell reserves its block of children in level d+1.
+__global__ void k_level(Cells C, const uint64_t *key, int d, int leaf, GCounts *gc, int32_t cap_cells)
+{
+    // after an overflow the level counts include blocks that were not written:
+    // nothing below reads them, and the host reports HH_ENOMEM
+    if (gc->overflow) return;
+    const int32_t c0 = gc->lvl_c0[d], nc = gc->lvl_n[d], next0 = c0 + nc;
+    if (blockIdx.x == 0 && threadIdx.x == 0) gc->lvl_c0[d + 1] = next0;
     for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
         const int32_t c = c0 + q;
-        const int32_t b = C.begin[c], e = C.end[c], d = C.depth[c];
+        const int32_t b = C.begin[c], e = C.end[c];
+        int32_t bound[9];
         int nch = 0;
         if (e - b > leaf && d < kMaxDepth) {
             int32_t lo = b;
@@ -149,47 +180,34 @@ __global__ void k_count_children(Cells C, const uint64_t *key, int32_t c0, int32
                     if (digit_at(key[mid], d) <= o) l = mid + 1;
                     else h = mid;
                 }
-                if (l > lo) nch++;
+                if (l > lo) bound[nch++] = lo;
                 lo = l;
             }
+            bound[nch] = e;
         }
-        C.nchild[c] = nch;
-        cnt[q] = nch;
-    }
-}
-
-__global__ void k_write_children(Cells C, const uint64_t *key, int32_t c0, int32_t nc, int leaf, const int32_t *offs,
-                                 int32_t next0)
-{
-    for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
-        const int32_t c = c0 + q;
-        const int32_t b = C.begin[c], e = C.end[c], d = C.depth[c];
-        int32_t w = next0 + offs[q];
+        C.first[c] = next0;
+        C.nchild[c] = 0;
+        if (nch == 0) continue;
+        const int32_t w = next0 + atomicAdd(&gc->lvl_n[d + 1], nch);
+        if ((int64_t)w + nch > cap_cells) {
+            atomicExch(&gc->overflow, 1);
+            continue;
+        }
         C.first[c] = w;
-        if (C.nchild[c] == 0) continue;
-        int32_t lo = b;
-        for (int o = 0; o < 8 && lo < e; o++) {
-            int32_t l = lo, h = e;
-            while (l < h) {
-                const int32_t mid = (l + h) >> 1;
-                if (digit_at(key[mid], d) <= o) l = mid + 1;
-                else h = mid;
-            }
-            if (l > lo) {
-                C.begin[w] = lo;
-                C.end[w] = l;
-                C.depth[w] = d + 1;
-                C.parent[w] = c;
-                w++;
-            }
-            lo = l;
+        C.nchild[c] = nch;
+        for (int k = 0; k < nch; k++) {
+            C.begin[w + k] = bound[k];
+            C.end[w + k] = bound[k + 1];
+            C.depth[w + k] = d + 1;
+            C.parent[w + k] = c;
         }
-        (void)leaf;
     }
 }
 
-__global__ void k_subtree_size(Cells C, int32_t c0, int32_t nc)
+__global__ void k_subtree_size(Cells C, const GCounts *gc, int d)
 {
+    if (gc->overflow) return;
+    const int32_t c0 = gc->lvl_c0[d], nc = gc->lvl_n[d];
     for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
         const int32_t c = c0 + q;
         int32_t sz = 1;
@@ -198,8 +216,10 @@ __global__ void k_subtree_size(Cells C, int32_t c0, int32_t nc)
     }
 }
 
-__global__ void k_preorder(Cells C, int32_t c0, int32_t nc)
+__global__ void k_preorder(Cells C, const GCounts *gc, int d)
 {
+    if (gc->overflow) return;
+    const int32_t c0 = gc->lvl_c0[d], nc = gc->lvl_n[d];
     for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
         const int32_t c = c0 + q;
         int32_t run = C.pre[c] + 1;
@@ -209,6 +229,13 @@ __global__ void k_preorder(Cells C, int32_t c0, int32_t nc)
             run += C.size[ch];
         }
     }
+}
+
+// cell count, and the synchronisation flag of the bounding-box pass
+__global__ void k_cells_done(GCounts *gc, const Box *b)
+{
+    gc->ncells = gc->lvl_c0[kMaxDepth + 1] + gc->lvl_n[kMaxDepth + 1];
+    gc->bad = b->bad;
 }
 
 // Pre-order cell table used by the group and list kernels.
@@ -262,8 +289,10 @@ __global__ void k_permute(const State src, State dst, const int32_t *perm, int64
 // of the members, bottom-up one tree level per launch: a leaf sums its
 // particles, an inner cell the sums of its children.  mom is [13][cap] in BFS
 // cell order.
-__global__ void k_moments_level(const State s, Cells C, int32_t c0, int32_t nc, int64_t cap, double *mom)
+__global__ void k_moments_level(const State s, Cells C, const GCounts *gc, int d, int64_t cap, double *mom)
 {
+    if (gc->overflow) return;
+    const int32_t c0 = gc->lvl_c0[d], nc = gc->lvl_n[d];
     for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
         const int32_t c = c0 + q;
         double acc[13];
@@ -336,9 +365,10 @@ __global__ void k_groups(PCells P, int32_t ncells, const int32_t *flag, const in
 }
 
 // Bounding box of each group's particles ([3][G] lo and hi), one warp per group.
-__global__ void k_group_box(const State s, PCells P, int32_t G, const int32_t *g_cell, double *box_lo, double *box_hi,
-                            float4 *box_f)
+__global__ void k_group_box(const State s, PCells P, const GCounts *gc, const int32_t *g_cell, double *box_lo,
+                            double *box_hi, float4 *box_f)
 {
+    const int32_t G = gc->G;
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t g = w0; g < G; g += nw) {
@@ -382,6 +412,20 @@ __global__ void k_above_flags(PCells P, int32_t ncells, int32_t S, int32_t *flag
 {
     for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x)
         flag[c] = P.size[c] > S ? 1 : 0;
+}
+
+// *dst = number of flagged cells (from the exclusive scan of the flags)
+__global__ void k_store_count(int32_t *dst, const int32_t *flag, const int32_t *pos, int32_t ncells)
+{
+    *dst = pos[ncells - 1] + flag[ncells - 1];
+}
+
+// list length and tile / work-item totals, from the ends of their scans
+__global__ void k_store_totals(GCounts *gc, const int64_t *off_end, const int64_t *tiles_end, const int64_t *parts_end)
+{
+    gc->L = *off_end;
+    gc->n_tiles = *tiles_end;
+    gc->total_parts = *parts_end;
 }
 
 __global__ void k_cut_write(int32_t ncells, const int32_t *flag, const int32_t *pos, int32_t *cut)
@@ -631,6 +675,8 @@ struct GTreeBuf {
     Box *box = nullptr;
     double *root_side = nullptr;
     float *xmax = nullptr;
+    GCounts *gc = nullptr;      // device
+    GCounts *gc_host = nullptr;  // pinned mirror
     float4 *box_f = nullptr;
     Cells C{};
     PCells P{};
@@ -676,6 +722,7 @@ void hh_gtree_free(GTreeBuf *g)
     if (g->tmp) cudaFree(g->tmp);
     if (g->pair_buf) cudaFree(g->pair_buf);
     if (g->top_buf) cudaFree(g->top_buf);
+    if (g->gc_host) cudaFreeHost(g->gc_host);
     delete g;
 }
 
@@ -712,7 +759,7 @@ GTreeBuf *gtree_alloc(hh_ctx *ctx)
               galloc(g, &g->C.pre, cc) && galloc(g, &g->P.begin, cc) && galloc(g, &g->P.end, cc) &&
               galloc(g, &g->P.nchild, cc) && galloc(g, &g->P.parent, cc) && galloc(g, &g->P.child, 8 * cc) &&
               galloc(g, &g->P.side, cc) && galloc(g, &g->P.size, cc) && galloc(g, &g->P.pack, cc) &&
-              galloc(g, &g->P.cf, cc) && galloc(g, &g->xmax, 1) && galloc(g, &g->box_f, 2 * ctx->cap_g) && galloc(g, &g->cnt, cc) &&
+              galloc(g, &g->P.cf, cc) && galloc(g, &g->xmax, 1) && galloc(g, &g->gc, 1) && galloc(g, &g->box_f, 2 * ctx->cap_g) && galloc(g, &g->cnt, cc) &&
               galloc(g, &g->offs, cc) && galloc(g, &g->gflag, cc) && galloc(g, &g->gpos, cc) &&
               galloc(g, &g->g_cell, ctx->cap_g) && galloc(g, &g->cut, cc) && galloc(g, &g->above, cc) && galloc(g, &g->mom, 13 * cc) &&
               galloc(g, &g->box_lo, 3 * ctx->cap_g) && galloc(g, &g->box_hi, 3 * ctx->cap_g) &&
@@ -726,6 +773,11 @@ GTreeBuf *gtree_alloc(hh_ctx *ctx)
          galloc(g, &g->alt.a, 3 * ctx->cap_j, false) && galloc(g, &g->alt.jk, 3 * ctx->cap_j, false) &&
          galloc(g, &g->alt.m, ctx->cap_j, false) && galloc(g, &g->alt.t, ctx->cap_j, false) &&
          galloc(g, &g->alt.dt, n, false);
+    if (ok && cudaHostAlloc((void **)&g->gc_host, sizeof(GCounts), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        g->gc_host = nullptr;
+        ok = false;
+    }
     if (!ok) {
         hh_gtree_free(g);
         return nullptr;
@@ -740,14 +792,6 @@ int64_t gtree_bytes(const hh_ctx *ctx)
            ctx->cap_j * 8 * (12 + 2) + n * 8;
 }
 
-template <typename T>
-T d2h(const T *p, cudaStream_t st)
-{
-    T v{};
-    cudaMemcpyAsync(&v, p, sizeof(T), cudaMemcpyDeviceToHost, st);
-    cudaStreamSynchronize(st);
-    return v;
-}
 
 }  // namespace
 
@@ -769,11 +813,19 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
     }
     GTreeBuf *g = ctx->gtree;
     const int grid = ctx->elem_grid;
+    int64_t launches = 0;
+    // Sizes stay on the device (GCounts) and the host reads them three times:
+    // after the cells, after groups and cut, and after the list counts.
+    auto read_counts = [&]() {
+        cudaMemcpyAsync(g->gc_host, g->gc, sizeof(GCounts), cudaMemcpyDeviceToHost, st);
+        return cudaStreamSynchronize(st) == cudaSuccess;
+    };
     // 1. bounding box, synchronisation check, keys, sort
+    k_root_init<<<1, 1, 0, st>>>(g->C, int32_t(n), g->gc);
     k_box_init<<<1, 1, 0, st>>>(g->box);
     k_box<<<grid, 256, 0, st>>>(ctx->st, n, t, g->box);
     k_keys<<<grid, 256, 0, st>>>(ctx->st, n, g->box, g->key, g->idx, g->root_side, g->xmax);
-    if (d2h(&g->box->bad, st)) return gfail(ctx, HH_ESTATE, "hh_rebuild: particles are not synchronised at t");
+    launches += 4;
     {
         size_t need = 0;
         if (cub::DeviceRadixSort::SortPairs(nullptr, need, g->key, g->key2, g->idx, g->perm, (int)n, 0, 63, st) !=
@@ -790,33 +842,19 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
             cudaSuccess)
             return gfail(ctx, HH_ECUDA, "hh_rebuild: key sort failed");
     }
-    // 2. cells level by level (BFS), subtree sizes, pre-order numbers
-    const int32_t root_b = 0, root_e = int32_t(n), zero = 0, m1 = -1;
-    cudaMemcpyAsync(g->C.begin, &root_b, 4, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(g->C.end, &root_e, 4, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(g->C.depth, &zero, 4, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(g->C.parent, &m1, 4, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(g->C.pre, &zero, 4, cudaMemcpyHostToDevice, st);
-    std::vector<int32_t> lvl0{0}, lvln{1};
+    // 2. cells level by level (BFS), subtree sizes bottom-up, pre-order numbers top-down
     const int64_t cap_cells = ctx->cap_j - n;
-    for (int d = 0; d <= kMaxDepth; d++) {
-        const int32_t c0 = lvl0.back(), nc = lvln.back();
-        k_count_children<<<grid, 256, 0, st>>>(g->C, g->key2, c0, nc, ctx->cfg.leaf, g->cnt);
-        int rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->cnt, g->offs, nc, st);
-        if (rc) return gfail(ctx, rc, "hh_rebuild: scan failed");
-        const int32_t last_off = d2h(g->offs + nc - 1, st), last_cnt = d2h(g->cnt + nc - 1, st);
-        const int32_t next = last_off + last_cnt;
-        if (int64_t(c0) + nc + next > cap_cells)
-            return gfail(ctx, HH_ENOMEM, "hh_rebuild: tree exceeds nj_max (more cells than room for nodes)");
-        k_write_children<<<grid, 256, 0, st>>>(g->C, g->key2, c0, nc, ctx->cfg.leaf, g->offs, c0 + nc);
-        if (next == 0) break;
-        lvl0.push_back(c0 + nc);
-        lvln.push_back(next);
-    }
-    const int32_t ncells = lvl0.back() + lvln.back();
-    for (int l = int(lvl0.size()) - 1; l >= 0; l--)
-        k_subtree_size<<<grid, 256, 0, st>>>(g->C, lvl0[size_t(l)], lvln[size_t(l)]);
-    for (size_t l = 0; l < lvl0.size(); l++) k_preorder<<<grid, 256, 0, st>>>(g->C, lvl0[l], lvln[l]);
+    for (int d = 0; d <= kMaxDepth; d++)
+        k_level<<<grid, 256, 0, st>>>(g->C, g->key2, d, ctx->cfg.leaf, g->gc, int32_t(std::min<int64_t>(cap_cells, INT32_MAX)));
+    for (int d = kMaxDepth; d >= 0; d--) k_subtree_size<<<grid, 256, 0, st>>>(g->C, g->gc, d);
+    for (int d = 0; d <= kMaxDepth; d++) k_preorder<<<grid, 256, 0, st>>>(g->C, g->gc, d);
+    k_cells_done<<<1, 1, 0, st>>>(g->gc, g->box);
+    launches += 3 * (kMaxDepth + 1) + 1;
+    if (!read_counts()) return gfail(ctx, HH_ECUDA, "hh_rebuild: tree build failed");
+    if (g->gc_host->bad) return gfail(ctx, HH_ESTATE, "hh_rebuild: particles are not synchronised at t");
+    if (g->gc_host->overflow)
+        return gfail(ctx, HH_ENOMEM, "hh_rebuild: tree exceeds nj_max (more cells than room for nodes)");
+    const int32_t ncells = g->gc_host->ncells;
     k_to_preorder<<<grid, 256, 0, st>>>(g->C, ncells, g->P, g->root_side);
     // 3. particles into Morton order (into the second buffer), then swap
     k_permute<<<grid, 256, 0, st>>>(ctx->st, g->alt, g->perm, n, g->ids, g->ids2);
@@ -830,16 +868,31 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
     std::swap(g->ids, g->ids2);
     // 4. node records (bottom-up moments), groups and their boxes
     const int64_t cap_c = g->cap_c;
-    for (int l = int(lvl0.size()) - 1; l >= 0; l--)
-        k_moments_level<<<grid, 256, 0, st>>>(ctx->st, g->C, lvl0[size_t(l)], lvln[size_t(l)], cap_c, g->mom);
+    for (int d = kMaxDepth; d >= 0; d--) k_moments_level<<<grid, 256, 0, st>>>(ctx->st, g->C, g->gc, d, cap_c, g->mom);
     k_node_records<<<grid, 256, 0, st>>>(ctx->st, g->C, g->P, ncells, cap_c, g->mom, n, t);
     k_group_flags<<<grid, 256, 0, st>>>(g->P, ncells, ctx->cfg.n_crit, g->gflag);
     int rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->gflag, g->gpos, ncells, st);
     if (rc) return gfail(ctx, rc, "hh_rebuild: scan failed");
-    const int32_t G = d2h(g->gpos + ncells - 1, st) + d2h(g->gflag + ncells - 1, st);
-    if (G > ctx->cap_g) return gfail(ctx, HH_ENOMEM, "hh_rebuild: more groups than groups_max");
+    k_store_count<<<1, 1, 0, st>>>(&g->gc->G, g->gflag, g->gpos, ncells);
     k_groups<<<grid, 256, 0, st>>>(g->P, ncells, g->gflag, g->gpos, g->g_cell, ctx->group_of);
-    k_group_box<<<grid, 256, 0, st>>>(ctx->st, g->P, G, g->g_cell, g->box_lo, g->box_hi, g->box_f);
+    k_group_box<<<grid, 256, 0, st>>>(ctx->st, g->P, g->gc, g->g_cell, g->box_lo, g->box_hi, g->box_f);
+    // 5. lists: cut of subtrees of <= S cells and the cells above it, then
+    //    per-(group, cut cell) counts, scans, offsets, write
+    const int32_t S = std::max<int32_t>(32, ncells / 256);
+    k_cut_flags<<<grid, 256, 0, st>>>(g->P, ncells, S, g->cnt);
+    if ((rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->cnt, g->offs, ncells, st)))
+        return gfail(ctx, rc, "hh_rebuild: scan failed");
+    k_store_count<<<1, 1, 0, st>>>(&g->gc->R, g->cnt, g->offs, ncells);
+    k_cut_write<<<grid, 256, 0, st>>>(ncells, g->cnt, g->offs, g->cut);
+    k_above_flags<<<grid, 256, 0, st>>>(g->P, ncells, S, g->gflag);
+    if ((rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->gflag, g->gpos, ncells, st)))
+        return gfail(ctx, rc, "hh_rebuild: scan failed");
+    k_store_count<<<1, 1, 0, st>>>(&g->gc->A, g->gflag, g->gpos, ncells);
+    k_cut_write<<<grid, 256, 0, st>>>(ncells, g->gflag, g->gpos, g->above);
+    launches += (kMaxDepth + 1) + 16;
+    if (!read_counts()) return gfail(ctx, HH_ECUDA, "hh_rebuild: group build failed");
+    const int32_t G = g->gc_host->G, R = g->gc_host->R, A = g->gc_host->A;
+    if (G > ctx->cap_g) return gfail(ctx, HH_ENOMEM, "hh_rebuild: more groups than groups_max");
     WalkArgs W;
     W.s = ctx->st;
     W.P = g->P;
@@ -852,21 +905,6 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
     W.theta = ctx->cfg.theta;
     W.theta_f = float(ctx->cfg.theta);
     W.xmax = g->xmax;
-    // 5. lists: cut of subtrees of <= S cells, per-(group, cut cell) counts,
-    //    scans, offsets, write
-    const int32_t S = std::max<int32_t>(32, ncells / 256);
-    k_cut_flags<<<grid, 256, 0, st>>>(g->P, ncells, S, g->cnt);
-    if ((rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->cnt, g->offs, ncells, st)))
-        return gfail(ctx, rc, "hh_rebuild: scan failed");
-    const int32_t R = d2h(g->offs + ncells - 1, st) + d2h(g->cnt + ncells - 1, st);
-    k_cut_write<<<grid, 256, 0, st>>>(ncells, g->cnt, g->offs, g->cut);
-    // cells above the cut (the group flags are free again) and, per group,
-    // the topmost unopened cell on the path to each of them
-    k_above_flags<<<grid, 256, 0, st>>>(g->P, ncells, S, g->gflag);
-    if ((rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->gflag, g->gpos, ncells, st)))
-        return gfail(ctx, rc, "hh_rebuild: scan failed");
-    const int32_t A = d2h(g->gpos + ncells - 1, st) + d2h(g->gflag + ncells - 1, st);
-    k_cut_write<<<grid, 256, 0, st>>>(ncells, g->gflag, g->gpos, g->above);
     const int64_t top_n = std::max<int64_t>(1, int64_t(G) * A);
     if (top_n > g->top_cap) {
         if (g->top_buf) cudaFree(g->top_buf);
@@ -878,8 +916,10 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
         }
         g->top_cap = top_n;
     }
-    if (A > 0)
+    if (A > 0) {
         k_top_above<<<unsigned((int64_t(G) * A + 127) / 128), 128, 0, st>>>(W, g->above, A, g->top_buf);
+        launches++;
+    }
     const int64_t pairs = int64_t(G) * R;
     if (pairs + 1 >= int64_t(INT32_MAX)) return gfail(ctx, HH_ENOMEM, "hh_rebuild: too many (group, subtree) pairs");
     if (4 * (pairs + 1) > g->pair_cap) {
@@ -896,13 +936,25 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
     const int64_t lgrid = std::min<int64_t>((pairs + 127) / 128, int64_t(1) << 30);
     k_lists_cut<false><<<unsigned(lgrid), 128, 0, st>>>(W, g->cut, R, g->gpos, g->top_buf, A, cnt_p, cnt_n, nullptr,
                                                         nullptr, nullptr);
+    launches++;
     cudaMemsetAsync(cnt_p + pairs, 0, sizeof(int64_t), st);
     cudaMemsetAsync(cnt_n + pairs, 0, sizeof(int64_t), st);
     if ((rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, cnt_p, scan_p, pairs + 1, st)) ||
         (rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, cnt_n, scan_n, pairs + 1, st)))
         return gfail(ctx, rc, "hh_rebuild: scan failed");
     k_list_off<<<grid, 256, 0, st>>>(G, R, scan_p, scan_n, ctx->off);
-    const int64_t L = d2h(ctx->off + G, st);
+    // 6. tiles and their work-item capacity (from the list lengths)
+    k_tile_counts<<<grid, 256, 0, st>>>(g->g_cell, g->P, G, ctx->tile_i, ctx->off, ctx->part_len, g->ntile, g->nparts);
+    cudaMemsetAsync(g->ntile + G, 0, sizeof(int64_t), st);
+    cudaMemsetAsync(g->nparts + G, 0, sizeof(int64_t), st);
+    if ((rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->ntile, g->tile_off, G + 1, st)) ||
+        (rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->nparts, g->parts_off, G + 1, st)))
+        return gfail(ctx, rc, "hh_rebuild: scan failed");
+    k_store_totals<<<1, 1, 0, st>>>(g->gc, ctx->off + G, g->tile_off + G, g->parts_off + G);
+    launches += 4;
+    if (!read_counts()) return gfail(ctx, HH_ECUDA, "hh_rebuild: list count failed");
+    const int64_t L = g->gc_host->L, n_tiles = g->gc_host->n_tiles, total_parts = g->gc_host->total_parts;
+    if (n_tiles > ctx->cap_tiles) return gfail(ctx, HH_ENOMEM, "hh_rebuild: too many tiles");
     if (L > ctx->cap_list) {  // the list buffer grows (by a quarter beyond the need)
         const int64_t cap = L + L / 4 + 1024;
         int32_t *idx = nullptr;
@@ -917,22 +969,11 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
     }
     k_lists_cut<true><<<unsigned(lgrid), 128, 0, st>>>(W, g->cut, R, g->gpos, g->top_buf, A, nullptr, nullptr, scan_p,
                                                        scan_n, ctx->idx);
-    // 6. tiles and their work-item capacity
-    k_tile_counts<<<grid, 256, 0, st>>>(g->g_cell, g->P, G, ctx->tile_i, ctx->off, ctx->part_len, g->ntile, g->nparts);
-    cudaMemsetAsync(g->ntile + G, 0, sizeof(int64_t), st);
-    cudaMemsetAsync(g->nparts + G, 0, sizeof(int64_t), st);
-    if ((rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->ntile, g->tile_off, G + 1, st)) ||
-        (rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->nparts, g->parts_off, G + 1, st)))
-        return gfail(ctx, rc, "hh_rebuild: scan failed");
-    const int64_t n_tiles = d2h(g->tile_off + G, st), total_parts = d2h(g->parts_off + G, st);
-    if (n_tiles > ctx->cap_tiles) return gfail(ctx, HH_ENOMEM, "hh_rebuild: too many tiles");
     k_tiles<<<grid, 256, 0, st>>>(g->g_cell, g->P, G, ctx->tile_i, g->tile_off, ctx->tiles);
+    launches += 2;
     const cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) return gfail(ctx, HH_ECUDA, cudaGetErrorString(ce));
-    // kernels of this file: 18 fixed (19 with the table above the cut) plus 5
-    // per tree level (count, write,
-    // subtree size, pre-order, moments); the radix sort and scans are CUB's
-    hh_count_launches(18 + (A > 0 ? 1 : 0) + 5 * int64_t(lvl0.size()));
+    hh_count_launches(launches);  // kernels of this file; the radix sort and the scans are CUB's
     ctx->nj = n + ncells;
     ctx->n_groups = G;
     ctx->list_len = L;
