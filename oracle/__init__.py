@@ -67,6 +67,12 @@ def lib():
         L.hho_initial_dt.restype = C.c_double
         L.hho_tree_build.argtypes = [C.c_int, _D, _D, _D, _D, _D, C.c_int, C.c_int, C.c_double]
         L.hho_tree_build.restype = C.c_void_p
+        L.hho_tree_build_ordered.argtypes = [C.c_int, _D, _D, _D, _D, _D, C.c_int, C.c_int, C.c_double, C.c_int]
+        L.hho_tree_build_ordered.restype = C.c_void_p
+        L.hho_morton_key.argtypes = [C.c_uint32] * 3
+        L.hho_morton_key.restype = C.c_uint64
+        L.hho_hilbert_key.argtypes = [C.c_uint32] * 3 + [C.c_int]
+        L.hho_hilbert_key.restype = C.c_uint64
         L.hho_tree_free.argtypes = [C.c_void_p]
         for f in ("hho_tree_n_cells", "hho_tree_n_groups"):
             getattr(L, f).argtypes = [C.c_void_p]
@@ -201,11 +207,24 @@ class Tree:
                 cat(m, self.node_m))
 
 
-def tree_build(x, v, a, jk, m, leaf=8, n_crit=64, theta=0.5) -> Tree:
+def morton_key(ix, iy, iz):
+    return int(lib().hho_morton_key(int(ix), int(iy), int(iz)))
+
+
+def hilbert_key(ix, iy, iz, bits):
+    """Peano-Hilbert index of cell (ix, iy, iz) of a 2^bits grid (Section 2's order)."""
+    return int(lib().hho_hilbert_key(int(ix), int(iy), int(iz), int(bits)))
+
+
+ORDERS = {"morton": 0, "hilbert": 1}
+
+
+def tree_build(x, v, a, jk, m, leaf=8, n_crit=64, theta=0.5, order="morton") -> Tree:
     n = len(m)
     L = lib()
-    h = L.hho_tree_build(n, _v3(x, n), _v3(v, n), _v3(a, n), _v3(jk, n),
-                         np.ascontiguousarray(m, dtype=np.float64), int(leaf), int(n_crit), float(theta))
+    h = L.hho_tree_build_ordered(n, _v3(x, n), _v3(v, n), _v3(a, n), _v3(jk, n),
+                                 np.ascontiguousarray(m, dtype=np.float64), int(leaf), int(n_crit), float(theta),
+                                 ORDERS[order])
     if not h:
         raise ValueError("hho_tree_build failed")
     try:

@@ -14,8 +14,9 @@
  *     Barnes 1990 grouping with n_crit (Section 2);
  *   - tree nodes as pseudo-particles with position, velocity, acceleration and
  *     jerk that are predicted like particles (Section 2, step 1).
- * Every point where the paper is silent is a documented reading; the tree is
- * Morton-ordered (the paper uses Peano-Hilbert order, Section 2).
+ * Every point where the paper is silent is a documented reading.  The tree is
+ * Morton-ordered by default; Peano-Hilbert order (the paper's, Section 2) is an
+ * option: it orders the same octree's children along the curve.
  *
  * Plain by intent: sums run in index order, no blocking or reordering; OpenMP
  * only splits independent i-particles (or groups) across threads.
@@ -277,6 +278,47 @@ static uint64_t spread3(uint32_t u)
     return out;
 }
 
+uint64_t hho_morton_key(uint32_t ix, uint32_t iy, uint32_t iz)
+{
+    return (spread3(ix) << 2) | (spread3(iy) << 1) | spread3(iz);
+}
+
+/* Peano-Hilbert index of cell (ix, iy, iz) of a 2^bits grid, after Skilling
+ * (2004, "Programming the Hilbert curve").  Working from the top bit down,
+ * each lower bit field of the three coordinates is brought into the frame of
+ * the sub-cube the higher bits selected: where a coordinate's current bit is
+ * set, the low bits of the first coordinate are complemented, otherwise the
+ * low bits of the first coordinate and that coordinate are swapped.  The
+ * coordinates are then Gray-coded against each other, a common correction
+ * from the last coordinate's bits is applied, and the bits are read out
+ * level by level, first coordinate first, giving 3 bits per level. */
+uint64_t hho_hilbert_key(uint32_t ix, uint32_t iy, uint32_t iz, int bits)
+{
+    uint32_t c[3] = {ix, iy, iz};
+    for (int lev = bits - 1; lev >= 1; lev--) {
+        const uint32_t bit = 1u << lev, low = bit - 1u;
+        for (int k = 0; k < 3; k++) {
+            if (c[k] & bit) {
+                c[0] ^= low;
+            } else {
+                const uint32_t diff = (c[0] ^ c[k]) & low;
+                c[0] ^= diff;
+                c[k] ^= diff;
+            }
+        }
+    }
+    c[1] ^= c[0];
+    c[2] ^= c[1];
+    uint32_t fix = 0;
+    for (int lev = bits - 1; lev >= 1; lev--)
+        if (c[2] & (1u << lev)) fix ^= (1u << lev) - 1u;
+    for (int k = 0; k < 3; k++) c[k] ^= fix;
+    uint64_t key = 0;
+    for (int lev = bits - 1; lev >= 0; lev--)
+        for (int k = 0; k < 3; k++) key = (key << 1) | ((c[k] >> lev) & 1u);
+    return key;
+}
+
 static int new_cell(hho_tree *t)
 {
     if (t->n_cells == t->cap_cells) {
@@ -409,6 +451,13 @@ hho_tree *hho_tree_build(int n, const double *x, const double *v, const double *
                          const double *jk, const double *m,
                          int leaf, int n_crit, double theta)
 {
+    return hho_tree_build_ordered(n, x, v, a, jk, m, leaf, n_crit, theta, 0);
+}
+
+hho_tree *hho_tree_build_ordered(int n, const double *x, const double *v, const double *a,
+                                 const double *jk, const double *m,
+                                 int leaf, int n_crit, double theta, int order)
+{
     if (n < 1 || leaf < 1 || n_crit < 1) return NULL;
     hho_tree *t = calloc(1, sizeof(hho_tree));
     t->n = n;
@@ -438,7 +487,7 @@ hho_tree *hho_tree_build(int n, const double *x, const double *v, const double *
             if (f > (double)MORTON_MAX) f = (double)MORTON_MAX;
             u[k] = (uint32_t)f;
         }
-        ki[i].key = (spread3(u[0]) << 2) | (spread3(u[1]) << 1) | spread3(u[2]);
+        ki[i].key = order == 1 ? hho_hilbert_key(u[0], u[1], u[2], MORTON_BITS) : hho_morton_key(u[0], u[1], u[2]);
         ki[i].idx = i;
     }
     qsort(ki, n, sizeof(key_idx), cmp_key_idx);

@@ -65,12 +65,23 @@ double hho_block_dt(double dt_want, double dt_old, double t_new, double dt_min, 
 double hho_initial_dt(double eta_s, const double a[3], const double j[3],
                       double dt_min, double dt_max);
 
-/* ---- Morton octree, groups and interaction lists ---- */
+/* ---- Octree (Morton or Peano-Hilbert order), groups and interaction lists ---- */
 typedef struct hho_tree hho_tree;
 
+/* 3-bits-per-level keys of grid cell (ix, iy, iz): Morton (bit interleaving,
+ * x highest) and Peano-Hilbert (Section 2; Skilling 2004) on a 2^bits grid. */
+uint64_t hho_morton_key(uint32_t ix, uint32_t iy, uint32_t iz);
+uint64_t hho_hilbert_key(uint32_t ix, uint32_t iy, uint32_t iz, int bits);
+
+/* order 0: Morton (hho_tree_build), 1: Peano-Hilbert.  The octree and the
+ * groups are the same in both orders; only the order of children, and so of
+ * particles, nodes and list entries, differs. */
 hho_tree *hho_tree_build(int n, const double *x, const double *v, const double *a,
                          const double *jk, const double *m,
                          int leaf, int n_crit, double theta);
+hho_tree *hho_tree_build_ordered(int n, const double *x, const double *v, const double *a,
+                                 const double *jk, const double *m,
+                                 int leaf, int n_crit, double theta, int order);
 void     hho_tree_free(hho_tree *t);
 int      hho_tree_n_cells(const hho_tree *t);
 int      hho_tree_n_groups(const hho_tree *t);

@@ -350,3 +350,76 @@ def test_table1_mean_list_length_soft(orc):
         assert 0.5 < nint / row["N_int"] < 2.0, (row, nint)
         got.append(nint)
     assert got[0] < got[1] < got[2]
+
+
+# ---- Peano-Hilbert order (Section 2 orders the tree along the curve) ----
+
+def _grid(bits):
+    n = 1 << bits
+    return [(i, j, k) for i in range(n) for j in range(n) for k in range(n)]
+
+
+@pytest.mark.parametrize("bits", [1, 2, 3, 4])
+def test_hilbert_key_is_a_unit_step_walk(orc, bits):
+    # a Peano-Hilbert curve visits every cell of the 2^bits grid once and each
+    # step moves to a face neighbour (one coordinate changes by one)
+    cells = _grid(bits)
+    keys = [orc.hilbert_key(*c, bits) for c in cells]
+    assert sorted(keys) == list(range(len(cells)))
+    by_key = [None] * len(cells)
+    for c, k in zip(cells, keys):
+        by_key[k] = c
+    for a, b in zip(by_key, by_key[1:]):
+        assert sum(abs(p - q) for p, q in zip(a, b)) == 1
+
+
+def test_hilbert_key_nests_octree_cubes(orc):
+    # every aligned sub-cube of side 2^s is one contiguous run of 8^s keys, and
+    # the key's top 3 (bits - s) bits name it: splitting sorted keys on 3-bit
+    # digits builds the octree, as with Morton keys
+    bits = 4
+    for s in (1, 2, 3):
+        prefix = {}
+        for c in _grid(bits):
+            cube = tuple(u >> s for u in c)
+            prefix.setdefault(cube, set()).add(orc.hilbert_key(*c, bits) >> (3 * s))
+        assert all(len(p) == 1 for p in prefix.values())
+        assert len({next(iter(p)) for p in prefix.values()}) == len(prefix)
+
+
+def test_morton_key_interleaves_bits(orc):
+    # bit b of x, y, z goes to bit 3b + 2, 3b + 1, 3b of the key
+    assert (orc.morton_key(1, 0, 0), orc.morton_key(0, 1, 0), orc.morton_key(0, 0, 1)) == (4, 2, 1)
+    assert orc.morton_key(2, 3, 1) == 32 + (2 + 16) + 1
+
+
+def test_hilbert_tree_is_the_same_octree(orc):
+    # The order changes which particle and node sit where, not the tree: the
+    # same cells (as node mass and centre), the same groups, the same list
+    # length per particle, and forces from either set of lists agree.
+    x, v, m = synth.plummer_salpeter(1500, 9)
+    a0, j0, _ = orc.direct_force(x, v, m, 1e-6)
+    Tm = orc.tree_build(x, v, a0, j0, m, leaf=8, n_crit=32, theta=0.5, order="morton")
+    Th = orc.tree_build(x, v, a0, j0, m, leaf=8, n_crit=32, theta=0.5, order="hilbert")
+    assert not np.array_equal(Tm.perm, Th.perm)
+    assert Tm.n_cells == Th.n_cells and Tm.n_groups == Th.n_groups
+    km = np.lexsort((Tm.node_x[:, 2], Tm.node_x[:, 1], Tm.node_x[:, 0], Tm.node_m))
+    kh = np.lexsort((Th.node_x[:, 2], Th.node_x[:, 1], Th.node_x[:, 0], Th.node_m))
+    np.testing.assert_allclose(Th.node_m[kh], Tm.node_m[km], rtol=1e-13)
+    np.testing.assert_allclose(Th.node_x[kh], Tm.node_x[km], rtol=1e-12, atol=1e-14)
+    len_m = np.empty(1500, np.int64)
+    len_h = np.empty(1500, np.int64)
+    len_m[Tm.perm] = np.diff(Tm.list_off)[Tm.group_of]
+    len_h[Th.perm] = np.diff(Th.list_off)[Th.group_of]
+    assert np.array_equal(len_m, len_h)
+    out = []
+    for T in (Tm, Th):
+        xj, vj, aj, jj, mj = T.j_array(x, v, a0, j0, m)
+        acc, jerk, pot = orc.list_force(xj, vj, mj, np.arange(1500), T.group_of, T.list_off, T.list_idx, 1e-6)
+        a_in = np.empty_like(acc)
+        a_in[T.perm] = acc
+        p_in = np.empty_like(pot)
+        p_in[T.perm] = pot
+        out.append((a_in, p_in))
+    np.testing.assert_allclose(out[1][0], out[0][0], rtol=1e-11, atol=1e-12 * np.abs(out[0][0]).max())
+    np.testing.assert_allclose(out[1][1], out[0][1], rtol=1e-12)
