@@ -70,6 +70,8 @@ def _args():
                    help="end time of every ensemble cluster (a multiple of dt_tree = 1/64)")
     p.add_argument("--serve-seconds", type=float, default=20.0, help="wall time of the serving measurement (0: skip)")
     p.add_argument("--no-autotune", action="store_true", help="skip the tile-shape autotuner (use the defaults)")
+    p.add_argument("--order", default="morton", choices=["morton", "hilbert"],
+                   help="order of particles and nodes in the tree (Peano-Hilbert is the paper's)")
     p.add_argument("--rebuild", default="device", choices=["device", "host"],
                    help="where the tree, groups and lists are rebuilt every dt_tree")
     p.add_argument("--loop", default="persistent", choices=["persistent", "graph"],
@@ -99,6 +101,7 @@ def _cfg(hh, prec, a):
     c.tile_i = a.tile_i or 0
     c.tile_j = (a.tile_j if prec == hh.HH_FP64 else a.tile_j_mixed) or 0
     c.work_item = (a.work_item if prec == hh.HH_FP64 else a.work_item_mixed) or 0
+    c.order = hh.HH_ORDER_HILBERT if a.order == "hilbert" else hh.HH_ORDER_MORTON
     return c
 
 
@@ -365,7 +368,8 @@ def _ensemble(hh, a):
         sub = [r for r, mb in zip(reqs, members) if mb.theta == th]
         srv = serve.Server(precision=hh.HH_MIXED, budget_bytes=150 * 10 ** 9, max_sims=256, max_steps=64,
                            theta=th, n_crit=a.n_crit, rebuild_threads=8,
-                           rebuild_device=a.rebuild == "device")
+                           rebuild_device=a.rebuild == "device",
+                           order=hh.HH_ORDER_HILBERT if a.order == "hilbert" else hh.HH_ORDER_MORTON)
         res, st = srv.run(sub, realtime=False)
         srv.close()
         results += res
@@ -400,7 +404,8 @@ def _serving(hh, a):
     reqs = [serve.SimRequest(r.rid, None, None, None, r.t_end, arrival_s=r.arrival_s,
                              make=(lambda n=r.n, sd=r.seed: synth.plummer_salpeter(n, sd))) for r in stream]
     srv = serve.Server(precision=hh.HH_MIXED, budget_bytes=150 * 10 ** 9, max_sims=256, max_steps=32,
-                       n_crit=a.n_crit, rebuild_threads=8, rebuild_device=a.rebuild == "device")
+                       n_crit=a.n_crit, rebuild_threads=8, rebuild_device=a.rebuild == "device",
+                       order=hh.HH_ORDER_HILBERT if a.order == "hilbert" else hh.HH_ORDER_MORTON)
     res, st = srv.run(reqs, realtime=True, max_wall_s=a.serve_seconds)
     srv.close()
     return {"requests_arrived": sum(1 for r in stream if r.arrival_s <= st.wall_s), "completed": len(res),
@@ -563,6 +568,7 @@ def main():
             "gpu_launches": int(tot[3]),
             "loop": a.loop,
             "rebuild": a.rebuild,
+            "order": a.order,
             "tuning": {"fp64": {"chosen": best64, "candidates": table64},
                        "mixed": {"chosen": bestmx, "candidates": tablemx},
                        "note": "autotuner runs before the timed region (paper_1602_02832_gb300/autotune.py)"},

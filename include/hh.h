@@ -74,7 +74,14 @@ typedef struct hh_config {
     int32_t work_item; /* 0 (default): every list part is tile_j entries long.  > 0: a tile with
                           n_a active particles takes parts of about work_item / n_a entries (at
                           least tile_j), so that work items cost about the same */
+    int32_t order;     /* particle and node order of hh_rebuild's tree: HH_ORDER_MORTON (0,
+                          default) or HH_ORDER_HILBERT (1, Peano-Hilbert, the paper's order,
+                          Section 2).  The octree, groups and interaction sets are the same;
+                          only the positions of particles, nodes and list entries differ */
 } hh_config;
+
+#define HH_ORDER_MORTON 0
+#define HH_ORDER_HILBERT 1
 
 typedef struct hh_counters {
     int64_t block_steps;    /* block steps executed (step 2-7 passes) */
@@ -324,6 +331,11 @@ int hh_force_static(int device, int precision, double eps2, int64_t n_j, const d
 typedef struct hh_tree hh_tree;
 int hh_tree_build(hh_tree **out, int64_t n, const double *x, const double *v, const double *a,
                   const double *jk, const double *m, int32_t leaf, int32_t n_crit, double theta);
+/* The same with the order of the tree: HH_ORDER_MORTON or HH_ORDER_HILBERT
+ * (HH_EINVAL otherwise). */
+int hh_tree_build_ordered(hh_tree **out, int64_t n, const double *x, const double *v, const double *a,
+                          const double *jk, const double *m, int32_t leaf, int32_t n_crit, double theta,
+                          int32_t order);
 int hh_tree_sizes(const hh_tree *t, int64_t *n_nodes, int32_t *n_groups, int64_t *list_len);
 /* perm[k] = input index of Morton slot k; node arrays SoA [3][n_nodes]. */
 int hh_tree_export(const hh_tree *t, int32_t *perm, double *node_x, double *node_v,

@@ -27,6 +27,7 @@ _lib = C.CDLL(LIB_PATH)
 
 HH_OK, HH_EINVAL, HH_ENOMEM, HH_ECUDA, HH_ETIMEOUT, HH_ESTATE = 0, -1, -2, -3, -4, -5
 HH_FP64, HH_MIXED = 0, 1
+HH_ORDER_MORTON, HH_ORDER_HILBERT = 0, 1
 _ERR_NAMES = {HH_EINVAL: "HH_EINVAL", HH_ENOMEM: "HH_ENOMEM", HH_ECUDA: "HH_ECUDA", HH_ETIMEOUT: "HH_ETIMEOUT",
               HH_ESTATE: "HH_ESTATE"}
 
@@ -41,7 +42,7 @@ class hh_config(C.Structure):
     _fields_ = [("eps2", C.c_double), ("eta", C.c_double), ("eta_s", C.c_double), ("dt_min", C.c_double),
                 ("dt_max", C.c_double), ("dt_tree", C.c_double), ("theta", C.c_double), ("leaf", C.c_int32),
                 ("n_crit", C.c_int32), ("precision", C.c_int32), ("tile_i", C.c_int32), ("tile_j", C.c_int32),
-                ("work_item", C.c_int32)]
+                ("work_item", C.c_int32), ("order", C.c_int32)]
 
 
 class hh_counters(C.Structure):
@@ -85,6 +86,8 @@ _SIGS = {
     "hh_kernel_launches": (C.c_int64, []),
     "hh_last_error": (C.c_char_p, [_P]),
     "hh_tree_build": (C.c_int, [C.POINTER(_P), C.c_int64, _D, _D, _D, _D, _D, C.c_int32, C.c_int32, C.c_double]),
+    "hh_tree_build_ordered": (C.c_int, [C.POINTER(_P), C.c_int64, _D, _D, _D, _D, _D, C.c_int32, C.c_int32, C.c_double,
+                                        C.c_int32]),
     "hh_tree_sizes": (C.c_int, [_P, _I64, _I32, _I64]),
     "hh_tree_export": (C.c_int, [_P, _I32, _D, _D, _D, _D, _D, _I64, _I32, _I32]),
     "hh_tree_free": (C.c_int, [_P]),
@@ -347,12 +350,14 @@ class Tree:
         return len(self.off) - 1
 
 
-def hh_tree_build(x, v, a, jk, m, leaf=8, n_crit=64, theta=0.5) -> Tree:
-    """Host tree, groups and lists (SoA [3, n] inputs, any particle order)."""
+def hh_tree_build(x, v, a, jk, m, leaf=8, n_crit=64, theta=0.5, order=0) -> Tree:
+    """Host tree, groups and lists (SoA [3, n] inputs, any particle order);
+    order HH_ORDER_MORTON (0) or HH_ORDER_HILBERT (1)."""
     n = len(m)
     arrs = [_f64(u, (3, n)) for u in (x, v, a, jk)] + [_f64(m, (n,))]
     h = _P()
-    _check(_lib.hh_tree_build(C.byref(h), n, *[_ptr(u) for u in arrs], int(leaf), int(n_crit), float(theta)))
+    _check(_lib.hh_tree_build_ordered(C.byref(h), n, *[_ptr(u) for u in arrs], int(leaf), int(n_crit), float(theta),
+                                      int(order)))
     try:
         nn, ng, ll = C.c_int64(), C.c_int32(), C.c_int64()
         _check(_lib.hh_tree_sizes(h, C.byref(nn), C.byref(ng), C.byref(ll)))

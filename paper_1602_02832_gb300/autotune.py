@@ -36,9 +36,9 @@ CANDIDATES = {
 _CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 
-def _key(device_name, precision, n, theta, rebuild_device):
+def _key(device_name, precision, n, theta, rebuild_device, order=0):
     return f"{device_name}|{'mixed' if precision == HH_MIXED else 'fp64'}|n2^{round(math.log2(max(n, 2)))}|" \
-           f"theta{theta}|{'dev' if rebuild_device else 'host'}"
+           f"theta{theta}|{'dev' if rebuild_device else 'host'}|order{order}"
 
 
 def _run_candidate(x, v, m, base, cand, intervals, warm, rebuild_device):
@@ -49,7 +49,7 @@ def _run_candidate(x, v, m, base, cand, intervals, warm, rebuild_device):
     for k, val in cand.items():
         setattr(cfg, k, val)
     z = np.zeros((3, n))
-    T = hh_tree_build(x.T, v.T, z, z, m, leaf=cfg.leaf, n_crit=cfg.n_crit, theta=cfg.theta)
+    T = hh_tree_build(x.T, v.T, z, z, m, leaf=cfg.leaf, n_crit=cfg.n_crit, theta=cfg.theta, order=cfg.order)
     dtt = cfg.dt_tree
     with Context(cfg, n, 2 * n, int(2 * len(T.idx)) + 1024, 2 * T.n_groups + 64) as ctx, \
             Batch(cfg.precision, max_sims=1, max_steps=4096) as b:
@@ -88,7 +88,7 @@ def tune(x, v, m, base_cfg, intervals=1, warm=1, use_cache=True, device_name=Non
             device_name = torch.cuda.get_device_name(0)
         except Exception:
             device_name = "cuda"
-    key = _key(device_name, base_cfg.precision, len(m), round(base_cfg.theta, 3), rebuild_device)
+    key = _key(device_name, base_cfg.precision, len(m), round(base_cfg.theta, 3), rebuild_device, base_cfg.order)
     cache = {}
     if use_cache and os.path.exists(_CACHE):
         try:

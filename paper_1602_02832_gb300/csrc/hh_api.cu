@@ -404,9 +404,10 @@ int hh_create(hh_ctx **out, int device, const hh_config *cfg, int64_t n_max, int
         return hh_set_global_error(HH_EINVAL, "hh_create: bad capacities");
     if (!(c.eps2 >= 0.0) || !(c.eta > 0.0) || !(c.eta_s > 0.0) || !is_pow2(c.dt_min) || !is_pow2(c.dt_max) ||
         c.dt_max < c.dt_min || !is_pow2(c.dt_tree) || c.dt_max > c.dt_tree || !(c.theta >= 0.0) || c.leaf < 1 ||
-        c.n_crit < 1 || (c.precision != HH_FP64 && c.precision != HH_MIXED))
+        c.n_crit < 1 || (c.precision != HH_FP64 && c.precision != HH_MIXED) ||
+        (c.order != HH_ORDER_MORTON && c.order != HH_ORDER_HILBERT))
         return hh_set_global_error(HH_EINVAL, "hh_create: bad configuration (steps must be powers of two, "
-                                              "dt_min <= dt_max <= dt_tree, eps2 >= 0, eta > 0)");
+                                              "dt_min <= dt_max <= dt_tree, eps2 >= 0, eta > 0, order 0 or 1)");
     if (c.tile_i == 0) c.tile_i = 32;
     if (c.tile_i < 1 || c.tile_i > kMaxTileI) return hh_set_global_error(HH_EINVAL, "hh_create: tile_i must be 1..32");
     const int chunk = c.precision == HH_MIXED ? kTjMix : kTjF64;
@@ -974,7 +975,8 @@ int hh_rebuild(hh_ctx *ctx, double t)
     CK(cudaStreamSynchronize(ctx->stream));
     for (int64_t q = 0; q < n; q++)
         if (ht[q] != t) return fail(ctx, HH_ESTATE, "hh_rebuild: particles are not synchronised at t");
-    if ((rc = hh_tree_rebuild(&ctx->tree, n, hx, hv, ha, hj, hm, ctx->cfg.leaf, ctx->cfg.n_crit, ctx->cfg.theta)))
+    if ((rc = hh_tree_rebuild(&ctx->tree, n, hx, hv, ha, hj, hm, ctx->cfg.leaf, ctx->cfg.n_crit, ctx->cfg.theta,
+                              ctx->cfg.order)))
         return fail(ctx, rc, std::string("hh_rebuild: ") + g_err);
     HhTreeView V;
     hh_tree_view(ctx->tree, &V);

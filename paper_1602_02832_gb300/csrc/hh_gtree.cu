@@ -52,6 +52,34 @@ __device__ __forceinline__ uint64_t spread_bits(uint32_t v)
 
 __device__ __forceinline__ int digit_at(uint64_t key, int depth) { return int((key >> (3 * (kBits - 1 - depth))) & 7u); }
 
+// Peano-Hilbert key of a cell of the 2^21 grid (Skilling 2004): the low bit
+// fields are mapped level by level into each sub-cube's frame, Gray-coded,
+// and the resulting transposed index is interleaved like a Morton key.
+__device__ __forceinline__ uint64_t hilbert_key(uint32_t a0, uint32_t a1, uint32_t a2)
+{
+    uint32_t c[3] = {a0, a1, a2};
+#pragma unroll 1
+    for (uint32_t q = 1u << (kBits - 1); q > 1u; q >>= 1) {
+        const uint32_t p = q - 1u;
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            const uint32_t t = (c[0] ^ c[i]) & p;
+            if (c[i] & q) {
+                c[0] ^= p;
+            } else {
+                c[0] ^= t;
+                c[i] ^= t;
+            }
+        }
+    }
+    c[1] ^= c[0];
+    c[2] ^= c[1];
+    uint32_t flip = 0;
+    for (uint32_t q = 1u << (kBits - 1); q > 1u; q >>= 1)
+        if (c[2] & q) flip ^= q - 1u;
+    return (spread_bits(c[0] ^ flip) << 2) | (spread_bits(c[1] ^ flip) << 1) | spread_bits(c[2] ^ flip);
+}
+
 struct Box {
     unsigned long long lo[3], hi[3];  // order bits
     int32_t bad;                      // a particle not at the tree time
@@ -95,7 +123,7 @@ __global__ void k_box(const State s, int64_t n, double t_tree, Box *b)
 }
 
 __global__ void k_keys(const State s, int64_t n, const Box *b, uint64_t *key, int32_t *idx, double *root_side,
-                       float *xmax)
+                       float *xmax, int order)
 {
     double lo[3], side = 0.0;
     for (int d = 0; d < 3; d++) {
@@ -112,14 +140,15 @@ __global__ void k_keys(const State s, int64_t n, const Box *b, uint64_t *key, in
         *xmax = float(xm) * 1.0001f;
     }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t k = 0;
+        uint32_t u[3];
         for (int d = 0; d < 3; d++) {
             double f = floor((s.x[d * s.cap_j + i] - lo[d]) * scale);
             f = f < 0.0 ? 0.0 : f;
             f = f > double((1u << kBits) - 1u) ? double((1u << kBits) - 1u) : f;
-            k |= spread_bits(uint32_t(f)) << (2 - d);
+            u[d] = uint32_t(f);
         }
-        key[i] = k;
+        key[i] = order == HH_ORDER_HILBERT ? hilbert_key(u[0], u[1], u[2])
+                                           : (spread_bits(u[0]) << 2) | (spread_bits(u[1]) << 1) | spread_bits(u[2]);
         idx[i] = int32_t(i);
     }
 }
@@ -824,7 +853,7 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
     k_root_init<<<1, 1, 0, st>>>(g->C, int32_t(n), g->gc);
     k_box_init<<<1, 1, 0, st>>>(g->box);
     k_box<<<grid, 256, 0, st>>>(ctx->st, n, t, g->box);
-    k_keys<<<grid, 256, 0, st>>>(ctx->st, n, g->box, g->key, g->idx, g->root_side, g->xmax);
+    k_keys<<<grid, 256, 0, st>>>(ctx->st, n, g->box, g->key, g->idx, g->root_side, g->xmax, ctx->cfg.order);
     launches += 4;
     {
         size_t need = 0;

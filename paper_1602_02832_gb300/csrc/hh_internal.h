@@ -22,4 +22,4 @@ struct HhTreeView {
 };
 int hh_tree_view(const hh_tree *t, HhTreeView *v);
 int hh_tree_rebuild(hh_tree **tp, int64_t n, const double *x, const double *v, const double *a, const double *jk,
-                    const double *m, int32_t leaf, int32_t n_crit, double theta);
+                    const double *m, int32_t leaf, int32_t n_crit, double theta, int32_t order);

@@ -42,6 +42,34 @@ inline uint64_t spread_bits(uint32_t v)
 
 inline int digit_at(uint64_t key, int depth) { return int((key >> (3 * (kBits - 1 - depth))) & 7u); }
 
+// Peano-Hilbert key (Skilling 2004): from the top bit level down, the lower
+// bits are mapped into the sub-cube's own frame (complement of the first
+// coordinate's low bits where a coordinate's bit is set, else an exchange of
+// low bits with the first coordinate), the coordinates are Gray-coded, and
+// the transposed index is interleaved like a Morton key.
+inline uint64_t hilbert_key(uint32_t c0, uint32_t c1, uint32_t c2)
+{
+    uint32_t c[3] = {c0, c1, c2};
+    for (uint32_t q = 1u << (kBits - 1); q > 1u; q >>= 1) {
+        const uint32_t p = q - 1u;
+        for (int i = 0; i < 3; i++) {
+            const uint32_t t = (c[0] ^ c[i]) & p;
+            if (c[i] & q) {
+                c[0] ^= p;
+            } else {
+                c[0] ^= t;
+                c[i] ^= t;
+            }
+        }
+    }
+    c[1] ^= c[0];
+    c[2] ^= c[1];
+    uint32_t flip = 0;
+    for (uint32_t q = 1u << (kBits - 1); q > 1u; q >>= 1)
+        if (c[2] & q) flip ^= q - 1u;
+    return (spread_bits(c[0] ^ flip) << 2) | (spread_bits(c[1] ^ flip) << 1) | spread_bits(c[2] ^ flip);
+}
+
 struct Cell {
     int32_t begin, end, depth, n_child;
     int32_t child[8];
@@ -230,9 +258,10 @@ void group_list(const hh_tree &t, int32_t g, double theta, const double *x, std:
 namespace {
 
 int check_inputs(int64_t n, const double *x, const double *v, const double *a, const double *jk, const double *m,
-                 int32_t leaf, int32_t n_crit, double theta)
+                 int32_t leaf, int32_t n_crit, double theta, int32_t order)
 {
-    if (n < 1 || n > INT32_MAX / 2 || !x || !v || !a || !jk || !m || leaf < 1 || n_crit < 1 || !(theta >= 0.0))
+    if (n < 1 || n > INT32_MAX / 2 || !x || !v || !a || !jk || !m || leaf < 1 || n_crit < 1 || !(theta >= 0.0) ||
+        (order != HH_ORDER_MORTON && order != HH_ORDER_HILBERT))
         return hh_set_global_error(HH_EINVAL, "hh_tree_build: bad arguments");
     for (int64_t i = 0; i < 3 * n; i++)
         if (!std::isfinite(x[i]) || !std::isfinite(v[i]) || !std::isfinite(a[i]) || !std::isfinite(jk[i]))
@@ -245,7 +274,7 @@ int check_inputs(int64_t n, const double *x, const double *v, const double *a, c
 
 // Builds into t, reusing the capacity of its vectors.
 int build_into(hh_tree *t, int64_t n, const double *x, const double *v, const double *a, const double *jk,
-               const double *m, int32_t leaf, int32_t n_crit, double theta)
+               const double *m, int32_t leaf, int32_t n_crit, double theta, int32_t order)
 {
     try {
         t->n = n;
@@ -271,13 +300,16 @@ int build_into(hh_tree *t, int64_t n, const double *x, const double *v, const do
         ki.resize(size_t(n));
 #pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; i++) {
-            uint64_t k = 0;
+            uint32_t u[3];
             for (int d = 0; d < 3; d++) {
                 double f = std::floor((x[d * n + i] - lo[d]) * scale);
                 f = f < 0.0 ? 0.0 : f;
                 f = f > double(kMaxCoord) ? double(kMaxCoord) : f;
-                k |= spread_bits(uint32_t(f)) << (2 - d);
+                u[d] = uint32_t(f);
             }
+            const uint64_t k = order == HH_ORDER_HILBERT
+                                   ? hilbert_key(u[0], u[1], u[2])
+                                   : (spread_bits(u[0]) << 2) | (spread_bits(u[1]) << 1) | spread_bits(u[2]);
             ki[size_t(i)] = {k, int32_t(i)};
         }
         std::sort(ki.begin(), ki.end());
@@ -316,13 +348,20 @@ int build_into(hh_tree *t, int64_t n, const double *x, const double *v, const do
 extern "C" int hh_tree_build(hh_tree **out, int64_t n, const double *x, const double *v, const double *a,
                              const double *jk, const double *m, int32_t leaf, int32_t n_crit, double theta)
 {
+    return hh_tree_build_ordered(out, n, x, v, a, jk, m, leaf, n_crit, theta, HH_ORDER_MORTON);
+}
+
+extern "C" int hh_tree_build_ordered(hh_tree **out, int64_t n, const double *x, const double *v, const double *a,
+                                     const double *jk, const double *m, int32_t leaf, int32_t n_crit, double theta,
+                                     int32_t order)
+{
     if (!out) return hh_set_global_error(HH_EINVAL, "hh_tree_build: out is NULL");
     *out = nullptr;
-    int rc = check_inputs(n, x, v, a, jk, m, leaf, n_crit, theta);
+    int rc = check_inputs(n, x, v, a, jk, m, leaf, n_crit, theta, order);
     if (rc) return rc;
     hh_tree *t = new (std::nothrow) hh_tree;
     if (!t) return hh_set_global_error(HH_ENOMEM, "hh_tree_build: out of host memory");
-    rc = build_into(t, n, x, v, a, jk, m, leaf, n_crit, theta);
+    rc = build_into(t, n, x, v, a, jk, m, leaf, n_crit, theta, order);
     if (rc) {
         delete t;
         return rc;
@@ -333,15 +372,15 @@ extern "C" int hh_tree_build(hh_tree **out, int64_t n, const double *x, const do
 
 // Internal: rebuild an existing tree object (or create one if *tp is NULL).
 int hh_tree_rebuild(hh_tree **tp, int64_t n, const double *x, const double *v, const double *a, const double *jk,
-                    const double *m, int32_t leaf, int32_t n_crit, double theta)
+                    const double *m, int32_t leaf, int32_t n_crit, double theta, int32_t order)
 {
-    int rc = check_inputs(n, x, v, a, jk, m, leaf, n_crit, theta);
+    int rc = check_inputs(n, x, v, a, jk, m, leaf, n_crit, theta, order);
     if (rc) return rc;
     if (!*tp) {
         *tp = new (std::nothrow) hh_tree;
         if (!*tp) return hh_set_global_error(HH_ENOMEM, "hh_tree_build: out of host memory");
     }
-    return build_into(*tp, n, x, v, a, jk, m, leaf, n_crit, theta);
+    return build_into(*tp, n, x, v, a, jk, m, leaf, n_crit, theta, order);
 }
 
 extern "C" int hh_tree_sizes(const hh_tree *t, int64_t *n_nodes, int32_t *n_groups, int64_t *list_len)

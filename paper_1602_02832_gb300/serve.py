@@ -82,7 +82,7 @@ class Server:
 
     def __init__(self, precision=HH_MIXED, budget_bytes=150 * 10 ** 9, max_sims=256, max_steps=64,
                  eps2=1e-8, eta=0.02, theta=0.5, n_crit=64, dt_tree=2.0 ** -6, rebuild_threads=4, device=0,
-                 rebuild_device=False):
+                 rebuild_device=False, order=0):
         self.precision = precision
         self.rebuild_device = bool(rebuild_device)
         self.budget = int(budget_bytes)
@@ -94,6 +94,7 @@ class Server:
         self.cfg.dt_max = dt_tree
         self.cfg.dt_tree = dt_tree
         self.cfg.precision = precision
+        self.cfg.order = order
         self.batch = Batch(precision, max_sims=max_sims, max_steps=max_steps, device=device)
         self.pool = ThreadPoolExecutor(max_workers=rebuild_threads)
         self.stats = ServerStats()

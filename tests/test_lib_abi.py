@@ -66,13 +66,15 @@ def _soa(a):
     return np.ascontiguousarray(np.asarray(a).T)
 
 
+@pytest.mark.parametrize("order", ["morton", "hilbert"])
 @pytest.mark.parametrize("n,theta,n_crit,salp", [(3000, 0.5, 64, False), (2500, 0.3, 16, True),
                                                  (4096, 0.75, 200, False), (777, 0.0, 32, True)])
-def test_host_tree_matches_oracle_exactly(hh, orc, n, theta, n_crit, salp):
+def test_host_tree_matches_oracle_exactly(hh, orc, n, theta, n_crit, salp, order):
     x, v, m = (synth.plummer_salpeter if salp else synth.plummer)(n, 21)
     a, j, _ = orc.direct_force(x, v, m, 1e-6)
-    T = orc.tree_build(x, v, a, j, m, leaf=8, n_crit=n_crit, theta=theta)
-    P = hh.hh_tree_build(_soa(x), _soa(v), _soa(a), _soa(j), m, leaf=8, n_crit=n_crit, theta=theta)
+    T = orc.tree_build(x, v, a, j, m, leaf=8, n_crit=n_crit, theta=theta, order=order)
+    P = hh.hh_tree_build(_soa(x), _soa(v), _soa(a), _soa(j), m, leaf=8, n_crit=n_crit, theta=theta,
+                         order=hh.HH_ORDER_HILBERT if order == "hilbert" else hh.HH_ORDER_MORTON)
     assert np.array_equal(P.perm, T.perm)
     assert P.n_nodes == T.n_cells
     assert np.array_equal(P.off, T.list_off)
