@@ -497,6 +497,45 @@ __device__ __forceinline__ void acc_shfl_add(AccMix &A, int off)
     A.P = f2_shfl(A.P, off);
 }
 
+// Adds the partner's sums (lane + delta) into this lane's where `take`; every
+// lane takes part in the shuffles.  The receiving lane's sums come first, so
+// the order of every addition is fixed.
+__device__ __forceinline__ double shfl_down_take(double x, int delta, bool take)
+{
+    const double o = __shfl_down_sync(0xffffffffu, x, delta);
+    return take ? x + o : x;
+}
+
+__device__ __forceinline__ void acc_shfl_down_add(AccF64 &A, int delta, bool take)
+{
+    A.ax = shfl_down_take(A.ax, delta, take);
+    A.ay = shfl_down_take(A.ay, delta, take);
+    A.az = shfl_down_take(A.az, delta, take);
+    A.jx = shfl_down_take(A.jx, delta, take);
+    A.jy = shfl_down_take(A.jy, delta, take);
+    A.jz = shfl_down_take(A.jz, delta, take);
+    A.p = shfl_down_take(A.p, delta, take);
+}
+
+__device__ __forceinline__ F2 f2_shfl_down_take(F2 a, int delta, bool take)
+{
+    F2 o;
+    o.h = __shfl_down_sync(0xffffffffu, a.h, delta);
+    o.l = __shfl_down_sync(0xffffffffu, a.l, delta);
+    return take ? f2_add(a, o) : a;
+}
+
+__device__ __forceinline__ void acc_shfl_down_add(AccMix &A, int delta, bool take)
+{
+    A.Ax = f2_shfl_down_take(A.Ax, delta, take);
+    A.Ay = f2_shfl_down_take(A.Ay, delta, take);
+    A.Az = f2_shfl_down_take(A.Az, delta, take);
+    A.Jx = f2_shfl_down_take(A.Jx, delta, take);
+    A.Jy = f2_shfl_down_take(A.Jy, delta, take);
+    A.Jz = f2_shfl_down_take(A.Jz, delta, take);
+    A.P = f2_shfl_down_take(A.P, delta, take);
+}
+
 struct RedF64 {
     double v[7];
 };
@@ -631,12 +670,17 @@ __device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict
     const int pj = part_len_for(n_a, pj_min, work);
     const int part = it.y & 0xFFFF, slot0 = it.w;
 
-    int I = 1;
-    while (I < n_a) I <<= 1;
-    const int islot = tid & (I - 1);
-    const int jslice = tid / I;
-    const int S = kThreads / I;
-    const bool has_i = islot < n_a;
+    // Lane mapping: every warp holds K = floor(32 / n_a) j slices of n_a lanes
+    // (lane = i slot + n_a * slice); the 32 - K n_a leftover lanes idle.  So no
+    // lane is spent on a missing particle (rounding n_a up to a power of two
+    // left up to half the lanes idle, and the FP64 pipe charges the whole warp).
+    const int I = n_a;
+    const int K = 32 / I;
+    const int islot = lane % I, kslice = lane / I;
+    const bool idle = kslice >= K;
+    const int jslice = warp * K + kslice;
+    const int S = (kThreads / 32) * K;
+    const bool has_i = !idle;
     int64_t pi = -1;
     {
         uint32_t mm = mask;
@@ -702,7 +746,7 @@ __device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict
         // FP32 partials are folded into the compensated sums every
         // kFold terms per thread (short plain-FP32 runs keep the
         // partial-sum rounding below the per-term rounding).
-        for (int e = jslice; e < nc;) {
+        for (int e = idle ? nc : jslice; e < nc;) {
             const int e_end = min(nc, e + kFold * S);
             for (; e < e_end; e += S) {
                 const int32_t j = sm.idx[b][e];
@@ -712,8 +756,15 @@ __device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict
         }
         group_sync(bar_id);  // buffer b is refilled two chunks later
     }
-    // reduce the S slices of each i slot: lanes l, l+I, ... then warps
-    for (int off = I; off < 32; off <<= 1) acc_shfl_add(A, off);
+    // reduce the slices of each i slot over lanes islot + n_a k of each warp
+    // (k < K), then over the warps: a butterfly when n_a is a power of two
+    // (K n_a = 32), else a tree towards slice 0
+    if ((I & (I - 1)) == 0) {
+        for (int off = I; off < 32; off <<= 1) acc_shfl_add(A, off);
+    } else {
+        for (int step = 1; step < K; step <<= 1)
+            acc_shfl_down_add(A, step * I, !idle && (kslice & (2 * step - 1)) == 0 && kslice + step < K);
+    }
     if (lane < I) {
         Red r;
         to_red(A, r);
