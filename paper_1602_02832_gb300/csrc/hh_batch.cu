@@ -83,32 +83,52 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
 
 // Grid-wide barrier for a cooperative launch (all CTAs resident).  Returns
 // false when any CTA has recorded an error (including a barrier timeout).
+__device__ __forceinline__ unsigned int atom_add_acq_rel_gpu(unsigned int *p, unsigned int v)
+{
+    unsigned int old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned int *p, unsigned int v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid barrier.  Arrivals count up monotonically within a launch (the host
+// zeroes the counters), so an arrival's count tells which barrier it belongs
+// to: the last arrival of barrier b publishes generation b + 1 with a release
+// store, and the others wait for it with acquire loads.  The arrivals are
+// acquire-release operations on one counter, so the last one has seen every
+// CTA's writes (each CTA's threads synchronise with its arriving thread
+// first), and its release passes them on to every waiter.  Waits give up
+// after kWaitNs / kSpinLimit with HH_ETIMEOUT.
 __device__ __forceinline__ bool grid_sync(BatchScalars *bs)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int *gen = &bs->bar_gen;
-        const unsigned int g = *gen;
-        __threadfence();
-        const unsigned int arrived = atomicAdd(&bs->bar_count, 1u) + 1u;
-        if (arrived == gridDim.x) {
-            bs->bar_count = 0u;
-            __threadfence();
-            atomicAdd(&bs->bar_gen, 1u);
+        const unsigned int v = atom_add_acq_rel_gpu(&bs->bar_count, 1u);
+        const unsigned int target = v / gridDim.x + 1u;
+        if (v % gridDim.x == gridDim.x - 1u) {
+            st_release_gpu(&bs->bar_gen, target);
         } else {
             long long it = 0;
             const unsigned long long t0 = globaltimer_ns();
-            while (*gen == g) {
+            while (ld_acquire_gpu(&bs->bar_gen) < target) {
                 if (++it > kSpinLimit || globaltimer_ns() - t0 > kWaitNs) {
                     atomicExch(&bs->err, HH_ETIMEOUT);
                     break;
                 }
                 if ((it & 255) == 0 && *(volatile int32_t *)&bs->err) break;  // another CTA gave up
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
-        __threadfence();
         s_ok = (*(volatile int32_t *)&bs->err) == 0;
     }
     __syncthreads();
