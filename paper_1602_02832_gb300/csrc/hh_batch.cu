@@ -83,23 +83,6 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
 
 // Grid-wide barrier for a cooperative launch (all CTAs resident).  Returns
 // false when any CTA has recorded an error (including a barrier timeout).
-__device__ __forceinline__ unsigned int atom_add_acq_rel_gpu(unsigned int *p, unsigned int v)
-{
-    unsigned int old;
-    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
-__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p)
-{
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release_gpu(unsigned int *p, unsigned int v)
-{
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 // Grid barrier.  Arrivals count up monotonically within a launch (the host
 // zeroes the counters), so an arrival's count tells which barrier it belongs
 // to: the last arrival of barrier b publishes generation b + 1 with a release

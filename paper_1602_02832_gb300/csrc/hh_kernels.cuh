@@ -642,6 +642,26 @@ struct ForceSmem {
     double tn[kThreads / 32];  // per-warp minimum of t + dt after the corrector
 };
 
+// GPU-scope acquire / release operations (PTX memory model): an
+// acquire-release arrival on a counter sees every earlier arrival's writes and
+// passes its own on, without full fences.
+__device__ __forceinline__ unsigned int atom_add_acq_rel_gpu(unsigned int *p, unsigned int v)
+{
+    unsigned int old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned int *p, unsigned int v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Barrier over the 128 threads working on one item: the whole CTA
 // (bar_id 0) or one of several 128-thread worker groups of a larger CTA
 // (named barrier bar_id = 1 + group).
@@ -778,18 +798,19 @@ __device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict
     }
     bool write_out = n_parts == 1;
     if (n_parts > 1) {
+        // the group's partials are ordered before its arrival by the group
+        // barrier and the arrival's release; the last arrival's acquire (and
+        // the barrier after it) orders the other parts' partials before the sum
         Red *mine = partials + ((int64_t)slot0 + part) * kMaxTileI;
         if (tid < n_a) mine[tid] = r;
-        __threadfence();
         group_sync(bar_id);
         if (tid == 0) {
-            const int old = atomicAdd(&L.tile_cnt[it.x], 1);
-            sm.last = (old == n_parts - 1);
+            const unsigned int old = atom_add_acq_rel_gpu(reinterpret_cast<unsigned int *>(&L.tile_cnt[it.x]), 1u);
+            sm.last = ((int)old == n_parts - 1);
         }
         group_sync(bar_id);
         write_out = sm.last;
         if (write_out) {
-            __threadfence();
             if (tid < n_a) {
                 const Red *base = partials + (int64_t)slot0 * kMaxTileI;
                 r = ld_red_cg(base + tid);
