@@ -118,3 +118,55 @@ def test_hilbert_order_run_matches_morton_run(hh, orc, prec):
         assert abs(ch["interactions"] / cm["interactions"] - 1) < 0.01
         assert np.abs(xh - xm).max() < 1e-4
     assert abs(ch["particle_steps"] / cm["particle_steps"] - 1) < 0.01
+
+
+def test_device_rebuild_grows_the_list_buffer(hh, orc):
+    # list_max far below the need: the device rebuild grows the buffer (and
+    # the context's byte count) instead of failing, and the lists are right
+    n = 4000
+    x, v, m = synth.plummer(n, 45)
+    cfg = hh.hh_config_default()
+    cfg.n_crit = 64
+    z = np.zeros_like(x)
+    T = orc.tree_build(x, v, z, z, m, leaf=8, n_crit=64, theta=0.5)
+    with hh.Context(cfg, n, 2 * n + 64, 1024, n // 4 + 64) as ctx:
+        ctx.hh_load_particles(x.T, v.T, m)
+        ctx.hh_set_rebuild_device(True)
+        b0 = ctx.device_bytes
+        ctx.hh_rebuild(0.0)
+        off, idx, gof = ctx.hh_get_lists()
+        assert ctx.device_bytes >= b0 + 4 * (len(T.list_idx) - 1024)
+        assert np.array_equal(off, T.list_off) and np.array_equal(idx, T.list_idx)
+        ctx.hh_run(0.0, 1 / 64)  # the loop runs on the grown lists
+        assert ctx.hh_get_counters()["rebuilds"] >= 3
+
+
+@pytest.mark.parametrize("loop", ["graph", "batch"])
+def test_tile_step_counter(hh, loop):
+    # every active tile of every block step is counted once: particle steps
+    # lie between the tile steps and tile_i times the tile steps
+    n = 3000
+    x, v, m = synth.plummer(n, 46)
+    cfg = hh.hh_config_default()
+    cfg.eps2, cfg.n_crit, cfg.tile_i = 1e-6, 64, 16
+    with hh.Context(cfg, n, 2 * n, 600 * n, n) as ctx:
+        ctx.hh_load_particles(x.T, v.T, m)
+        ctx.hh_run(0.0, 0.0)
+        ctx.hh_reset_counters()
+        if loop == "graph":
+            ctx.hh_advance(1 / 64)
+        else:
+            with hh.Batch(hh.HH_FP64, max_sims=1, max_steps=4096) as b:
+                b.hh_batch_run([ctx], [1 / 64])
+        c = ctx.hh_get_counters()
+    assert 0 < c["tile_steps"] <= c["particle_steps"] <= 16 * c["tile_steps"]
+
+
+def test_perfmodel_measures_on_the_gpu(hh):
+    from paper_1602_02832_gb300 import perfmodel
+    r = perfmodel.measure(4096, 0.5, 64, hh.HH_MIXED, intervals=1, warm=1)
+    assert r["particle_steps"] > 0 and r["block_steps"] > 0
+    assert 100 < r["N_int"] < 4096 and 1.0 <= r["n_i"] <= 32.0
+    assert all(r[k] > 0 for k in ("T_force", "T_predict", "T_tree"))
+    rows = perfmodel.sweep_n_i(4096, 0.5, 256, hh.HH_FP64, ks=(1, 3, 8), reps=2)
+    assert [q["k"] for q in rows] == [1, 3, 8] and all(q["interactions_per_s"] > 0 for q in rows)

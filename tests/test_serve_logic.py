@@ -113,3 +113,55 @@ def test_server_rejects_a_request_above_the_budget(monkeypatch):
     with pytest.raises(MemoryError):
         srv.run([req], realtime=False)
     srv.close()
+
+
+class FakeCtxFewGroups(FakeCtx):
+    """Fails its first tree build when groups_max is below n (as a device
+    rebuild does with HH_ENOMEM when the tree has more groups than room)."""
+    created = []
+
+    def __init__(self, cfg, n_max=1, nj_max=1, list_max=1, groups_max=1, device=0):
+        super().__init__(cfg, n_max, nj_max, list_max, groups_max, device)
+        self.caps = dict(n_max=n_max, nj_max=nj_max, list_max=list_max, groups_max=groups_max)
+        FakeCtxFewGroups.created.append(self.caps)
+
+    def hh_run(self, t0, t1):
+        if self.caps["groups_max"] < self.n:
+            raise hh.HHError(hh.HH_ENOMEM, "hh_rebuild: more groups than groups_max")
+        super().hh_run(t0, t1)
+
+
+def test_admission_retries_with_bound_capacities(monkeypatch):
+    # with device rebuilds the server sizes groups at n/4 without building a
+    # tree; a rebuild that finds more groups fails with HH_ENOMEM and the
+    # request is admitted again with the bounds themselves (groups n, j 3n)
+    monkeypatch.setattr(serve, "Context", FakeCtxFewGroups)
+    monkeypatch.setattr(serve, "Batch", FakeBatch)
+    FakeCtx.live = FakeCtx.peak = 0
+    FakeCtxFewGroups.created = []
+    n = 400
+    req = serve.SimRequest(0, np.zeros((n, 3)), np.zeros((n, 3)), np.ones(n) / n, t_end=1 / 64)
+    srv = serve.Server(budget_bytes=10 ** 9, max_sims=2, max_steps=4, rebuild_device=True)
+    est, caps = srv.estimate_bytes(req)
+    assert caps["groups_max"] < n and caps["nj_max"] == 2 * n + 64 and est > 0
+    res, _ = srv.run([req], realtime=False)
+    srv.close()
+    assert [c["groups_max"] for c in FakeCtxFewGroups.created] == [caps["groups_max"], n]
+    assert FakeCtxFewGroups.created[1]["nj_max"] == 3 * n + 64
+    assert len(res) == 1 and FakeCtx.live == 0 and srv.used_bytes == 0
+
+
+def test_admission_error_other_than_memory_is_raised(monkeypatch):
+    class FakeCtxBad(FakeCtx):
+        def hh_run(self, t0, t1):
+            raise hh.HHError(hh.HH_EINVAL, "bad particles")
+
+    monkeypatch.setattr(serve, "Context", FakeCtxBad)
+    monkeypatch.setattr(serve, "Batch", FakeBatch)
+    FakeCtx.live = 0
+    req = serve.SimRequest(0, np.zeros((10, 3)), np.zeros((10, 3)), np.ones(10) / 10, t_end=1 / 64)
+    srv = serve.Server(budget_bytes=10 ** 9, max_sims=2, max_steps=4, rebuild_device=True)
+    with pytest.raises(hh.HHError):
+        srv.run([req], realtime=False)
+    srv.close()
+    assert FakeCtx.live == 0
