@@ -366,7 +366,7 @@ def _ensemble(hh, a):
     tot = {"block_steps": 0, "interactions": 0, "step_us": [], "live": [], "launches": 0, "wall": 0.0}
     for th in sorted({mb.theta for mb in members}):
         sub = [r for r, mb in zip(reqs, members) if mb.theta == th]
-        srv = serve.Server(precision=hh.HH_MIXED, budget_bytes=150 * 10 ** 9, max_sims=256, max_steps=64,
+        srv = serve.Server(precision=hh.HH_MIXED, budget_bytes=150 * 10 ** 9, max_sims=256, max_steps=256,
                            theta=th, n_crit=a.n_crit, rebuild_threads=8,
                            rebuild_device=a.rebuild == "device",
                            order=hh.HH_ORDER_HILBERT if a.order == "hilbert" else hh.HH_ORDER_MORTON)

@@ -82,9 +82,10 @@ class Server:
 
     def __init__(self, precision=HH_MIXED, budget_bytes=150 * 10 ** 9, max_sims=256, max_steps=64,
                  eps2=1e-8, eta=0.02, theta=0.5, n_crit=64, dt_tree=2.0 ** -6, rebuild_threads=4, device=0,
-                 rebuild_device=False, order=0):
+                 rebuild_device=False, order=0, gang=True):
         self.precision = precision
         self.rebuild_device = bool(rebuild_device)
+        self.gang = bool(gang)
         self.budget = int(budget_bytes)
         self.max_sims = int(max_sims)
         self.max_steps = int(max_steps)
@@ -210,7 +211,12 @@ class Server:
                 s = f.result()
                 self.used_bytes += s.bytes - est
                 live.append(s)
-            for s in [s for s in live if s.busy and rebuilding[id(s)].done()]:
+            # Gang scheduling: the rebuilds of the simulations that reached a
+            # rebuild time are finished before the next launch, so every live
+            # simulation takes part in it.  (Their kernels cannot run beside
+            # a batched launch, which fills every SM; launching without them
+            # leaves them waiting a whole launch with most simulations idle.)
+            for s in [s for s in live if s.busy and (self.gang or rebuilding[id(s)].done())]:
                 rebuilding.pop(id(s)).result()
                 s.busy = False
             runnable = [s for s in live if not s.busy]
