@@ -72,8 +72,9 @@ def _args():
     p.add_argument("--no-autotune", action="store_true", help="skip the tile-shape autotuner (use the defaults)")
     p.add_argument("--order", default="morton", choices=["morton", "hilbert"],
                    help="order of particles and nodes in the tree (Peano-Hilbert is the paper's)")
-    p.add_argument("--rebuild", default="device", choices=["device", "host"],
-                   help="where the tree, groups and lists are rebuilt every dt_tree")
+    p.add_argument("--rebuild", default="auto", choices=["auto", "device", "host"],
+                   help="where the tree, groups and lists are rebuilt every dt_tree (auto: on the device from "
+                        "N = 4096, on the host below, where a device build is bound by launch latency)")
     p.add_argument("--loop", default="persistent", choices=["persistent", "graph"],
                    help="block-step loop: one persistent cooperative kernel per interval, or CUDA-graph replays")
     return p.parse_args()
@@ -103,6 +104,14 @@ def _cfg(hh, prec, a):
     c.work_item = (a.work_item if prec == hh.HH_FP64 else a.work_item_mixed) or 0
     c.order = hh.HH_ORDER_HILBERT if a.order == "hilbert" else hh.HH_ORDER_MORTON
     return c
+
+
+def _on_device(a, n):
+    return a.rebuild == "device" or (a.rebuild == "auto" and n >= 4096)
+
+
+def _server_rebuild(a):
+    return "auto" if a.rebuild == "auto" else a.rebuild == "device"
 
 
 def _workload(a):
@@ -255,7 +264,7 @@ def _tuned(hh, a, prec, seed):
 
     x, v, m = synth.plummer(a.n, seed)
     best, table = autotune.tune(x, v, m, _cfg(hh, prec, a), intervals=1, warm=1,
-                                rebuild_device=a.rebuild == "device")
+                                rebuild_device=_on_device(a, a.n))
     return best, [{"config": c, "particle_steps_per_s": ps, "interactions_per_s": r} for c, ps, r in table]
 
 
@@ -277,7 +286,7 @@ def _run_form(hh, torch, a, prec, seed, steps, warmup, flush, e2e_steps=0, over=
     ctx.hh_set_stream(stream.cuda_stream)
     dtt = cfg.dt_tree
     ctx.hh_load_particles(x.T, v.T, m)
-    ctx.hh_set_rebuild_device(a.rebuild == "device")
+    ctx.hh_set_rebuild_device(_on_device(a, a.n))
     ctx.hh_run(0.0, 0.0)  # rebuild, initial forces, rebuild with node derivatives, initial steps
     loop = _Loop(hh, ctx, prec, a.loop)
     t = 0.0
@@ -368,7 +377,7 @@ def _ensemble(hh, a):
         sub = [r for r, mb in zip(reqs, members) if mb.theta == th]
         srv = serve.Server(precision=hh.HH_MIXED, budget_bytes=150 * 10 ** 9, max_sims=256, max_steps=256,
                            theta=th, n_crit=a.n_crit, rebuild_threads=8,
-                           rebuild_device=a.rebuild == "device",
+                           rebuild_device=_server_rebuild(a),
                            order=hh.HH_ORDER_HILBERT if a.order == "hilbert" else hh.HH_ORDER_MORTON)
         res, st = srv.run(sub, realtime=False)
         srv.close()
@@ -404,7 +413,7 @@ def _serving(hh, a):
     reqs = [serve.SimRequest(r.rid, None, None, None, r.t_end, arrival_s=r.arrival_s,
                              make=(lambda n=r.n, sd=r.seed: synth.plummer_salpeter(n, sd))) for r in stream]
     srv = serve.Server(precision=hh.HH_MIXED, budget_bytes=150 * 10 ** 9, max_sims=256, max_steps=32,
-                       n_crit=a.n_crit, rebuild_threads=8, rebuild_device=a.rebuild == "device",
+                       n_crit=a.n_crit, rebuild_threads=8, rebuild_device=_server_rebuild(a),
                        order=hh.HH_ORDER_HILBERT if a.order == "hilbert" else hh.HH_ORDER_MORTON)
     res, st = srv.run(reqs, realtime=True, max_wall_s=a.serve_seconds)
     srv.close()

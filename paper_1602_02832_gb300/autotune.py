@@ -26,8 +26,8 @@ from . import HH_FP64, HH_MIXED, Batch, Context, hh_config_default, hh_tree_buil
 
 CANDIDATES = {
     HH_FP64: [dict(n_crit=nc, tile_i=ti, tile_j=tj, work_item=0)
-              for nc in (64, 256) for ti in (32, 16) for tj in (128, 256, 512)]
-             + [dict(n_crit=nc, tile_i=16, tile_j=256, work_item=0) for nc in (128, 1024)],
+              for nc in (64, 256) for ti in (32, 16, 8) for tj in (128, 256, 512)]
+             + [dict(n_crit=nc, tile_i=ti, tile_j=256, work_item=0) for nc in (128, 1024) for ti in (16, 8)],
     HH_MIXED: [dict(n_crit=nc, tile_i=ti, tile_j=tj, work_item=0)
                for nc in (64, 256) for ti in (32, 16) for tj in (256, 512, 1024)]
               + [dict(n_crit=nc, tile_i=32, tile_j=512, work_item=0) for nc in (128, 1024)],

@@ -987,7 +987,7 @@ int hh_rebuild(hh_ctx *ctx, double t)
     double *Jx = J, *Jv = J + 3 * nj, *Ja = J + 6 * nj, *Jj = J + 9 * nj, *Jm = J + 12 * nj, *Jt = J + 13 * nj;
     std::vector<double> dt_new(static_cast<size_t>(n));
     std::vector<int64_t> ids_new(static_cast<size_t>(n));
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (n >= 8192)
     for (int64_t k = 0; k < n; k++) {
         const int64_t i = V.perm[k];
         for (int d = 0; d < 3; d++) {
@@ -1001,7 +1001,7 @@ int hh_rebuild(hh_ctx *ctx, double t)
         dt_new[size_t(k)] = dtv[size_t(i)];
         ids_new[size_t(k)] = ctx->ids[size_t(i)];
     }
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (n >= 8192)
     for (int64_t c = 0; c < nn; c++) {
         for (int d = 0; d < 3; d++) {
             Jx[d * nj + n + c] = V.cx[3 * c + d];

@@ -28,6 +28,10 @@ namespace {
 
 constexpr int kBits = 21;
 constexpr uint32_t kMaxCoord = (1u << kBits) - 1u;
+// below this many particles a build runs on the calling thread: small trees
+// are built by several server threads at once, and a thread team per build
+// costs more than it saves
+constexpr int64_t kOmpMinN = 8192;
 
 inline uint64_t spread_bits(uint32_t v)
 {
@@ -147,7 +151,7 @@ void node_moments(hh_tree &t, const double *x, const double *v, const double *a,
     t.cv.assign(3 * size_t(nc), 0.0);
     t.ca.assign(3 * size_t(nc), 0.0);
     t.cj.assign(3 * size_t(nc), 0.0);
-#pragma omp parallel for schedule(dynamic, 32)
+#pragma omp parallel for schedule(dynamic, 32) if (t.n >= kOmpMinN)
     for (int32_t c = 0; c < nc; c++) {
         double M = 0.0, sx[3] = {0, 0, 0}, sv[3] = {0, 0, 0}, sa[3] = {0, 0, 0}, sj[3] = {0, 0, 0};
         for (int32_t q = t.cells[c].begin; q < t.cells[c].end; q++) {
@@ -298,7 +302,7 @@ int build_into(hh_tree *t, int64_t n, const double *x, const double *v, const do
         const double scale = double(1u << kBits) / side;
         auto &ki = t->ki;
         ki.resize(size_t(n));
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (n >= kOmpMinN)
         for (int64_t i = 0; i < n; i++) {
             uint32_t u[3];
             for (int d = 0; d < 3; d++) {
@@ -325,7 +329,7 @@ int build_into(hh_tree *t, int64_t n, const double *x, const double *v, const do
         const int32_t G = int32_t(t->g_cell.size());
         auto &lists = t->lists;
         if (lists.size() < size_t(G)) lists.resize(size_t(G));
-#pragma omp parallel
+#pragma omp parallel if (n >= kOmpMinN)
         {
             std::vector<int32_t> stack, nodes;
 #pragma omp for schedule(dynamic, 4)
@@ -334,7 +338,7 @@ int build_into(hh_tree *t, int64_t n, const double *x, const double *v, const do
         t->off.assign(size_t(G) + 1, 0);
         for (int32_t g = 0; g < G; g++) t->off[size_t(g) + 1] = t->off[size_t(g)] + int64_t(lists[size_t(g)].size());
         t->idx.resize(size_t(t->off[size_t(G)]));
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (n >= kOmpMinN)
         for (int32_t g = 0; g < G; g++)
             std::copy(lists[size_t(g)].begin(), lists[size_t(g)].end(), t->idx.begin() + t->off[size_t(g)]);
     } catch (const std::bad_alloc &) {

@@ -77,14 +77,23 @@ class ServerStats:
     wall_s: float = 0.0
 
 
+AUTO_DEVICE_MIN_N = 4096
+
+
 class Server:
     """Continuous batching of block steps across resident simulations."""
+
+    def _on_device(self, n):
+        return n >= AUTO_DEVICE_MIN_N if self.rebuild_device == "auto" else self.rebuild_device
 
     def __init__(self, precision=HH_MIXED, budget_bytes=150 * 10 ** 9, max_sims=256, max_steps=64,
                  eps2=1e-8, eta=0.02, theta=0.5, n_crit=64, dt_tree=2.0 ** -6, rebuild_threads=4, device=0,
                  rebuild_device=False, order=0, gang=True):
         self.precision = precision
-        self.rebuild_device = bool(rebuild_device)
+        # True / False, or "auto": the device builder from AUTO_DEVICE_MIN_N
+        # particles up, the host builder below (a small tree's device build
+        # is bound by kernel-launch latency)
+        self.rebuild_device = rebuild_device if rebuild_device == "auto" else bool(rebuild_device)
         self.gang = bool(gang)
         self.budget = int(budget_bytes)
         self.max_sims = int(max_sims)
@@ -115,7 +124,7 @@ class Server:
         for Plummer spheres.  With host rebuilds the capacities come from a host
         build of the tree."""
         n = len(req.m)
-        if self.rebuild_device:
+        if self._on_device(n):
             th = max(self.cfg.theta, 0.05)
             per = min(2.0 * n, 400.0 * (0.5 / th) ** 2)  # list entries per particle, generous
             caps = dict(n_max=n, nj_max=2 * n + 64, list_max=16 * n + 4096, groups_max=n // 4 + 64)
@@ -137,7 +146,7 @@ class Server:
             ctx = Context(self.cfg, device=self.device, **caps)
             try:
                 ctx.hh_load_particles(np.ascontiguousarray(req.x.T), np.ascontiguousarray(req.v.T), req.m)
-                ctx.hh_set_rebuild_device(self.rebuild_device)
+                ctx.hh_set_rebuild_device(self._on_device(len(req.m)))
                 ctx.hh_run(0.0, 0.0)  # tree, initial forces, node derivatives, initial steps
                 break
             except HHError as e:
