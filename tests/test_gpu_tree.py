@@ -170,3 +170,20 @@ def test_perfmodel_measures_on_the_gpu(hh):
     assert all(r[k] > 0 for k in ("T_force", "T_predict", "T_tree"))
     rows = perfmodel.sweep_n_i(4096, 0.5, 256, hh.HH_FP64, ks=(1, 3, 8), reps=2)
     assert [q["k"] for q in rows] == [1, 3, 8] and all(q["interactions_per_s"] > 0 for q in rows)
+
+
+def test_device_rebuild_reports_too_few_cells(hh):
+    # room for 10 cells only: the build stops (no cell is written past the
+    # capacity and no later level is read) and reports HH_ENOMEM before it
+    # reorders anything, so the particle state stays as loaded
+    n = 2000
+    x, v, m = synth.plummer(n, 47)
+    cfg = hh.hh_config_default()
+    with hh.Context(cfg, n, n + 10, 600 * n, n) as ctx:
+        ctx.hh_load_particles(x.T, v.T, m)
+        ctx.hh_set_rebuild_device(True)
+        with pytest.raises(hh.HHError) as e:
+            ctx.hh_rebuild(0.0)
+        assert e.value.code == hh.HH_ENOMEM and "nj_max" in str(e.value)
+        got = ctx.hh_get_j(0, n)
+        assert np.array_equal(got["x"], np.ascontiguousarray(x.T)) and np.array_equal(ctx.hh_get_ids(), np.arange(n))
