@@ -295,6 +295,7 @@ def _run_form(hh, torch, a, prec, seed, steps, warmup, flush, e2e_steps=0, over=
         ctx.hh_rebuild(t + dtt)
         t += dtt
     c0 = ctx.hh_get_counters()
+    h0 = ctx.hh_get_tile_histogram()
     l0 = hh.hh_kernel_launches()
     loop.enable(True)
     times = []
@@ -314,12 +315,14 @@ def _run_form(hh, torch, a, prec, seed, steps, warmup, flush, e2e_steps=0, over=
     force_ms, force_launches = loop.force_ms, loop.force_launches
     launches = hh.hh_kernel_launches() - l0
     c1 = ctx.hh_get_counters()
+    hist = (ctx.hh_get_tile_histogram() - h0).tolist()
     res = {
         "ms": sum(times), "step_ms": times,
         "interactions": c1["interactions"] - c0["interactions"],
         "block_steps": c1["block_steps"] - c0["block_steps"],
         "particle_steps": c1["particle_steps"] - c0["particle_steps"],
         "force_ms": force_ms, "force_launches": force_launches, "gpu_launches": launches, "t_end": t,
+        "n_i_hist": hist,
     }
     if e2e_steps:
         # end to end through host buffers: upload the step's particle state,
@@ -433,6 +436,17 @@ def _lat(us):
     u = np.asarray(us)
     return {"p50": float(np.quantile(u, 0.5)), "p99": float(np.quantile(u, 0.99)), "mean": float(u.mean()),
             "n": int(len(u)), "note": "device time of one block step (all three phases) in the persistent loop"}
+
+
+def _n_i(r):
+    """Active particles per evaluated i tile (the paper's n_i per staged list
+    chunk): mean and histogram counts[k] for k + 1 active particles."""
+    h = r.get("n_i_hist") or []
+    tot = sum(h)
+    if not tot:
+        return None
+    last = max(k for k, c in enumerate(h) if c)
+    return {"mean": sum((k + 1) * c for k, c in enumerate(h)) / tot, "tiles": tot, "counts": h[:last + 1]}
 
 
 def _split(r, steps):
@@ -583,6 +597,7 @@ def main():
                        "note": "autotuner runs before the timed region (paper_1602_02832_gb300/autotune.py)"},
             "time_split_ms_per_step": _split(res, a.steps),
             "block_step_latency_us": _lat(res["step_us"]),
+            "active_per_tile": _n_i(res),
             "force_kernel_share": res["force_ms"] / res["ms"],
             "peaks_measured": peaks,
         }
@@ -596,6 +611,7 @@ def main():
                 "speedup_vs_plain": mv / (res["interactions"] / (res["ms"] * 1e-3)),
                 "time_split_ms_per_step": _split(mixed, a.steps),
                 "block_step_latency_us": _lat(mixed["step_us"]),
+                "active_per_tile": _n_i(mixed),
                 "roofline": {"kernel": ("k_batch force phase (list force + corrector), mixed"
                                         if a.loop == "persistent" else "k_force<RecMix> (mixed list force)"),
                              "bound": "alu", "achieved": mach,

@@ -223,6 +223,11 @@ int64_t hh_n_particles(const hh_ctx *ctx);
 int64_t hh_n_j(const hh_ctx *ctx);
 int hh_get_counters(hh_ctx *ctx, hh_counters *out);
 int hh_reset_counters(hh_ctx *ctx);
+/* Active i tiles by their number of active particles: counts[k] = tiles
+ * evaluated with k + 1 active particles, summed over block steps since the
+ * last reset (the distribution of the paper's n_i, Eq. 3, per staged list
+ * chunk). */
+int hh_get_tile_histogram(hh_ctx *ctx, int64_t counts[32]);
 
 /* Kernel-time accounting: CUDA-event time (ms) of the list-force kernel
  * launches since the last reset, and their number.  Events are recorded on

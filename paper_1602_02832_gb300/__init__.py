@@ -82,6 +82,7 @@ _SIGS = {
     "hh_n_j": (C.c_int64, [_P]),
     "hh_get_counters": (C.c_int, [_P, C.POINTER(hh_counters)]),
     "hh_reset_counters": (C.c_int, [_P]),
+    "hh_get_tile_histogram": (C.c_int, [_P, _P]),
     "hh_force_timing": (C.c_int, [_P, C.c_int, _D, _I64]),
     "hh_kernel_launches": (C.c_int64, []),
     "hh_last_error": (C.c_char_p, [_P]),
@@ -312,6 +313,12 @@ class Context:
         self._c(_lib.hh_get_counters(self.h, C.byref(c)))
         return dict(block_steps=c.block_steps, particle_steps=c.particle_steps, interactions=c.interactions,
                     rebuilds=c.rebuilds, tile_steps=c.tile_steps)
+
+    def hh_get_tile_histogram(self):
+        """counts[k] = active i tiles evaluated with k + 1 active particles."""
+        h = np.zeros(32, np.int64)
+        self._c(_lib.hh_get_tile_histogram(self.h, _ptr(h, C.c_int64)))
+        return h
 
     def hh_reset_counters(self):
         self._c(_lib.hh_reset_counters(self.h))

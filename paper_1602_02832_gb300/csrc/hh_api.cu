@@ -857,7 +857,18 @@ int hh_get_counters(hh_ctx *ctx, hh_counters *out)
     out->particle_steps = int64_t(ctx->h_ds->particle_steps);
     out->interactions = int64_t(ctx->h_ds->interactions);
     out->rebuilds = ctx->rebuilds;
-    out->tile_steps = int64_t(ctx->h_ds->tile_steps);
+    out->tile_steps = 0;
+    for (int k = 0; k < 32; k++) out->tile_steps += int64_t(ctx->h_ds->na_hist[k]);
+    return HH_OK;
+}
+
+int hh_get_tile_histogram(hh_ctx *ctx, int64_t counts[32])
+{
+    int rc = check_ctx(ctx);
+    if (rc) return rc;
+    if (!counts) return fail(ctx, HH_EINVAL, "hh_get_tile_histogram: NULL");
+    if ((rc = sync_and_check(ctx))) return rc;
+    for (int k = 0; k < 32; k++) counts[k] = int64_t(ctx->h_ds->na_hist[k]);
     return HH_OK;
 }
 
@@ -865,7 +876,8 @@ int hh_reset_counters(hh_ctx *ctx)
 {
     int rc = check_ctx(ctx);
     if (rc) return rc;
-    CK(cudaMemsetAsync(&ctx->ds->block_steps, 0, 4 * sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(&ctx->ds->block_steps, 0, 3 * sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(ctx->ds->na_hist, 0, sizeof(ctx->ds->na_hist), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->rebuilds = 0;
     return HH_OK;

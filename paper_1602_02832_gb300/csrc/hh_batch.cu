@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                 const uint32_t mask = __ballot_sync(0xffffffffu, act);
                 if (mask)
                     append_tile_items(sd.L, tile, td, mask, sd.pj, sd.work, &B.bs->n_items[par], &sd.ds->slot_par[par], B.items,
-                                      s, &sd.ds->tile_steps);
+                                      s, sd.ds->na_hist);
             }
         }
         if (!grid_sync(B.bs)) return;

@@ -40,7 +40,7 @@ struct DevScalars {
     int32_t n_tiles;             // static i tiles
     int32_t pad0;
     unsigned long long block_steps, particle_steps, interactions;
-    unsigned long long tile_steps;  // active i tiles summed over block steps
+    unsigned long long na_hist[32];  // active i tiles summed over block steps, by n_a - 1
     // block-step levels (level k <=> dt = 2^-k), kept by the batched loop
     int32_t lvl_cnt[32];          // particles per level
     unsigned long long t_cur_bits;  // latest block time (max t_i), positive-double bits
@@ -157,7 +157,7 @@ __device__ __forceinline__ int parts_of(int64_t len, int pj) { return len > 0 ? 
 // item = (tile, part | sim << 16, active mask, first partial-sum slot).
 __device__ __forceinline__ void append_tile_items(const Lists &L, int tile, const int4 td, uint32_t mask, int pj_min,
                                                   int work, uint32_t *n_items, uint32_t *slot_ctr, int4 *items, int sim,
-                                                  unsigned long long *tile_ctr)
+                                                  unsigned long long *na_hist)
 {
     const int lane = threadIdx.x & 31;
     const int64_t len = L.off[td.z + 1] - L.off[td.z];
@@ -166,7 +166,7 @@ __device__ __forceinline__ void append_tile_items(const Lists &L, int tile, cons
     if (lane == 0) {
         base = (int)atomicAdd(n_items, (uint32_t)n_parts);
         slot = n_parts > 1 ? (int)atomicAdd(slot_ctr, (uint32_t)n_parts) : 0;
-        atomicAdd(tile_ctr, 1ull);
+        atomicAdd(&na_hist[__popc(mask) - 1], 1ull);
     }
     base = __shfl_sync(0xffffffffu, base, 0);
     slot = __shfl_sync(0xffffffffu, slot, 0);
@@ -187,7 +187,7 @@ __device__ __forceinline__ void select_tiles(const State &s, const Lists &L, Dev
         const bool act = (p < td.y) && is_active(s, c, p, tnow);
         const uint32_t mask = __ballot_sync(0xffffffffu, act);
         if (mask == 0u) continue;
-        append_tile_items(L, (int)tile, td, mask, pj, work, &ds->n_items, &ds->slot_ctr, L.items, 0, &ds->tile_steps);
+        append_tile_items(L, (int)tile, td, mask, pj, work, &ds->n_items, &ds->slot_ctr, L.items, 0, ds->na_hist);
     }
 }
 

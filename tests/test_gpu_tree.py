@@ -159,7 +159,11 @@ def test_tile_step_counter(hh, loop):
             with hh.Batch(hh.HH_FP64, max_sims=1, max_steps=4096) as b:
                 b.hh_batch_run([ctx], [1 / 64])
         c = ctx.hh_get_counters()
+        h = ctx.hh_get_tile_histogram()
     assert 0 < c["tile_steps"] <= c["particle_steps"] <= 16 * c["tile_steps"]
+    # each corrected particle sits in exactly one evaluated tile of its step
+    assert h.sum() == c["tile_steps"] and not h[16:].any()
+    assert int((np.arange(1, 33) * h).sum()) == c["particle_steps"]
 
 
 def test_perfmodel_measures_on_the_gpu(hh):
