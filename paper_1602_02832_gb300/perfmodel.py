@@ -114,6 +114,26 @@ def measure(n, theta, n_crit, precision, intervals=2, warm=1, seed=0, tile_i=0, 
     }
 
 
+def equivalent_performance(n, precision, theta=0.5, n_crit=64, intervals=1, warm=1, seed=0):
+    """The paper's equivalent performance S = 57 N n_step,h / T (Eq. 1): the
+    speed a direct Hermite code would need to reach the tree code's time to
+    solution.  n_step,h comes from the same loop with theta = 0 (every list is
+    all particles, i.e. direct Hermite with the same block steps), over the
+    same tree intervals as the tree run timed for T.  Returns S for the tree
+    run and the tree and direct runs' rates."""
+    tree = measure(n, theta, n_crit, precision, intervals, warm, seed)
+    direct = measure(n, 0.0, n_crit, precision, intervals, warm, seed)
+    t_tree = tree["particle_steps"] * (tree["T_force"] + tree["T_predict"] + tree["T_tree"] + tree["T_host"])
+    t_direct = direct["particle_steps"] * (direct["T_force"] + direct["T_predict"] + direct["T_tree"] +
+                                           direct["T_host"])
+    return {"n": n, "form": tree["form"], "theta": theta, "n_crit": n_crit, "intervals": intervals,
+            "steps_ratio_direct_over_tree": direct["particle_steps"] / tree["particle_steps"],
+            "S_tree_tflops": 57.0 * direct["particle_steps"] * n / t_tree / 1e12,
+            "tree_interactions_per_s": tree["N_int"] * tree["particle_steps"] / t_tree,
+            "direct_interactions_per_s": direct["N_int"] * direct["particle_steps"] / t_direct,
+            "speedup_over_direct": t_direct / t_tree}
+
+
 def _tiles(off, group_of, tile_i):
     """Static i tiles (begin, end) as the library forms them: runs of at most
     tile_i consecutive particles inside each group (groups are contiguous in
@@ -230,6 +250,8 @@ def main(argv=None):
     p.add_argument("--warm", type=int, default=1)
     p.add_argument("--out", default=".")
     p.add_argument("--sweep-n", type=int, default=65536, help="N of the controlled n_i sweep (0: skip)")
+    p.add_argument("--equiv-n", type=int, default=65536,
+                   help="N of the equivalent-performance comparison with direct Hermite (0: skip)")
     a = p.parse_args(argv)
     sweep, sweep_fits = [], {}
     if a.sweep_n:
@@ -240,6 +262,12 @@ def main(argv=None):
             sweep_fits[form] = fit_force_model(part)
             for r in part:
                 print(json.dumps(r), flush=True)
+    equiv = []
+    if a.equiv_n:
+        for form in a.forms:
+            e = equivalent_performance(a.equiv_n, HH_FP64 if form == "fp64" else HH_MIXED)
+            equiv.append(e)
+            print(json.dumps(e), flush=True)
     rows = []
     for form in a.forms:
         for n in a.n:
@@ -251,10 +279,18 @@ def main(argv=None):
     fits = {form: fit_force_model([r for r in rows if r["form"] == form]) for form in a.forms if rows}
     os.makedirs(a.out, exist_ok=True)
     with open(os.path.join(a.out, "perfmodel.json"), "w") as f:
-        json.dump({"rows": rows, "fits": fits, "sweep": sweep, "sweep_fits": sweep_fits}, f, indent=1)
+        json.dump({"rows": rows, "fits": fits, "sweep": sweep, "sweep_fits": sweep_fits, "equiv": equiv}, f, indent=1)
     with open(os.path.join(a.out, "perfmodel.md"), "w") as f:
         if sweep:
             f.write(sweep_markdown(sweep, sweep_fits) + "\n")
+        if equiv:
+            f.write("Equivalent performance (Eq. 1), tree theta 0.5 against direct Hermite (theta 0) over the same "
+                    "interval:\n\n| form | N | S (Tflops, 57 flop) | tree / direct time | direct steps / tree steps | "
+                    "direct interactions/s |\n|---|---:|---:|---:|---:|---:|\n")
+            for e in equiv:
+                f.write(f"| {e['form']} | {e['n']} | {e['S_tree_tflops']:.2f} | 1/{e['speedup_over_direct']:.1f} | "
+                        f"{e['steps_ratio_direct_over_tree']:.3f} | {e['direct_interactions_per_s']:.3e} |\n")
+            f.write("\n")
         f.write(table_markdown(rows, fits))
     print(json.dumps({"fits": fits, "sweep_fits": sweep_fits}), flush=True)
     return 0

@@ -49,3 +49,23 @@ def test_static_tiles_follow_groups():
     gof = np.array([0] * 5 + [1] * 40 + [2])
     tiles = perfmodel._tiles(None, gof, 16)
     assert tiles == [(0, 5), (5, 21), (21, 37), (37, 45), (45, 46)]
+
+
+def test_equivalent_performance_formula(monkeypatch):
+    # S = 57 N n_step,h / T (Eq. 1): with a tree run of 1000 particle steps in
+    # 1 ms and a direct run of 950 steps, S = 57 * 950 * N / 1e-3
+    calls = []
+
+    def fake_measure(n, theta, n_crit, precision, intervals, warm, seed):
+        calls.append(theta)
+        ps = 1000 if theta > 0 else 950
+        per = 1e-6 if theta > 0 else 2e-5  # seconds per particle step, in T_force only
+        return {"form": "fp64", "particle_steps": ps, "N_int": 2000.0 if theta > 0 else n - 1,
+                "T_force": per, "T_predict": 0.0, "T_tree": 0.0, "T_host": 0.0}
+
+    monkeypatch.setattr(perfmodel, "measure", fake_measure)
+    e = perfmodel.equivalent_performance(4096, 0)
+    assert calls == [0.5, 0.0]
+    assert abs(e["S_tree_tflops"] - 57 * 950 * 4096 / 1e-3 / 1e12) < 1e-9
+    assert abs(e["speedup_over_direct"] - (950 * 2e-5) / 1e-3) < 1e-12
+    assert abs(e["steps_ratio_direct_over_tree"] - 0.95) < 1e-12
