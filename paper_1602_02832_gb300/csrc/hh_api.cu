@@ -785,7 +785,7 @@ int hh_get_state(hh_ctx *ctx, double *x, double *v, double *a, double *jk, doubl
 {
     int rc = check_ctx(ctx);
     if (rc) return rc;
-    if (!ctx->have_lists) return fail(ctx, HH_ESTATE, "hh_get_state: no tree yet (call hh_rebuild, hh_set_lists or hh_run)");
+    if (ctx->n < 1 || !ctx->have_j) return fail(ctx, HH_ESTATE, "hh_get_state: no particles loaded");
     const int64_t n = ctx->n;
     double *src[4] = {ctx->st.x, ctx->st.v, ctx->st.a, ctx->st.jk};
     double *dst[4] = {x, v, a, jk};
@@ -958,6 +958,9 @@ int hh_rebuild(hh_ctx *ctx, double t)
     int rc = check_ctx(ctx);
     if (rc) return rc;
     if (!ctx->have_j || ctx->n < 2) return fail(ctx, HH_ESTATE, "hh_rebuild: no particles loaded");
+    // until this rebuild succeeds the lists are not valid (a failure part way
+    // may have overwritten them); the state stays readable
+    ctx->have_lists = false;
     if (ctx->rebuild_device) {
         if (ctx->gtree && !ctx->ids_on_device &&
             hh_gtree_set_ids(ctx->gtree, ctx->ids.data(), ctx->n, ctx->stream) != HH_OK)

@@ -189,5 +189,10 @@ def test_device_rebuild_reports_too_few_cells(hh):
         with pytest.raises(hh.HHError) as e:
             ctx.hh_rebuild(0.0)
         assert e.value.code == hh.HH_ENOMEM and "nj_max" in str(e.value)
+        with pytest.raises(hh.HHError) as e2:  # no valid lists until a rebuild succeeds
+            ctx.hh_step()
+        assert e2.value.code == hh.HH_ESTATE
+        st = ctx.hh_get_state()  # the state stays readable
+        assert np.array_equal(st["x"], np.ascontiguousarray(x.T))
         got = ctx.hh_get_j(0, n)
         assert np.array_equal(got["x"], np.ascontiguousarray(x.T)) and np.array_equal(ctx.hh_get_ids(), np.arange(n))
