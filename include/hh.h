@@ -175,8 +175,12 @@ int hh_advance(hh_ctx *ctx, double t_end, int64_t *n_steps_out);
 /* Step 1 done by the library: copies the (synchronised) particle state to
  * the host, rebuilds the Morton octree, groups (n_crit) and lists (theta,
  * leaf) with the library's own host builder, reorders particles into Morton
- * order, and uploads particles, nodes (tree time t) and lists.  All
- * particles must be at time t. */
+ * order, and uploads particles, nodes (tree time t) and lists (or does all of
+ * this on the device, see hh_set_rebuild_device).  All particles must be at
+ * time t (HH_ESTATE otherwise).  If it fails (HH_ENOMEM for a tree beyond
+ * nj_max / groups_max, HH_ECUDA, ...), the lists are invalid until a later
+ * hh_rebuild succeeds (calls that need them return HH_ESTATE); the particle
+ * state is unchanged, or consistently reordered together with hh_get_ids. */
 int hh_rebuild(hh_ctx *ctx, double t);
 
 /* Selects where hh_rebuild does step 1 of the tree loop (Section 2: tree,
