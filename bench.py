@@ -178,7 +178,7 @@ class Clocks:
 
 
 def _peaks(hh_dir):
-    """Measured FMA peaks (TFLOP/s) from libhh_peaks.so, plus the driver's HBM/bf16 figures."""
+    """Measured FMA peaks (TFLOP/s) from libhh_peaks.so, plus the measured HBM / bf16 figures (MEASURED_PEAKS.json)."""
     out = {}
     lib = C.CDLL(os.path.join(hh_dir, "libhh_peaks.so"))
     lib.hh_fma_peak.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]
