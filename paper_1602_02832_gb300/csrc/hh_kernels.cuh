@@ -632,10 +632,16 @@ __device__ __forceinline__ void cp_async_rec(Rec *dst, const Rec *src)
         cp_async16(reinterpret_cast<char *>(dst) + 16 * q, reinterpret_cast<const char *>(src) + 16 * q);
 }
 
+// Staged list chunks per 128-thread group: one is summed while kStages - 1
+// are in flight.  (Three stages measured no faster in the tree loop and up to
+// 18% slower for short list parts: the deeper prologue adds latency to every
+// part, and parts are only a few chunks long.)
+constexpr int kStages = 2;
+
 template <typename Rec, int TJ>
 struct ForceSmem {
-    Rec rec[2][TJ];      // double-buffered staging of list chunks
-    int32_t idx[2][TJ];
+    Rec rec[kStages][TJ];  // ring of staged list chunks
+    int32_t idx[kStages][TJ];
     typename Traits<Rec>::Red red[kThreads / 32][kMaxTileI];
     int item;
     int last;
@@ -724,9 +730,11 @@ __device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict
     const int64_t le = min(ge, lb + (int64_t)pj);
     const int64_t len = le - lb;
     if (tid == 0 && part == 0) n_int += (unsigned long long)n_a * (unsigned long long)(ge - gb - 1);
-    // Chunks of TJ list entries are staged in two shared buffers: while one
-    // is summed, cp.async fills the other; the list indices of the chunk
-    // after that are already loading into registers.
+    // Chunks of TJ list entries are staged in a ring of kStages shared
+    // buffers: while one is summed, cp.async fills the next kStages - 1; the
+    // list indices of the chunk after those are already loading into
+    // registers.  Every step commits one copy group (empty past the end), so
+    // waiting for all but the newest kStages - 1 groups means chunk c landed.
     constexpr int EPT = TJ / kThreads;  // staged entries per thread and chunk
     const int n_chunks = (int)((len + TJ - 1) / TJ);
     int32_t nxt[EPT];
@@ -737,31 +745,32 @@ __device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict
             nxt[q] = (c < n_chunks && e < len) ? L.idx[lb + e] : -1;
         }
     };
-    auto issue = [&](int c) {  // chunk c's records into buffer c & 1, indices from nxt
-        const int b = c & 1;
+    auto issue = [&](int c) {  // chunk c's records into buffer c % kStages, indices from nxt
+        if (c < n_chunks) {
+            const int b = c % kStages;
 #pragma unroll
-        for (int q = 0; q < EPT; q++) {
-            const int e = q * kThreads + tid;
-            sm.idx[b][e] = nxt[q];
-            if (nxt[q] >= 0) cp_async_rec(&sm.rec[b][e], &rec[nxt[q]]);
+            for (int q = 0; q < EPT; q++) {
+                const int e = q * kThreads + tid;
+                sm.idx[b][e] = nxt[q];
+                if (nxt[q] >= 0) cp_async_rec(&sm.rec[b][e], &rec[nxt[q]]);
+            }
         }
         cp_async_commit();
     };
     if (n_chunks > 0) {
-        load_idx(0);
-        issue(0);
-        load_idx(1);
+#pragma unroll
+        for (int k = 0; k < kStages - 1; k++) {
+            load_idx(k);
+            issue(k);
+        }
+        load_idx(kStages - 1);
     }
     for (int c = 0; c < n_chunks; c++) {
-        const int b = c & 1;
+        const int b = c % kStages;
         const int nc = (len - (int64_t)c * TJ < (int64_t)TJ) ? (int)(len - (int64_t)c * TJ) : TJ;
-        if (c + 1 < n_chunks) {
-            issue(c + 1);
-            load_idx(c + 2);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
+        issue(c + kStages - 1);  // into the buffer summed in step c - 1 (freed by its closing barrier)
+        load_idx(c + kStages);
+        cp_async_wait<kStages - 1>();
         group_sync(bar_id);
         // FP32 partials are folded into the compensated sums every
         // kFold terms per thread (short plain-FP32 runs keep the
@@ -774,7 +783,7 @@ __device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict
             }
             fold_chunk(A);
         }
-        group_sync(bar_id);  // buffer b is refilled two chunks later
+        group_sync(bar_id);  // buffer b is refilled by the next step's issue
     }
     // reduce the slices of each i slot over lanes islot + n_a k of each warp
     // (k < K), then over the warps: a butterfly when n_a is a power of two
