@@ -424,18 +424,18 @@ def _serving(hh, a):
             "wall_s": st.wall_s, "launches": st.launches,
             "block_steps_per_s": st.block_steps / st.wall_s, "interactions_per_s": st.interactions / st.wall_s,
             "block_step_latency_us": _lat(st.step_us),
-            "request_latency_s": _lat([(r.done_s - r.arrival_s) * 1e6 for r in res]) if res else None,
-            "note": "requests arrive in real time over the window; unfinished ones are stopped at its end; "
-                    "request_latency uses the same percentile fields in seconds*1e6"}
+            "request_latency_s": _lat([r.done_s - r.arrival_s for r in res],
+                                      "wall seconds from a request's arrival to its completion") if res else None,
+            "note": "requests arrive in real time over the window; unfinished ones are stopped at its end"}
 
 
-def _lat(us):
+def _lat(vals, note="device time of one block step (all three phases) in the persistent loop"):
     import numpy as np
-    if not us:
+    if not vals:
         return None
-    u = np.asarray(us)
+    u = np.asarray(vals)
     return {"p50": float(np.quantile(u, 0.5)), "p99": float(np.quantile(u, 0.99)), "mean": float(u.mean()),
-            "n": int(len(u)), "note": "device time of one block step (all three phases) in the persistent loop"}
+            "n": int(len(u)), "note": note}
 
 
 def _n_i(r):
