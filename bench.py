@@ -375,7 +375,8 @@ def _ensemble(hh, a):
     results, stats = [], None
     t0 = time.perf_counter()
     # one server per theta value (the opening angle is a per-context setting)
-    tot = {"block_steps": 0, "interactions": 0, "step_us": [], "live": [], "launches": 0, "wall": 0.0}
+    tot = {"block_steps": 0, "interactions": 0, "step_us": [], "live": [], "launches": 0, "wall": 0.0,
+           "phase_us": [0.0, 0.0]}
     for th in sorted({mb.theta for mb in members}):
         sub = [r for r, mb in zip(reqs, members) if mb.theta == th]
         srv = serve.Server(precision=hh.HH_MIXED, budget_bytes=150 * 10 ** 9, max_sims=256, max_steps=256,
@@ -391,6 +392,7 @@ def _ensemble(hh, a):
         tot["live"] += st.live_per_step
         tot["launches"] += st.launches
         tot["wall"] += st.wall_s
+        tot["phase_us"] = [u + w for u, w in zip(tot["phase_us"], st.phase_us)]
     wall = time.perf_counter() - t0
     lat = _lat(tot["step_us"])
     return {"clusters": len(members), "n_total": int(sum(mb.n for mb in members)), "t_end": t_end,
@@ -399,6 +401,7 @@ def _ensemble(hh, a):
             "equiv_tflops": FLOP_PER_INT * tot["interactions"] / wall / 1e12,
             "mean_live_sims_per_step": float(np.mean(tot["live"])) if tot["live"] else None,
             "block_step_latency_us": lat,
+            "device_s": {"predict_select": tot["phase_us"][0] * 1e-6, "force_correct": tot["phase_us"][1] * 1e-6},
             "note": "wall time includes admission (host tree build for the memory estimate, initial forces) "
                     "and the rebuilds; "
                     "block steps are summed over clusters; latency = device time of one global block step"}

@@ -256,7 +256,12 @@ const char *hh_last_error(const hh_ctx *ctx);
  * so they equal what hh_advance computes for it alone.
  *
  * hh_batch_create: device, precision (every context of a run must match it),
- *   up to max_sims simulations per run and max_steps global steps per run.
+ *   up to max_sims (1..32767) simulations per run and max_steps (1..2^20)
+ *   global steps per run.  It captures a run once as a CUDA graph: one
+ *   fixed-size copy from a pinned host block of the simulation descriptors,
+ *   the cooperative launch, and one fixed-size copy back of the step count,
+ *   next times and phase stamps; hh_batch_run fills the host block and
+ *   replays the graph.  A batch is used by one thread at a time.
  * hh_batch_run: runs the n contexts (distinct, same device and precision,
  *   with lists and steps set) until each one's next block time exceeds its
  *   t_end[s] (normally its next rebuild time) or max_steps global steps have

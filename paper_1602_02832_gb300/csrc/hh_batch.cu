@@ -1,4 +1,4 @@
-// Batched, persistent block-step loop (scope row a7): one cooperative launch
+// Batched, persistent block-step loop: one cooperative launch
 // advances many independent simulations, each by its own block steps (Section 2,
 // tree-loop steps 2-7), until each reaches its stop time or the step budget.
 //
@@ -18,6 +18,9 @@
 // queue, so small block steps of many simulations fill the GPU together.
 // Results of a simulation do not depend on what else is in the batch: its
 // tiles, active masks and list parts are its own, and sums run in fixed order.
+//
+// A run is one captured CUDA graph (upload of the descriptors, the launch,
+// read-back of the outputs), replayed with new descriptors each time.
 //
 // Grid barriers spin with an iteration limit; on expiry the kernel records
 // HH_ETIMEOUT and every CTA returns.
@@ -63,15 +66,22 @@ struct BatchScalars {
     int32_t steps_done;
 };
 
-struct BatchDev {
-    const SimDesc *sims;
+// What changes from one run to the next, read by the kernel from device
+// memory, so that the launch itself (captured once in a CUDA graph) keeps
+// fixed arguments.
+struct BatchHdr {
     int32_t n_sims;
     int32_t max_steps;
-    const int64_t *jbase, *pbase, *tbase;  // prefix sums [n_sims + 1]
-    int4 *items;
+    int4 *items;  // work queue (grows with the simulations' list parts)
+};
+
+struct BatchDev {
+    const BatchHdr *hdr;
+    const SimDesc *sims;                   // [max_sims]
+    const int64_t *jbase, *pbase, *tbase;  // prefix sums [n_sims + 1], each of capacity max_sims + 1
     BatchScalars *bs;
     unsigned long long *step_ns;  // [3 max_steps + 1] global timer at the start and after each phase
-    double *t_next_out;           // [n_sims]
+    double *t_next_out;           // [max_sims]
 };
 
 __device__ __forceinline__ unsigned long long globaltimer_ns()
@@ -350,7 +360,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
     ForceSmem<Rec, TJ> &sm = reinterpret_cast<ForceSmem<Rec, TJ> *>(smem_raw)[group];
     const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + tid;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-    const int n_sims = B.n_sims;
+    const int n_sims = B.hdr->n_sims, max_steps = B.hdr->max_steps;
+    int4 *const items = B.hdr->items;
     const int64_t NJ = B.jbase[n_sims], NP = B.pbase[n_sims], NT = B.tbase[n_sims];
 
     // phase 0: every simulation's first block time, latest time, level
@@ -422,7 +433,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
         }
 
     int step = 0;
-    for (; step < B.max_steps; step++) {
+    for (; step < max_steps; step++) {
         const int par = step & 1;
         // ---- phase 1: predict + select
         cache_times(sc, B.sims, n_sims, par);
@@ -470,7 +481,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                 const bool act = (p < td.y) && (sd.st.t[p] + sd.st.dt[p] == tnow);
                 const uint32_t mask = __ballot_sync(0xffffffffu, act);
                 if (mask)
-                    append_tile_items(sd.L, tile, td, mask, sd.pj, sd.work, &B.bs->n_items[par], &sd.ds->slot_par[par], B.items,
+                    append_tile_items(sd.L, tile, td, mask, sd.pj, sd.work, &B.bs->n_items[par], &sd.ds->slot_par[par], items,
                                       s, sd.ds->na_hist);
             }
         }
@@ -492,7 +503,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
             int item = group * (int)gridDim.x + (int)blockIdx.x;
             for (;;) {
                 if (item >= (int)n_items) break;
-                const int4 it = B.items[item];
+                const int4 it = items[item];
                 const int s = it.y >> 16;
                 const SimDesc &sd = B.sims[s];
                 unsigned long long n_int = 0;
@@ -552,6 +563,17 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
 
 }  // namespace
 
+// Host and device copies of one block holding everything a run uploads
+// (header, simulation descriptors, prefix sums, zeroed scalars) followed by
+// everything it reads back (scalars, next times, phase stamps), so that a run
+// is one captured graph: one host-to-device copy, the cooperative launch and
+// one device-to-host copy, all of fixed size.
+struct BatchLayout {
+    size_t hdr = 0, sims = 0, base = 0, bs = 0, tnext = 0, step_ns = 0, total = 0;
+    size_t up_bytes() const { return bs + sizeof(BatchScalars); }
+    size_t down_bytes() const { return total - bs; }
+};
+
 struct hh_batch {
     int device = 0;
     int precision = HH_FP64;
@@ -559,14 +581,12 @@ struct hh_batch {
     int grid = 0;
     size_t smem = 0;
     cudaStream_t stream = nullptr;
-    SimDesc *d_sims = nullptr;
-    int64_t *d_base = nullptr;  // 3 x (max_sims + 1)
+    BatchLayout lay;
+    unsigned char *d_blk = nullptr;  // device block
+    unsigned char *h_blk = nullptr;  // pinned host mirror
     int4 *d_items = nullptr;
     int64_t cap_items = 0;
-    BatchScalars *d_bs = nullptr;
-    unsigned long long *d_step_ns = nullptr;
-    double *d_tnext = nullptr;
-    std::vector<unsigned long long> h_step_ns;
+    cudaGraphExec_t graph = nullptr;  // upload, k_batch, read-back
     std::string err;
 };
 
@@ -578,14 +598,70 @@ int bfail(hh_batch *b, int code, const std::string &m)
     return hh_set_global_error(code, m.c_str());
 }
 
+size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+BatchLayout batch_layout(int32_t max_sims, int32_t max_steps)
+{
+    BatchLayout L;
+    L.hdr = 0;
+    L.sims = align16(sizeof(BatchHdr));
+    L.base = align16(L.sims + sizeof(SimDesc) * size_t(max_sims));
+    L.bs = align16(L.base + sizeof(int64_t) * 3 * (size_t(max_sims) + 1));
+    L.tnext = align16(L.bs + sizeof(BatchScalars));
+    L.step_ns = align16(L.tnext + sizeof(double) * size_t(max_sims));
+    L.total = L.step_ns + sizeof(unsigned long long) * (3 * size_t(max_steps) + 1);
+    return L;
+}
+
+// Captures the run's graph on the batch stream (thread-local capture mode:
+// other threads may use CUDA meanwhile).
+int capture_graph(hh_batch *b)
+{
+    const BatchLayout &L = b->lay;
+    unsigned char *d = b->d_blk;
+    BatchDev B;
+    B.hdr = reinterpret_cast<const BatchHdr *>(d + L.hdr);
+    B.sims = reinterpret_cast<const SimDesc *>(d + L.sims);
+    const int64_t *base = reinterpret_cast<const int64_t *>(d + L.base);
+    B.jbase = base;
+    B.pbase = base + (b->max_sims + 1);
+    B.tbase = base + 2 * (size_t(b->max_sims) + 1);
+    B.bs = reinterpret_cast<BatchScalars *>(d + L.bs);
+    B.t_next_out = reinterpret_cast<double *>(d + L.tnext);
+    B.step_ns = reinterpret_cast<unsigned long long *>(d + L.step_ns);
+    void *args[] = {&B};
+    const void *fn = b->precision == HH_MIXED ? (const void *)k_batch<RecMix, kTjMix>
+                                              : (const void *)k_batch<RecF64, kTjF64>;
+    cudaStream_t st = b->stream;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return bfail(b, HH_ECUDA, "hh_batch_create: cannot begin graph capture");
+    cudaError_t e = cudaMemcpyAsync(d, b->h_blk, L.up_bytes(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaLaunchCooperativeKernel(fn, dim3(b->grid), dim3(kBlock), args, b->smem, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->h_blk + L.bs, d + L.bs, L.down_bytes(), cudaMemcpyDeviceToHost, st);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e_end = cudaStreamEndCapture(st, &g);
+    if (e == cudaSuccess) e = e_end;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b->graph = nullptr;
+        return bfail(b, HH_ECUDA, std::string("hh_batch_create: graph capture: ") + cudaGetErrorString(e));
+    }
+    return HH_OK;
+}
+
 }  // namespace
 
 extern "C" int hh_batch_create(hh_batch **out, int device, int precision, int32_t max_sims, int32_t max_steps)
 {
     if (!out) return hh_set_global_error(HH_EINVAL, "hh_batch_create: out is NULL");
     *out = nullptr;
-    if ((precision != HH_FP64 && precision != HH_MIXED) || max_sims < 1 || max_sims > 32767 || max_steps < 1)
-        return hh_set_global_error(HH_EINVAL, "hh_batch_create: bad precision, max_sims (1..32767) or max_steps");
+    if ((precision != HH_FP64 && precision != HH_MIXED) || max_sims < 1 || max_sims > 32767 || max_steps < 1 ||
+        max_steps > (1 << 20))
+        return hh_set_global_error(HH_EINVAL,
+                                   "hh_batch_create: bad precision, max_sims (1..32767) or max_steps (1..2^20)");
     hh_batch *b = new (std::nothrow) hh_batch;
     if (!b) return hh_set_global_error(HH_ENOMEM, "hh_batch_create: out of host memory");
     b->device = device;
@@ -616,15 +692,18 @@ extern "C" int hh_batch_create(hh_batch **out, int device, int precision, int32_
     }
     if (per < 1) return bail(HH_ECUDA, "hh_batch_create: kernel does not fit on an SM");
     b->grid = prop.multiProcessorCount;  // one persistent CTA per SM
-    if (cudaMalloc(&b->d_sims, sizeof(SimDesc) * max_sims) != cudaSuccess ||
-        cudaMalloc(&b->d_base, sizeof(int64_t) * 3 * (max_sims + 1)) != cudaSuccess ||
-        cudaMalloc(&b->d_bs, sizeof(BatchScalars)) != cudaSuccess ||
-        cudaMalloc(&b->d_step_ns, sizeof(unsigned long long) * (3 * size_t(max_steps) + 1)) != cudaSuccess ||
-        cudaMalloc(&b->d_tnext, sizeof(double) * max_sims) != cudaSuccess) {
+    b->lay = batch_layout(max_sims, max_steps);
+    if (cudaMalloc(&b->d_blk, b->lay.total) != cudaSuccess ||
+        cudaMallocHost(&b->h_blk, b->lay.total) != cudaSuccess) {
         cudaGetLastError();
-        return bail(HH_ENOMEM, "hh_batch_create: device allocation failed");
+        return bail(HH_ENOMEM, "hh_batch_create: allocation failed");
     }
-    b->h_step_ns.resize(3 * size_t(max_steps) + 1);
+    std::memset(b->h_blk, 0, b->lay.total);
+    if (int rc = capture_graph(b)) {
+        const std::string m = b->err;
+        hh_batch_destroy(b);
+        return hh_set_global_error(rc, m.c_str());
+    }
     *out = b;
     return HH_OK;
 }
@@ -634,9 +713,10 @@ extern "C" int hh_batch_destroy(hh_batch *b)
     if (!b) return HH_OK;
     cudaSetDevice(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
-    void *p[] = {b->d_sims, b->d_base, b->d_items, b->d_bs, b->d_step_ns, b->d_tnext};
-    for (void *q : p)
-        if (q) cudaFree(q);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->d_blk) cudaFree(b->d_blk);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->h_blk) cudaFreeHost(b->h_blk);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
     return HH_OK;
@@ -649,9 +729,11 @@ extern "C" int hh_batch_run(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const d
     if (n < 1 || n > b->max_sims || !ctxs || !t_end) return bfail(b, HH_EINVAL, "hh_batch_run: bad n or NULL arrays");
     if (max_steps < 1 || max_steps > b->max_steps) return bfail(b, HH_EINVAL, "hh_batch_run: max_steps out of range");
     if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, HH_ECUDA, "hh_batch_run: cudaSetDevice failed");
-    std::vector<SimDesc> sims(static_cast<size_t>(n));
-    std::vector<int64_t> base(3 * (static_cast<size_t>(n) + 1), 0);
-    int64_t *jb = base.data(), *pb = jb + n + 1, *tb = pb + n + 1;
+    const BatchLayout &Ly = b->lay;
+    SimDesc *sims = reinterpret_cast<SimDesc *>(b->h_blk + Ly.sims);
+    int64_t *jb = reinterpret_cast<int64_t *>(b->h_blk + Ly.base);
+    int64_t *pb = jb + (b->max_sims + 1), *tb = pb + (b->max_sims + 1);
+    jb[0] = pb[0] = tb[0] = 0;
     int64_t items_needed = 0;
     for (int32_t s = 0; s < n; s++) {
         hh_ctx *c = ctxs[s];
@@ -662,7 +744,7 @@ extern "C" int hh_batch_run(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const d
         for (int32_t q = 0; q < s; q++)
             if (ctxs[q] == c) return bfail(b, HH_EINVAL, "hh_batch_run: a context appears twice");
         if (!(t_end[s] == t_end[s])) return bfail(b, HH_EINVAL, "hh_batch_run: NaN stop time");
-        SimDesc &d = sims[size_t(s)];
+        SimDesc &d = sims[s];
         std::memset(&d, 0, sizeof(d));
         d.st = c->st;
         d.rec = c->rec;
@@ -705,40 +787,20 @@ extern "C" int hh_batch_run(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const d
         }
         b->cap_items = cap;
     }
-    cudaStream_t st = b->stream;
-    if (cudaMemcpyAsync(b->d_sims, sims.data(), sizeof(SimDesc) * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(b->d_base, base.data(), sizeof(int64_t) * base.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemsetAsync(b->d_bs, 0, sizeof(BatchScalars), st) != cudaSuccess)
-        return bfail(b, HH_ECUDA, "hh_batch_run: upload failed");
-    BatchDev B;
-    B.sims = b->d_sims;
-    B.n_sims = n;
-    B.max_steps = max_steps;
-    B.jbase = b->d_base;
-    B.pbase = b->d_base + (n + 1);
-    B.tbase = b->d_base + 2 * (n + 1);
-    B.items = b->d_items;
-    B.bs = b->d_bs;
-    B.step_ns = b->d_step_ns;
-    B.t_next_out = b->d_tnext;
-    void *args[] = {&B};
-    cudaError_t e;
-    if (b->precision == HH_MIXED)
-        e = cudaLaunchCooperativeKernel((const void *)k_batch<RecMix, kTjMix>, dim3(b->grid), dim3(kBlock), args, b->smem,
-                                        st);
-    else
-        e = cudaLaunchCooperativeKernel((const void *)k_batch<RecF64, kTjF64>, dim3(b->grid), dim3(kBlock), args, b->smem,
-                                        st);
-    if (e != cudaSuccess) return bfail(b, HH_ECUDA, std::string("hh_batch_run: launch: ") + cudaGetErrorString(e));
+    BatchHdr *hdr = reinterpret_cast<BatchHdr *>(b->h_blk + Ly.hdr);
+    hdr->n_sims = n;
+    hdr->max_steps = max_steps;
+    hdr->items = b->d_items;
+    std::memset(b->h_blk + Ly.bs, 0, sizeof(BatchScalars));
+    if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) {
+        const cudaError_t e = cudaGetLastError();
+        return bfail(b, HH_ECUDA, std::string("hh_batch_run: launch: ") + cudaGetErrorString(e));
+    }
     hh_count_launches(1);
-    BatchScalars hbs;
-    std::vector<double> tn(static_cast<size_t>(n));
-    if (cudaMemcpyAsync(&hbs, b->d_bs, sizeof(hbs), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaMemcpyAsync(tn.data(), b->d_tnext, sizeof(double) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaMemcpyAsync(b->h_step_ns.data(), b->d_step_ns, sizeof(unsigned long long) * (3 * size_t(max_steps) + 1),
-                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess)
         return bfail(b, HH_ECUDA, "hh_batch_run: kernel execution failed");
+    BatchScalars hbs;
+    std::memcpy(&hbs, b->h_blk + Ly.bs, sizeof(hbs));
     if (hbs.err == HH_ETIMEOUT) return bfail(b, hbs.err, "hh_batch_run: grid barrier timed out");
     if (hbs.err)
         return bfail(b, hbs.err, "hh_batch_run: block-step state breaks the block rule (a step that is not a power "
@@ -748,8 +810,8 @@ extern "C" int hh_batch_run(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const d
         ctxs[s]->have_forces = true;
     }
     if (steps_out) *steps_out = hbs.steps_done;
-    if (t_next_out) std::copy(tn.begin(), tn.end(), t_next_out);
-    const unsigned long long *T = b->h_step_ns.data();
+    if (t_next_out) std::memcpy(t_next_out, b->h_blk + Ly.tnext, sizeof(double) * size_t(n));
+    const unsigned long long *T = reinterpret_cast<const unsigned long long *>(b->h_blk + Ly.step_ns);
     for (int32_t q = 0; q < hbs.steps_done; q++) {
         const size_t k = 3 * size_t(q);
         if (step_us_out) step_us_out[q] = double(T[k + 3] - T[k]) * 1e-3;

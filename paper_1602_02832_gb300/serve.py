@@ -1,4 +1,4 @@
-"""Continuous-batching server of cluster simulations over libhh (scope row a8).
+"""Continuous-batching server of cluster simulations over libhh.
 
 Requests (independent N-body simulations with their own N, masses and end
 time) are admitted while their device memory fits a budget, stay resident on
@@ -71,6 +71,7 @@ class _Live:
 class ServerStats:
     step_us: list = field(default_factory=list)       # duration of each global block step
     live_per_step: list = field(default_factory=list)  # simulations advanced in that launch
+    phase_us: list = field(default_factory=lambda: [0.0, 0.0])  # device time in predict + select, force + correct
     launches: int = 0
     block_steps: int = 0          # sum over simulations of block steps
     interactions: int = 0
@@ -241,6 +242,10 @@ class Server:
             self.stats.launches += 1
             self.stats.step_us.extend(us.tolist())
             self.stats.live_per_step.extend([len(runnable)] * len(us))
+            ph = getattr(self.batch, "last_phase_us", None)
+            if ph is not None and len(ph):
+                self.stats.phase_us[0] += float(ph[:, 0].sum())
+                self.stats.phase_us[1] += float(ph[:, 1].sum() + ph[:, 2].sum())
             for s, t_next in zip(runnable, tn):
                 if t_next <= s.t_stop:
                     continue  # still inside its interval

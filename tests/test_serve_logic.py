@@ -73,6 +73,8 @@ class FakeBatch:
                 if c.done_steps % c.steps_per_interval == 0:
                     c.t = ts
             tn.append(ts + 1.0 / 128 if c.t >= ts else c.t + 1e-3)
+        # per global step: predict + select, force (+ corrector), an empty third phase
+        self.last_phase_us = np.tile([0.25, 0.75, 0.0], (max_steps, 1))
         return max_steps, np.array(tn), np.ones(max_steps)
 
     def close(self):
@@ -101,6 +103,9 @@ def test_server_budget_order_and_completion(monkeypatch):
     assert FakeCtx.peak <= 4
     assert max(srv.batch.calls) >= 2  # simulations were batched together
     assert stats.launches == len(srv.batch.calls)
+    # the device-time split adds up the kernel's phases over every launch
+    assert stats.phase_us[0] == pytest.approx(0.25 * len(stats.step_us))
+    assert stats.phase_us[1] == pytest.approx(0.75 * len(stats.step_us))
 
 
 def test_server_rejects_a_request_above_the_budget(monkeypatch):
