@@ -291,6 +291,16 @@ const char *hh_batch_last_error(const hh_batch *b);
  * NULL) receives the kernel's duration. */
 int hh_barrier_selftest(int device, int skip_cta, double *elapsed_s);
 
+/* Self-test of the corrector's timestep criterion (Aarseth's formula, used
+ * at step 6 of Section 2): for i < n, out[i] = the device's value of the
+ * criterion from the squared norms A = |a|^2, J = |j|^2, S = |a2|^2,
+ * T = |a3|^2 (host arrays of n doubles, caller-owned) and eta.  Where the
+ * device decides in FP32 the value is the exact power of two at or below
+ * sqrt(eta (sqrt(A S) + J) / (sqrt(J T) + S)) evaluated in FP64; elsewhere it
+ * is that FP64 value.  n <= 2^26; synchronises. */
+int hh_selftest_aarseth(int device, int64_t n, const double *A, const double *J, const double *S, const double *T,
+                        double eta, double *out);
+
 /* Device memory held by a context (bytes), for admission by memory budget. */
 int64_t hh_ctx_device_bytes(const hh_ctx *ctx);
 

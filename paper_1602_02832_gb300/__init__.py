@@ -100,6 +100,7 @@ _SIGS = {
     "hh_batch_last_error": (C.c_char_p, [_P]),
     "hh_ctx_device_bytes": (C.c_int64, [_P]),
     "hh_barrier_selftest": (C.c_int, [C.c_int, C.c_int, _D]),
+    "hh_selftest_aarseth": (C.c_int, [C.c_int, C.c_int64, _D, _D, _D, _D, C.c_double, _D]),
     "hh_set_rebuild_device": (C.c_int, [_P, C.c_int]),
     "hh_get_lists": (C.c_int, [_P, _I32, _I64, _I64, _I32, _I32]),
     "hh_get_j": (C.c_int, [_P, C.c_int64, C.c_int64, _D, _D, _D, _D, _D, _D]),
@@ -440,6 +441,15 @@ class Batch:
             raise HHError(rc, (_lib.hh_batch_last_error(self.h) or b"").decode())
         self.last_phase_us = ph[:steps.value]
         return steps.value, tn, us[:steps.value]
+
+
+def hh_selftest_aarseth(A, J, S, T, eta, device=0):
+    """Device value of the timestep criterion for squared norms A, J, S, T."""
+    arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (A, J, S, T)]
+    n = len(arrs[0])
+    out = np.zeros(n)
+    _check(_lib.hh_selftest_aarseth(int(device), n, *[_ptr(x) for x in arrs], float(eta), _ptr(out)))
+    return out
 
 
 def hh_barrier_selftest(skip_cta=-1, device=0):

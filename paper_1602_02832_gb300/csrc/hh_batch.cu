@@ -91,16 +91,28 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
     return t;
 }
 
-// Grid-wide barrier for a cooperative launch (all CTAs resident).  Returns
-// false when any CTA has recorded an error (including a barrier timeout).
-// Grid barrier.  Arrivals count up monotonically within a launch (the host
-// zeroes the counters), so an arrival's count tells which barrier it belongs
-// to: the last arrival of barrier b publishes generation b + 1 with a release
-// store, and the others wait for it with acquire loads.  The arrivals are
+// Grid barrier for a cooperative launch (all CTAs resident).  Arrivals
+// count up monotonically within a launch (the host zeroes the counters), so
+// an arrival's count tells which barrier it belongs to: the last arrival of
+// barrier b raises the generation word to b + 1 with a release operation,
+// and the others wait for it with acquire loads.  The arrivals are
 // acquire-release operations on one counter, so the last one has seen every
 // CTA's writes (each CTA's threads synchronise with its arriving thread
-// first), and its release passes them on to every waiter.  Waits give up
-// after kWaitNs / kSpinLimit with HH_ETIMEOUT.
+// first), and its release passes them on to every waiter.
+//
+// Errors travel in the same word: raise_error sets its top bit, which every
+// waiter sees at once, so a passed barrier needs no second read.  (A CTA that
+// releases a barrier after another CTA has failed runs one more phase and
+// stops at the next barrier.)  Waits give up after kWaitNs / kSpinLimit with
+// HH_ETIMEOUT.  Returns false once an error is known.
+constexpr unsigned int kGenErr = 0x80000000u;
+
+__device__ __forceinline__ void raise_error(BatchScalars *bs, int code)
+{
+    atomicExch(&bs->err, code);
+    atomicOr(&bs->bar_gen, kGenErr);
+}
+
 __device__ __forceinline__ bool grid_sync(BatchScalars *bs)
 {
     __shared__ int s_ok;
@@ -108,21 +120,28 @@ __device__ __forceinline__ bool grid_sync(BatchScalars *bs)
     if (threadIdx.x == 0) {
         const unsigned int v = atom_add_acq_rel_gpu(&bs->bar_count, 1u);
         const unsigned int target = v / gridDim.x + 1u;
+        int ok = 1;
         if (v % gridDim.x == gridDim.x - 1u) {
-            st_release_gpu(&bs->bar_gen, target);
+            red_release_max_gpu(&bs->bar_gen, target);
         } else {
             long long it = 0;
             const unsigned long long t0 = globaltimer_ns();
-            while (ld_acquire_gpu(&bs->bar_gen) < target) {
-                if (++it > kSpinLimit || globaltimer_ns() - t0 > kWaitNs) {
-                    atomicExch(&bs->err, HH_ETIMEOUT);
+            for (;;) {
+                const unsigned int g = ld_acquire_gpu(&bs->bar_gen);
+                if (g & kGenErr) {
+                    ok = 0;
                     break;
                 }
-                if ((it & 255) == 0 && *(volatile int32_t *)&bs->err) break;  // another CTA gave up
+                if (g >= target) break;
+                if (++it > kSpinLimit || globaltimer_ns() - t0 > kWaitNs) {
+                    raise_error(bs, HH_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
                 __nanosleep(32);
             }
         }
-        s_ok = (*(volatile int32_t *)&bs->err) == 0;
+        s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
@@ -195,9 +214,10 @@ __device__ __forceinline__ double due_below_warp(const int32_t *lvl_cnt, double 
 // or 32 are active, so this cuts the corrector's FP64 issue per small step
 // about threefold.  Same arithmetic as correct_particle, component by
 // component.  Returns (in every lane) the minimum of t + dt over the tile's
-// corrected particles and updates the simulation's level histogram.
+// corrected particles, updates the simulation's level histogram and leaves
+// each corrected particle's new level in lv_out[its index among the active].
 __device__ __forceinline__ double correct_tile_3lane(const SimDesc &sd, const int4 td, uint32_t mask, double tnow,
-                                                     int lane, int k_first, int k_step)
+                                                     int lane, int k_first, int k_step, int *lv_out)
 {
     const unsigned full = 0xffffffffu;
     const State &s = sd.st;
@@ -240,6 +260,7 @@ __device__ __forceinline__ double correct_tile_3lane(const SimDesc &sd, const in
                 s.t[p] = tnow;
                 s.dt[p] = dtn;
                 const int lv_old = level_of(dt_old), lv_new = level_of(dtn);
+                lv_out[k] = lv_new;
                 if (lv_new != lv_old) {
                     atomicSub(&sd.ds->lvl_cnt[lv_old], 1);
                     atomicAdd(&sd.ds->lvl_cnt[lv_new & 31], 1);
@@ -392,11 +413,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                 t = sd.st.t[p];
                 dt = sd.st.dt[p];
                 if (!is_level_step(dt) || !(t >= 0.0)) {
-                    atomicExch(&B.bs->err, HH_EINVAL);
+                    raise_error(B.bs, HH_EINVAL);
                 } else {
                     lv = level_of(dt);
                     const double u = t * pow2i(lv);
-                    if (u != floor(u)) atomicExch(&B.bs->err, HH_EINVAL);  // t_i not a multiple of dt_i
+                    if (u != floor(u)) raise_error(B.bs, HH_EINVAL);  // t_i not a multiple of dt_i
                 }
                 mc_push(B.sims, acc, s, t + dt, 0, 0);
             }
@@ -429,7 +450,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
         for (int s = tid; s < n_sims; s += blockDim.x) {
             const DevScalars *ds = B.sims[s].ds;
             const double tcur = __longlong_as_double((long long)__ldcg(&ds->t_cur_bits));
-            if (!(sim_time(B.sims[s], 0) > tcur)) atomicExch(&B.bs->err, HH_EINVAL);  // an overdue particle
+            if (!(sim_time(B.sims[s], 0) > tcur)) raise_error(B.bs, HH_EINVAL);  // an overdue particle
         }
 
     int step = 0;
@@ -516,12 +537,18 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                     const double tnow = cached_time(sc, B.sims, s, par);
                     const int4 td = sd.L.tiles[it.x];
                     const uint32_t mask = (uint32_t)it.z;
-                    const double tn = correct_tile_3lane(sd, td, mask, tnow, glane, 10 * gw, 10 * (kThreads / 32));
+                    // steps of the tile's particles that are not corrected now,
+                    // loaded while the corrector runs
+                    const int64_t pw = td.x + glane;
+                    const double dt_keep = (gw == 0 && pw < td.y && !((mask >> glane) & 1u)) ? sd.st.dt[pw] : 0.0;
+                    const double tn =
+                        correct_tile_3lane(sd, td, mask, tnow, glane, 10 * gw, 10 * (kThreads / 32), sm.lv);
                     if (glane == 0) sm.tn[gw] = tn;
-                    group_sync(bar);  // new steps and times are visible to the group
+                    group_sync(bar);  // new levels and times are visible to the group
                     if (gw == 0) {
-                        const int64_t p = td.x + glane;
-                        const uint32_t bit = (p < td.y) ? (1u << (level_of(sd.st.dt[p]) & 31)) : 0u;
+                        const bool corrected = (mask >> glane) & 1u;
+                        const int lv = corrected ? sm.lv[__popc(mask & ((1u << glane) - 1u))] : level_of(dt_keep);
+                        const uint32_t bit = (pw < td.y) ? (1u << (lv & 31)) : 0u;
                         const uint32_t lvm = __reduce_or_sync(0xffffffffu, bit);
                         if (glane == 0) {
                             double m = sm.tn[0];
@@ -871,5 +898,45 @@ extern "C" int hh_barrier_selftest(int device, int skip_cta, double *elapsed_s)
     if (e != cudaSuccess) return hh_set_global_error(HH_ECUDA, cudaGetErrorString(e));
     hh_count_launches(1);
     if (h.err) return hh_set_global_error(h.err, "hh_barrier_selftest: a grid barrier timed out");
+    return HH_OK;
+}
+
+namespace {
+
+__global__ void k_aarseth_selftest(int64_t n, const double *A, const double *J, const double *S, const double *T,
+                                   double eta, double *out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = aarseth_want(A[i], J[i], S[i], T[i], eta);
+}
+
+}  // namespace
+
+extern "C" int hh_selftest_aarseth(int device, int64_t n, const double *A, const double *J, const double *S,
+                                   const double *T, double eta, double *out)
+{
+    if (n < 0 || (n > 0 && (!A || !J || !S || !T || !out)))
+        return hh_set_global_error(HH_EINVAL, "hh_selftest_aarseth: bad n or NULL array");
+    if (n == 0) return HH_OK;
+    if (n > (int64_t(1) << 26)) return hh_set_global_error(HH_EINVAL, "hh_selftest_aarseth: n above 2^26");
+    if (cudaSetDevice(device) != cudaSuccess) return hh_set_global_error(HH_ECUDA, "hh_selftest_aarseth: bad device");
+    double *d = nullptr;
+    const size_t bytes = sizeof(double) * size_t(n);
+    if (cudaMalloc(&d, 5 * bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return hh_set_global_error(HH_ENOMEM, "hh_selftest_aarseth: allocation failed");
+    }
+    cudaError_t e = cudaSuccess;
+    const double *src[4] = {A, J, S, T};
+    for (int q = 0; q < 4 && e == cudaSuccess; q++) e = cudaMemcpy(d + q * n, src[q], bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        const int grid = int(std::min<int64_t>((n + 255) / 256, 4096));
+        k_aarseth_selftest<<<grid, 256>>>(n, d, d + n, d + 2 * n, d + 3 * n, eta, d + 4 * n);
+        hh_count_launches(1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, d + 4 * n, bytes, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return hh_set_global_error(HH_ECUDA, cudaGetErrorString(e));
     return HH_OK;
 }

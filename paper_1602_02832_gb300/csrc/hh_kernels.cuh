@@ -200,17 +200,21 @@ static __global__ void k_select(State s, Lists L, DevScalars *ds, StepCtl c)
 
 // -------------------------------------------------------------- predictor
 // x + v D + a D^2/2 + jk D^3/6 and v + a D + jk D^2/2, in Horner form.
+// Taylor predictor of one component over D (Section 2, step 3).
+__device__ __forceinline__ void predict_xv(double D, double x, double v, double a, double j, double &xp, double &vp)
+{
+    const double h = 0.5 * D, th = D * (1.0 / 3.0);
+    xp = x + D * (v + h * (a + th * j));
+    vp = v + D * (a + h * j);
+}
+
 __device__ __forceinline__ void predict_one(const State &s, int64_t e, double tnow, double xp[3], double vp[3])
 {
     const double D = tnow - s.t[e];
-    const double h = 0.5 * D, th = D * (1.0 / 3.0);
 #pragma unroll
-    for (int d = 0; d < 3; d++) {
-        const double x = s.x[d * s.cap_j + e], v = s.v[d * s.cap_j + e];
-        const double a = s.a[d * s.cap_j + e], j = s.jk[d * s.cap_j + e];
-        xp[d] = x + D * (v + h * (a + th * j));
-        vp[d] = v + D * (a + h * j);
-    }
+    for (int d = 0; d < 3; d++)
+        predict_xv(D, s.x[d * s.cap_j + e], s.v[d * s.cap_j + e], s.a[d * s.cap_j + e], s.jk[d * s.cap_j + e], xp[d],
+                   vp[d]);
 }
 
 template <typename Rec>
@@ -274,10 +278,8 @@ __device__ __forceinline__ void refresh_base(const State &s, int64_t e)
 // Mixed predictor: the FP64 base position (as a float pair) plus an FP32
 // increment D (v + D (a/2 + D jerk/6)), added with TwoSum; v + D (a + D jerk/2)
 // in FP32.  D = t - t_e is exact in FP32 (a multiple of dt_min below dt_tree).
-__device__ __forceinline__ void predict_mix(const State &s, RecMix *rec, int64_t e, double tnow)
+__device__ __forceinline__ RecMix mix_from_base(const BaseMix &b, float D)
 {
-    const float D = __double2float_rn(tnow - s.t[e]);
-    const BaseMix b = s.base[e];
     const float hx[3] = {b.hm.x, b.hm.y, b.hm.z}, lx[3] = {b.lo.x, b.lo.y, b.lo.z};
     const float vv[3] = {b.v.x, b.v.y, b.v.z}, aa[3] = {b.a2.x, b.a2.y, b.a2.z}, jj[3] = {b.j6.x, b.j6.y, b.j6.z};
     float ho[3], lo[3], vo[3];
@@ -295,23 +297,70 @@ __device__ __forceinline__ void predict_mix(const State &s, RecMix *rec, int64_t
     r.hm = make_float4(ho[0], ho[1], ho[2], b.hm.w);
     r.lo = make_float4(lo[0], lo[1], lo[2], 0.f);
     r.v = make_float4(vo[0], vo[1], vo[2], 0.f);
-    rec[e] = r;
+    return r;
+}
+
+// Inputs of one entry's prediction, loaded ahead of its arithmetic so that a
+// thread can keep several entries' loads in flight (pred_load, then
+// pred_store: the same arithmetic as predict_one / mix_from_base).
+template <typename Rec>
+struct PredIn;
+template <>
+struct PredIn<RecF64> {
+    double t, m, x[3], v[3], a[3], j[3];
+};
+template <>
+struct PredIn<RecMix> {
+    double t;
+    BaseMix b;
+};
+
+template <typename Rec>
+__device__ __forceinline__ void pred_load(const State &s, int64_t e, PredIn<Rec> &in);
+template <>
+__device__ __forceinline__ void pred_load<RecF64>(const State &s, int64_t e, PredIn<RecF64> &in)
+{
+    in.t = s.t[e];
+    in.m = s.m[e];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        in.x[d] = s.x[d * s.cap_j + e];
+        in.v[d] = s.v[d * s.cap_j + e];
+        in.a[d] = s.a[d * s.cap_j + e];
+        in.j[d] = s.jk[d * s.cap_j + e];
+    }
+}
+template <>
+__device__ __forceinline__ void pred_load<RecMix>(const State &s, int64_t e, PredIn<RecMix> &in)
+{
+    in.t = s.t[e];
+    in.b = s.base[e];
+}
+
+template <typename Rec>
+__device__ __forceinline__ void pred_store(const PredIn<Rec> &in, Rec *rec, int64_t e, double tnow);
+template <>
+__device__ __forceinline__ void pred_store<RecF64>(const PredIn<RecF64> &in, RecF64 *rec, int64_t e, double tnow)
+{
+    const double D = tnow - in.t;
+    double xp[3], vp[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) predict_xv(D, in.x[d], in.v[d], in.a[d], in.j[d], xp[d], vp[d]);
+    store_rec<RecF64>(rec, e, xp, vp, in.m);
+}
+template <>
+__device__ __forceinline__ void pred_store<RecMix>(const PredIn<RecMix> &in, RecMix *rec, int64_t e, double tnow)
+{
+    rec[e] = mix_from_base(in.b, __double2float_rn(tnow - in.t));
 }
 
 // Predicted record of entry e at tnow, in the form's own arithmetic.
 template <typename Rec>
-__device__ __forceinline__ void predict_entry(const State &s, Rec *rec, int64_t e, double tnow);
-template <>
-__device__ __forceinline__ void predict_entry<RecF64>(const State &s, RecF64 *rec, int64_t e, double tnow)
+__device__ __forceinline__ void predict_entry(const State &s, Rec *rec, int64_t e, double tnow)
 {
-    double xp[3], vp[3];
-    predict_one(s, e, tnow, xp, vp);
-    store_rec<RecF64>(rec, e, xp, vp, s.m[e]);
-}
-template <>
-__device__ __forceinline__ void predict_entry<RecMix>(const State &s, RecMix *rec, int64_t e, double tnow)
-{
-    predict_mix(s, rec, e, tnow);
+    PredIn<Rec> in;
+    pred_load<Rec>(s, e, in);
+    pred_store<Rec>(in, rec, e, tnow);
 }
 
 template <typename Rec>
@@ -646,6 +695,7 @@ struct ForceSmem {
     int item;
     int last;
     double tn[kThreads / 32];  // per-warp minimum of t + dt after the corrector
+    int lv[kMaxTileI];         // new step level of each corrected particle, by active index
 };
 
 // GPU-scope acquire / release operations (PTX memory model): an
@@ -663,9 +713,9 @@ __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p)
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_gpu(unsigned int *p, unsigned int v)
+__device__ __forceinline__ void red_release_max_gpu(unsigned int *p, unsigned int v)
 {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    asm volatile("red.release.gpu.global.max.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // Barrier over the 128 threads working on one item: the whole CTA
@@ -964,22 +1014,59 @@ __device__ __forceinline__ double sq(double u) { return __dmul_rn(u, u); }
 
 // Aarseth's criterion dt^2 = eta (|a||a2| + |j|^2) / (|j||a3| + |a2|^2) from
 // A = |a|^2, J = |j|^2, S = |a2|^2, T = |a3|^2.  Only the largest power of
-// two below dt is used (block_dt), so it is evaluated in FP32: with A, J, S,
-// T in [1e-18, 1e18] the FP32 value is within 6 * 2^-24 (relative) of the
-// FP64 one, and when its mantissa is at least 2^-17 away from a power-of-two
-// boundary the exact power of two below it is returned.  Otherwise (near a
-// boundary, or out of that range) the FP64 expression decides.
+// two below dt is used (block_dt), so it is screened in FP32, which keeps the
+// narrow FP64 pipe free.
+//
+// The criterion is invariant under a change of time unit (J, S, T scale as
+// c^-2, c^-4, c^-6 and dt as c) and under a common factor on A, J, S, T.  So
+// the four norms are first normalised by exact powers of two taken from the
+// exponents of A and J (A' in [1, 2), J' in [1, 8)), which brings the
+// shortest steps' huge higher derivatives into FP32 range, and the power of
+// two found for the normalised step is shifted back.  Error bound of the
+// FP32 value w' against the FP64 expression of the same normalised inputs:
+// truncation to FP32 2^-23 per input, the products, sums, quotient, eta
+// product and roots add at most 5.75 * 2^-24 in all (positive terms only), so
+// when the mantissa of w' is at least 64 ulps (2^-18 relative) away from a
+// power-of-two boundary both lie in the same binade and the exact power of
+// two below the FP64 value is returned.  Otherwise (near a boundary, zero or
+// non-normal inputs, normalised values outside [2^-60, 2^61), eta outside
+// [2^-30, 2^30], or products and steps near the FP64 range's ends, where the
+// FP64 expression itself would lose range) the FP64 expression decides.
+__device__ __forceinline__ int exp2_of(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7ff) - 1023; }
+
+// x * 2^m in FP32 for a positive normal double x, mantissa truncated; the
+// caller keeps the exponent in FP32's normal range.
+__device__ __forceinline__ float f32_scaled(double x, int m)
+{
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023 + m;
+    return __int_as_float(((e + 127) << 23) | (int)((b >> 29) & 0x7fffff));
+}
+
+__device__ __forceinline__ bool normal_pos(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b >= 0x0010000000000000ll && b < 0x7ff0000000000000ll;
+}
+
 __device__ __forceinline__ double aarseth_want(double A, double J, double S, double T, double eta)
 {
-    const float Af = __double2float_rn(A), Jf = __double2float_rn(J), Sf = __double2float_rn(S),
-                Tf = __double2float_rn(T);
-    const float lo = 1e-18f, hi = 1e18f;
-    if (Af >= lo && Af <= hi && Jf >= lo && Jf <= hi && Sf >= lo && Sf <= hi && Tf >= lo && Tf <= hi) {
-        const float w = sqrtf(__double2float_rn(eta) * (sqrtf(Af * Sf) + Jf) / (sqrtf(Jf * Tf) + Sf));
-        const int wb = __float_as_int(w);
-        const int frac = wb & 0x7fffff, ex = (wb >> 23) & 0xff;
-        if (ex > 0 && ex < 255 && frac >= 64 && frac <= 0x7fffff - 64)
-            return __longlong_as_double((long long)(ex - 127 + 1023) << 52);
+    if (normal_pos(A) && normal_pos(J) && normal_pos(S) && normal_pos(T) && eta >= 0x1p-30 && eta <= 0x1p30) {
+        const int eA = exp2_of(A), eJ = exp2_of(J), eS = exp2_of(S), eT = exp2_of(T);
+        const int k = (eJ - eA) >> 1;  // 2^2k ~ J / A: the time unit
+        const int mA = -eA, mJ = -eA - 2 * k, mS = -eA - 4 * k, mT = -eA - 6 * k;
+        const int xS = eS + mS, xT = eT + mT;
+        // the FP64 expression of the original inputs stays finite and normal
+        const bool fp64_ok = eA + eS > -1000 && eA + eS < 1000 && eJ + eT > -1000 && eJ + eT < 1000;
+        if (fp64_ok && xS >= -60 && xS <= 60 && xT >= -60 && xT <= 60) {
+            const float Af = f32_scaled(A, mA), Jf = f32_scaled(J, mJ), Sf = f32_scaled(S, mS), Tf = f32_scaled(T, mT);
+            const float w = sqrtf(__double2float_rn(eta) * ((sqrtf(Af * Sf) + Jf) / (sqrtf(Jf * Tf) + Sf)));
+            const int wb = __float_as_int(w);
+            const int frac = wb & 0x7fffff, ex = (wb >> 23) & 0xff;
+            const int e2 = ex - 127 - k;  // dt = w' / 2^k: exponent of the power of two below dt
+            if (ex > 0 && ex < 255 && frac >= 64 && frac <= 0x7fffff - 64 && e2 > -400 && e2 < 400)
+                return __longlong_as_double((long long)(e2 + 1023) << 52);
+        }
     }
     return sqrt(eta * (sqrt(A * S) + J) / (sqrt(J * T) + S));
 }
