@@ -466,7 +466,7 @@ int hh_create(hh_ctx **out, int device, const hh_config *cfg, int64_t n_max, int
         {(void **)&ctx->tile_cnt, sizeof(int32_t) * ctx->cap_tiles},
         {(void **)&ctx->tile_lv, sizeof(uint32_t) * ctx->cap_tiles},
         {(void **)&ctx->st.base, c.precision == HH_MIXED ? sizeof(BaseMix) * nj_max : 0},
-        {(void **)&ctx->items, sizeof(int4) * ctx->cap_parts},
+        {(void **)&ctx->items, sizeof(WorkItem) * ctx->cap_parts},
         {(void **)&ctx->partials, sizeof(RedF64) * kMaxTileI * ctx->cap_parts},
     };
     for (auto &al : allocs) {
@@ -553,9 +553,9 @@ int ensure_parts(hh_ctx *ctx, int64_t total_parts)
     if (total_parts <= ctx->cap_parts) return HH_OK;
     CK(cudaStreamSynchronize(ctx->stream));
     const int64_t cap = total_parts + total_parts / 4 + 64;
-    int4 *items = nullptr;
+    WorkItem *items = nullptr;
     void *partials = nullptr;
-    if (cudaMalloc(&items, sizeof(int4) * cap) != cudaSuccess ||
+    if (cudaMalloc(&items, sizeof(WorkItem) * cap) != cudaSuccess ||
         cudaMalloc(&partials, sizeof(RedF64) * kMaxTileI * cap) != cudaSuccess) {
         cudaGetLastError();
         if (items) cudaFree(items);
@@ -563,7 +563,7 @@ int ensure_parts(hh_ctx *ctx, int64_t total_parts)
     }
     cudaFree(ctx->items);
     cudaFree(ctx->partials);
-    ctx->device_bytes += (cap - ctx->cap_parts) * int64_t(sizeof(int4) + sizeof(RedF64) * kMaxTileI);
+    ctx->device_bytes += (cap - ctx->cap_parts) * int64_t(sizeof(WorkItem) + sizeof(RedF64) * kMaxTileI);
     ctx->items = items;
     ctx->partials = partials;
     ctx->cap_parts = cap;

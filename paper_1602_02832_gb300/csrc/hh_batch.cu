@@ -72,7 +72,7 @@ struct BatchScalars {
 struct BatchHdr {
     int32_t n_sims;
     int32_t max_steps;
-    int4 *items;  // work queue (grows with the simulations' list parts)
+    WorkItem *items;  // work queue (grows with the simulations' list parts; at least kGroups x grid)
 };
 
 struct BatchDev {
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
     const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + tid;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
     const int n_sims = B.hdr->n_sims, max_steps = B.hdr->max_steps;
-    int4 *const items = B.hdr->items;
+    WorkItem *const items = B.hdr->items;
     const int64_t NJ = B.jbase[n_sims], NP = B.pbase[n_sims], NT = B.tbase[n_sims];
 
     // phase 0: every simulation's first block time, latest time, level
@@ -520,12 +520,14 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
             // SMs (item i -> SM i mod grid): the few items of a small step
             // land on different SMs instead of sharing one SM's FP64 pipe.
             // Later items come from the shared queue.
+            // The queue holds at least n_static slots, so the first item is
+            // read together with the count (and used only below it).
             const int n_static = (int)gridDim.x * kGroups;
             int item = group * (int)gridDim.x + (int)blockIdx.x;
+            WorkItem it = items[item];
             for (;;) {
                 if (item >= (int)n_items) break;
-                const int4 it = items[item];
-                const int s = it.y >> 16;
+                const int s = it.part_sim >> 16;
                 const SimDesc &sd = B.sims[s];
                 unsigned long long n_int = 0;
                 const bool done = force_item<Rec, TJ, false>(sd.st, (const Rec *)sd.rec, sd.L, sd.pj, sd.work,
@@ -535,8 +537,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                 if (done) {
                     group_sync(bar);  // the tile's new forces are visible to the group
                     const double tnow = cached_time(sc, B.sims, s, par);
-                    const int4 td = sd.L.tiles[it.x];
-                    const uint32_t mask = (uint32_t)it.z;
+                    const int4 td = make_int4(it.p_begin, it.p_end, it.group, it.slot);
+                    const uint32_t mask = it.mask;
                     // steps of the tile's particles that are not corrected now,
                     // loaded while the corrector runs
                     const int64_t pw = td.x + glane;
@@ -554,7 +556,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                             double m = sm.tn[0];
                             for (int w = 1; w < kThreads / 32; w++) m = fmin(m, sm.tn[w]);
                             const int c = __popc(mask);
-                            sd.tile_lv[it.x] = lvm;
+                            sd.tile_lv[it.tile] = lvm;
                             atomicMin(&sd.ds->tmin[par ^ 1], (unsigned long long)__double_as_longlong(m));
                             atomicAdd(&sd.ds->particle_steps, (unsigned long long)c);
                             atomicAdd(&sd.ds->n_act_last, c);
@@ -564,6 +566,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                 if (gt == 0) sm.item = n_static + (int)atomicAdd(&B.bs->work[par], 1u);
                 group_sync(bar);  // also ends the use of the shared buffers by this item
                 item = sm.item;   // rewritten only after the next item's group barriers
+                if (item < (int)n_items) it = items[item];
             }
         }
         if (!grid_sync(B.bs)) return;
@@ -611,7 +614,7 @@ struct hh_batch {
     BatchLayout lay;
     unsigned char *d_blk = nullptr;  // device block
     unsigned char *h_blk = nullptr;  // pinned host mirror
-    int4 *d_items = nullptr;
+    WorkItem *d_items = nullptr;
     int64_t cap_items = 0;
     cudaGraphExec_t graph = nullptr;  // upload, k_batch, read-back
     std::string err;
@@ -803,11 +806,13 @@ extern "C" int hh_batch_run(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const d
         if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bfail(b, HH_ECUDA, "hh_batch_run: context stream failed");
     }
     if (items_needed > INT32_MAX / 2) return bfail(b, HH_ENOMEM, "hh_batch_run: too many work items");
-    if (items_needed > b->cap_items) {
+    // every worker group reads its first slot before it knows the count
+    const int64_t min_items = int64_t(b->grid) * kGroups;
+    if (items_needed > b->cap_items || b->cap_items < min_items) {
         if (b->d_items) cudaFree(b->d_items);
         b->d_items = nullptr;
-        const int64_t cap = items_needed + items_needed / 4 + 64;
-        if (cudaMalloc(&b->d_items, sizeof(int4) * cap) != cudaSuccess) {
+        const int64_t cap = std::max(items_needed + items_needed / 4 + 64, min_items);
+        if (cudaMalloc(&b->d_items, sizeof(WorkItem) * cap) != cudaSuccess) {
             cudaGetLastError();
             b->cap_items = 0;
             return bfail(b, HH_ENOMEM, "hh_batch_run: cannot allocate the work queue");

@@ -39,7 +39,7 @@ struct hh_ctx {
     int64_t *off = nullptr;
     int32_t *idx = nullptr, *group_of = nullptr;
     int4 *tiles = nullptr;
-    int4 *items = nullptr;      // [cap_parts]
+    hh::WorkItem *items = nullptr;  // [cap_parts]
     void *partials = nullptr;   // [cap_parts][32] partial sums (scratch)
     int32_t *tile_cnt = nullptr;  // [cap_tiles]
     uint32_t *tile_lv = nullptr;  // [cap_tiles] levels present in each tile (batched loop)

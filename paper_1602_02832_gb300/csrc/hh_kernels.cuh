@@ -90,11 +90,40 @@ struct State {
     int64_t cap_j, cap_n;
 };
 
+// One work item: a part of one i tile's interaction list.  It carries the
+// tile record and the group's list range, so a worker reads one record before
+// it can load particles and list indices.
+struct __align__(16) WorkItem {
+    int32_t tile;      // static tile index
+    int32_t part_sim;  // list part | simulation << 16
+    uint32_t mask;     // active lanes of the tile
+    int32_t slot;      // first partial-sum slot of the tile's parts (0 with one part)
+    int32_t p_begin, p_end, group, pad;  // the tile's particles and list group
+    int64_t gb, ge;    // the group's list [gb, ge) in idx
+};
+
+__device__ __forceinline__ WorkItem make_item(int tile, int part_sim, uint32_t mask, int slot, const int4 td, int64_t gb,
+                                              int64_t ge)
+{
+    WorkItem w;
+    w.tile = tile;
+    w.part_sim = part_sim;
+    w.mask = mask;
+    w.slot = slot;
+    w.p_begin = td.x;
+    w.p_end = td.y;
+    w.group = td.z;
+    w.pad = 0;
+    w.gb = gb;
+    w.ge = ge;
+    return w;
+}
+
 struct Lists {
     const int64_t *off;
     const int32_t *idx;
     const int4 *tiles;  // static i tiles: (p_begin, p_end, group, first part slot)
-    int4 *items;        // this step's work: (tile, part, active mask, parts of the tile)
+    WorkItem *items;    // this step's work
     void *partials;     // per (tile part, i slot) sums of split lists [part slots][32]
     int32_t *tile_cnt;  // arrivals per tile (reset by the last arriver)
     const int32_t *i_map;  // optional: i slot position -> j index (kMapI kernels only)
@@ -156,11 +185,12 @@ __device__ __forceinline__ int parts_of(int64_t len, int pj) { return len > 0 ? 
 // Warp-collective: appends one work item per part of tile `tile`'s list;
 // item = (tile, part | sim << 16, active mask, first partial-sum slot).
 __device__ __forceinline__ void append_tile_items(const Lists &L, int tile, const int4 td, uint32_t mask, int pj_min,
-                                                  int work, uint32_t *n_items, uint32_t *slot_ctr, int4 *items, int sim,
-                                                  unsigned long long *na_hist)
+                                                  int work, uint32_t *n_items, uint32_t *slot_ctr, WorkItem *items,
+                                                  int sim, unsigned long long *na_hist)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t len = L.off[td.z + 1] - L.off[td.z];
+    const int64_t gb = L.off[td.z], ge = L.off[td.z + 1];
+    const int64_t len = ge - gb;
     const int n_parts = parts_of(len, part_len_for(__popc(mask), pj_min, work));
     int base = 0, slot = 0;
     if (lane == 0) {
@@ -170,7 +200,7 @@ __device__ __forceinline__ void append_tile_items(const Lists &L, int tile, cons
     }
     base = __shfl_sync(0xffffffffu, base, 0);
     slot = __shfl_sync(0xffffffffu, slot, 0);
-    for (int q = lane; q < n_parts; q += 32) items[base + q] = make_int4(tile, q | (sim << 16), (int)mask, slot);
+    for (int q = lane; q < n_parts; q += 32) items[base + q] = make_item(tile, q | (sim << 16), mask, slot, td, gb, ge);
 }
 
 __device__ __forceinline__ void select_tiles(const State &s, const Lists &L, DevScalars *ds, const StepCtl &c,
@@ -732,7 +762,7 @@ __device__ __forceinline__ void group_sync(int bar_id)
 // of the group) for the item that wrote the tile's final forces.
 template <typename Rec, int TJ, bool kMapI>
 __device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict__ rec, const Lists &L, int pj_min,
-                                           int work, typename Traits<Rec>::Eps eps2, const int4 it,
+                                           int work, typename Traits<Rec>::Eps eps2, const WorkItem &it,
                                            ForceSmem<Rec, TJ> &sm, unsigned long long &n_int, const int tid,
                                            const int bar_id)
 {
@@ -740,11 +770,11 @@ __device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict
     using Red = typename T::Red;
     const int lane = tid & 31, warp = tid >> 5;
     Red *partials = reinterpret_cast<Red *>(L.partials);
-    const int4 td = L.tiles[it.x];
-    const uint32_t mask = (uint32_t)it.z;
+    const int p0 = it.p_begin;
+    const uint32_t mask = it.mask;
     const int n_a = __popc(mask);
     const int pj = part_len_for(n_a, pj_min, work);
-    const int part = it.y & 0xFFFF, slot0 = it.w;
+    const int part = it.part_sim & 0xFFFF, slot0 = it.slot;
 
     // Lane mapping: every warp holds K = floor(32 / n_a) j slices of n_a lanes
     // (lane = i slot + n_a * slice); the 32 - K n_a leftover lanes idle.  So no
@@ -761,9 +791,9 @@ __device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict
     {
         uint32_t mm = mask;
         for (int q = 0; q < islot && mm; q++) mm &= mm - 1;
-        if (has_i) pi = td.x + (__ffs(mm) - 1);
+        if (has_i) pi = p0 + (__ffs(mm) - 1);
     }
-    int64_t pload = has_i ? pi : td.x + (__ffs(mask) - 1);  // spare slots repeat a live one; dropped
+    int64_t pload = has_i ? pi : p0 + (__ffs(mask) - 1);  // spare slots repeat a live one; dropped
     if constexpr (kMapI) {
         // slots are positions in a caller's active list; i is its j index
         pload = L.i_map[pload];
@@ -774,7 +804,7 @@ __device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict
     typename T::Acc A;
     A.zero();
 
-    const int64_t gb = L.off[td.z], ge = L.off[td.z + 1];
+    const int64_t gb = it.gb, ge = it.ge;
     const int n_parts = parts_of(ge - gb, pj);
     const int64_t lb = gb + (int64_t)part * pj;
     const int64_t le = min(ge, lb + (int64_t)pj);
@@ -864,7 +894,7 @@ __device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict
         if (tid < n_a) mine[tid] = r;
         group_sync(bar_id);
         if (tid == 0) {
-            const unsigned int old = atom_add_acq_rel_gpu(reinterpret_cast<unsigned int *>(&L.tile_cnt[it.x]), 1u);
+            const unsigned int old = atom_add_acq_rel_gpu(reinterpret_cast<unsigned int *>(&L.tile_cnt[it.tile]), 1u);
             sm.last = ((int)old == n_parts - 1);
         }
         group_sync(bar_id);
@@ -875,13 +905,13 @@ __device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict
                 r = ld_red_cg(base + tid);
                 for (int q = 1; q < n_parts; q++) red_add(r, ld_red_cg(base + (int64_t)q * kMaxTileI + tid));
             }
-            if (tid == 0) L.tile_cnt[it.x] = 0;
+            if (tid == 0) L.tile_cnt[it.tile] = 0;
         }
     }
     if (write_out && tid < n_a) {
         uint32_t mm = mask;
         for (int q = 0; q < tid; q++) mm &= mm - 1;
-        const int64_t p = td.x + (__ffs(mm) - 1);
+        const int64_t p = p0 + (__ffs(mm) - 1);
         s.acc1[0 * s.cap_n + p] = red_get(r, 0);
         s.acc1[1 * s.cap_n + p] = red_get(r, 1);
         s.acc1[2 * s.cap_n + p] = red_get(r, 2);

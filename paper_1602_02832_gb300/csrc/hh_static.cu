@@ -29,7 +29,7 @@ constexpr size_t kOffDs = 0;
 constexpr size_t kOffCnt = kOffDs + align256(sizeof(DevScalars));
 constexpr size_t kOffTiles = kOffCnt + align256(sizeof(int32_t) * kStaticMaxAct);
 constexpr size_t kOffItems = kOffTiles + align256(sizeof(int4) * kStaticMaxAct);
-constexpr size_t kOffParts = kOffItems + align256(sizeof(int4) * kStaticMaxParts);
+constexpr size_t kOffParts = kOffItems + align256(sizeof(WorkItem) * kStaticMaxParts);
 constexpr size_t kOffRec = kOffParts + align256(sizeof(RedF64) * kMaxTileI * kStaticMaxParts);
 constexpr size_t kScratchBytes = kOffRec + align256(sizeof(RecF64) * kStaticMaxJ);
 constexpr size_t kZeroBytes = kOffTiles;  // DevScalars and tile counters start at zero
@@ -87,7 +87,7 @@ __global__ void k_static_pack(Rec *rec, const double *x, const double *v, const 
 // becomes a work item.  Overflowing the fixed item capacity sets ds->err and
 // writes nothing out of bounds.
 __global__ void k_static_tiles(const int32_t *gid, int32_t n_act, int32_t n_groups, const int64_t *off,
-                               int4 *tiles, int4 *items, DevScalars *ds)
+                               int4 *tiles, WorkItem *items, DevScalars *ds)
 {
     if (*(volatile int32_t *)&ds->err) return;  // inputs failed the checks
     const int lane = threadIdx.x & 31;
@@ -118,9 +118,10 @@ __global__ void k_static_tiles(const int32_t *gid, int32_t n_act, int32_t n_grou
             if ((int64_t)base + n_parts > kStaticMaxParts) {
                 atomicExch(&ds->err, HH_ENOMEM);
             } else {
-                tiles[t] = make_int4((int)k, (int)k + n_a, g, (int)base);
+                const int4 td = make_int4((int)k, (int)k + n_a, g, (int)base);
+                tiles[t] = td;
                 const uint32_t mask = n_a == 32 ? 0xffffffffu : ((1u << n_a) - 1u);
-                for (int q = 0; q < n_parts; q++) items[base + q] = make_int4(t, q, (int)mask, (int)base);
+                for (int q = 0; q < n_parts; q++) items[base + q] = make_item(t, q, mask, (int)base, td, off[g], off[g + 1]);
             }
         }
     }
@@ -192,7 +193,7 @@ extern "C" int hh_force_static(int device, int precision, double eps2, int64_t n
     L.off = off;
     L.idx = idx;
     L.tiles = reinterpret_cast<int4 *>(base + kOffTiles);
-    L.items = reinterpret_cast<int4 *>(base + kOffItems);
+    L.items = reinterpret_cast<WorkItem *>(base + kOffItems);
     L.partials = base + kOffParts;
     L.tile_cnt = reinterpret_cast<int32_t *>(base + kOffCnt);
     L.i_map = i_idx;
