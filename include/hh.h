@@ -301,6 +301,15 @@ int hh_barrier_selftest(int device, int skip_cta, double *elapsed_s);
 int hh_selftest_aarseth(int device, int64_t n, const double *A, const double *J, const double *S, const double *T,
                         double eta, double *out);
 
+/* Self-test of the corrector's block quantisation (Section 2, step 6: the
+ * new step is the largest power of two below the criterion, at most double
+ * the old one, doubled only where the new time is a multiple of the doubled
+ * step, clamped to [dt_min, dt_max]): out[i] = the device's step for want[i],
+ * dt_old[i], t_new[i] (host arrays of n doubles, caller-owned).  n <= 2^26;
+ * synchronises. */
+int hh_selftest_block_dt(int device, int64_t n, const double *want, const double *dt_old, const double *t_new,
+                         double dt_min, double dt_max, double *out);
+
 /* Device memory held by a context (bytes), for admission by memory budget. */
 int64_t hh_ctx_device_bytes(const hh_ctx *ctx);
 

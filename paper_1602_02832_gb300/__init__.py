@@ -101,6 +101,7 @@ _SIGS = {
     "hh_ctx_device_bytes": (C.c_int64, [_P]),
     "hh_barrier_selftest": (C.c_int, [C.c_int, C.c_int, _D]),
     "hh_selftest_aarseth": (C.c_int, [C.c_int, C.c_int64, _D, _D, _D, _D, C.c_double, _D]),
+    "hh_selftest_block_dt": (C.c_int, [C.c_int, C.c_int64, _D, _D, _D, C.c_double, C.c_double, _D]),
     "hh_set_rebuild_device": (C.c_int, [_P, C.c_int]),
     "hh_get_lists": (C.c_int, [_P, _I32, _I64, _I64, _I32, _I32]),
     "hh_get_j": (C.c_int, [_P, C.c_int64, C.c_int64, _D, _D, _D, _D, _D, _D]),
@@ -449,6 +450,15 @@ def hh_selftest_aarseth(A, J, S, T, eta, device=0):
     n = len(arrs[0])
     out = np.zeros(n)
     _check(_lib.hh_selftest_aarseth(int(device), n, *[_ptr(x) for x in arrs], float(eta), _ptr(out)))
+    return out
+
+
+def hh_selftest_block_dt(want, dt_old, t_new, dt_min, dt_max, device=0):
+    """Device block quantisation of the corrector for arrays want, dt_old, t_new."""
+    arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (want, dt_old, t_new)]
+    n = len(arrs[0])
+    out = np.zeros(n)
+    _check(_lib.hh_selftest_block_dt(int(device), n, *[_ptr(x) for x in arrs], float(dt_min), float(dt_max), _ptr(out)))
     return out
 
 

@@ -223,7 +223,9 @@ __device__ __forceinline__ double correct_tile_3lane(const SimDesc &sd, const in
     const State &s = sd.st;
     const int na = __popc(mask);
     const int q = lane / 3, d = lane - 3 * q, g = 3 * q;
-    double tn_min = __longlong_as_double(0x7FF0000000000000LL);
+    // next times are positive and finite: their minimum is the integer minimum
+    // of the bit patterns (no FP64 instruction)
+    unsigned long long tn_min = 0x7FF0000000000000ull;
     for (int base = k_first; base < na; base += k_step) {
         const int k = base + q;
         const bool on = lane < 30 && k < na;
@@ -265,12 +267,12 @@ __device__ __forceinline__ double correct_tile_3lane(const SimDesc &sd, const in
                     atomicSub(&sd.ds->lvl_cnt[lv_old], 1);
                     atomicAdd(&sd.ds->lvl_cnt[lv_new & 31], 1);
                 }
-                tn_min = fmin(tn_min, tnow + dtn);
+                tn_min = min(tn_min, (unsigned long long)__double_as_longlong(tnow + dtn));
             }
         }
     }
-    for (int off = 16; off > 0; off >>= 1) tn_min = fmin(tn_min, __shfl_xor_sync(full, tn_min, off));
-    return tn_min;
+    for (int off = 16; off > 0; off >>= 1) tn_min = min(tn_min, __shfl_xor_sync(full, tn_min, off));
+    return __longlong_as_double((long long)tn_min);
 }
 
 // Per-CTA copy of each simulation's block time for the current step
@@ -554,7 +556,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                         const uint32_t lvm = __reduce_or_sync(0xffffffffu, bit);
                         if (glane == 0) {
                             double m = sm.tn[0];
-                            for (int w = 1; w < kThreads / 32; w++) m = fmin(m, sm.tn[w]);
+                            for (int w = 1; w < kThreads / 32; w++)
+                                if (__double_as_longlong(sm.tn[w]) < __double_as_longlong(m)) m = sm.tn[w];
                             const int c = __popc(mask);
                             sd.tile_lv[it.tile] = lvm;
                             atomicMin(&sd.ds->tmin[par ^ 1], (unsigned long long)__double_as_longlong(m));
@@ -915,7 +918,43 @@ __global__ void k_aarseth_selftest(int64_t n, const double *A, const double *J, 
         out[i] = aarseth_want(A[i], J[i], S[i], T[i], eta);
 }
 
+__global__ void k_block_dt_selftest(int64_t n, const double *want, const double *dt_old, const double *t_new,
+                                    double dt_min, double dt_max, double *out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = block_dt(want[i], dt_old[i], t_new[i], dt_min, dt_max);
+}
+
 }  // namespace
+
+extern "C" int hh_selftest_block_dt(int device, int64_t n, const double *want, const double *dt_old,
+                                    const double *t_new, double dt_min, double dt_max, double *out)
+{
+    if (n < 0 || (n > 0 && (!want || !dt_old || !t_new || !out)))
+        return hh_set_global_error(HH_EINVAL, "hh_selftest_block_dt: bad n or NULL array");
+    if (n == 0) return HH_OK;
+    if (n > (int64_t(1) << 26)) return hh_set_global_error(HH_EINVAL, "hh_selftest_block_dt: n above 2^26");
+    if (cudaSetDevice(device) != cudaSuccess) return hh_set_global_error(HH_ECUDA, "hh_selftest_block_dt: bad device");
+    double *d = nullptr;
+    const size_t bytes = sizeof(double) * size_t(n);
+    if (cudaMalloc(&d, 4 * bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return hh_set_global_error(HH_ENOMEM, "hh_selftest_block_dt: allocation failed");
+    }
+    cudaError_t e = cudaSuccess;
+    const double *src[3] = {want, dt_old, t_new};
+    for (int q = 0; q < 3 && e == cudaSuccess; q++) e = cudaMemcpy(d + q * n, src[q], bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        const int grid = int(std::min<int64_t>((n + 255) / 256, 4096));
+        k_block_dt_selftest<<<grid, 256>>>(n, d, d + n, d + 2 * n, dt_min, dt_max, d + 3 * n);
+        hh_count_launches(1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, d + 3 * n, bytes, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return hh_set_global_error(HH_ECUDA, cudaGetErrorString(e));
+    return HH_OK;
+}
 
 extern "C" int hh_selftest_aarseth(int device, int64_t n, const double *A, const double *J, const double *S,
                                    const double *T, double eta, double *out)

@@ -14,6 +14,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace hh {
@@ -630,34 +631,20 @@ __device__ __forceinline__ void to_red(const AccMix &A, RedMix &r)
 {
     r.v[0] = A.Ax; r.v[1] = A.Ay; r.v[2] = A.Az; r.v[3] = A.Jx; r.v[4] = A.Jy; r.v[5] = A.Jz; r.v[6] = A.P;
 }
-__device__ __forceinline__ void red_add(RedF64 &a, const RedF64 &b)
-{
-#pragma unroll
-    for (int q = 0; q < 7; q++) a.v[q] += b.v[q];
-}
-__device__ __forceinline__ void red_add(RedMix &a, const RedMix &b)
-{
-#pragma unroll
-    for (int q = 0; q < 7; q++) a.v[q] = f2_add(a.v[q], b.v[q]);
-}
 __device__ __forceinline__ double red_get(const RedF64 &r, int q) { return r.v[q]; }
 __device__ __forceinline__ double red_get(const RedMix &r, int q) { return (double)r.v[q].h + (double)r.v[q].l; }
-// partial sums written by other CTAs: read through L2 (bypassing L1)
-__device__ __forceinline__ RedF64 ld_red_cg(const RedF64 *p)
+// partial sums written by other CTAs are read through L2 (bypassing L1)
+// One component of a reduction record (double, or an FP32 pair).
+__device__ __forceinline__ void comp_add(double &a, double b) { a += b; }
+__device__ __forceinline__ void comp_add(F2 &a, const F2 &b) { a = f2_add(a, b); }
+__device__ __forceinline__ double comp_get(double a) { return a; }
+__device__ __forceinline__ double comp_get(const F2 &a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ double ld_comp_cg(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ F2 ld_comp_cg(const F2 *p)
 {
-    RedF64 r;
-#pragma unroll
-    for (int q = 0; q < 7; q++) r.v[q] = __ldcg(&p->v[q]);
-    return r;
-}
-__device__ __forceinline__ RedMix ld_red_cg(const RedMix *p)
-{
-    RedMix r;
-#pragma unroll
-    for (int q = 0; q < 7; q++) {
-        r.v[q].h = __ldcg(&p->v[q].h);
-        r.v[q].l = __ldcg(&p->v[q].l);
-    }
+    F2 r;
+    r.h = __ldcg(&p->h);
+    r.l = __ldcg(&p->l);
     return r;
 }
 
@@ -880,10 +867,21 @@ __device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict
         sm.red[warp][lane] = r;
     }
     group_sync(bar_id);
-    Red r;
-    if (tid < n_a) {
-        r = sm.red[0][tid];
-        for (int w = 1; w < kThreads / 32; w++) red_add(r, sm.red[w][tid]);
+    // The rest runs one thread per (i slot, component): per component the same
+    // sums in the same order as whole records (warps 0..3, then parts
+    // 0..n_parts-1), but in parallel lanes, since a warp instruction costs the
+    // FP64 pipe the same with one lane active.  7 n_a <= 224 outputs: at most
+    // two per thread.
+    using E = typename std::remove_reference<decltype(sm.red[0][0].v[0])>::type;
+    const int n_out = 7 * n_a;
+    E r[2];
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+        const int t = tid + u * kThreads, slot = t / 7, comp = t - 7 * (t / 7);
+        if (t < n_out) {
+            r[u] = sm.red[0][slot].v[comp];
+            for (int w = 1; w < kThreads / 32; w++) comp_add(r[u], sm.red[w][slot].v[comp]);
+        }
     }
     bool write_out = n_parts == 1;
     if (n_parts > 1) {
@@ -891,7 +889,11 @@ __device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict
         // barrier and the arrival's release; the last arrival's acquire (and
         // the barrier after it) orders the other parts' partials before the sum
         Red *mine = partials + ((int64_t)slot0 + part) * kMaxTileI;
-        if (tid < n_a) mine[tid] = r;
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+            const int t = tid + u * kThreads, slot = t / 7, comp = t - 7 * (t / 7);
+            if (t < n_out) mine[slot].v[comp] = r[u];
+        }
         group_sync(bar_id);
         if (tid == 0) {
             const unsigned int old = atom_add_acq_rel_gpu(reinterpret_cast<unsigned int *>(&L.tile_cnt[it.tile]), 1u);
@@ -900,25 +902,33 @@ __device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict
         group_sync(bar_id);
         write_out = sm.last;
         if (write_out) {
-            if (tid < n_a) {
-                const Red *base = partials + (int64_t)slot0 * kMaxTileI;
-                r = ld_red_cg(base + tid);
-                for (int q = 1; q < n_parts; q++) red_add(r, ld_red_cg(base + (int64_t)q * kMaxTileI + tid));
+            const Red *base = partials + (int64_t)slot0 * kMaxTileI;
+#pragma unroll
+            for (int u = 0; u < 2; u++) {
+                const int t = tid + u * kThreads, slot = t / 7, comp = t - 7 * (t / 7);
+                if (t < n_out) {
+                    r[u] = ld_comp_cg(&base[slot].v[comp]);
+                    for (int q = 1; q < n_parts; q++)
+                        comp_add(r[u], ld_comp_cg(&base[(int64_t)q * kMaxTileI + slot].v[comp]));
+                }
             }
             if (tid == 0) L.tile_cnt[it.tile] = 0;
         }
     }
-    if (write_out && tid < n_a) {
-        uint32_t mm = mask;
-        for (int q = 0; q < tid; q++) mm &= mm - 1;
-        const int64_t p = p0 + (__ffs(mm) - 1);
-        s.acc1[0 * s.cap_n + p] = red_get(r, 0);
-        s.acc1[1 * s.cap_n + p] = red_get(r, 1);
-        s.acc1[2 * s.cap_n + p] = red_get(r, 2);
-        s.jerk1[0 * s.cap_n + p] = red_get(r, 3);
-        s.jerk1[1 * s.cap_n + p] = red_get(r, 4);
-        s.jerk1[2 * s.cap_n + p] = red_get(r, 5);
-        s.pot1[p] = -red_get(r, 6);
+    if (write_out) {
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+            const int t = tid + u * kThreads, slot = t / 7, comp = t - 7 * (t / 7);
+            if (t < n_out) {
+                uint32_t mm = mask;
+                for (int q = 0; q < slot; q++) mm &= mm - 1;
+                const int64_t p = p0 + (__ffs(mm) - 1);
+                const double v = comp_get(r[u]);
+                if (comp < 3) s.acc1[comp * s.cap_n + p] = v;
+                else if (comp < 6) s.jerk1[(comp - 3) * s.cap_n + p] = v;
+                else s.pot1[p] = -v;
+            }
+        }
     }
     // callers put a barrier before the shared buffers are reused
     return write_out;
@@ -949,22 +959,66 @@ __global__ void __launch_bounds__(kThreads, 6) k_force(State s, const Rec *__res
 // -------------------------------------------------------------- corrector
 __device__ __forceinline__ double norm3(double a, double b, double c) { return sqrt(a * a + b * b + c * c); }
 
-// Block quantisation (McMillan 1986): largest power of two <= want, at most
-// doubling, doubling only where t_new is a multiple of the doubled step,
-// clamped to [dt_min, dt_max]; NaN keeps the old step, +inf asks to double.
+// Largest power of two <= |x| for finite x, as frexp / ldexp give it (so 1/2
+// for a zero, whose frexp exponent is 0), on the bits.
+__device__ __forceinline__ long long pow2_floor_abs_bits(long long W)
+{
+    const long long b = W & 0x7FFFFFFFFFFFFFFFll;
+    if (b == 0) return 0x3FE0000000000000ll;                          // 1/2
+    if ((b >> 52) == 0) return 1ll << (63 - __clzll((unsigned long long)b));  // subnormal: its top bit
+    return b & (long long)0xFFF0000000000000ull;
+}
+
+// fmod(t, 2^k) == 0 on t's bits: t finite and a multiple of 2^k (fmod of an
+// infinity or a NaN is a NaN, so those are not).
+__device__ __forceinline__ bool multiple_of_pow2(double t, int k)
+{
+    const long long b = __double_as_longlong(t) & 0x7FFFFFFFFFFFFFFFll;  // |t|
+    if (b == 0) return true;
+    const int ef = (int)(b >> 52);
+    if (ef == 0x7ff) return false;
+    const long long m = ef ? ((b & 0xFFFFFFFFFFFFFll) | (1ll << 52)) : b;  // |t| = m 2^(max(ef, 1) - 1075)
+    return (ef ? ef : 1) - 1075 + (__ffsll(m) - 1) >= k;
+}
+
+// Block quantisation (McMillan 1986): the largest power of two <= want, at
+// most double the old step, doubled only where t_new is a multiple of the
+// new step, clamped to [dt_min, dt_max]; a NaN keeps the old step and an
+// infinity asks to double.  (The largest power of two below |want| follows
+// frexp, so a zero asks for 1/2.)  When dt_old is a normal power of two (as
+// in the block-step loops) and dt_min, dt_max are positive normal values,
+// every candidate is a positive power of two, IEEE order is the integer order
+// of the bits and the multiple test is exact on t_new's bits: the path below
+// then uses no FP64 instruction (the FP64 pipe is narrow); otherwise the same
+// rule runs in FP64.
 __device__ __forceinline__ double block_dt(double want, double dt_old, double t_new, double dt_min, double dt_max)
 {
-    double q;
-    if (want != want) q = dt_old;
-    else if (want > 1.0e300) q = 2.0 * dt_old;
-    else q = pow2_floor(want);
-    if (q > 2.0 * dt_old) q = 2.0 * dt_old;
-    if (q > dt_old) {
-        // t_new / q for a power of two q, as an exact product with 1 / q
-        const double inv = __longlong_as_double((long long)(2046 - ((__double_as_longlong(q) >> 52) & 0x7ff)) << 52);
-        const double r = t_new * inv;
-        if (r != floor(r)) q = dt_old;
+    const long long O = __double_as_longlong(dt_old), Mn = __double_as_longlong(dt_min),
+                    Mx = __double_as_longlong(dt_max);
+    const long long kNormLo = 0x0010000000000000ll, kTop = 0x7FE0000000000000ll;  // normal, doubling stays finite
+    if (O >= kNormLo && O < kTop && (O & 0xFFFFFFFFFFFFFll) == 0 && Mn >= kNormLo && Mn < 0x7FF0000000000000ll && Mx >= kNormLo &&
+        Mx < 0x7FF0000000000000ll) {
+        const long long W = __double_as_longlong(want);
+        const long long O2 = O + (1ll << 52);  // 2 dt_old
+        long long Q;
+        if ((W & 0x7FF0000000000000ll) == 0x7FF0000000000000ll) Q = (W & 0xFFFFFFFFFFFFFll) ? O : O2;  // NaN, inf
+        else Q = pow2_floor_abs_bits(W);
+        if (Q > O2) Q = O2;
+        if (Q > O && !multiple_of_pow2(t_new, (int)((Q >> 52) & 0x7ff) - 1023)) Q = O;
+        if (Q > Mx) Q = Mx;
+        if (Q < Mn) Q = Mn;
+        return __longlong_as_double(Q);
     }
+    double q;
+    if (isnan(want)) q = dt_old;
+    else if (isinf(want)) q = 2.0 * dt_old;
+    else {
+        int e;
+        frexp(want, &e);
+        q = ldexp(1.0, e - 1);
+    }
+    if (q > 2.0 * dt_old) q = 2.0 * dt_old;
+    if (q > dt_old && fmod(t_new, q) != 0.0) q = dt_old;
     if (q > dt_max) q = dt_max;
     if (q < dt_min) q = dt_min;
     return q;

@@ -87,3 +87,26 @@ def test_criterion_next_to_power_of_two_boundaries():
     frac = _check(A, J / c ** 2, S / c ** 4, T / c ** 6)
     # both sides of the screen's margin (2^-18) are exercised
     assert 0.05 < frac < 0.95
+
+
+def test_block_quantisation_matches_oracle():
+    # the device's block quantisation (integer path and FP64 path) against the
+    # oracle's, on block-rule inputs and on special values
+    oracle = pytest.importorskip("oracle")
+    rng = np.random.default_rng(4)
+    n = 6000
+    dt_min, dt_max = 2.0 ** -30, 2.0 ** -6
+    lv = rng.integers(6, 31, n)
+    dt_old = 2.0 ** -lv
+    t_new = rng.integers(0, 2 ** 20, n) * dt_old           # multiples of dt_old
+    t_new[::3] = rng.integers(0, 2 ** 30, n)[::3] * dt_min  # any multiple of dt_min
+    want = dt_old * 10.0 ** rng.uniform(-3, 3, n)
+    want[::7] = dt_old[::7] * 2.0 ** rng.integers(-3, 4, n)[::7]  # exact powers of two
+    specials = [np.nan, -np.nan, np.inf, -np.inf, 0.0, -0.0, 5e-324, -3.0, 1e300, 2e300, 1e-310]
+    want[: len(specials)] = specials
+    t_new[20:30] = [0.0, 1e-320, np.inf, 2.0 ** -1000, 1.5, 3.0, 0.25, -0.5, 1e300, 2.0 ** -959]
+    dt_old[40:45] = [1.0, 2.0, 0.75, 2.0 ** -1023, 3e-308]
+    dev = hh.hh_selftest_block_dt(want, dt_old, t_new, dt_min, dt_max)
+    ref = np.array([oracle.block_dt(w, d, t, dt_min, dt_max) for w, d, t in zip(want, dt_old, t_new)])
+    same = (dev == ref) | (np.isnan(dev) & np.isnan(ref))
+    assert same.all(), [(want[i], dt_old[i], t_new[i], dev[i], ref[i]) for i in np.flatnonzero(~same)[:5]]
