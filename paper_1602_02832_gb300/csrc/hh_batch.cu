@@ -531,6 +531,18 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                 if (item >= (int)n_items) break;
                 const int s = it.part_sim >> 16;
                 const SimDesc &sd = B.sims[s];
+                if (gt < 42) {
+                    // the corrector's inputs (14 state arrays, <= 3 cache lines
+                    // of each for the tile's <= 32 particles) into this SM's L1,
+                    // in case this group completes the tile
+                    const int arr = gt / 3, ln = gt - 3 * arr;
+                    const State &st = sd.st;
+                    const double *a = arr < 12 ? (arr < 3 ? st.x : arr < 6 ? st.v : arr < 9 ? st.a : st.jk) +
+                                                     (int64_t)(arr % 3) * st.cap_j
+                                               : (arr == 12 ? st.t : st.dt);
+                    const int64_t q = min((int64_t)it.p_begin + 16 * ln, (int64_t)it.p_end - 1);
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(a + q));
+                }
                 unsigned long long n_int = 0;
                 const bool done = force_item<Rec, TJ, false>(sd.st, (const Rec *)sd.rec, sd.L, sd.pj, sd.work,
                                                              (typename Traits<Rec>::Eps)sd.prm.eps2, it, sm, n_int,
@@ -566,7 +578,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                         }
                     }
                 }
-                if (gt == 0) sm.item = n_static + (int)atomicAdd(&B.bs->work[par], 1u);
+                // (with no more items than groups every item was a first item:
+                // no queue round trip before the barrier)
+                if (gt == 0)
+                    sm.item = (int)n_items <= n_static ? (int)n_items
+                                                       : n_static + (int)atomicAdd(&B.bs->work[par], 1u);
                 group_sync(bar);  // also ends the use of the shared buffers by this item
                 item = sm.item;   // rewritten only after the next item's group barriers
                 if (item < (int)n_items) it = items[item];
