@@ -678,12 +678,18 @@ __device__ __forceinline__ void fold_chunk(AccMix &A) { A.fold(); }
 // tile's last part (arrival counter, threadfence pattern: no waiting) adds
 // the parts in part order.  So each particle's result depends only on its
 // list, its tile's active count and the part length, never on scheduling.
-// Asynchronous global -> shared copies (16 B each, through L2 only: the
-// records are rewritten every block step) for chunk staging.
+// Asynchronous global -> shared copies (16 B each) for chunk staging,
+// cached in L1: the 16-byte pieces of one record, and the records of
+// neighbouring list entries (consecutive particles of a leaf, sibling
+// cells), share sectors, which L1 then serves instead of L2.  Measured on
+// real tree lists (N = 65536, staging alone) at 1.0e11 records/s against
+// 5.9e10 through L2 only.  The records are rewritten every block step, but
+// always before a grid barrier or a kernel boundary that orders them before
+// these (weak) reads, as for any plain load.
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
