@@ -74,7 +74,7 @@ def _args():
                    help="order of particles and nodes in the tree (Peano-Hilbert is the paper's)")
     p.add_argument("--rebuild", default="auto", choices=["auto", "device", "host"],
                    help="where the tree, groups and lists are rebuilt every dt_tree (auto: on the device from "
-                        "N = 4096, on the host below, where a device build is bound by launch latency)")
+                        "N = 2048, on the host below, where a device build is bound by launch latency)")
     p.add_argument("--loop", default="persistent", choices=["persistent", "graph"],
                    help="block-step loop: one persistent cooperative kernel per interval, or CUDA-graph replays")
     return p.parse_args()
@@ -107,7 +107,9 @@ def _cfg(hh, prec, a):
 
 
 def _on_device(a, n):
-    return a.rebuild == "device" or (a.rebuild == "auto" and n >= 4096)
+    from paper_1602_02832_gb300 import serve
+
+    return a.rebuild == "device" or (a.rebuild == "auto" and n >= serve.AUTO_DEVICE_MIN_N)
 
 
 def _server_rebuild(a):
