@@ -278,6 +278,11 @@ const char *hh_last_error(const hh_ctx *ctx);
  *   and per-tile level masks, so a block step touches only the due tiles. */
 typedef struct hh_batch hh_batch;
 int hh_batch_create(hh_batch **out, int device, int precision, int32_t max_sims, int32_t max_steps);
+/* Number of persistent CTAs (one per SM) of the batch's launches: n_ctas > 0
+ * uses that many SMs, n_ctas <= 0 all SMs but |n_ctas|, which stay free for
+ * other streams' kernels (tree rebuilds of simulations outside the launch).
+ * The default is every SM.  HH_EINVAL outside [1, SM count]. */
+int hh_batch_set_ctas(hh_batch *b, int32_t n_ctas);
 int hh_batch_destroy(hh_batch *b);
 int hh_batch_run(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const double *t_end, int32_t max_steps,
                  int32_t *steps_out, double *t_next_out, double *step_us_out, double *phase_us_out);

@@ -101,6 +101,7 @@ _SIGS = {
     "hh_ctx_device_bytes": (C.c_int64, [_P]),
     "hh_barrier_selftest": (C.c_int, [C.c_int, C.c_int, _D]),
     "hh_selftest_aarseth": (C.c_int, [C.c_int, C.c_int64, _D, _D, _D, _D, C.c_double, _D]),
+    "hh_batch_set_ctas": (C.c_int, [_P, C.c_int32]),
     "hh_selftest_block_dt": (C.c_int, [C.c_int, C.c_int64, _D, _D, _D, C.c_double, C.c_double, _D]),
     "hh_set_rebuild_device": (C.c_int, [_P, C.c_int]),
     "hh_get_lists": (C.c_int, [_P, _I32, _I64, _I64, _I32, _I32]),
@@ -424,6 +425,12 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+    def hh_batch_set_ctas(self, n_ctas):
+        """CTAs (SMs) of the launches: > 0 that many, <= 0 all but |n_ctas|."""
+        rc = _lib.hh_batch_set_ctas(self.h, int(n_ctas))
+        if rc != HH_OK:
+            raise HHError(rc, (_lib.hh_batch_last_error(self.h) or b"").decode())
 
     def hh_batch_run(self, ctxs, t_end, max_steps=None):
         """Runs the contexts until each passes its t_end (or max_steps global

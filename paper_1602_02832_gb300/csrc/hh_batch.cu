@@ -757,6 +757,23 @@ extern "C" int hh_batch_create(hh_batch **out, int device, int precision, int32_
     return HH_OK;
 }
 
+extern "C" int hh_batch_set_ctas(hh_batch *b, int32_t n_ctas)
+{
+    if (!b) return hh_set_global_error(HH_EINVAL, "hh_batch_set_ctas: NULL batch");
+    if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, HH_ECUDA, "hh_batch_set_ctas: cudaSetDevice failed");
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
+        return bfail(b, HH_ECUDA, "hh_batch_set_ctas: no SM count");
+    const int32_t want = n_ctas > 0 ? n_ctas : sms + n_ctas;
+    if (want < 1 || want > sms) return bfail(b, HH_EINVAL, "hh_batch_set_ctas: CTA count outside [1, SM count]");
+    if (want == b->grid) return HH_OK;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, HH_ECUDA, "hh_batch_set_ctas: stream failed");
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->grid = want;
+    return capture_graph(b);
+}
+
 extern "C" int hh_batch_destroy(hh_batch *b)
 {
     if (!b) return HH_OK;

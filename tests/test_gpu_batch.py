@@ -62,6 +62,29 @@ def test_batch_equals_alone(hh, prec):
     assert steps == max(c[1]["block_steps"] for c in alone)
 
 
+def test_batch_result_does_not_depend_on_cta_count(hh):
+    # the same batch on every SM and on 37 of them (items land on other SMs,
+    # in another order): identical states
+    P = hh.HH_MIXED
+    t1 = 2.0 ** -7
+    states = []
+    for ctas in (0, 37):
+        ctxs = [_ctx(hh, P, n, seed, th, salpeter=sal) for n, seed, th, sal in SPECS]
+        with hh.Batch(P, max_sims=8, max_steps=4096) as b:
+            if ctas:
+                b.hh_batch_set_ctas(ctas)
+            b.hh_batch_run(ctxs, [t1] * len(ctxs))
+        states.append([c.hh_get_state() for c in ctxs])
+        for c in ctxs:
+            c.close()
+    for a, b_ in zip(*states):
+        for k in ("x", "v", "a", "jk", "t", "dt"):
+            assert np.array_equal(a[k], b_[k]), k
+    with hh.Batch(P, max_sims=2, max_steps=8) as b:
+        with pytest.raises(hh.HHError):
+            b.hh_batch_set_ctas(100000)
+
+
 def test_batch_in_short_launches_and_with_rebuilds(hh):
     # continuous batching: the same simulations advanced in launches of 7
     # global steps, rebuilt at each dt_tree, reach the same state as one
