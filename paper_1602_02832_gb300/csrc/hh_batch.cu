@@ -216,8 +216,11 @@ __device__ __forceinline__ double due_below_warp(const int32_t *lvl_cnt, double 
 // component.  Returns (in every lane) the minimum of t + dt over the tile's
 // corrected particles, updates the simulation's level histogram and leaves
 // each corrected particle's new level in lv_out[its index among the active].
+// The new forces come from fin[active index] (the force tail's copy in
+// shared memory; the same values as acc1 / jerk1).
 __device__ __forceinline__ double correct_tile_3lane(const SimDesc &sd, const int4 td, uint32_t mask, double tnow,
-                                                     int lane, int k_first, int k_step, int *lv_out)
+                                                     int lane, int k_first, int k_step, int *lv_out,
+                                                     const double (*fin)[7])
 {
     const unsigned full = 0xffffffffu;
     const State &s = sd.st;
@@ -236,8 +239,8 @@ __device__ __forceinline__ double correct_tile_3lane(const SimDesc &sd, const in
             dt_old = s.dt[p];
             const StepPowers P = step_powers(tnow - s.t[p]);
             const double a0 = s.a[d * s.cap_j + p], j0 = s.jk[d * s.cap_j + p];
-            a1 = s.acc1[d * s.cap_n + p];
-            j1 = s.jerk1[d * s.cap_n + p];
+            a1 = fin[k][d];
+            j1 = fin[k][3 + d];
             c = correct_component(s.x[d * s.cap_j + p], s.v[d * s.cap_j + p], a0, j0, a1, j1, P);
             sa = sq(a1);
             sj = sq(j1);
@@ -257,7 +260,7 @@ __device__ __forceinline__ double correct_tile_3lane(const SimDesc &sd, const in
             s.v[d * s.cap_j + p] = c.v;
             s.a[d * s.cap_j + p] = a1;
             s.jk[d * s.cap_j + p] = j1;
-            if (s.base) refresh_base_component(s, p, d);
+            if (s.base) refresh_base_values(s, p, d, c.x, c.v, a1, j1, d == 0 ? s.m[p] : 0.0);
             if (d == 0) {
                 s.t[p] = tnow;
                 s.dt[p] = dtn;
@@ -378,6 +381,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ StepCache sc;
+    __shared__ SimDesc sd_sm[kGroups];  // each worker group's current simulation (for its corrector)
+    static_assert(sizeof(SimDesc) % 8 == 0 && sizeof(SimDesc) / 8 <= kThreads - 64, "descriptor copy by 64 threads");
     const int tid = threadIdx.x;
     const int group = tid / kThreads, gt = tid - group * kThreads;
     ForceSmem<Rec, TJ> &sm = reinterpret_cast<ForceSmem<Rec, TJ> *>(smem_raw)[group];
@@ -531,17 +536,22 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                 if (item >= (int)n_items) break;
                 const int s = it.part_sim >> 16;
                 const SimDesc &sd = B.sims[s];
-                if (gt < 42) {
-                    // the corrector's inputs (14 state arrays, <= 3 cache lines
+                if (gt < 45) {
+                    // the corrector's inputs (15 state arrays, <= 3 cache lines
                     // of each for the tile's <= 32 particles) into this SM's L1,
                     // in case this group completes the tile
                     const int arr = gt / 3, ln = gt - 3 * arr;
                     const State &st = sd.st;
                     const double *a = arr < 12 ? (arr < 3 ? st.x : arr < 6 ? st.v : arr < 9 ? st.a : st.jk) +
                                                      (int64_t)(arr % 3) * st.cap_j
-                                               : (arr == 12 ? st.t : st.dt);
+                                               : (arr == 12 ? st.t : arr == 13 ? st.dt : st.m);
                     const int64_t q = min((int64_t)it.p_begin + 16 * ln, (int64_t)it.p_end - 1);
                     asm volatile("prefetch.global.L1 [%0];" ::"l"(a + q));
+                } else if (gt >= 64 && gt < 64 + (int)(sizeof(SimDesc) / 8)) {
+                    // and the simulation's descriptor into shared memory (the
+                    // item's record staging through L1 may evict its lines)
+                    reinterpret_cast<long long *>(&sd_sm[group])[gt - 64] =
+                        reinterpret_cast<const long long *>(&B.sims[s])[gt - 64];
                 }
                 unsigned long long n_int = 0;
                 const bool done = force_item<Rec, TJ, false>(sd.st, (const Rec *)sd.rec, sd.L, sd.pj, sd.work,
@@ -550,15 +560,16 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                 if (gt == 0 && n_int) atomicAdd(&sd.ds->interactions, n_int);
                 if (done) {
                     group_sync(bar);  // the tile's new forces are visible to the group
+                    const SimDesc &sdc = sd_sm[group];  // copied at the item's start
                     const double tnow = cached_time(sc, B.sims, s, par);
                     const int4 td = make_int4(it.p_begin, it.p_end, it.group, it.slot);
                     const uint32_t mask = it.mask;
                     // steps of the tile's particles that are not corrected now,
                     // loaded while the corrector runs
                     const int64_t pw = td.x + glane;
-                    const double dt_keep = (gw == 0 && pw < td.y && !((mask >> glane) & 1u)) ? sd.st.dt[pw] : 0.0;
+                    const double dt_keep = (gw == 0 && pw < td.y && !((mask >> glane) & 1u)) ? sdc.st.dt[pw] : 0.0;
                     const double tn =
-                        correct_tile_3lane(sd, td, mask, tnow, glane, 10 * gw, 10 * (kThreads / 32), sm.lv);
+                        correct_tile_3lane(sdc, td, mask, tnow, glane, 10 * gw, 10 * (kThreads / 32), sm.lv, sm.fin);
                     if (glane == 0) sm.tn[gw] = tn;
                     group_sync(bar);  // new levels and times are visible to the group
                     if (gw == 0) {
@@ -571,10 +582,10 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                             for (int w = 1; w < kThreads / 32; w++)
                                 if (__double_as_longlong(sm.tn[w]) < __double_as_longlong(m)) m = sm.tn[w];
                             const int c = __popc(mask);
-                            sd.tile_lv[it.tile] = lvm;
-                            atomicMin(&sd.ds->tmin[par ^ 1], (unsigned long long)__double_as_longlong(m));
-                            atomicAdd(&sd.ds->particle_steps, (unsigned long long)c);
-                            atomicAdd(&sd.ds->n_act_last, c);
+                            sdc.tile_lv[it.tile] = lvm;
+                            atomicMin(&sdc.ds->tmin[par ^ 1], (unsigned long long)__double_as_longlong(m));
+                            atomicAdd(&sdc.ds->particle_steps, (unsigned long long)c);
+                            atomicAdd(&sdc.ds->n_act_last, c);
                         }
                     }
                 }

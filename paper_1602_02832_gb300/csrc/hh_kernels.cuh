@@ -279,25 +279,33 @@ __device__ __forceinline__ void store_rec<RecMix>(RecMix *out, int64_t e, const 
 }
 
 // FP32 copy of entry e's FP64 state for the mixed predictor, one component
-// (d = 0, 1, 2); the mass goes with component 0.
-__device__ __forceinline__ void refresh_base_component(const State &s, int64_t e, int d)
+// (d = 0, 1, 2) from the values x, v, a, jk of that component; the mass m goes
+// with component 0.
+__device__ __forceinline__ void refresh_base_values(const State &s, int64_t e, int d, double x, double v, double a,
+                                                    double jk, double m)
 {
-    const double x = s.x[d * s.cap_j + e];
     const float hi = __double2float_rn(x);
     const float lo = __double2float_rn(x - (double)hi);
-    const float v = __double2float_rn(s.v[d * s.cap_j + e]);
-    const float a2 = 0.5f * __double2float_rn(s.a[d * s.cap_j + e]);
-    const float j6 = __double2float_rn(s.jk[d * s.cap_j + e]) * (1.0f / 6.0f);
+    const float vf = __double2float_rn(v);
+    const float a2 = 0.5f * __double2float_rn(a);
+    const float j6 = __double2float_rn(jk) * (1.0f / 6.0f);
     float *b = reinterpret_cast<float *>(&s.base[e]);  // hm, lo, v, a2, j6: float4 each
     b[0 + d] = hi;
     b[4 + d] = lo;
-    b[8 + d] = v;
+    b[8 + d] = vf;
     b[12 + d] = a2;
     b[16 + d] = j6;
     if (d == 0) {
-        b[3] = __double2float_rn(s.m[e]);
+        b[3] = __double2float_rn(m);
         b[7] = b[11] = b[15] = b[19] = 0.f;
     }
+}
+
+// The same from the state arrays.
+__device__ __forceinline__ void refresh_base_component(const State &s, int64_t e, int d)
+{
+    refresh_base_values(s, e, d, s.x[d * s.cap_j + e], s.v[d * s.cap_j + e], s.a[d * s.cap_j + e],
+                        s.jk[d * s.cap_j + e], d == 0 ? s.m[e] : 0.0);
 }
 
 __device__ __forceinline__ void refresh_base(const State &s, int64_t e)
@@ -719,6 +727,7 @@ struct ForceSmem {
     int last;
     double tn[kThreads / 32];  // per-warp minimum of t + dt after the corrector
     int lv[kMaxTileI];         // new step level of each corrected particle, by active index
+    double fin[kMaxTileI][7];  // the completed tile's new acc, jerk, pot by active index (for its corrector)
 };
 
 // GPU-scope acquire / release operations (PTX memory model): an
@@ -930,6 +939,7 @@ __device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict
                 for (int q = 0; q < slot; q++) mm &= mm - 1;
                 const int64_t p = p0 + (__ffs(mm) - 1);
                 const double v = comp_get(r[u]);
+                sm.fin[slot][comp] = v;
                 if (comp < 3) s.acc1[comp * s.cap_n + p] = v;
                 else if (comp < 6) s.jerk1[(comp - 3) * s.cap_n + p] = v;
                 else s.pot1[p] = -v;
@@ -1112,13 +1122,18 @@ __device__ __forceinline__ double sq(double u) { return __dmul_rn(u, u); }
 // the four norms are first normalised by exact powers of two taken from the
 // exponents of A and J (A' in [1, 2), J' in [1, 8)), which brings the
 // shortest steps' huge higher derivatives into FP32 range, and the power of
-// two found for the normalised step is shifted back.  Error bound of the
-// FP32 value w' against the FP64 expression of the same normalised inputs:
-// truncation to FP32 2^-23 per input, the products, sums, quotient, eta
-// product and roots add at most 5.75 * 2^-24 in all (positive terms only), so
-// when the mantissa of w' is at least 64 ulps (2^-18 relative) away from a
-// power-of-two boundary both lie in the same binade and the exact power of
-// two below the FP64 value is returned.  Otherwise (near a boundary, zero or
+// two found for the normalised step is shifted back.  The screen works on
+// w2 = dt'^2 itself: the power of two below dt' = sqrt(w2) is 2^floor(e / 2)
+// for w2's exponent e, and its boundaries are w2's even powers of two.
+// Error bound of the FP32 w2 against the exact value of the same normalised
+// inputs: truncation to FP32 2^-23 per input (and eta), the square roots as
+// y rsqrtf(y) (rsqrtf within 2 ulp), the quotient by __fdividef (within 2
+// ulp), the sums of positive terms and the products: at most 24 * 2^-24 in
+// all.  When w2 is at least 128 ulps (>= 2^-17 relative) from the even power
+// of two on its side (the lower one for an even exponent, the upper one for
+// an odd exponent), the exact value and the FP64 expression (within ~1e-15 of
+// it) lie between the same two even powers of two, and the exact power of two
+// below the FP64 value is returned.  Otherwise (near a boundary, zero or
 // non-normal inputs, normalised values outside [2^-60, 2^61), eta outside
 // [2^-30, 2^30], or products and steps near the FP64 range's ends, where the
 // FP64 expression itself would lose range) the FP64 expression decides.
@@ -1150,11 +1165,14 @@ __device__ __forceinline__ double aarseth_want(double A, double J, double S, dou
         const bool fp64_ok = eA + eS > -1000 && eA + eS < 1000 && eJ + eT > -1000 && eJ + eT < 1000;
         if (fp64_ok && xS >= -60 && xS <= 60 && xT >= -60 && xT <= 60) {
             const float Af = f32_scaled(A, mA), Jf = f32_scaled(J, mJ), Sf = f32_scaled(S, mS), Tf = f32_scaled(T, mT);
-            const float w = sqrtf(__double2float_rn(eta) * ((sqrtf(Af * Sf) + Jf) / (sqrtf(Jf * Tf) + Sf)));
-            const int wb = __float_as_int(w);
+            const float p1 = Af * Sf, p2 = Jf * Tf;
+            const float num = p1 * rsqrtf(p1) + Jf, den = p2 * rsqrtf(p2) + Sf;
+            const float w2 = f32_scaled(eta, 0) * __fdividef(num, den);
+            const int wb = __float_as_int(w2);
             const int frac = wb & 0x7fffff, ex = (wb >> 23) & 0xff;
-            const int e2 = ex - 127 - k;  // dt = w' / 2^k: exponent of the power of two below dt
-            if (ex > 0 && ex < 255 && frac >= 64 && frac <= 0x7fffff - 64 && e2 > -400 && e2 < 400)
+            const int e = ex - 127, odd = e & 1;
+            const int e2 = (e >> 1) - k;  // dt = sqrt(w2) / 2^k: exponent of the power of two below dt
+            if (ex > 0 && ex < 255 && (odd ? frac <= 0x7fffff - 128 : frac >= 128) && e2 > -400 && e2 < 400)
                 return __longlong_as_double((long long)(e2 + 1023) << 52);
         }
     }
