@@ -44,6 +44,7 @@ constexpr long long kSpinLimit = 1ll << 28;            // iteration backstop for
 constexpr int kGroups = 4;                   // 128-thread worker groups per CTA (one CTA per SM)
 constexpr int kBlock = kThreads * kGroups;
 constexpr int kSimCache = 256;               // simulations whose step data a CTA keeps in shared memory
+constexpr int kSdCache = 32;                 // simulations whose descriptors a CTA keeps in shared memory
 
 struct SimDesc {
     State st;
@@ -382,6 +383,10 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ StepCache sc;
     __shared__ SimDesc sd_sm[kGroups];  // each worker group's current simulation (for its corrector)
+    // Descriptors do not change during a launch: the first kSdCache live in
+    // shared memory, so a worker reaches a simulation's arrays without an L2
+    // round trip at the start of every item and every corrector.
+    __shared__ SimDesc sd_all[kSdCache];
     static_assert(sizeof(SimDesc) % 8 == 0 && sizeof(SimDesc) / 8 <= kThreads - 64, "descriptor copy by 64 threads");
     const int tid = threadIdx.x;
     const int group = tid / kThreads, gt = tid - group * kThreads;
@@ -391,6 +396,10 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
     const int n_sims = B.hdr->n_sims, max_steps = B.hdr->max_steps;
     WorkItem *const items = B.hdr->items;
     const int64_t NJ = B.jbase[n_sims], NP = B.pbase[n_sims], NT = B.tbase[n_sims];
+    for (int w = tid; w < min(n_sims, kSdCache) * (int)(sizeof(SimDesc) / 8); w += blockDim.x)
+        reinterpret_cast<long long *>(sd_all)[w] = reinterpret_cast<const long long *>(B.sims)[w];
+    // (visible after the first grid barrier's block barrier, before any use below it)
+    auto SD = [&](int s) -> const SimDesc & { return s < kSdCache ? sd_all[s] : B.sims[s]; };
 
     // phase 0: every simulation's first block time, latest time, level
     // histogram and tile level masks; the block rule is checked here
@@ -415,7 +424,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
             double t = 0.0, dt = 0.0;
             if (valid) {
                 s = find_sim(B.pbase, n_sims, g);
-                const SimDesc &sd = B.sims[s];
+                const SimDesc &sd = SD(s);
                 const int64_t p = g - B.pbase[s];
                 t = sd.st.t[p];
                 dt = sd.st.dt[p];
@@ -443,7 +452,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
         const int64_t w0 = gtid >> 5, nw = nth >> 5;
         for (int64_t wt = w0; wt < NT; wt += nw) {
             const int s = find_sim(B.tbase, n_sims, wt);  // warp-uniform
-            const SimDesc &sd = B.sims[s];
+            const SimDesc &sd = SD(s);
             const int tile = (int)(wt - B.tbase[s]);
             const int4 td = sd.L.tiles[tile];
             const int64_t p = td.x + lane;
@@ -489,7 +498,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
         }
         for (int64_t g = gtid; g < NJ; g += nth) {
             const int s = find_sim(B.jbase, n_sims, g);
-            const SimDesc &sd = B.sims[s];
+            const SimDesc &sd = SD(s);
             const double tnow = cached_time(sc, B.sims, s, par);
             if (!(tnow <= sd.t_end)) continue;
             predict_entry<Rec>(sd.st, (Rec *)sd.rec, g - B.jbase[s], tnow);
@@ -499,7 +508,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
             const int64_t w0 = gtid >> 5, nw = nth >> 5;
             for (int64_t wt = w0; wt < NT; wt += nw) {
                 const int s = find_sim(B.tbase, n_sims, wt);  // warp-uniform
-                const SimDesc &sd = B.sims[s];
+                const SimDesc &sd = SD(s);
                 const double tnow = cached_time(sc, B.sims, s, par);
                 if (!(tnow <= sd.t_end)) continue;
                 const int tile = (int)(wt - B.tbase[s]);
@@ -535,7 +544,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
             for (;;) {
                 if (item >= (int)n_items) break;
                 const int s = it.part_sim >> 16;
-                const SimDesc &sd = B.sims[s];
+                const SimDesc &sd = SD(s);
                 if (gt < 45) {
                     // the corrector's inputs (15 state arrays, <= 3 cache lines
                     // of each for the tile's <= 32 particles) into this SM's L1,
@@ -547,7 +556,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                                                : (arr == 12 ? st.t : arr == 13 ? st.dt : st.m);
                     const int64_t q = min((int64_t)it.p_begin + 16 * ln, (int64_t)it.p_end - 1);
                     asm volatile("prefetch.global.L1 [%0];" ::"l"(a + q));
-                } else if (gt >= 64 && gt < 64 + (int)(sizeof(SimDesc) / 8)) {
+                } else if (s >= kSdCache && gt >= 64 && gt < 64 + (int)(sizeof(SimDesc) / 8)) {
                     // and the simulation's descriptor into shared memory (the
                     // item's record staging through L1 may evict its lines)
                     reinterpret_cast<long long *>(&sd_sm[group])[gt - 64] =
@@ -560,7 +569,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                 if (gt == 0 && n_int) atomicAdd(&sd.ds->interactions, n_int);
                 if (done) {
                     group_sync(bar);  // the tile's new forces are visible to the group
-                    const SimDesc &sdc = sd_sm[group];  // copied at the item's start
+                    const SimDesc &sdc = s < kSdCache ? sd_all[s] : sd_sm[group];  // copied at the item's start
                     const double tnow = cached_time(sc, B.sims, s, par);
                     const int4 td = make_int4(it.p_begin, it.p_end, it.group, it.slot);
                     const uint32_t mask = it.mask;
