@@ -387,6 +387,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
     // shared memory, so a worker reaches a simulation's arrays without an L2
     // round trip at the start of every item and every corrector.
     __shared__ SimDesc sd_all[kSdCache];
+    __shared__ int64_t base_sm[3][kSdCache + 1];  // jbase, pbase, tbase of a batch of <= kSdCache simulations
     static_assert(sizeof(SimDesc) % 8 == 0 && sizeof(SimDesc) / 8 <= kThreads - 64, "descriptor copy by 64 threads");
     const int tid = threadIdx.x;
     const int group = tid / kThreads, gt = tid - group * kThreads;
@@ -398,8 +399,17 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
     const int64_t NJ = B.jbase[n_sims], NP = B.pbase[n_sims], NT = B.tbase[n_sims];
     for (int w = tid; w < min(n_sims, kSdCache) * (int)(sizeof(SimDesc) / 8); w += blockDim.x)
         reinterpret_cast<long long *>(sd_all)[w] = reinterpret_cast<const long long *>(B.sims)[w];
+    const bool small_batch = n_sims <= kSdCache;
+    if (small_batch)
+        for (int w = tid; w < 3 * (n_sims + 1); w += blockDim.x) {
+            const int a = w / (n_sims + 1), q = w - a * (n_sims + 1);
+            base_sm[a][q] = (a == 0 ? B.jbase : a == 1 ? B.pbase : B.tbase)[q];
+        }
     // (visible after the first grid barrier's block barrier, before any use below it)
     auto SD = [&](int s) -> const SimDesc & { return s < kSdCache ? sd_all[s] : B.sims[s]; };
+    const int64_t *const JB = small_batch ? base_sm[0] : B.jbase;
+    const int64_t *const PB = small_batch ? base_sm[1] : B.pbase;
+    const int64_t *const TB = small_batch ? base_sm[2] : B.tbase;
 
     // phase 0: every simulation's first block time, latest time, level
     // histogram and tile level masks; the block rule is checked here
@@ -423,9 +433,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
             int s = -1, lv = -1;
             double t = 0.0, dt = 0.0;
             if (valid) {
-                s = find_sim(B.pbase, n_sims, g);
+                s = find_sim(PB, n_sims, g);
                 const SimDesc &sd = SD(s);
-                const int64_t p = g - B.pbase[s];
+                const int64_t p = g - PB[s];
                 t = sd.st.t[p];
                 dt = sd.st.dt[p];
                 if (!is_level_step(dt) || !(t >= 0.0)) {
@@ -451,9 +461,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
         mc_block_flush(B.sims, acc, 0);
         const int64_t w0 = gtid >> 5, nw = nth >> 5;
         for (int64_t wt = w0; wt < NT; wt += nw) {
-            const int s = find_sim(B.tbase, n_sims, wt);  // warp-uniform
+            const int s = find_sim(TB, n_sims, wt);  // warp-uniform
             const SimDesc &sd = SD(s);
-            const int tile = (int)(wt - B.tbase[s]);
+            const int tile = (int)(wt - TB[s]);
             const int4 td = sd.L.tiles[tile];
             const int64_t p = td.x + lane;
             const uint32_t bit = (p < td.y) ? (1u << (level_of(sd.st.dt[p]) & 31)) : 0u;
@@ -497,21 +507,21 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
             }
         }
         for (int64_t g = gtid; g < NJ; g += nth) {
-            const int s = find_sim(B.jbase, n_sims, g);
+            const int s = find_sim(JB, n_sims, g);
             const SimDesc &sd = SD(s);
             const double tnow = cached_time(sc, B.sims, s, par);
             if (!(tnow <= sd.t_end)) continue;
-            predict_entry<Rec>(sd.st, (Rec *)sd.rec, g - B.jbase[s], tnow);
+            predict_entry<Rec>(sd.st, (Rec *)sd.rec, g - JB[s], tnow);
         }
         {
             const int lane = tid & 31;
             const int64_t w0 = gtid >> 5, nw = nth >> 5;
             for (int64_t wt = w0; wt < NT; wt += nw) {
-                const int s = find_sim(B.tbase, n_sims, wt);  // warp-uniform
+                const int s = find_sim(TB, n_sims, wt);  // warp-uniform
                 const SimDesc &sd = SD(s);
                 const double tnow = cached_time(sc, B.sims, s, par);
                 if (!(tnow <= sd.t_end)) continue;
-                const int tile = (int)(wt - B.tbase[s]);
+                const int tile = (int)(wt - TB[s]);
                 if ((sd.tile_lv[tile] >> kmin_of(tnow)) == 0u) continue;  // no due level in this tile
                 const int4 td = sd.L.tiles[tile];
                 const int64_t p = td.x + lane;
