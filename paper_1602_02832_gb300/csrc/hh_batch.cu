@@ -824,6 +824,7 @@ extern "C" int hh_batch_run(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const d
     if (!b) return hh_set_global_error(HH_EINVAL, "hh_batch_run: NULL batch");
     if (n < 1 || n > b->max_sims || !ctxs || !t_end) return bfail(b, HH_EINVAL, "hh_batch_run: bad n or NULL arrays");
     if (max_steps < 1 || max_steps > b->max_steps) return bfail(b, HH_EINVAL, "hh_batch_run: max_steps out of range");
+    if (!b->graph) return bfail(b, HH_ESTATE, "hh_batch_run: the batch has no captured launch (a failed re-capture)");
     if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, HH_ECUDA, "hh_batch_run: cudaSetDevice failed");
     const BatchLayout &Ly = b->lay;
     SimDesc *sims = reinterpret_cast<SimDesc *>(b->h_blk + Ly.sims);
