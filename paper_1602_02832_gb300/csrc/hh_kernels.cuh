@@ -677,15 +677,16 @@ __device__ __forceinline__ void fold_chunk(AccF64 &) {}
 __device__ __forceinline__ void fold_chunk(AccMix &A) { A.fold(); }
 
 // ------------------------------------------------------------ list force
-// One CTA (4 warps) per work item = (tile, part of its group's list).  With
-// n_a active particles in the tile, lane l serves i slot (l mod I),
-// I = next power of two >= n_a, and the CTA's 128 threads form 128 / I
-// j slices that stride through each staged chunk of the part.  Slices are
-// summed in a fixed order (shuffles, then warps).  A list split into several
-// parts leaves per-part sums in the partials buffer; the CTA that finishes a
-// tile's last part (arrival counter, threadfence pattern: no waiting) adds
-// the parts in part order.  So each particle's result depends only on its
-// list, its tile's active count and the part length, never on scheduling.
+// One 128-thread group (4 warps) per work item = (tile, part of its group's
+// list).  With n_a active particles in the tile each warp holds floor(32 /
+// n_a) j slices of n_a lanes (lane = i slot + n_a * slice; leftover lanes
+// idle), and the slices stride through each staged chunk of the part.
+// Slices are summed in a fixed order (shuffles, then warps).  A list split
+// into several parts leaves per-part sums in the partials buffer; the group
+// that finishes a tile's last part (acquire-release arrival counter: no
+// waiting) adds the parts in part order.  So each particle's result depends
+// only on its list, its tile's active count and the part length, never on
+// scheduling.
 // Asynchronous global -> shared copies (16 B each) for chunk staging,
 // cached in L1: the 16-byte pieces of one record, and the records of
 // neighbouring list entries (consecutive particles of a leaf, sibling
