@@ -29,6 +29,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -483,6 +484,18 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
     for (; step < max_steps; step++) {
         const int par = step & 1;
         // ---- phase 1: predict + select
+        // The inputs of this thread's first predicted entry (mixed form; the
+        // plain form's FP64 inputs would not fit in registers, and its
+        // predictor is bound by the FP64 pipe) and the level mask of its
+        // warp's first tile do not depend on the block time: their loads go
+        // out before the block times are read.
+        constexpr bool kEarly = std::is_same<Rec, RecMix>::value;
+        PredIn<Rec> in0;
+        const int s_p0 = gtid < NJ ? find_sim(JB, n_sims, gtid) : 0;
+        if (kEarly && gtid < NJ) pred_load<Rec>(SD(s_p0).st, gtid - JB[s_p0], in0);
+        const int64_t w_first = gtid >> 5;
+        const int s_t0 = w_first < NT ? find_sim(TB, n_sims, w_first) : 0;
+        const uint32_t lv_first = w_first < NT ? SD(s_t0).tile_lv[w_first - TB[s_t0]] : 0u;
         cache_times(sc, B.sims, n_sims, par);
         if (blockIdx.x == 0) {
             // counters of the previous step (other parity) are free again
@@ -507,11 +520,12 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
             }
         }
         for (int64_t g = gtid; g < NJ; g += nth) {
-            const int s = find_sim(JB, n_sims, g);
+            const int s = g == gtid ? s_p0 : find_sim(JB, n_sims, g);
             const SimDesc &sd = SD(s);
             const double tnow = cached_time(sc, B.sims, s, par);
             if (!(tnow <= sd.t_end)) continue;
-            predict_entry<Rec>(sd.st, (Rec *)sd.rec, g - JB[s], tnow);
+            if (kEarly && g == gtid) pred_store<Rec>(in0, (Rec *)sd.rec, g - JB[s], tnow);
+            else predict_entry<Rec>(sd.st, (Rec *)sd.rec, g - JB[s], tnow);
         }
         {
             const int lane = tid & 31;
@@ -522,7 +536,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                 const double tnow = cached_time(sc, B.sims, s, par);
                 if (!(tnow <= sd.t_end)) continue;
                 const int tile = (int)(wt - TB[s]);
-                if ((sd.tile_lv[tile] >> kmin_of(tnow)) == 0u) continue;  // no due level in this tile
+                const uint32_t lv = wt == w_first ? lv_first : sd.tile_lv[tile];
+                if ((lv >> kmin_of(tnow)) == 0u) continue;  // no due level in this tile
                 const int4 td = sd.L.tiles[tile];
                 const int64_t p = td.x + lane;
                 const bool act = (p < td.y) && (sd.st.t[p] + sd.st.dt[p] == tnow);
