@@ -643,6 +643,14 @@ __device__ __forceinline__ double red_get(const RedF64 &r, int q) { return r.v[q
 __device__ __forceinline__ double red_get(const RedMix &r, int q) { return (double)r.v[q].h + (double)r.v[q].l; }
 // partial sums written by other CTAs are read through L2 (bypassing L1)
 // One component of a reduction record (double, or an FP32 pair).
+__device__ __forceinline__ double shfl_down_e(double v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ F2 shfl_down_e(const F2 &v, int d)
+{
+    F2 r;
+    r.h = __shfl_down_sync(0xffffffffu, v.h, d);
+    r.l = __shfl_down_sync(0xffffffffu, v.l, d);
+    return r;
+}
 __device__ __forceinline__ void comp_add(double &a, double b) { a += b; }
 __device__ __forceinline__ void comp_add(F2 &a, const F2 &b) { a = f2_add(a, b); }
 __device__ __forceinline__ double comp_get(double a) { return a; }
@@ -868,36 +876,79 @@ __device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict
         }
         group_sync(bar_id);  // buffer b is refilled by the next step's issue
     }
-    // reduce the slices of each i slot over lanes islot + n_a k of each warp
-    // (k < K), then over the warps: a butterfly when n_a is a power of two
-    // (K n_a = 32), else a tree towards slice 0
-    if ((I & (I - 1)) == 0) {
-        for (int off = I; off < 32; off <<= 1) acc_shfl_add(A, off);
-    } else {
-        for (int step = 1; step < K; step <<= 1)
-            acc_shfl_down_add(A, step * I, !idle && (kslice & (2 * step - 1)) == 0 && kslice + step < K);
+    // Plain form: sum over the group's 4 K slices for each (i slot,
+    // component): the partials go to shared memory, then P contiguous lanes of
+    // one warp (P a power of two, P * 7 n_a <= 128) each add a contiguous run
+    // of slices in order and a shuffle tree adds the P runs.  A fixed order,
+    // with about 4 K / P + log2 P adds per thread, where a butterfly over the
+    // lanes costs 7 adds per level for every lane (a warp instruction costs the
+    // FP64 pipe the same with one lane active).  With P = 1 a thread may own
+    // two outputs (7 n_a <= 224).  Mixed form (FP32 pair adds are cheap, the
+    // extra barriers are not): a butterfly over the lanes when n_a is a power
+    // of two, else a tree towards slice 0, then a sum over the four warps.
+    constexpr bool kTreeTail = std::is_same<Rec, RecF64>::value;
+    if (!kTreeTail) {
+        if ((I & (I - 1)) == 0) {
+            for (int off = I; off < 32; off <<= 1) acc_shfl_add(A, off);
+        } else {
+            for (int step = 1; step < K; step <<= 1)
+                acc_shfl_down_add(A, step * I, !idle && (kslice & (2 * step - 1)) == 0 && kslice + step < K);
+        }
     }
-    if (lane < I) {
-        Red r;
-        to_red(A, r);
-        sm.red[warp][lane] = r;
+    if (kTreeTail ? !idle : lane < I) {
+        Red rr;
+        to_red(A, rr);
+        sm.red[warp][lane] = rr;
     }
     group_sync(bar_id);
-    // The rest runs one thread per (i slot, component): per component the same
-    // sums in the same order as whole records (warps 0..3, then parts
-    // 0..n_parts-1), but in parallel lanes, since a warp instruction costs the
-    // FP64 pipe the same with one lane active.  7 n_a <= 224 outputs: at most
-    // two per thread.
     using E = typename std::remove_reference<decltype(sm.red[0][0].v[0])>::type;
     const int n_out = 7 * n_a;
-    E r[2];
+    const int n_sl = kTreeTail ? (kThreads / 32) * K : kThreads / 32;  // terms per output
+    int P = 1;  // (mixed form: one thread per output, warps 0..3 in order)
+    if (kTreeTail)
+        while (P < 32 && 2 * P * n_out <= kThreads && 2 * P <= n_sl) P <<= 1;
+    const int per = (n_sl + P - 1) / P;
+    E r[2] = {E{}, E{}};
+    bool has[2] = {false, false};
 #pragma unroll
     for (int u = 0; u < 2; u++) {
-        const int t = tid + u * kThreads, slot = t / 7, comp = t - 7 * (t / 7);
-        if (t < n_out) {
-            r[u] = sm.red[0][slot].v[comp];
-            for (int w = 1; w < kThreads / 32; w++) comp_add(r[u], sm.red[w][slot].v[comp]);
+        const int t = tid + u * kThreads;
+        const int o = t / P, q = t - o * P;
+        if ((u == 0 || P == 1) && o < n_out) {
+            const int slot = o / 7, comp = o - 7 * slot;
+            const int x1 = min(n_sl, (q + 1) * per);
+            for (int x = q * per; x < x1; x++) {
+                const int w = kTreeTail ? x / K : x, k = kTreeTail ? x - w * K : 0;
+                const E v = sm.red[w][k * I + slot].v[comp];
+                if (has[u]) comp_add(r[u], v);
+                else {
+                    r[u] = v;
+                    has[u] = true;
+                }
+            }
         }
+        if (u == 0)
+            for (int off = P >> 1; off > 0; off >>= 1) {  // P is the same in every lane
+                const E ov = shfl_down_e(r[0], off);
+                const bool oh = __shfl_down_sync(0xffffffffu, (int)has[0], off) != 0;
+                if (q < off && oh) {
+                    if (has[0]) comp_add(r[0], ov);
+                    else {
+                        r[0] = ov;
+                        has[0] = true;
+                    }
+                }
+            }
+    }
+    // the sums, one per output, back into slot order: thread t then holds
+    // output t (and t + 128) for the part merge below (already so when P = 1)
+    if (P > 1) {
+        group_sync(bar_id);
+        E *outv = &sm.red[0][0].v[0];
+        const int o = tid / P;
+        if (o < n_out && tid - o * P == 0) outv[o] = r[0];
+        group_sync(bar_id);
+        if (tid < n_out) r[0] = outv[tid];
     }
     bool write_out = n_parts == 1;
     if (n_parts > 1) {
