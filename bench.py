@@ -44,7 +44,7 @@ sys.path.insert(0, ROOT)
 FLOP_PER_INT = 60
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_batch launch (plain FP64,
 # one tree interval of the N = 65536 run), from profiles/batch_kernel_plummer65536.md
-TRAFFIC_FP64_PER_LAUNCH = 69.479936e6 + 29.872384e6
+TRAFFIC_FP64_PER_LAUNCH = 69.430016e6 + 29.625088e6
 METRIC = "interactions/s & equiv. Tflops (60 flop/int); block-steps/s, p50/p99 latency vs plain"
 
 
