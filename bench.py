@@ -505,7 +505,8 @@ def main_reference(a):
     val = tot_int / tot_s
     sample = (f"each step: FP64 oracle tree-loop run of N={a.n} Plummer over t in [0, 1/1024] "
               f"(start-up interval of the same workload)")
-    line = {"metric": METRIC, "value": val, "unit": "interactions/s", "n_gpus": 0, "steps": a.steps,
+    # n_gpus is the launch's N (the oracle itself runs on rank 0's host cores)
+    line = {"metric": METRIC, "value": val, "unit": "interactions/s", "n_gpus": max(world, a.gpus), "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": tot_s * 1e3 / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
