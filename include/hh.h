@@ -269,7 +269,9 @@ const char *hh_last_error(const hh_ctx *ctx);
  *   each simulation's next block time (> t_end[s] when it reached t_end[s]);
  *   step_us_out[max_steps], the duration of each global step in
  *   microseconds (device timer); phase_us_out[3 max_steps], per step the
- *   durations of the predict/select, force and correct phases.  Synchronises.
+ *   durations of the predict/select phase, the force phase (which includes
+ *   the corrector: the worker that completes a tile corrects it) and a third,
+ *   empty correct phase (0, kept for the layout).  Synchronises.
  *   A grid-barrier wait gives up after 2 s (HH_ETIMEOUT).
  *   Every particle must follow the block rule (dt a power of two in
  *   [2^-31, 1], t a multiple of dt, t + dt after the latest t), as states
