@@ -101,3 +101,30 @@ def test_host_tree_degenerate_inputs(hh):
     xx[0, 3] = np.nan
     with pytest.raises(hh.HHError):
         hh.hh_tree_build(xx, v, v, v, m)
+
+
+def test_autotuner_candidates_are_valid_configurations(hh):
+    # every candidate passes the library's configuration checks, which run
+    # before any device call: on a machine without a GPU a valid candidate
+    # gets past them (and fails only at the device), an invalid one is
+    # refused with HH_EINVAL
+    import torch
+    from paper_1602_02832_gb300 import autotune
+
+    if torch.cuda.is_available():
+        pytest.skip("needs a machine without a GPU (no context is created)")
+    for prec, cands in autotune.CANDIDATES.items():
+        for cand in cands:
+            c = hh.hh_config_default()
+            c.precision = prec
+            for k, v in cand.items():
+                setattr(c, k, v)
+            with pytest.raises(hh.HHError) as e:
+                hh.Context(c, 16, 32, 64, 4)
+            assert e.value.code != hh.HH_EINVAL, (prec, cand, str(e.value))
+    c = hh.hh_config_default()
+    c.precision = hh.HH_MIXED
+    c.tile_j = 128  # not a multiple of the mixed form's 256-entry chunk
+    with pytest.raises(hh.HHError) as e:
+        hh.Context(c, 16, 32, 64, 4)
+    assert e.value.code == hh.HH_EINVAL
