@@ -178,6 +178,47 @@ def test_list_partitions_all_mass(orc, theta):
     np.testing.assert_allclose(sums, 1.0, rtol=1e-13)
 
 
+@pytest.mark.parametrize("theta", [0.3, 0.75])
+def test_list_entries_follow_opening_criterion(orc, theta):
+    # Brute-force check of each list against the opening rule (Barnes' modified
+    # algorithm, Section 2): a node entry satisfies side < theta * d, with d the
+    # distance from its centre of mass to the box around the group's members,
+    # and every cell above an entry that is not an ancestor of the group failed
+    # that test (was opened).  Node entries hold more than one particle.  A
+    # reversed or shifted inequality, or a wrong distance, breaks one of these.
+    x, v, m = synth.plummer_salpeter(2000, 11)
+    z = np.zeros_like(x)
+    T = orc.tree_build(x, v, z, z, m, leaf=8, n_crit=64, theta=theta)
+    n = 2000
+    xs = x[T.perm]
+    cb, ce, depth = T.cell_begin, T.cell_end, T.cell_depth
+    n_node_entries = n_opened_checked = 0
+    for g in range(T.n_groups):
+        gb, ge = T.g_begin[g], T.g_end[g]
+        lo, hi = xs[gb:ge].min(0), xs[gb:ge].max(0)
+        gap = np.maximum(lo - T.node_x, 0.0) + np.maximum(T.node_x - hi, 0.0)
+        d = np.sqrt((gap * gap).sum(1))
+        margin = T.cell_side - theta * d
+        sure = np.abs(margin) > 1e-12 * T.cell_side  # leave exact ties out
+        accept = margin < 0
+        anc_g = (cb <= gb) & (ge <= ce)
+        lst = T.list_idx[T.list_off[g]:T.list_off[g + 1]]
+        for e in lst:
+            if e < n:
+                if gb <= e < ge:
+                    continue
+                above = (cb <= e) & (e < ce) & ~anc_g & (ce - cb > 1)
+            else:
+                c = e - n
+                n_node_entries += 1
+                assert ce[c] - cb[c] > 1
+                assert accept[c] or not sure[c]
+                above = (cb <= cb[c]) & (ce[c] <= ce) & (depth < depth[c]) & ~anc_g
+            assert np.all(~accept[above] | ~sure[above]), (g, e)
+            n_opened_checked += int(above.sum())
+    assert n_node_entries > 100 and n_opened_checked > 100
+
+
 def test_tree_geometry_and_groups(orc):
     # Cell members fit in the cell's cube; leaves hold <= leaf particles; groups
     # are maximal cells with <= n_crit particles and tile the Morton order.
