@@ -360,6 +360,28 @@ def test_energy_conservation_direct_and_tree(orc):
     assert drift["t03"] <= drift["t075"]
 
 
+def test_tree_step_count_close_to_direct(orc):
+    # Section 3: the tree's force errors raise the number of individual steps
+    # only a little over the direct Hermite run (a ratio of 1.042 printed for
+    # theta = 0.75 at N = 512k; read as tree over direct).  Over four tree
+    # intervals (the lists change at each rebuild) the ratio stays within a few
+    # per cent of 1, grows with theta and shrinks as groups grow (more of each
+    # list is direct).  Soft pin: the paper's runs are far larger.
+    n = 8192
+    x, v, m = synth.plummer(n, 6)
+    eps2 = (1.0 / n) ** 2
+
+    def steps(use_tree, theta, n_crit):
+        p = orc.RunParams(eps2=eps2, eta=0.02, use_tree=use_tree, theta=theta, n_crit=n_crit)
+        return orc.run(x, v, m, 1.0 / 16, p)["stats"]["particle_steps"]
+
+    direct = steps(False, 0.0, 64)
+    r = {key: steps(True, *key) / direct for key in ((0.3, 1024), (0.5, 1024), (0.75, 1024), (0.5, 64))}
+    assert 1.0 <= r[0.3, 1024] < r[0.5, 1024] < r[0.75, 1024] < 1.15
+    assert r[0.5, 64] > r[0.5, 1024]
+    assert abs(r[0.75, 1024] - 1.042) < 0.1
+
+
 def test_plummer_standard_units(orc):
     # Standard units M = G = -4E = 1 (Section 3): with 16k particles E = -1/4
     # and 2K = -W = 1/2 within sampling noise (the 0.999 mass cap binds a
