@@ -219,6 +219,48 @@ def test_list_entries_follow_opening_criterion(orc, theta):
     assert n_node_entries > 100 and n_opened_checked > 100
 
 
+def test_degenerate_inputs(orc):
+    # One particle: a list of itself and no force.  Two: the list path gives the
+    # softened two-body closed form.  Coincident particles: the octree stops at
+    # depth 21 with one leaf holding all of them, and each feels only the
+    # softened potential -sum_{j != i} m_j / eps with zero acceleration.
+    z1 = np.zeros((1, 3))
+    T = orc.tree_build(np.ones((1, 3)), z1, z1, z1, np.ones(1), leaf=8, n_crit=2, theta=0.5)
+    assert T.n_cells == 1 and T.n_groups == 1 and list(T.list_idx) == [0]
+    xj, vj, _, _, mj = T.j_array(np.ones((1, 3)), z1, z1, z1, np.ones(1))
+    a, j, p = orc.list_force(xj, vj, mj, np.arange(1), T.group_of, T.list_off, T.list_idx, 1e-4)
+    assert np.all(a == 0) and np.all(j == 0) and np.all(p == 0)
+
+    eps2 = 1e-3
+    x = np.array([[-0.25, 0, 0], [0.25, 0, 0]])
+    v = np.array([[0, -0.3, 0], [0, 0.3, 0]])
+    m = np.array([0.5, 0.5])
+    z = np.zeros_like(x)
+    T = orc.tree_build(x, v, z, z, m, leaf=8, n_crit=1, theta=0.5)
+    xj, vj, _, _, mj = T.j_array(x, v, z, z, m)
+    a, j, p = orc.list_force(xj, vj, mj, np.arange(2), T.group_of, T.list_off, T.list_idx, eps2)
+    s = 0.5 ** 2 + eps2
+    k = T.perm  # tree position -> input index
+    ax = np.where(k == 0, 1.0, -1.0) * 0.5 * 0.5 / s ** 1.5  # towards the other particle
+    np.testing.assert_allclose(a[:, 0], ax, rtol=1e-15)
+    jy = np.where(k == 0, 1.0, -1.0) * 0.5 * 0.6 / s ** 1.5  # r . v = 0: jerk = m v_rel / s^3/2
+    np.testing.assert_allclose(j[:, 1], jy, rtol=1e-15)
+    np.testing.assert_allclose(p, -0.5 / math.sqrt(s), rtol=1e-15)
+
+    n = 5
+    xc = np.full((n, 3), 0.125)
+    zc = np.zeros((n, 3))
+    mc = np.full(n, 1.0 / n)
+    eps = 0.05
+    T = orc.tree_build(xc, zc, zc, zc, mc, leaf=2, n_crit=2, theta=0.5)
+    assert T.cell_depth.max() == 21 and T.n_groups == 1
+    assert np.all(T.cell_end - T.cell_begin == n)  # a chain of cells down to one leaf
+    xj, vj, _, _, mj = T.j_array(xc, zc, zc, zc, mc)
+    a, j, p = orc.list_force(xj, vj, mj, np.arange(n), T.group_of, T.list_off, T.list_idx, eps * eps)
+    assert np.all(a == 0) and np.all(j == 0)
+    np.testing.assert_allclose(p, -(n - 1) / n / eps, rtol=1e-15)
+
+
 def test_tree_geometry_and_groups(orc):
     # Cell members fit in the cell's cube; leaves hold <= leaf particles; groups
     # are maximal cells with <= n_crit particles and tile the Morton order.
