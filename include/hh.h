@@ -95,7 +95,7 @@ typedef struct hh_counters {
 
 /* Fills cfg with defaults: eps2 = 1e-8, eta = 0.02, eta_s = 0.01,
  * dt in [2^-30, 2^-6], dt_tree = 2^-6, theta = 0.5, leaf = 8, n_crit = 64,
- * HH_FP64, default tiles and work items. */
+ * HH_FP64, default tiles and work items.  A NULL cfg is ignored. */
 void hh_config_default(hh_config *cfg);
 
 /* Creates a context on CUDA device `device` with room for n_max particles,
@@ -107,14 +107,22 @@ int hh_create(hh_ctx **out, int device, const hh_config *cfg, int64_t n_max, int
 int hh_destroy(hh_ctx *ctx);
 
 /* Uses the given cudaStream_t (NULL = the context's own stream) for all
- * following work of this context. */
+ * following work of this context, after synchronising the stream in use.
+ * The caller owns the stream and keeps it alive while the context uses it.
+ * Errors: HH_EINVAL for a NULL context; HH_ECUDA if the synchronisation
+ * fails (the old stream stays in use). */
 int hh_set_stream(hh_ctx *ctx, void *cuda_stream);
 
 /* Step 1 (Section 2): writes j entries [first, first + n) — particles and/or
  * nodes — with their positions, velocities, accelerations, jerks, masses and
  * times t (the time at which x, v, a, jk hold; for nodes the tree time).
  * Host SoA arrays [3][n] (m, t: [n]).  Requires first + n <= nj_max; masses
- * must be > 0 and all values finite. */
+ * must be > 0 and all values finite.  Errors: HH_EINVAL for a range outside
+ * [0, nj_max), a NULL array (n > 0), a non-finite value or a mass that is not
+ * positive (checked on the host before anything is copied); HH_ECUDA if a
+ * copy fails.  hh_set_j_dev takes device arrays and checks the values on the
+ * device after the copy, so a failed call (HH_EINVAL) has written the range,
+ * which must be rewritten before use. */
 int hh_set_j(hh_ctx *ctx, int64_t first, int64_t n, const double *x, const double *v,
              const double *a, const double *jk, const double *m, const double *t);
 int hh_set_j_dev(hh_ctx *ctx, int64_t first, int64_t n, const double *x, const double *v,
@@ -123,19 +131,27 @@ int hh_set_j_dev(hh_ctx *ctx, int64_t first, int64_t n, const double *x, const d
 /* Step 1: interaction lists (host arrays).  n_particles particles occupy j
  * entries [0, n_particles) and n_j entries are in use.  Every idx must be in
  * [0, n_j); group ranges must tile [0, n_particles) in ascending order.  The
- * static i tiles are built here.  Validated before any kernel reads them. */
+ * static i tiles are built here.  Validated before any kernel reads them.
+ * Errors: HH_EINVAL for n_particles outside [1, n_max], n_j outside
+ * [n_particles, nj_max], n_groups outside [1, groups_max], a NULL array,
+ * off[0] != 0, a decreasing off, an index outside [0, n_j) or groups that are
+ * not ascending contiguous ranges; HH_ENOMEM for more than list_max entries
+ * or more tiles and list parts than the work-item buffers hold. */
 int hh_set_lists(hh_ctx *ctx, int64_t n_particles, int64_t n_j, int32_t n_groups,
                  const int64_t *off, const int32_t *idx, const int32_t *group_of);
 
 /* Per-particle block steps dt[n_particles] (powers of two).  hh_init_dt
  * derives them from the stored a and jk instead (dt = eta_s |a| / |jk|,
- * quantised).  Both set nothing else. */
+ * quantised).  Both set nothing else.  Errors: HH_ESTATE before
+ * hh_set_lists (which fixes n_particles); HH_EINVAL for a NULL dt or a step
+ * that is not a positive power of two (hh_set_dt, nothing is copied then). */
 int hh_set_dt(hh_ctx *ctx, const double *dt);
 int hh_init_dt(hh_ctx *ctx);
 
 /* Step 4 (GRAPE predictor): predicts every j entry to time t into the
  * context's predicted-record buffer: x + v D + a D^2/2 + jk D^3/6 and
- * v + a D + jk D^2/2, with D = t - t_entry. */
+ * v + a D + jk D^2/2, with D = t - t_entry.  Errors: HH_ESTATE before
+ * hh_set_lists; HH_EINVAL for a non-finite t. */
 int hh_predict(hh_ctx *ctx, double t);
 
 /* Steps 4a + 5: acc, jerk and potential on the n_act particles i_idx (indices
@@ -143,7 +159,14 @@ int hh_predict(hh_ctx *ctx, double t);
  * hh_predict, each particle summing over its group's list and skipping its
  * own entry.  Outputs host SoA acc[3][n_act], jerk[3][n_act], pot[n_act]
  * (any of them may be NULL).  The results also stay on the device for
- * hh_correct. */
+ * hh_correct.  hh_force_dev takes device arrays (i_idx included) used on the
+ * context's stream.  Errors: HH_ESTATE without lists, or when the j
+ * entries, lists or particle state changed (hh_set_j, hh_set_lists,
+ * hh_correct, hh_advance, hh_rebuild, a batch run) after the last
+ * prediction (hh_predict; hh_init_forces and hh_step also leave every entry
+ * predicted); HH_EINVAL for n_act outside [0, n_particles], a NULL i_idx
+ * (n_act > 0), or an index outside [0, n_particles) (hh_force also rejects
+ * repeats; hh_force_dev checks the range on the device); HH_ECUDA. */
 int hh_force(hh_ctx *ctx, int32_t n_act, const int32_t *i_idx, double *acc, double *jerk,
              double *pot);
 int hh_force_dev(hh_ctx *ctx, int32_t n_act, const int32_t *i_idx_dev, double *acc_dev,
@@ -153,23 +176,32 @@ int hh_force_dev(hh_ctx *ctx, int32_t n_act, const int32_t *i_idx_dev, double *a
  * last hh_force, then sets each one's new block step (Aarseth criterion,
  * power-of-two quantisation, at most doubling, doubling only on a boundary
  * of the doubled step, clamped to [dt_min, dt_max]) and its time to t.
- * Every particle of i_idx must have t_i + dt_i == t. */
+ * Every particle of i_idx must have t_i + dt_i == t.  Errors: HH_ESTATE
+ * without a hh_force and steps (hh_set_dt / hh_init_dt) before it; HH_EINVAL
+ * for bad i_idx as in hh_force, or for a particle that is not due at t
+ * (found on the device: that particle is left as it was, the others of the
+ * call are corrected); HH_ECUDA. */
 int hh_correct(hh_ctx *ctx, double t, int32_t n_act, const int32_t *i_idx);
 
 /* Initial forces: evaluates acc and jerk of ALL particles at their (common)
  * time t from the current j entries and lists and stores them as the
- * particles' a and jk (nodes are left unchanged). */
+ * particles' a and jk (nodes are left unchanged).  Errors: HH_ESTATE before
+ * hh_set_lists; HH_EINVAL for an error found on the device; HH_ECUDA. */
 int hh_init_forces(hh_ctx *ctx, double t);
 
 /* One block step on the device: t_next = min(t_i + dt_i); active particles
  * {t_i + dt_i == t_next}; predict; force; correct.  Returns t_next and the
- * number of active particles (synchronises the stream). */
+ * number of active particles (synchronises the stream).  Errors: HH_ESTATE
+ * without lists and steps; HH_EINVAL for an error found on the device;
+ * HH_ECUDA. */
 int hh_step(hh_ctx *ctx, double *t_next_out, int32_t *n_act_out);
 
 /* Block steps on the device until the next block time would exceed t_end,
  * without host round trips per step (CUDA graph of unrolled block steps,
  * replayed; each kernel becomes a no-op once done).  *n_steps_out (may be
- * NULL) receives the number of block steps taken. */
+ * NULL) receives the number of block steps taken.  Errors: HH_ESTATE
+ * without lists and steps; HH_EINVAL for a NaN t_end or an error found on
+ * the device; HH_ETIMEOUT if the replays stop making progress; HH_ECUDA. */
 int hh_advance(hh_ctx *ctx, double t_end, int64_t *n_steps_out);
 
 /* Step 1 done by the library: copies the (synchronised) particle state to
@@ -202,7 +234,11 @@ int hh_set_rebuild_device(hh_ctx *ctx, int on_device);
 
 /* Loads n particles (host SoA, any order) at time t with a = jk = 0 and
  * assigns them ids 0..n-1; hh_get_ids reports each slot's id after Morton
- * reordering. */
+ * reordering.  Any lists, steps and forces of an earlier load are dropped
+ * (calls that need lists return HH_ESTATE until hh_rebuild or hh_run).
+ * Errors: HH_EINVAL for n < 2, n above n_max, a NULL array, a non-finite
+ * position or velocity, a mass that is not finite and positive, or a
+ * non-finite t (nothing is copied then); HH_ECUDA if the copy fails. */
 int hh_load_particles(hh_ctx *ctx, int64_t n, const double *x, const double *v, const double *m,
                       double t);
 
@@ -212,15 +248,19 @@ int hh_load_particles(hh_ctx *ctx, int64_t n, const double *x, const double *v, 
  * every dt_tree. */
 int hh_run(hh_ctx *ctx, double t0, double t_end);
 
-/* Copies particle state [0, n_particles) to host SoA arrays (any may be NULL). */
+/* Copies particle state [0, n_particles) to host SoA arrays (any may be
+ * NULL).  Errors: HH_ESTATE before any particles are loaded; HH_ECUDA. */
 int hh_get_state(hh_ctx *ctx, double *x, double *v, double *a, double *jk, double *t, double *dt);
 int hh_get_ids(hh_ctx *ctx, int64_t *ids);
 /* The current lists (step 1 output): group count, list length, and host
  * copies of off[n_groups + 1], idx[list_len], group_of[n_particles] (any
- * array may be NULL; call with NULL arrays first to size them). */
+ * array may be NULL; call with NULL arrays first to size them).  Errors:
+ * HH_ESTATE when there are no valid lists (none set, or a failed rebuild);
+ * HH_ECUDA. */
 int hh_get_lists(hh_ctx *ctx, int32_t *n_groups, int64_t *list_len, int64_t *off, int32_t *idx, int32_t *group_of);
 /* Host SoA copies of j entries [first, first + count): x, v, a, jk [3][count],
- * m, t [count] (any may be NULL), e.g. the node records after a rebuild. */
+ * m, t [count] (any may be NULL), e.g. the node records after a rebuild.
+ * Errors: HH_EINVAL for a range outside [0, n_j); HH_ECUDA. */
 int hh_get_j(hh_ctx *ctx, int64_t first, int64_t count, double *x, double *v, double *a, double *jk, double *m,
              double *t);
 int64_t hh_n_particles(const hh_ctx *ctx);
@@ -230,12 +270,15 @@ int hh_reset_counters(hh_ctx *ctx);
 /* Active i tiles by their number of active particles: counts[k] = tiles
  * evaluated with k + 1 active particles, summed over block steps since the
  * last reset (the distribution of the paper's n_i, Eq. 3, per staged list
- * chunk). */
+ * chunk).  Errors: HH_EINVAL for NULL counts, or for an error found on the
+ * device since the last check (returned once, then cleared); HH_ECUDA. */
 int hh_get_tile_histogram(hh_ctx *ctx, int64_t counts[32]);
 
 /* Kernel-time accounting: CUDA-event time (ms) of the list-force kernel
- * launches since the last reset, and their number.  Events are recorded on
- * the stream the kernels run on. */
+ * launches since the last reset, and their number (*ms_out and
+ * *launches_out, each may be NULL).  enable >= 0 then switches the timing on
+ * (1) or off (0) and resets both; enable < 0 only reads.  Events are recorded
+ * on the stream the kernels run on.  Errors: HH_EINVAL for a NULL context. */
 int hh_force_timing(hh_ctx *ctx, int enable, double *ms_out, int64_t *launches_out);
 
 /* Total number of kernels this library launched in the process (all
@@ -304,7 +347,9 @@ int hh_barrier_selftest(int device, int skip_cta, double *elapsed_s);
  * T = |a3|^2 (host arrays of n doubles, caller-owned) and eta.  Where the
  * device decides in FP32 the value is the exact power of two at or below
  * sqrt(eta (sqrt(A S) + J) / (sqrt(J T) + S)) evaluated in FP64; elsewhere it
- * is that FP64 value.  n <= 2^26; synchronises. */
+ * is that FP64 value.  n <= 2^26; synchronises.  Errors: HH_EINVAL for
+ * n < 0, n > 2^26 or a NULL array (n > 0); HH_ECUDA for a bad device or a
+ * failed launch; HH_ENOMEM if the device buffers do not fit. */
 int hh_selftest_aarseth(int device, int64_t n, const double *A, const double *J, const double *S, const double *T,
                         double eta, double *out);
 
@@ -313,7 +358,7 @@ int hh_selftest_aarseth(int device, int64_t n, const double *A, const double *J,
  * the old one, doubled only where the new time is a multiple of the doubled
  * step, clamped to [dt_min, dt_max]): out[i] = the device's step for want[i],
  * dt_old[i], t_new[i] (host arrays of n doubles, caller-owned).  n <= 2^26;
- * synchronises. */
+ * synchronises.  Errors: as hh_selftest_aarseth. */
 int hh_selftest_block_dt(int device, int64_t n, const double *want, const double *dt_old, const double *t_new,
                          double dt_min, double dt_max, double *out);
 
@@ -367,7 +412,13 @@ int hh_force_static(int device, int precision, double eps2, int64_t n_j, const d
  * one particle enters as that particle, any other cell enters as a node when
  * side < theta * (distance from its centre of mass to the group's bounding
  * box), otherwise it is opened (a leaf gives its particles).  Lists are
- * sorted ascending.  Node j index = n + cell number (cells in pre-order). */
+ * sorted ascending.  Node j index = n + cell number (cells in pre-order).
+ * The tree is host memory owned by the caller until hh_tree_free.  Errors
+ * (hh_tree_build*): HH_EINVAL for a NULL out or array, n outside
+ * [1, 2^30), leaf or n_crit < 1, theta < 0 or NaN, a non-finite position,
+ * velocity, acceleration or jerk, or a mass that is not positive and finite;
+ * HH_ENOMEM if host memory runs out.  The other calls return HH_EINVAL for
+ * a NULL tree; hh_tree_free accepts NULL. */
 typedef struct hh_tree hh_tree;
 int hh_tree_build(hh_tree **out, int64_t n, const double *x, const double *v, const double *a,
                   const double *jk, const double *m, int32_t leaf, int32_t n_crit, double theta);
@@ -377,7 +428,9 @@ int hh_tree_build_ordered(hh_tree **out, int64_t n, const double *x, const doubl
                           const double *jk, const double *m, int32_t leaf, int32_t n_crit, double theta,
                           int32_t order);
 int hh_tree_sizes(const hh_tree *t, int64_t *n_nodes, int32_t *n_groups, int64_t *list_len);
-/* perm[k] = input index of Morton slot k; node arrays SoA [3][n_nodes]. */
+/* perm[k] = input index of slot k in the tree's order; node arrays SoA
+ * [3][n_nodes], off[n_groups + 1], idx[list_len], group_of[n] (any may be
+ * NULL; hh_tree_sizes gives the sizes). */
 int hh_tree_export(const hh_tree *t, int32_t *perm, double *node_x, double *node_v,
                    double *node_a, double *node_jk, double *node_m, int64_t *off, int32_t *idx,
                    int32_t *group_of);
