@@ -104,6 +104,9 @@ void hh_config_default(hh_config *cfg);
  * not fit.  *out is NULL on failure; hh_last_error(NULL) then holds the reason. */
 int hh_create(hh_ctx **out, int device, const hh_config *cfg, int64_t n_max, int64_t nj_max,
               int64_t list_max, int32_t groups_max);
+/* Waits for the context's work, then frees everything it holds (a stream set
+ * with hh_set_stream stays the caller's).  A NULL context is accepted; the
+ * call returns HH_OK. */
 int hh_destroy(hh_ctx *ctx);
 
 /* Uses the given cudaStream_t (NULL = the context's own stream) for all
@@ -245,12 +248,17 @@ int hh_load_particles(hh_ctx *ctx, int64_t n, const double *x, const double *v, 
 /* Full run of the tree loop from the loaded state at time t0 to t_end
  * (a multiple of dt_tree): rebuild, initial forces, rebuild with node
  * derivatives, initial steps, then alternate hh_advance and hh_rebuild
- * every dt_tree. */
+ * every dt_tree.  Errors: HH_EINVAL unless t0 and t_end are multiples of
+ * dt_tree with t_end >= t0; otherwise the first failing call's code (the
+ * state is left where that call stopped). */
 int hh_run(hh_ctx *ctx, double t0, double t_end);
 
 /* Copies particle state [0, n_particles) to host SoA arrays (any may be
  * NULL).  Errors: HH_ESTATE before any particles are loaded; HH_ECUDA. */
 int hh_get_state(hh_ctx *ctx, double *x, double *v, double *a, double *jk, double *t, double *dt);
+/* ids[n_particles]: the id (input index at hh_load_particles) of each
+ * particle slot.  Errors: HH_EINVAL for a NULL context or array; HH_ECUDA if
+ * the ids kept on the device by a device rebuild cannot be copied. */
 int hh_get_ids(hh_ctx *ctx, int64_t *ids);
 /* The current lists (step 1 output): group count, list length, and host
  * copies of off[n_groups + 1], idx[list_len], group_of[n_particles] (any
@@ -263,8 +271,12 @@ int hh_get_lists(hh_ctx *ctx, int32_t *n_groups, int64_t *list_len, int64_t *off
  * Errors: HH_EINVAL for a range outside [0, n_j); HH_ECUDA. */
 int hh_get_j(hh_ctx *ctx, int64_t first, int64_t count, double *x, double *v, double *a, double *jk, double *m,
              double *t);
+/* Particles and j entries in use; -1 for a NULL context. */
 int64_t hh_n_particles(const hh_ctx *ctx);
 int64_t hh_n_j(const hh_ctx *ctx);
+/* Work counters since the last hh_reset_counters (synchronises).  Errors:
+ * HH_EINVAL for a NULL out, or for an error found on the device since the
+ * last check (returned once, then cleared); HH_ECUDA. */
 int hh_get_counters(hh_ctx *ctx, hh_counters *out);
 int hh_reset_counters(hh_ctx *ctx);
 /* Active i tiles by their number of active particles: counts[k] = tiles
@@ -282,7 +294,7 @@ int hh_get_tile_histogram(hh_ctx *ctx, int64_t counts[32]);
 int hh_force_timing(hh_ctx *ctx, int enable, double *ms_out, int64_t *launches_out);
 
 /* Total number of kernels this library launched in the process (all
- * contexts; graph replays count every kernel node). */
+ * contexts; graph replays count every kernel node).  Cannot fail. */
 int64_t hh_kernel_launches(void);
 
 const char *hh_last_error(const hh_ctx *ctx);
@@ -322,12 +334,25 @@ const char *hh_last_error(const hh_ctx *ctx);
  *   HH_EINVAL.  The loop keeps a per-simulation histogram of step levels
  *   and per-tile level masks, so a block step touches only the due tiles. */
 typedef struct hh_batch hh_batch;
+/* Errors of hh_batch_create (message in hh_last_error(NULL)): HH_EINVAL for a
+ * NULL out, a bad precision, max_sims or max_steps; HH_ECUDA for a bad device,
+ * one without cooperative launch, or a failed capture; HH_ENOMEM if its
+ * buffers do not fit.  Errors of hh_batch_run (message in
+ * hh_batch_last_error): HH_EINVAL for n outside [1, max_sims], a NULL array
+ * or context, max_steps outside [1, the batch's max_steps], a context that
+ * appears twice or differs in device or precision, a NaN t_end, or a state
+ * that breaks the block rule; HH_ESTATE for a context without lists or
+ * steps, or a batch whose launch could not be captured again
+ * (hh_batch_set_ctas); HH_ENOMEM if the work queue cannot grow to the
+ * contexts' tiles; HH_ETIMEOUT for a grid-barrier wait that gave up;
+ * HH_ECUDA. */
 int hh_batch_create(hh_batch **out, int device, int precision, int32_t max_sims, int32_t max_steps);
 /* Number of persistent CTAs (one per SM) of the batch's launches: n_ctas > 0
  * uses that many SMs, n_ctas <= 0 all SMs but |n_ctas|, which stay free for
  * other streams' kernels (tree rebuilds of simulations outside the launch).
  * The default is every SM.  HH_EINVAL outside [1, SM count]. */
 int hh_batch_set_ctas(hh_batch *b, int32_t n_ctas);
+/* Waits for the batch's work and frees it; a NULL batch is accepted. */
 int hh_batch_destroy(hh_batch *b);
 int hh_batch_run(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const double *t_end, int32_t max_steps,
                  int32_t *steps_out, double *t_next_out, double *step_us_out, double *phase_us_out);
@@ -362,7 +387,8 @@ int hh_selftest_aarseth(int device, int64_t n, const double *A, const double *J,
 int hh_selftest_block_dt(int device, int64_t n, const double *want, const double *dt_old, const double *t_new,
                          double dt_min, double dt_max, double *out);
 
-/* Device memory held by a context (bytes), for admission by memory budget. */
+/* Device memory held by a context (bytes), for admission by memory budget;
+ * -1 for a NULL context. */
 int64_t hh_ctx_device_bytes(const hh_ctx *ctx);
 
 /* ---- Allocation-free force call ---------------------------------------- */
