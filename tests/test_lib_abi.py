@@ -85,22 +85,52 @@ def test_host_tree_matches_oracle_exactly(hh, orc, n, theta, n_crit, salp, order
     np.testing.assert_allclose(P.node_jk.T, T.node_j, rtol=1e-15, atol=0)
 
 
-def test_host_tree_degenerate_inputs(hh):
-    # all particles at one point: the depth limit ends the split; one group
+def _degenerate_positions():
+    rng = np.random.default_rng(0)
+    grid = np.stack(np.meshgrid(*[np.arange(4.0)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    return {
+        "one": np.array([[0.3, -0.2, 0.1]]),
+        "two": np.array([[0.0, 0.0, 0.0], [1e-9, 0.0, 0.0]]),
+        # all at one point: the depth limit (21) ends the split with one leaf
+        "coincident": np.zeros((20, 3)),
+        # a clump far below the finest cell of the root cube, and one outlier
+        "clump_outlier": np.concatenate([rng.normal(size=(50, 3)) * 1e-7, [[1e3, 1e3, 1e3]]]),
+        # ties on every cell boundary
+        "grid": grid,
+    }
+
+
+@pytest.mark.parametrize("case", list(_degenerate_positions()))
+@pytest.mark.parametrize("leaf,n_crit,theta", [(8, 4, 0.5), (1, 1, 0.75), (8, 64, 0.0)])
+def test_host_tree_degenerate_inputs_match_oracle(hh, orc, case, leaf, n_crit, theta):
+    x = _degenerate_positions()[case]
+    n = len(x)
+    rng = np.random.default_rng(1)
+    v, a, j = (rng.normal(size=(n, 3)) for _ in range(3))
+    m = rng.uniform(0.5, 1.5, n)
+    T = orc.tree_build(x, v, a, j, m, leaf=leaf, n_crit=n_crit, theta=theta)
+    P = hh.hh_tree_build(_soa(x), _soa(v), _soa(a), _soa(j), m, leaf=leaf, n_crit=n_crit, theta=theta)
+    assert np.array_equal(P.perm, T.perm) and P.n_nodes == T.n_cells
+    assert np.array_equal(P.off, T.list_off) and np.array_equal(P.idx, T.list_idx)
+    assert np.array_equal(P.group_of, T.group_of)
+    assert np.array_equal(P.node_m, T.node_m) and np.array_equal(P.node_x.T, T.node_x)
+
+
+def test_host_tree_rejects_bad_inputs(hh):
     n = 20
     x = np.zeros((3, n))
     v = np.zeros((3, n))
     m = np.full(n, 1.0 / n)
-    P = hh.hh_tree_build(x, v, v, v, m, leaf=8, n_crit=4, theta=0.5)
-    assert sorted(P.perm) == list(range(n))
-    assert np.all(np.diff(P.off) >= n) or P.n_groups >= 1
-    # bad inputs are rejected, not crashed on
     with pytest.raises(hh.HHError):
         hh.hh_tree_build(x, v, v, v, np.zeros(n))
     xx = x.copy()
     xx[0, 3] = np.nan
     with pytest.raises(hh.HHError):
         hh.hh_tree_build(xx, v, v, v, m)
+    with pytest.raises(hh.HHError):
+        hh.hh_tree_build(x, v, v, v, m, theta=-0.1)
+    with pytest.raises(hh.HHError):
+        hh.hh_tree_build(x, v, v, v, m, leaf=0)
 
 
 def test_autotuner_candidates_are_valid_configurations(hh):
