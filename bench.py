@@ -179,7 +179,7 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def _peaks(hh_dir):
+def _peaks(hh_dir, device=0):
     """Measured FMA peaks (TFLOP/s) from libhh_peaks.so, plus the measured HBM / bf16 figures (MEASURED_PEAKS.json)."""
     out = {}
     lib = C.CDLL(os.path.join(hh_dir, "libhh_peaks.so"))
@@ -188,14 +188,15 @@ def _peaks(hh_dir):
         best = 0.0
         for _ in range(3):
             v = C.c_double()
-            if lib.hh_fma_peak(0 if "CUDA_VISIBLE_DEVICES" in os.environ else 0, fp64, iters, C.byref(v)) == 0:
+            if lib.hh_fma_peak(device, fp64, iters, C.byref(v)) == 0:
                 best = max(best, v.value)
         out[name] = best
     try:
-        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mp = json.load(f)
         out["hbm_gbs"] = mp.get("hbm_gbs")
         out["bf16_tflops"] = mp.get("bf16_tflops")
-    except OSError:
+    except (OSError, ValueError):
         out["hbm_gbs"] = None
     return out
 
@@ -538,7 +539,7 @@ def main():
         dist.barrier()
     import paper_1602_02832_gb300 as hh
 
-    peaks = _peaks(os.path.dirname(hh.LIB_PATH)) if rank == 0 else {}
+    peaks = _peaks(os.path.dirname(hh.LIB_PATH), local) if rank == 0 else {}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     if a.mixed_only:
         r = _run_form(hh, torch, a, hh.HH_MIXED, rank, a.steps, a.warmup, flush)

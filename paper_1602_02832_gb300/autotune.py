@@ -92,7 +92,8 @@ def tune(x, v, m, base_cfg, intervals=1, warm=1, use_cache=True, device_name=Non
     cache = {}
     if use_cache and os.path.exists(_CACHE):
         try:
-            cache = json.load(open(_CACHE))
+            with open(_CACHE) as f:
+                cache = json.load(f)
         except (OSError, ValueError):
             cache = {}
         if key in cache:
