@@ -85,7 +85,8 @@ static void force_on(int i, int n, const double *x, const double *v, const doubl
     *pot = p;
 }
 
-/* Original GRAPE-6 Hermite loop, step 5: force from all other particles. */
+/* Section 2, the original (GRAPE-6) Hermite loop, step 5: force from all
+ * other particles. */
 void hho_direct_force(int n, const double *x, const double *v, const double *m,
                       double eps2, double *acc, double *jerk, double *pot)
 {
@@ -103,7 +104,8 @@ void hho_direct_force_subset(int n, const double *x, const double *v, const doub
         force_on(i_idx[k], n, x, v, m, eps2, &acc[3 * k], &jerk[3 * k], &pot[k]);
 }
 
-/* Tree loop, steps 4a and 5: the force on i from its group's list only. */
+/* Section 2, tree loop steps 4a and 5: the force on i from its group's list
+ * only (nodes enter as particles at their predicted centre of mass). */
 void hho_list_force(int n_j, const double *xj, const double *vj, const double *mj,
                     int n_act, const int32_t *i_idx, const int32_t *gid,
                     const int64_t *list_off, const int32_t *list_idx, double eps2,
@@ -231,8 +233,9 @@ double hho_initial_dt(double eta_s, const double a[3], const double j[3],
 }
 
 /* ------------------------------------------------------------------------ */
-/* Morton octree (reading: the paper orders particles along a Peano-Hilbert  */
-/* curve; this oracle uses Morton order, 21 bits per axis).                  */
+/* Section 2, tree loop step 1: the octree.  Morton order by default        */
+/* (reading: the paper orders particles along a Peano-Hilbert curve, which  */
+/* hho_tree_build_ordered offers; 21 bits per axis either way).              */
 /*   root cube: lo_c = min_k x_kc, S = max_c (max_k x_kc - lo_c) (1 if 0);   */
 /*   key digit at level l (0 = coarsest) is (bx<<2)|(by<<1)|bz of bit 20-l;  */
 /*   u_c = floor((x_c - lo_c) * (2^21 / S)), clamped to [0, 2^21 - 1];      */
