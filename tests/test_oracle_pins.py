@@ -424,6 +424,36 @@ def test_tree_step_count_close_to_direct(orc):
     assert abs(r[0.75, 1024] - 1.042) < 0.1
 
 
+_THREADS_SCRIPT = """
+import sys, numpy as np
+sys.path.insert(0, sys.argv[1])
+import oracle, synth
+x, v, m = synth.plummer_salpeter(600, 12)
+r = oracle.run(x, v, m, 1.0 / 32, oracle.RunParams(eps2=1e-6, n_crit=32, theta=0.6))
+a, j, p = oracle.direct_force(x, v, m, 1e-6)
+np.save(sys.argv[2], np.concatenate([r["x"].ravel(), r["v"].ravel(), r["t"], r["dt"], a.ravel(), p,
+                                     [r["stats"]["interactions"], oracle.num_threads()]]))
+"""
+
+
+def test_results_do_not_depend_on_thread_count(orc, tmp_path):
+    # OpenMP only splits independent particles or groups, so one thread and
+    # many give the same bits (a reduction whose order followed the thread
+    # count would break this)
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = {}
+    for k in ("1", "4"):
+        env = dict(os.environ, OMP_NUM_THREADS=k)
+        subprocess.run([sys.executable, "-c", _THREADS_SCRIPT, root, str(tmp_path / k)], env=env, check=True,
+                       timeout=300)
+        out[k] = np.load(tmp_path / (k + ".npy"))
+    assert out["1"][-1] == 1 and out["4"][-1] == 4
+    assert np.array_equal(out["1"][:-1], out["4"][:-1])
+
+
 def test_plummer_standard_units(orc):
     # Standard units M = G = -4E = 1 (Section 3): with 16k particles E = -1/4
     # and 2K = -W = 1/2 within sampling noise (the 0.999 mass cap binds a
