@@ -158,3 +158,18 @@ def test_autotuner_candidates_are_valid_configurations(hh):
     with pytest.raises(hh.HHError) as e:
         hh.Context(c, 16, 32, 64, 4)
     assert e.value.code == hh.HH_EINVAL
+
+
+@pytest.mark.parametrize("lang,std", [("c", "c99"), ("c++", "c++17")])
+def test_header_is_plain_c_and_cpp(lang, std):
+    # the boundary header compiles on its own as C99 and as C++ without warnings
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    r = subprocess.run([cc, f"-std={std}", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-x", lang,
+                        os.path.join(inc, "hh.h")], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
