@@ -173,3 +173,19 @@ def test_header_is_plain_c_and_cpp(lang, std):
     r = subprocess.run([cc, f"-std={std}", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-x", lang,
                         os.path.join(inc, "hh.h")], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
+
+
+def test_binding_constants_match_header(hh):
+    # every #define of the header has the same value in the binding, and every
+    # error code has a name for HHError messages
+    import re
+
+    with open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "hh.h")) as f:
+        hdr = f.read()
+    defs = {k: int(v) for k, v in re.findall(r"#define (HH_[A-Z0-9_]+) \(?(-?\d+)\)?", hdr)}
+    assert {"HH_OK", "HH_EINVAL", "HH_ESTATE", "HH_MIXED", "HH_ORDER_HILBERT"} <= set(defs)
+    for k, v in defs.items():
+        assert getattr(hh, k) == v, k
+    for k, v in defs.items():
+        if k.startswith("HH_E"):
+            assert hh.HHError(v, "x").args[0].startswith(k + ":"), k
