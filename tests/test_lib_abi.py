@@ -189,3 +189,22 @@ def test_binding_constants_match_header(hh):
     for k, v in defs.items():
         if k.startswith("HH_E"):
             assert hh.HHError(v, "x").args[0].startswith(k + ":"), k
+
+
+@pytest.mark.parametrize("sname", ["hh_config", "hh_counters"])
+def test_binding_structs_match_header(hh, sname):
+    # field names, order and sizes of the ctypes structures follow the header
+    import ctypes as C
+    import re
+
+    with open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "hh.h")) as f:
+        hdr = f.read()
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (sname, sname), hdr, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"(double|int32_t|int64_t)\s+([a-z_0-9]+)\s*;", body)
+    size = {"double": 8, "int32_t": 4, "int64_t": 8}
+    cls = getattr(hh, sname)
+    assert [n for n, _ in cls._fields_] == [n for _, n in fields]
+    assert [C.sizeof(t) for _, t in cls._fields_] == [size[t] for t, _ in fields]
+    assert all(t is not C.c_float for _, t in cls._fields_)
+    assert [t in (C.c_double,) for _, t in cls._fields_] == [t == "double" for t, _ in fields]
