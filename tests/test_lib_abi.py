@@ -208,3 +208,43 @@ def test_binding_structs_match_header(hh, sname):
     assert [C.sizeof(t) for _, t in cls._fields_] == [size[t] for t, _ in fields]
     assert all(t is not C.c_float for _, t in cls._fields_)
     assert [t in (C.c_double,) for _, t in cls._fields_] == [t == "double" for t, _ in fields]
+
+
+def _kind_c(decl):
+    decl = decl.strip()
+    if "*" in decl or "[" in decl:
+        return "ptr"
+    base = decl.replace("const ", "").split()[0]
+    return {"double": "f64", "int": "i32", "int32_t": "i32", "int64_t": "i64", "void": "void"}[base]
+
+
+def _kind_ctypes(t):
+    import ctypes as C
+
+    if t is None:
+        return "void"
+    if t in (C.c_void_p, C.c_char_p) or hasattr(t, "_type_") and isinstance(t._type_, type):
+        return "ptr"
+    if t is C.c_double:
+        return "f64"
+    return {4: "i32", 8: "i64"}[C.sizeof(t)]
+
+
+def test_binding_signatures_match_header(hh):
+    # return and argument kinds (pointer, double, 32- or 64-bit integer) of
+    # every bound call equal the header's prototype
+    import re
+
+    with open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "hh.h")) as f:
+        hdr = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+    protos = {}
+    for ret, name, args in re.findall(r"\n((?:const )?(?:int|void|int64_t|char)\s*\**)\s*(hh_\w+)\(([^)]*)\);", hdr):
+        args = [a for a in (s.strip() for s in args.split(",")) if a and a != "void"]
+        protos[name] = (_kind_c(ret), [_kind_c(a) for a in args])
+    assert len(protos) >= 40
+    sigs = hh._SIGS
+    assert set(sigs) <= set(protos), set(sigs) - set(protos)
+    for name, (res, args) in sigs.items():
+        want_res, want_args = protos[name]
+        assert _kind_ctypes(res) == want_res, name
+        assert [_kind_ctypes(a) for a in args] == want_args, name
