@@ -383,6 +383,26 @@ def test_block_quantisation_rules(orc):
     assert orc.initial_dt(0.01, a, np.zeros(3), 2.0 ** -30, 2.0 ** -3) == 2.0 ** -3
 
 
+def test_block_quantisation_equals_brute_force_search(orc):
+    # Section 2, step 6 block rule as a search: the largest power of two in
+    # [dt_min, dt_max] that is <= the request, at most twice the old step, and
+    # (when above the old step) divides the new time; dt_min if none is.
+    dt_min, dt_max = 2.0 ** -30, 2.0 ** -6
+    rng = np.random.default_rng(7)
+
+    def search(want, dt_old, t_new):
+        ok = [2.0 ** -k for k in range(6, 31)
+              if 2.0 ** -k <= want and 2.0 ** -k <= 2 * dt_old
+              and (2.0 ** -k <= dt_old or math.fmod(t_new, 2.0 ** -k) == 0.0)]
+        return min(max(max(ok, default=dt_min), dt_min), dt_max)
+
+    for i in range(3000):
+        dt_old = 2.0 ** -int(rng.integers(6, 31))
+        t_new = float(rng.integers(0, 2 ** 20)) * dt_old if i % 3 else float(rng.integers(0, 2 ** 30)) * dt_min
+        want = dt_old * 10.0 ** rng.uniform(-3, 3)
+        assert orc.block_dt(want, dt_old, t_new, dt_min, dt_max) == search(want, dt_old, t_new), (want, dt_old, t_new)
+
+
 def test_energy_conservation_direct_and_tree(orc):
     # Small softened Plummer run: the direct Hermite run conserves energy to
     # ~1e-8; theta = 0.3 stays close to it and theta = 0.75 drifts more
