@@ -88,6 +88,9 @@ def lib():
         L.hho_run.argtypes = [C.c_int, _D, _D, _D, C.c_double, C.POINTER(HhoParams), _D, _D, _D, _D,
                               C.POINTER(HhoStats)]
         L.hho_run.restype = C.c_int
+        L.hho_resume.argtypes = [C.c_int, _D, _D, _D, _D, _D, _D, C.c_double, C.c_double, C.POINTER(HhoParams),
+                                 C.POINTER(HhoStats)]
+        L.hho_resume.restype = C.c_int
         L.hho_energy.argtypes = [C.c_int, _D, _D, _D, C.c_double]
         L.hho_energy.restype = C.c_double
         L.hho_num_threads.restype = C.c_int
@@ -283,6 +286,24 @@ def run(x, v, m, t_end, params: RunParams):
     if rc != 0:
         raise RuntimeError(f"hho_run failed: {rc}")
     return dict(x=x, v=v, a=a, jk=jk, t=t, dt=dt,
+                stats=dict(block_steps=st.block_steps, particle_steps=st.particle_steps,
+                           interactions=st.interactions, rebuilds=st.rebuilds))
+
+
+def resume(x, v, a, jk, dt, m, t0, t_end, params: RunParams):
+    """The run continued from a synchronised state at t0 (a multiple of
+    dt_tree): x, v, a, jk [n, 3] and dt [n] of every particle at t0.  Returns
+    dict(x, v, a, jk, dt, stats) at t_end; the inputs are not modified."""
+    n = len(m)
+    x, v, a, jk = (_v3(u, n).copy() for u in (x, v, a, jk))
+    dt = np.ascontiguousarray(dt, dtype=np.float64).copy()
+    st = HhoStats()
+    cp = params.c()
+    rc = lib().hho_resume(n, x, v, a, jk, dt, np.ascontiguousarray(m, dtype=np.float64), float(t0), float(t_end),
+                          C.byref(cp), C.byref(st))
+    if rc != 0:
+        raise RuntimeError(f"hho_resume failed: {rc}")
+    return dict(x=x, v=v, a=a, jk=jk, dt=dt,
                 stats=dict(block_steps=st.block_steps, particle_steps=st.particle_steps,
                            interactions=st.interactions, rebuilds=st.rebuilds))
 

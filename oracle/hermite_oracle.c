@@ -727,36 +727,17 @@ static void eval_forces(int n, const double *x, const double *v, const double *a
     free(ia); free(gd); free(xp); free(vp);
 }
 
-int hho_run(int n, double *x, double *v, const double *m, double t_end,
-            const hho_params *p, double *a_out, double *jk_out, double *t_out, double *dt_out,
-            hho_stats *stats)
+/* Block steps from a synchronised state at t_tree (every t_i = t_tree) with
+ * forces a, jk at t_tree, steps dti and the tree view tv built at t_tree,
+ * until the next block time passes t_end.  Updates x, v, a, jk, ti, dti in
+ * place and adds to *st. */
+static int run_loop(int n, double *x, double *v, double *a, double *jk, double *ti, double *dti,
+                    const double *m, double t_tree, double t_end, const hho_params *p, tree_view *tv,
+                    hho_stats *st)
 {
-    if (n < 2 || p->dt_min <= 0.0 || p->dt_max < p->dt_min) return -1;
-    if (p->use_tree && (p->dt_max > p->dt_tree)) return -1;
-    hho_stats st = {0, 0, 0, 0};
-    double *a = calloc(3 * n, sizeof(double)), *jk = calloc(3 * n, sizeof(double));
-    double *ti = calloc(n, sizeof(double)), *dti = calloc(n, sizeof(double));
     double *acc = malloc(sizeof(double) * 3 * n), *jerk = malloc(sizeof(double) * 3 * n);
     double *pot = malloc(sizeof(double) * n);
     int32_t *act = malloc(sizeof(int32_t) * n);
-    tree_view tv;
-    memset(&tv, 0, sizeof(tv));
-    double t_tree = 0.0;
-
-    /* initial forces at t = 0, all particles */
-    for (int i = 0; i < n; i++) act[i] = i;
-    int64_t dummy = 0;
-    if (p->use_tree) view_build(&tv, n, x, v, a, jk, m, ti, 0.0, p);
-    eval_forces(n, x, v, a, jk, m, ti, 0.0, n, act, &tv, p, acc, jerk, pot, &dummy);
-    memcpy(a, acc, sizeof(double) * 3 * n);
-    memcpy(jk, jerk, sizeof(double) * 3 * n);
-    if (p->use_tree) {
-        view_free(&tv);
-        view_build(&tv, n, x, v, a, jk, m, ti, 0.0, p);
-        st.rebuilds++;
-    }
-    for (int i = 0; i < n; i++) dti[i] = hho_initial_dt(p->eta_s, &a[3 * i], &jk[3 * i], p->dt_min, p->dt_max);
-
     int rc = 0;
     for (;;) {
         double t_next = ti[0] + dti[0];
@@ -766,7 +747,7 @@ int hho_run(int n, double *x, double *v, const double *m, double t_end,
         int n_act = 0;
         for (int i = 0; i < n; i++)
             if (ti[i] + dti[i] == t_next) act[n_act++] = i;
-        eval_forces(n, x, v, a, jk, m, ti, t_next, n_act, act, &tv, p, acc, jerk, pot, &st.interactions);
+        eval_forces(n, x, v, a, jk, m, ti, t_next, n_act, act, tv, p, acc, jerk, pot, &st->interactions);
         for (int k = 0; k < n_act; k++) {
             int i = act[k];
             double d = t_next - ti[i];
@@ -788,25 +769,87 @@ int hho_run(int n, double *x, double *v, const double *m, double t_end,
             ti[i] = t_next;
             dti[i] = nd;
         }
-        st.block_steps++;
-        st.particle_steps += n_act;
+        st->block_steps++;
+        st->particle_steps += n_act;
         if (p->use_tree && t_next == t_tree + p->dt_tree) {
             for (int i = 0; i < n; i++)
                 if (ti[i] != t_next) rc = -2;
             if (rc) break;
-            view_free(&tv);
+            view_free(tv);
             t_tree = t_next;
-            view_build(&tv, n, x, v, a, jk, m, ti, t_tree, p);
-            st.rebuilds++;
+            view_build(tv, n, x, v, a, jk, m, ti, t_tree, p);
+            st->rebuilds++;
         }
     }
-    if (p->use_tree && tv.t) view_free(&tv);
+    free(acc); free(jerk); free(pot); free(act);
+    return rc;
+}
+
+static void copy_out(int n, const double *a, const double *jk, const double *ti, const double *dti,
+                     double *a_out, double *jk_out, double *t_out, double *dt_out)
+{
     if (a_out) memcpy(a_out, a, sizeof(double) * 3 * n);
     if (jk_out) memcpy(jk_out, jk, sizeof(double) * 3 * n);
     if (t_out) memcpy(t_out, ti, sizeof(double) * n);
     if (dt_out) memcpy(dt_out, dti, sizeof(double) * n);
+}
+
+int hho_run(int n, double *x, double *v, const double *m, double t_end,
+            const hho_params *p, double *a_out, double *jk_out, double *t_out, double *dt_out,
+            hho_stats *stats)
+{
+    if (n < 2 || p->dt_min <= 0.0 || p->dt_max < p->dt_min) return -1;
+    if (p->use_tree && (p->dt_max > p->dt_tree)) return -1;
+    hho_stats st = {0, 0, 0, 0};
+    double *a = calloc(3 * n, sizeof(double)), *jk = calloc(3 * n, sizeof(double));
+    double *ti = calloc(n, sizeof(double)), *dti = calloc(n, sizeof(double));
+    double *acc = malloc(sizeof(double) * 3 * n), *jerk = malloc(sizeof(double) * 3 * n);
+    double *pot = malloc(sizeof(double) * n);
+    int32_t *act = malloc(sizeof(int32_t) * n);
+    tree_view tv;
+    memset(&tv, 0, sizeof(tv));
+
+    /* initial forces at t = 0, all particles */
+    for (int i = 0; i < n; i++) act[i] = i;
+    int64_t dummy = 0;
+    if (p->use_tree) view_build(&tv, n, x, v, a, jk, m, ti, 0.0, p);
+    eval_forces(n, x, v, a, jk, m, ti, 0.0, n, act, &tv, p, acc, jerk, pot, &dummy);
+    memcpy(a, acc, sizeof(double) * 3 * n);
+    memcpy(jk, jerk, sizeof(double) * 3 * n);
+    if (p->use_tree) {
+        view_free(&tv);
+        view_build(&tv, n, x, v, a, jk, m, ti, 0.0, p);
+        st.rebuilds++;
+    }
+    for (int i = 0; i < n; i++) dti[i] = hho_initial_dt(p->eta_s, &a[3 * i], &jk[3 * i], p->dt_min, p->dt_max);
+
+    int rc = run_loop(n, x, v, a, jk, ti, dti, m, 0.0, t_end, p, &tv, &st);
+    if (p->use_tree && tv.t) view_free(&tv);
+    copy_out(n, a, jk, ti, dti, a_out, jk_out, t_out, dt_out);
     if (stats) *stats = st;
     free(a); free(jk); free(ti); free(dti); free(acc); free(jerk); free(pot); free(act);
+    return rc;
+}
+
+/* The same loop continued from a synchronised state at t0 = k dt_tree (every
+ * particle at t0 with its forces a, jk there and its block step dt): step 1
+ * rebuilds the tree from that state (Section 2), then block steps follow as
+ * in hho_run until t_end.  x, v, a, jk, dt are updated in place. */
+int hho_resume(int n, double *x, double *v, double *a, double *jk, double *dt, const double *m, double t0,
+               double t_end, const hho_params *p, hho_stats *stats)
+{
+    if (n < 2 || p->dt_min <= 0.0 || p->dt_max < p->dt_min || !(t_end >= t0)) return -1;
+    if (p->use_tree && (p->dt_max > p->dt_tree || floor(t0 / p->dt_tree) != t0 / p->dt_tree)) return -1;
+    hho_stats st = {0, 0, 0, 0};
+    double *ti = malloc(sizeof(double) * n);
+    for (int i = 0; i < n; i++) ti[i] = t0;
+    tree_view tv;
+    memset(&tv, 0, sizeof(tv));
+    if (p->use_tree) view_build(&tv, n, x, v, a, jk, m, ti, t0, p);
+    int rc = run_loop(n, x, v, a, jk, ti, dt, m, t0, t_end, p, &tv, &st);
+    if (p->use_tree && tv.t) view_free(&tv);
+    if (stats) *stats = st;
+    free(ti);
     return rc;
 }
 

@@ -117,6 +117,14 @@ int hho_run(int n, double *x, double *v, const double *m, double t_end,
             const hho_params *p, double *a, double *jk, double *t, double *dt,
             hho_stats *stats);
 
+/* hho_run continued from a synchronised state at t0, a multiple of dt_tree:
+ * every particle at t0 with its forces a, jk there and its block step dt.
+ * The tree is rebuilt from that state (Section 2, step 1) and block steps
+ * follow until t_end; x, v, a, jk, dt are updated in place.  Resuming the
+ * state hho_run reached at t0 gives the same result as one hho_run. */
+int hho_resume(int n, double *x, double *v, double *a, double *jk, double *dt, const double *m, double t0,
+               double t_end, const hho_params *p, hho_stats *stats);
+
 /* Total energy: kinetic plus the direct-summation softened potential energy. */
 double hho_energy(int n, const double *x, const double *v, const double *m, double eps2);
 

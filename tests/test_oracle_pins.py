@@ -475,6 +475,28 @@ def test_results_do_not_depend_on_thread_count(orc):
     assert np.array_equal(out["1"][:-1], out["4"][:-1])
 
 
+def test_resume_continues_the_run_exactly(orc):
+    # Step 1 rebuilds the tree from the synchronised state at every t_tree
+    # (Section 2), so the state at a rebuild time (x, v, a, jerk, dt of every
+    # particle) determines the rest of the run: stopping at t_tree and
+    # resuming there gives the bits of one uninterrupted run, and the step,
+    # interaction and rebuild counts add up.
+    x, v, m = synth.plummer(700, 41)
+    p = orc.RunParams(eps2=1e-6, eta=0.02, theta=0.5, n_crit=32)
+    dtt = p.dt_tree
+    whole = orc.run(x, v, m, 3 * dtt, p)
+    first = orc.run(x, v, m, dtt, p)
+    assert np.all(first["t"] == dtt)
+    rest = orc.resume(first["x"], first["v"], first["a"], first["jk"], first["dt"], m, dtt, 3 * dtt, p)
+    for k in ("x", "v", "a", "jk", "dt"):
+        assert np.array_equal(rest[k], whole[k]), k
+    for k in ("block_steps", "particle_steps", "interactions", "rebuilds"):
+        assert first["stats"][k] + rest["stats"][k] == whole["stats"][k], k
+    # a start that is not a rebuild time is refused
+    with pytest.raises(RuntimeError):
+        orc.resume(first["x"], first["v"], first["a"], first["jk"], first["dt"], m, dtt / 2, 3 * dtt, p)
+
+
 def test_plummer_standard_units(orc):
     # Standard units M = G = -4E = 1 (Section 3): with 16k particles E = -1/4
     # and 2K = -W = 1/2 within sampling noise (the 0.999 mass cap binds a
