@@ -392,8 +392,8 @@ int hh_selftest_block_dt(int device, int64_t n, const double *want, const double
 int64_t hh_ctx_device_bytes(const hh_ctx *ctx);
 
 /* ---- Allocation-free force call ---------------------------------------- */
-/* The paper has no counterpart to this call.  It is the list force of steps
- * 4a + 5 (the same kernel as hh_force) for callers that cannot allocate
+/* The paper has no counterpart to this call.  It computes the same list
+ * force as hh_force, with the same kernel, for callers that cannot allocate
  * device memory: code whose device memory all comes from another allocator
  * or pool, and loops that must not call cudaMalloc / cudaFree because those
  * calls synchronise the whole device.  It calls no cudaMalloc, cudaFree or
@@ -425,7 +425,9 @@ int64_t hh_ctx_device_bytes(const hh_ctx *ctx);
  * keeps the last call's contents; each call clears what must start at zero.
  * Calls whose kernels overlap on the GPU (other streams, other host threads)
  * race on the scratch and must be serialised by the caller.  The call
- * synchronises `stream` before it returns. */
+ * synchronises `stream` before it returns.  `stream` must belong to
+ * `device`; the calling thread's current device is the same after the call
+ * as before it. */
 int hh_force_static(int device, int precision, double eps2, int64_t n_j, const double *xj, const double *vj,
                     const double *mj, int32_t n_groups, const int64_t *off, const int32_t *idx, int32_t n_act,
                     const int32_t *i_idx, const int32_t *gid, double *acc, double *jerk, double *pot,

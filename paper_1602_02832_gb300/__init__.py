@@ -385,15 +385,52 @@ def hh_tree_build(x, v, a, jk, m, leaf=8, n_crit=64, theta=0.5, order=0) -> Tree
     return Tree(perm, nx, nv, na, nj, nm, off, idx[:ll], gof)
 
 
+_STATIC_DTYPES = {"xj": "float64", "vj": "float64", "mj": "float64", "off": "int64", "idx": "int32",
+                  "i_idx": "int32", "gid": "int32", "acc": "float64", "jerk": "float64", "pot": "float64"}
+
+
+def _static_check_args(device, **t):
+    """Dtype, element count and device of every hh_force_static tensor, checked
+    before the call: the C function trusts the pointers and sizes it gets, so a
+    wrong dtype or a short buffer would make its kernels read or write past the
+    caller's memory."""
+    for name, u in t.items():
+        if not hasattr(u, "numel") or not hasattr(u, "dtype"):
+            raise ValueError(f"hh_force_static: {name} must be a tensor")
+        want = _STATIC_DTYPES[name]
+        if str(u.dtype).replace("torch.", "") != want:
+            raise ValueError(f"hh_force_static: {name} must be {want}, got {u.dtype}")
+        if not u.is_contiguous():
+            raise ValueError(f"hh_force_static: {name} must be contiguous")
+    n_j = t["mj"].numel()
+    n_groups = t["off"].numel() - 1
+    n_act = t["i_idx"].numel()
+    sizes = {"xj": 3 * n_j, "vj": 3 * n_j, "gid": n_act, "acc": 3 * n_act, "jerk": 3 * n_act, "pot": n_act}
+    for name, want in sizes.items():
+        if t[name].numel() != want:
+            raise ValueError(f"hh_force_static: {name} has {t[name].numel()} elements, expected {want}")
+    if n_groups < 1:
+        raise ValueError("hh_force_static: off needs at least two elements (n_groups >= 1)")
+    for name, u in t.items():
+        if not u.is_cuda or u.device.index != int(device):
+            raise ValueError(f"hh_force_static: {name} must be on cuda:{int(device)}, got {u.device}")
+    # the list length off[n_groups] must fit idx (one small device-to-host read)
+    list_len = int(t["off"][-1].item())
+    if list_len > t["idx"].numel():
+        raise ValueError(f"hh_force_static: off[-1] = {list_len} exceeds idx's {t['idx'].numel()} elements")
+    return n_j, n_groups, n_act
+
+
 def hh_force_static(xj, vj, mj, off, idx, i_idx, gid, acc, jerk, pot, eps2=1e-8, precision=HH_FP64, device=0,
                     stream=None):
-    """Allocation-free list force on caller-owned device arrays (CUDA tensors
-    or raw device pointers; shapes as in include/hh.h).  Raises HHError."""
-    n_j = mj.numel() if hasattr(mj, "numel") else None
-    n_groups = (off.numel() - 1) if hasattr(off, "numel") else None
-    n_act = i_idx.numel() if hasattr(i_idx, "numel") else None
-    if n_j is None or n_groups is None or n_act is None:
-        raise ValueError("pass tensors for mj, off and i_idx (sizes are taken from them)")
+    """Allocation-free list force on caller-owned torch CUDA tensors (shapes
+    and dtypes as in include/hh.h: float64 xj, vj [3, n_j], mj [n_j], acc,
+    jerk [3, n_act], pot [n_act]; int64 off [n_groups + 1]; int32 idx,
+    i_idx, gid).  Sizes are taken from mj, off and i_idx; every tensor is
+    checked for dtype, element count and device before the call (ValueError).
+    Raises HHError for the library's own errors."""
+    n_j, n_groups, n_act = _static_check_args(device, xj=xj, vj=vj, mj=mj, off=off, idx=idx, i_idx=i_idx, gid=gid,
+                                              acc=acc, jerk=jerk, pot=pot)
     s = stream if isinstance(stream, int) else (stream.cuda_stream if stream is not None else None)
     _check(_lib.hh_force_static(int(device), int(precision), float(eps2), n_j, _dev_ptr(xj), _dev_ptr(vj),
                                 _dev_ptr(mj), n_groups, _dev_ptr(off), _dev_ptr(idx), n_act, _dev_ptr(i_idx),

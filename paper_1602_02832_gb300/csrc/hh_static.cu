@@ -161,6 +161,17 @@ __global__ void k_static_finish(DevScalars *ds)
     ds->part_len = kStaticPartLen;
 }
 
+// Restores the current device of the calling thread when it goes out of scope.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    DeviceGuard() { ok = cudaGetDevice(&prev) == cudaSuccess; }
+    ~DeviceGuard()
+    {
+        if (ok) cudaSetDevice(prev);
+    }
+};
+
 }  // namespace
 
 extern "C" int hh_force_static(int device, int precision, double eps2, int64_t n_j, const double *xj,
@@ -179,6 +190,9 @@ extern "C" int hh_force_static(int device, int precision, double eps2, int64_t n
     if (n_groups < 1) return hh_set_global_error(HH_EINVAL, "hh_force_static: n_groups must be >= 1");
     if (!xj || !vj || !mj || !off || !idx || (n_act > 0 && (!i_idx || !gid || !acc || !jerk || !pot)))
         return hh_set_global_error(HH_EINVAL, "hh_force_static: NULL array");
+    // the caller's current device is put back on every return
+    DeviceGuard guard;
+    if (!guard.ok) return hh_set_global_error(HH_ECUDA, "hh_force_static: cudaGetDevice failed");
     if (cudaSetDevice(device) != cudaSuccess) return hh_set_global_error(HH_ECUDA, "hh_force_static: cudaSetDevice failed");
     DeviceSetup &st = g_setup[device];
     std::call_once(st.once, [&] { setup_device(device, st); });

@@ -248,3 +248,54 @@ def test_binding_signatures_match_header(hh):
         want_res, want_args = protos[name]
         assert _kind_ctypes(res) == want_res, name
         assert [_kind_ctypes(a) for a in args] == want_args, name
+
+
+def test_force_static_binding_rejects_bad_tensors_before_any_call(hh, monkeypatch):
+    # hh_force_static trusts its pointers and sizes, so the binding checks the
+    # dtype, element count and device of every tensor first (ValueError).  The
+    # C function is replaced by a recorder: none of these cases may reach it.
+    torch = pytest.importorskip("torch")
+    calls = []
+    monkeypatch.setattr(hh, "_lib", _Recorder(hh._lib, calls))
+    nj, na = 6, 2
+    good = dict(xj=torch.zeros((3, nj), dtype=torch.float64), vj=torch.zeros((3, nj), dtype=torch.float64),
+                mj=torch.ones(nj, dtype=torch.float64), off=torch.tensor([0, 3], dtype=torch.int64),
+                idx=torch.tensor([0, 1, 2], dtype=torch.int32), i_idx=torch.tensor([0, 1], dtype=torch.int32),
+                gid=torch.zeros(na, dtype=torch.int32), acc=torch.zeros((3, na), dtype=torch.float64),
+                jerk=torch.zeros((3, na), dtype=torch.float64), pot=torch.zeros(na, dtype=torch.float64))
+    bad_cases = [
+        ("off", torch.tensor([0, 3], dtype=torch.int32), "int64"),
+        ("idx", torch.tensor([0, 1, 2], dtype=torch.int64), "int32"),
+        ("mj", torch.ones(nj, dtype=torch.float32), "float64"),
+        ("gid", torch.zeros(na, dtype=torch.int64), "int32"),
+        ("acc", torch.zeros((3, na + 1), dtype=torch.float64), "elements"),
+        ("xj", torch.zeros((3, nj - 1), dtype=torch.float64), "elements"),
+        ("pot", torch.zeros(na + 1, dtype=torch.float64), "elements"),
+        ("jerk", torch.zeros((na, 3), dtype=torch.float64).t(), "contiguous"),
+        ("xj", None, "tensor"),
+    ]
+    for name, val, word in bad_cases:
+        args = dict(good, **{name: val})
+        with pytest.raises(ValueError) as e:
+            hh.hh_force_static(**args)
+        assert word in str(e.value), (name, str(e.value))
+    # well-typed host tensors are refused for their device
+    with pytest.raises(ValueError) as e:
+        hh.hh_force_static(**good)
+    assert "cuda" in str(e.value)
+    assert calls == []
+
+
+class _Recorder:
+    """Stands in for the loaded library: records hh_force_static calls, passes
+    every other attribute through."""
+
+    def __init__(self, lib, calls):
+        self._lib, self._calls = lib, calls
+
+    def hh_force_static(self, *a):
+        self._calls.append(a)
+        return 0
+
+    def __getattr__(self, name):
+        return getattr(self._lib, name)
