@@ -42,13 +42,37 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FLOP_PER_INT = 60
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_batch launch (plain FP64,
-# one tree interval of the N = 65536 run), from profiles/batch_kernel_plummer65536.md
-TRAFFIC_FP64_PER_LAUNCH = 69.430016e6 + 29.625088e6
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_batch
+# launch, plain FP64, one 1/64 interval of the N = 65536 run, from one ncu
+# capture of that launch.  It holds only for the kernel sources it was taken
+# with (their digest below): when they differ, the line reports null.
+TRAFFIC_FP64 = {"bytes": None, "sources_sha16": None,
+                "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none "
+                           "-k regex:k_batch -s 1 -c 1 on bench.py --steps 1 --warmup 1 --no-mixed "
+                           "--no-autotune --ensemble 0 --serve-seconds 0 --no-cpu-baseline --no-config1 "
+                           "--no-config3"}
+KERNEL_SOURCES = ("paper_1602_02832_gb300/csrc/hh_batch.cu", "paper_1602_02832_gb300/csrc/hh_kernels.cuh")
 METRIC = "interactions/s & equiv. Tflops (60 flop/int); block-steps/s, p50/p99 latency vs plain"
+CPU_SAMPLE_T = 1.0 / 256  # oracle sample: the first quarter of the first timed interval
 
 
-def _args():
+def _sources_sha16():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic():
+    """Captured DRAM bytes per launch if the kernel sources are those of the capture, else None."""
+    if TRAFFIC_FP64["bytes"] and TRAFFIC_FP64["sources_sha16"] == _sources_sha16():
+        return TRAFFIC_FP64["bytes"]
+    return None
+
+
+def _args(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=8)
@@ -77,7 +101,11 @@ def _args():
                         "N = 2048, on the host below, where a device build is bound by launch latency)")
     p.add_argument("--loop", default="persistent", choices=["persistent", "graph"],
                    help="block-step loop: one persistent cooperative kernel per interval, or CUDA-graph replays")
-    return p.parse_args()
+    p.add_argument("--no-config1", action="store_true",
+                   help="skip the N = 4096 single force evaluation (direct sum and tree lists)")
+    p.add_argument("--no-config3", action="store_true",
+                   help="skip the N = 2^20 Plummer-Salpeter mixed-precision run to t = 0.125")
+    return p.parse_args(argv)
 
 
 def _dist():
@@ -271,7 +299,26 @@ def _tuned(hh, a, prec, seed):
     return best, [{"config": c, "particle_steps_per_s": ps, "interactions_per_s": r} for c, ps, r in table]
 
 
-def _run_form(hh, torch, a, prec, seed, steps, warmup, flush, e2e_steps=0, over=None):
+def _state_in_input_order(ctx, m, t):
+    """The context's particle state (x, v, a, jerk [n, 3], dt [n]) in the order
+    of the input arrays, with the masses m and time t."""
+    import numpy as np
+
+    st = ctx.hh_get_state()
+    ids = ctx.hh_get_ids()
+    n = len(m)
+    out = {"m": m, "t": t}
+    for k in ("x", "v", "a", "jk"):
+        u = np.zeros((n, 3))
+        u[ids] = st[k].T
+        out[k] = u
+    dt = np.zeros(n)
+    dt[ids] = st["dt"]
+    out["dt"] = dt
+    return out
+
+
+def _run_form(hh, torch, a, prec, seed, steps, warmup, flush, e2e_steps=0, over=None, keep_state=False):
     import numpy as np
     import synth
 
@@ -297,6 +344,9 @@ def _run_form(hh, torch, a, prec, seed, steps, warmup, flush, e2e_steps=0, over=
         loop.advance(t + dtt)
         ctx.hh_rebuild(t + dtt)
         t += dtt
+    # the synchronised state at the start of the timed window (the CPU
+    # baseline resumes the oracle from it, so both time the same work)
+    warm_state = _state_in_input_order(ctx, m, t) if keep_state else None
     c0 = ctx.hh_get_counters()
     h0 = ctx.hh_get_tile_histogram()
     l0 = hh.hh_kernel_launches()
@@ -325,7 +375,7 @@ def _run_form(hh, torch, a, prec, seed, steps, warmup, flush, e2e_steps=0, over=
         "block_steps": c1["block_steps"] - c0["block_steps"],
         "particle_steps": c1["particle_steps"] - c0["particle_steps"],
         "force_ms": force_ms, "force_launches": force_launches, "gpu_launches": launches, "t_end": t,
-        "n_i_hist": hist,
+        "n_i_hist": hist, "warm_state": warm_state,
     }
     if e2e_steps:
         # end to end through host buffers: upload the step's particle state,
@@ -435,6 +485,141 @@ def _serving(hh, a):
             "note": "requests arrive in real time over the window; unfinished ones are stopped at its end"}
 
 
+def _j_from_tree(hh, x, v, m, T):
+    """j arrays (particles in the tree's order, then its nodes), [nj, 3] / [nj]."""
+    import numpy as np
+
+    xj = np.concatenate([x[T.perm], T.node_x.T])
+    vj = np.concatenate([v[T.perm], T.node_v.T])
+    mj = np.concatenate([m[T.perm], T.node_m])
+    return xj, vj, mj
+
+
+def _config1(hh, a, peaks):
+    """One force evaluation (acc, jerk, pot) of all N = 4096 particles of the
+    seeded Plummer sphere (eps = 1e-4): by the direct sum (theta = 0: every
+    list holds all particles, so every staged entry is shared by a whole i
+    tile) and by the Barnes-Hut lists (theta = 0.5, leaf 8, n_crit 64); both
+    precisions.  Device time of the force kernel (k_force) per evaluation,
+    CUDA events on the context's stream, best of the repetitions."""
+    import numpy as np
+    import synth
+
+    n, eps2 = 4096, 1e-8
+    x, v, m = synth.plummer(n, 0)
+    z = np.zeros((3, n))
+    out = {"workload": "Plummer N=4096 (seed 0), eps=1e-4, one force evaluation of all particles; direct: "
+                       "theta=0 lists (all N per group); tree: theta=0.5, leaf 8, n_crit 64",
+           "note": "interactions = sum over particles of list length minus self; time = k_force device time "
+                   "(CUDA events), best of the repetitions after two warm-up evaluations"}
+    for lists, theta in (("direct", 0.0), ("tree", 0.5)):
+        T = hh.hh_tree_build(x.T, v.T, z, z, m, leaf=8, n_crit=64, theta=theta)
+        xj, vj, mj = _j_from_tree(hh, x, v, m, T)
+        nj = len(mj)
+        n_int = int((np.diff(T.off)[T.group_of] - 1).sum())
+        for prec, name, peak_key in ((hh.HH_FP64, "fp64", "fp64_tflops"), (hh.HH_MIXED, "mixed", "fp32_tflops")):
+            c = hh.hh_config_default()
+            c.eps2, c.precision, c.theta, c.n_crit = eps2, prec, theta, 64
+            c.tile_i = 32
+            with hh.Context(c, n, nj, len(T.idx), T.n_groups) as ctx:
+                ctx.hh_set_j(0, xj.T, vj.T, np.zeros((3, nj)), np.zeros((3, nj)), mj, np.zeros(nj))
+                ctx.hh_set_lists(n, nj, T.off, T.idx, T.group_of)
+                ctx.hh_predict(0.0)
+                ia = np.arange(n, dtype=np.int32)
+                for _ in range(2):
+                    ctx.hh_force(ia, want=(False, False, False))
+                best = math.inf
+                for _ in range(5 if prec == hh.HH_FP64 else 30):
+                    ctx.hh_force_timing(1)
+                    ctx.hh_force(ia, want=(False, False, False))
+                    ms, _ = ctx.hh_force_timing(0)
+                    best = min(best, ms)
+            ips = n_int / (best * 1e-3)
+            tf = FLOP_PER_INT * ips / 1e12
+            pk = peaks.get(peak_key)
+            out[f"{lists}_{name}"] = {"interactions": n_int, "kernel_ms": best, "interactions_per_s": ips,
+                                      "equiv_tflops": tf, "peak_tflops": pk, "frac": tf / pk if pk else None,
+                                      "peak": f"measured {'FP64' if prec == hh.HH_FP64 else 'FP32'} FMA throughput "
+                                              "(of measured)",
+                                      "mean_list": float(np.diff(T.off).mean()), "groups": int(T.n_groups)}
+    return out
+
+
+def _config3(hh, torch, a, flush, peaks, over=None):
+    """N = 2^20 Plummer sphere with a Salpeter mass spectrum (slope -2.35,
+    mass ratio 100, total mass 1), mixed precision, 4th-order Hermite with
+    block steps to t = 0.125 (eight 1/64 intervals, device rebuilds), theta
+    0.5, leaf 8, eps 1e-4.  The whole run after set-up is timed (CUDA events
+    on the context's stream).  Returns the figures and the data the CPU leg
+    needs for its sampled oracle check."""
+    import numpy as np
+    import synth
+
+    n = 1 << 20
+    x, v, m = synth.plummer_salpeter(n, 0)
+    cfg = _cfg(hh, hh.HH_MIXED, a)
+    for k, val in (over or {}).items():
+        setattr(cfg, k, val)
+    ctx = hh.Context(cfg, n, 2 * n + 64, 16 * n + 4096, n // 4 + 64)
+    stream = torch.cuda.Stream()
+    ctx.hh_set_stream(stream.cuda_stream)
+    w0 = time.perf_counter()
+    ctx.hh_load_particles(x.T, v.T, m)
+    ctx.hh_set_rebuild_device(True)
+    ctx.hh_run(0.0, 0.0)
+    setup_s = time.perf_counter() - w0
+    loop = _Loop(hh, ctx, hh.HH_MIXED, "persistent")
+    dtt = cfg.dt_tree
+    t, t_end = 0.0, 0.125
+    loop.enable(True)
+    flush.zero_()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    while t < t_end:
+        loop.advance(t + dtt)
+        ctx.hh_rebuild(t + dtt)
+        t += dtt
+    e1.record(stream)
+    e1.synchronize()
+    loop.enable(False)
+    ms = e0.elapsed_time(e1)
+    c = ctx.hh_get_counters()
+    hist = ctx.hh_get_tile_histogram().tolist()
+    # sampled forces at t = 0.125 on the j entries and lists just rebuilt
+    off, idx, gof = ctx.hh_get_lists()
+    J = ctx.hh_get_j(0, ctx.nj)
+    ctx.hh_predict(t_end)
+    sample = np.sort(np.random.default_rng(3).choice(n, 200, replace=False)).astype(np.int32)
+    gpu = ctx.hh_force(sample)
+    dev_gb = ctx.device_bytes / 1e9
+    loop.close()
+    ctx.close()
+    ips = c["interactions"] / (ms * 1e-3)
+    force_ms = loop.phase_ms[1]
+    tf_force = FLOP_PER_INT * c["interactions"] / (force_ms * 1e-3) / 1e12 if force_ms else None
+    pk = peaks.get("fp32_tflops")
+    res = {"workload": "Plummer N=2^20 with Salpeter masses (slope -2.35, ratio 100, M=1), seed 0, mixed precision, "
+                       "4th-order Hermite block steps to t=0.125 (8 intervals of 1/64, device rebuilds), theta=0.5, "
+                       f"leaf 8, n_crit {cfg.n_crit}, eps=1e-4",
+           "value": ips, "unit": "interactions/s", "equiv_tflops": FLOP_PER_INT * ips / 1e12,
+           "run_s": ms * 1e-3, "setup_s": setup_s, "device_gb": dev_gb,
+           "block_steps_per_s": c["block_steps"] / (ms * 1e-3), "block_steps": c["block_steps"],
+           "particle_steps": c["particle_steps"], "interactions": c["interactions"],
+           "mean_list": c["interactions"] / max(1, c["particle_steps"]) + 1,
+           "time_split_s": {"predict_select": loop.phase_ms[0] * 1e-3, "force": force_ms * 1e-3,
+                            "rebuild_and_launch": ms * 1e-3 - (loop.phase_ms[0] + force_ms) * 1e-3},
+           "block_step_latency_us": _lat(loop.step_us),
+           "active_per_tile": _n_i({"n_i_hist": hist}),
+           "roofline": {"kernel": "k_batch force phase (list force + corrector), mixed", "bound": "alu",
+                        "achieved": tf_force, "peak": pk, "unit": "TFLOP/s",
+                        "frac": tf_force / pk if (pk and tf_force) else None}}
+    check = {"xj": np.ascontiguousarray(J["x"].T), "vj": np.ascontiguousarray(J["v"].T), "mj": J["m"],
+             "off": off, "idx": idx, "gof": gof, "sample": sample, "gpu": gpu}
+    return res, check
+
+
 def _lat(vals, note="device time of one block step (all three phases) in the persistent loop"):
     import numpy as np
     if not vals:
@@ -463,26 +648,63 @@ def _split(r, steps):
             "rebuild_and_launch": (r["ms"] - sum(ph)) / steps}
 
 
-def _cpu_baseline(a, seed):
-    """The FP64 oracle on a bounded sample: one run over t in [0, 1/256] of the same N."""
+def _oracle_params(a):
     import oracle
-    import synth
+
+    return oracle.RunParams(eps2=1e-8, eta=0.02, eta_s=0.01, dt_min=2.0 ** -30, dt_max=2.0 ** -6,
+                            dt_tree=2.0 ** -6, theta=a.theta, leaf=8, n_crit=a.n_crit, use_tree=True)
+
+
+def _cpu_baseline(a, state, cfg3=None):
+    """The CPU leg: the FP64 oracle, as it stands, on the host cores.
+    (1) Timed on a bounded sample of the timed window: resumed from the GPU
+    arm's synchronised state at the start of its first timed interval, over
+    the first quarter of that interval (the same block steps, lists and
+    interactions, up to rounding).  (2) With cfg3, the oracle's list force on
+    the sampled particles of the N = 2^20 run, on the GPU's own j entries and
+    lists, compared with the GPU's forces."""
+    import numpy as np
+    import oracle
 
     oracle.build()
-    x, v, m = synth.plummer(a.n, seed)
-    p = oracle.RunParams(eps2=1e-8, eta=0.02, eta_s=0.01, dt_min=2.0 ** -30, dt_max=2.0 ** -6,
-                         dt_tree=2.0 ** -6, theta=a.theta, leaf=8, n_crit=a.n_crit, use_tree=True)
-    t0 = time.perf_counter()
-    r = oracle.run(x, v, m, 1.0 / 256, p)
-    dt = time.perf_counter() - t0
-    return {"value": r["stats"]["interactions"] / dt, "unit": "interactions/s", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"FP64 oracle tree-loop run of the same N={a.n} Plummer workload over t in [0, 1/256] "
-                      f"({r['stats']['particle_steps']} particle steps, {r['stats']['interactions']} interactions, "
-                      f"{dt:.1f} s)"}
+    p = _oracle_params(a)
+    t0 = state["t"]
+    w0 = time.perf_counter()
+    r = oracle.resume(state["x"], state["v"], state["a"], state["jk"], state["dt"], state["m"], t0,
+                      t0 + CPU_SAMPLE_T, p)
+    dt = time.perf_counter() - w0
+    out = {"value": r["stats"]["interactions"] / dt, "unit": "interactions/s", "cores": oracle.num_threads(),
+           "kind": "oracle",
+           "sample": f"FP64 oracle tree loop resumed from the GPU arm's state at t = {t0:g} (the start of its "
+                     f"first timed interval, N={a.n}) over t in [{t0:g}, {t0 + CPU_SAMPLE_T:g}] "
+                     f"({r['stats']['particle_steps']} particle steps, {r['stats']['interactions']} "
+                     f"interactions, {dt:.1f} s)"}
+    if cfg3:
+        s = cfg3["sample"]
+        w0 = time.perf_counter()
+        ra, rj, rp = oracle.list_force(cfg3["xj"], cfg3["vj"], cfg3["mj"], s, cfg3["gof"][s], cfg3["off"],
+                                       cfg3["idx"], 1e-8)
+        dt3 = time.perf_counter() - w0
+        acc, jerk, pot = cfg3["gpu"]
+        ea = np.linalg.norm(acc.T - ra, axis=1) / np.linalg.norm(ra, axis=1)
+        ej = np.linalg.norm(jerk.T - rj, axis=1) / np.linalg.norm(rj, axis=1)
+        ep = np.abs(pot - rp) / np.abs(rp)
+        n_int = int((np.diff(cfg3["off"])[cfg3["gof"][s]] - 1).sum())
+        out["config3_check"] = {
+            "particles": int(len(s)), "acc_max_rel": float(ea.max()), "jerk_max_rel": float(ej.max()),
+            "jerk_p999_rel": float(np.quantile(ej, 0.999)), "pot_max_rel": float(ep.max()),
+            "bars": "acc, pot <= 1e-6; jerk <= 1e-5 (or <= 1e-6 of J_scale where it nearly cancels)",
+            "oracle_interactions_per_s": n_int / dt3,
+            "note": "mixed-form forces of sampled particles at t = 0.125 against the FP64 oracle's list force "
+                    "on the same j entries and lists"}
+    return out
 
 
 def main_reference(a):
+    """The FP64 oracle as the reference arm, on the host cores: the same
+    workload run from t = 0 to the start of the GPU arm's timed window (W
+    intervals of 1/64), then each step is the oracle resumed from that
+    synchronised state over the first quarter of the next interval."""
     world, rank, _ = _dist()
     if rank != 0:
         return 0
@@ -491,21 +713,25 @@ def main_reference(a):
 
     oracle.build()
     x, v, m = synth.plummer(a.n, 0)
-    p = oracle.RunParams(eps2=1e-8, eta=0.02, eta_s=0.01, dt_min=2.0 ** -30, dt_max=2.0 ** -6,
-                         dt_tree=2.0 ** -6, theta=a.theta, leaf=8, n_crit=a.n_crit, use_tree=True)
-    sample_t = 1.0 / 1024
+    p = _oracle_params(a)
+    t0 = a.warmup * p.dt_tree
+    w0 = time.perf_counter()
+    r0 = oracle.run(x, v, m, t0, p)
+    prep_s = time.perf_counter() - w0
+    st = (r0["x"], r0["v"], r0["a"], r0["jk"], r0["dt"], m, t0, t0 + CPU_SAMPLE_T, p)
     for _ in range(a.warmup):
-        oracle.run(x, v, m, sample_t, p)
+        oracle.resume(*st)
     tot_int, tot_s, tot_bs = 0, 0.0, 0
     for _ in range(a.steps):
-        t0 = time.perf_counter()
-        r = oracle.run(x, v, m, sample_t, p)
-        tot_s += time.perf_counter() - t0
+        w0 = time.perf_counter()
+        r = oracle.resume(*st)
+        tot_s += time.perf_counter() - w0
         tot_int += r["stats"]["interactions"]
         tot_bs += r["stats"]["block_steps"]
     val = tot_int / tot_s
-    sample = (f"each step: FP64 oracle tree-loop run of N={a.n} Plummer over t in [0, 1/1024] "
-              f"(start-up interval of the same workload)")
+    sample = (f"each step: FP64 oracle tree loop of N={a.n} Plummer resumed from its own state at t = {t0:g} "
+              f"(reached by an untimed run from t = 0 in {prep_s:.1f} s: the start of the GPU arm's timed window) "
+              f"over t in [{t0:g}, {t0 + CPU_SAMPLE_T:g}]")
     # n_gpus is the launch's N (the oracle itself runs on rank 0's host cores)
     line = {"metric": METRIC, "value": val, "unit": "interactions/s", "n_gpus": max(world, a.gpus), "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": tot_s * 1e3 / a.steps, "higher_is_better": True,
@@ -553,20 +779,25 @@ def main():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        res = _run_form(hh, torch, a, hh.HH_FP64, rank, a.steps, a.warmup, flush, e2e_steps=a.steps, over=best64)
+        res = _run_form(hh, torch, a, hh.HH_FP64, rank, a.steps, a.warmup, flush, e2e_steps=a.steps, over=best64,
+                        keep_state=True)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
     mixed = None
     if not a.no_mixed:
         mixed = _run_form(hh, torch, a, hh.HH_MIXED, rank, a.steps, a.warmup, flush, over=bestmx)
+    cfg3, cfg3_check = (None, None)
+    if not a.no_config3 and rank == 0:
+        cfg3, cfg3_check = _config3(hh, torch, a, flush, peaks, over=bestmx)
+    cfg1 = _config1(hh, a, peaks) if (not a.no_config1 and rank == 0) else None
     tot, mx = reduce_over_ranks(
         [res["interactions"], res["block_steps"], res["particle_steps"], res["gpu_launches"], res["e2e"]["interactions"]],
         [res["ms"], res["e2e"]["ms"]], torch.device("cuda", local), world)
     if rank == 0:
         value = tot[0] / (mx[0] * 1e-3)
         achieved = FLOP_PER_INT * res["interactions"] / (res["force_ms"] * 1e-3) / 1e12
-        cpu = None if (a.no_cpu_baseline or world > 1) else _cpu_baseline(a, 0)
+        cpu = None if (a.no_cpu_baseline or world > 1) else _cpu_baseline(a, res["warm_state"], cfg3_check)
         line = {
             "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": mx[0] / a.steps, "higher_is_better": True, "scaling": "weak",
@@ -585,14 +816,15 @@ def main():
                          "bound": "alu",
                          "achieved": achieved, "peak": peaks.get("fp64_tflops"), "unit": "TFLOP/s",
                          "frac": achieved / peaks["fp64_tflops"] if peaks.get("fp64_tflops") else None,
-                         "traffic": TRAFFIC_FP64_PER_LAUNCH if a.loop == "persistent" else None,
+                         "traffic": _traffic() if a.loop == "persistent" else None,
+                         "traffic_capture": TRAFFIC_FP64["capture"],
                          "note": "achieved = 60 algorithmic flop per interaction / device time of the force "
                                  "phases (persistent loop: %globaltimer stamps at the phase barriers, the phase "
                                  "includes the corrector of each completed tile; graph loop: CUDA events around "
                                  "the force kernel); peak = measured FP64 FMA throughput "
                                  "(of measured, libhh_peaks.so); traffic = DRAM bytes of one k_batch launch "
-                                 "(one interval, all phases) from the ncu capture summarised in "
-                                 "profiles/batch_kernel_plummer65536.md"},
+                                 "(one interval, all phases) from one ncu capture of that launch "
+                                 "(traffic_capture), null when the kernel sources differ from the captured ones"},
             "e2e": {"value": tot[4] / (mx[1] * 1e-3), "unit": "interactions/s",
                     "h2d_bytes_per_step": res["e2e"]["bi"], "d2h_bytes_per_step": res["e2e"]["bo"]},
             "gpu_launches": int(tot[3]),
@@ -625,6 +857,10 @@ def main():
                              "peak": peaks.get("fp32_tflops"), "unit": "TFLOP/s",
                              "frac": mach / peaks["fp32_tflops"] if peaks.get("fp32_tflops") else None},
             }
+        if cfg3:
+            line["config3"] = cfg3
+        if cfg1:
+            line["config1"] = cfg1
         if a.ensemble > 0:
             line["batched"] = _ensemble(hh, a)
             line["batched"]["block_steps_per_s_vs_plain"] = line["batched"]["block_steps_per_s"] / line["block_steps_per_s"]

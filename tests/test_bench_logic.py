@@ -62,3 +62,41 @@ def test_reference_arm_prints_one_contract_line():
     env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, env=env, cwd=root)
     assert r.returncode == 0 and not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_traffic_is_reported_only_for_the_captured_kernel_sources(monkeypatch):
+    monkeypatch.setitem(bench.TRAFFIC_FP64, "bytes", 123.0)
+    monkeypatch.setitem(bench.TRAFFIC_FP64, "sources_sha16", bench._sources_sha16())
+    assert bench._traffic() == 123.0
+    monkeypatch.setitem(bench.TRAFFIC_FP64, "sources_sha16", "0" * 16)
+    assert bench._traffic() is None
+    monkeypatch.setitem(bench.TRAFFIC_FP64, "bytes", None)
+    assert bench._traffic() is None
+
+
+def test_cpu_leg_resumes_the_given_state_and_checks_sampled_forces(orc):
+    # the CPU baseline starts the oracle from the state it is handed (the GPU
+    # arm's, at the start of its timed window) and, given config-3 data,
+    # compares the handed forces with the oracle's list force
+    import synth
+
+    n = 600
+    x, v, m = synth.plummer(n, 4)
+    a = bench._args(["--n", str(n), "--n-crit", "32"])
+    p = bench._oracle_params(a)
+    r = orc.run(x, v, m, p.dt_tree, p)
+    state = {"x": r["x"], "v": r["v"], "a": r["a"], "jk": r["jk"], "dt": r["dt"], "m": m, "t": p.dt_tree}
+    T = orc.tree_build(r["x"], r["v"], r["a"], r["jk"], m, leaf=8, n_crit=32, theta=0.5)
+    xj, vj, aj, jj, mj = T.j_array(r["x"], r["v"], r["a"], r["jk"], m)
+    s = np.arange(0, n, 7, dtype=np.int32)
+    ra, rj, rp = orc.list_force(xj, vj, mj, s, T.group_of[s], T.list_off, T.list_idx, 1e-8)
+    gpu = (ra.T * (1 + 1e-9), rj.T, rp)
+    cfg3 = {"xj": xj, "vj": vj, "mj": mj, "off": T.list_off, "idx": T.list_idx, "gof": T.group_of, "sample": s,
+            "gpu": gpu}
+    out = bench._cpu_baseline(a, state, cfg3)
+    assert out["value"] > 0 and out["kind"] == "oracle" and out["cores"] >= 1
+    assert f"t = {p.dt_tree:g}" in out["sample"]
+    ck = out["config3_check"]
+    assert ck["particles"] == len(s)
+    assert ck["acc_max_rel"] == pytest.approx(1e-9, rel=1e-3)
+    assert ck["jerk_max_rel"] == 0.0 and ck["pot_max_rel"] == 0.0
