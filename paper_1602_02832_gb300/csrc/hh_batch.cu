@@ -60,8 +60,7 @@ struct SimDesc {
 };
 
 struct BatchScalars {
-    unsigned int bar_count;
-    unsigned int bar_gen;
+    unsigned int bar_count;  // grid-barrier arrivals; top bit: an error was raised
     int32_t err;
     uint32_t work[2];     // force queue head, by step parity
     uint32_t n_items[2];  // work items, by step parity
@@ -94,25 +93,27 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
 }
 
 // Grid barrier for a cooperative launch (all CTAs resident).  Arrivals
-// count up monotonically within a launch (the host zeroes the counters), so
-// an arrival's count tells which barrier it belongs to: the last arrival of
-// barrier b raises the generation word to b + 1 with a release operation,
-// and the others wait for it with acquire loads.  The arrivals are
-// acquire-release operations on one counter, so the last one has seen every
-// CTA's writes (each CTA's threads synchronise with its arriving thread
-// first), and its release passes them on to every waiter.
+// count up monotonically within a launch (the host zeroes the counter), so
+// an arrival's count tells which barrier it belongs to: barrier b is passed
+// once the counter reaches (b + 1) x gridDim.x.  Each CTA's threads
+// synchronise with its arriving thread first; the arrival is an
+// acquire-release add, and the waiters poll the counter itself with acquire
+// loads.  The adds form one release sequence, so a waiter that reads the
+// final count has seen every CTA's writes, and the last arrival is released
+// by its own add: no second write and no second round trip through L2.
 //
-// Errors travel in the same word: raise_error sets its top bit, which every
-// waiter sees at once, so a passed barrier needs no second read.  (A CTA that
-// releases a barrier after another CTA has failed runs one more phase and
-// stops at the next barrier.)  Waits give up after kWaitNs / kSpinLimit with
-// HH_ETIMEOUT.  Returns false once an error is known.
+// Errors travel in the counter's top bit: raise_error sets it, every waiter
+// sees it with the count it polls, and an arrival after it sees it in the
+// value its add returns.  (A CTA that passed a barrier before another CTA
+// failed runs one more phase and stops at the next barrier.)  Waits give up
+// after kWaitNs / kSpinLimit with HH_ETIMEOUT.  Returns false once an error
+// is known.
 constexpr unsigned int kGenErr = 0x80000000u;
 
 __device__ __forceinline__ void raise_error(BatchScalars *bs, int code)
 {
     atomicExch(&bs->err, code);
-    atomicOr(&bs->bar_gen, kGenErr);
+    atomicOr(&bs->bar_count, kGenErr);
 }
 
 __device__ __forceinline__ bool grid_sync(BatchScalars *bs)
@@ -121,26 +122,24 @@ __device__ __forceinline__ bool grid_sync(BatchScalars *bs)
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned int v = atom_add_acq_rel_gpu(&bs->bar_count, 1u);
-        const unsigned int target = v / gridDim.x + 1u;
-        int ok = 1;
-        if (v % gridDim.x == gridDim.x - 1u) {
-            red_release_max_gpu(&bs->bar_gen, target);
-        } else {
+        const unsigned int cnt = v & ~kGenErr;
+        const unsigned int target = (cnt / gridDim.x + 1u) * gridDim.x;
+        int ok = (v & kGenErr) ? 0 : 1;
+        if (ok && cnt + 1u < target) {
             long long it = 0;
             const unsigned long long t0 = globaltimer_ns();
             for (;;) {
-                const unsigned int g = ld_acquire_gpu(&bs->bar_gen);
+                const unsigned int g = ld_acquire_gpu(&bs->bar_count);
                 if (g & kGenErr) {
                     ok = 0;
                     break;
                 }
                 if (g >= target) break;
-                if (++it > kSpinLimit || globaltimer_ns() - t0 > kWaitNs) {
+                if ((++it & 15) == 0 && (it > kSpinLimit || globaltimer_ns() - t0 > kWaitNs)) {
                     raise_error(bs, HH_ETIMEOUT);
                     ok = 0;
                     break;
                 }
-                __nanosleep(32);
             }
         }
         s_ok = ok;
@@ -389,6 +388,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
     // round trip at the start of every item and every corrector.
     __shared__ SimDesc sd_all[kSdCache];
     __shared__ int64_t base_sm[3][kSdCache + 1];  // jbase, pbase, tbase of a batch of <= kSdCache simulations
+    // each worker group's current and next work item (by item parity): kept
+    // in shared memory instead of 12 registers live across the whole item
+    __shared__ WorkItem it_sm[kGroups][2];
     static_assert(sizeof(SimDesc) % 8 == 0 && sizeof(SimDesc) / 8 <= kThreads - 64, "descriptor copy by 64 threads");
     const int tid = threadIdx.x;
     const int group = tid / kThreads, gt = tid - group * kThreads;
@@ -565,9 +567,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
             // read together with the count (and used only below it).
             const int n_static = (int)gridDim.x * kGroups;
             int item = group * (int)gridDim.x + (int)blockIdx.x;
-            WorkItem it = items[item];
+            int ip = 0;  // parity of it_sm[group] holding the current item
+            if (gt < 3)
+                reinterpret_cast<int4 *>(&it_sm[group][0])[gt] = reinterpret_cast<const int4 *>(&items[item])[gt];
+            group_sync(bar);
             for (;;) {
                 if (item >= (int)n_items) break;
+                const WorkItem &it = it_sm[group][ip];
                 const int s = it.part_sim >> 16;
                 const SimDesc &sd = SD(s);
                 if (gt < 45) {
@@ -625,12 +631,22 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                 }
                 // (with no more items than groups every item was a first item:
                 // no queue round trip before the barrier)
-                if (gt == 0)
-                    sm.item = (int)n_items <= n_static ? (int)n_items
-                                                       : n_static + (int)atomicAdd(&B.bs->work[par], 1u);
+                if (gt == 0) {
+                    const int nx = (int)n_items <= n_static ? (int)n_items
+                                                            : n_static + (int)atomicAdd(&B.bs->work[par], 1u);
+                    sm.item = nx;
+                    // the next item into the other slot (nobody reads it now)
+                    if (nx < (int)n_items) {
+                        const int4 *src = reinterpret_cast<const int4 *>(&items[nx]);
+                        int4 *dst = reinterpret_cast<int4 *>(&it_sm[group][ip ^ 1]);
+                        dst[0] = src[0];
+                        dst[1] = src[1];
+                        dst[2] = src[2];
+                    }
+                }
                 group_sync(bar);  // also ends the use of the shared buffers by this item
                 item = sm.item;   // rewritten only after the next item's group barriers
-                if (item < (int)n_items) it = items[item];
+                ip ^= 1;
             }
         }
         if (!grid_sync(B.bs)) return;
