@@ -358,6 +358,51 @@ int hh_batch_run(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const double *t_en
                  int32_t *steps_out, double *t_next_out, double *step_us_out, double *phase_us_out);
 const char *hh_batch_last_error(const hh_batch *b);
 
+/* ---- Resident set: admission by device-memory budget, continuous batching -- */
+/* The serving form of the batched loop.  Simulations are admitted to a
+ * batch's resident set while their device memory fits a budget; each
+ * hh_batch_step is one hh_batch_run over the running residents, followed by
+ * the tree rebuild (Section 2, step 1) of every simulation that reached its
+ * next rebuild time; a simulation that reached its end time is reported once
+ * and stays resident (its state readable) until the caller retires it.
+ * Contexts stay owned by the caller: the batch borrows them while resident,
+ * and a resident context must not be destroyed or used elsewhere until
+ * retired.  Calls on one batch come from one thread at a time.
+ *
+ * hh_batch_set_budget: budget_bytes of device memory for the resident
+ *   contexts together (their hh_ctx_device_bytes at admission; 0 = no
+ *   limit) and launch_particles, the most particles advanced by one launch
+ *   (0 = no limit; at least one simulation runs per launch).  With a cap,
+ *   launches take the running residents in round-robin order, so each global
+ *   block step carries a bounded amount of work (its latency stays bounded)
+ *   and every resident advances in turn.  HH_EINVAL for negative values.
+ * hh_batch_admit: adds ctx (same device and precision as the batch, with
+ *   lists and steps set, e.g. by hh_run(ctx, t0, t0)) to the resident set,
+ *   to run from its last rebuild time to t_end, a multiple of dt_tree not
+ *   before it.  HH_ENOMEM if every slot (max_sims) is taken or the context's
+ *   device bytes do not fit the budget beside the residents (nothing
+ *   changes; retry after a retirement); HH_EINVAL for a NULL or already
+ *   resident context, another device or precision, or a bad t_end;
+ *   HH_ESTATE for a context without lists or steps.
+ * hh_batch_step: one launch (at most max_steps global steps) over the
+ *   running residents, each to its next rebuild time, then the rebuilds of
+ *   those that reached it (concurrently on their own streams).  Outputs (may
+ *   be NULL): global steps run, simulations launched, the number and the
+ *   contexts (done_out, room for max_sims) that reached their end time since
+ *   the last call, and the per-step times of hh_batch_run.  With no running
+ *   resident it launches nothing.  Errors: those of hh_batch_run; a failed
+ *   rebuild returns its code, and that context stops running (retire it).
+ * hh_batch_retire: removes ctx from the resident set and frees its share of
+ *   the budget.  HH_EINVAL if it is not resident.
+ * hh_batch_resident: resident count, running count and device bytes held
+ *   against the budget (each output may be NULL). */
+int hh_batch_set_budget(hh_batch *b, int64_t budget_bytes, int64_t launch_particles);
+int hh_batch_admit(hh_batch *b, hh_ctx *ctx, double t_end);
+int hh_batch_step(hh_batch *b, int32_t max_steps, int32_t *steps_out, int32_t *launched_out, int32_t *n_done_out,
+                  hh_ctx **done_out, double *step_us_out, double *phase_us_out);
+int hh_batch_retire(hh_batch *b, hh_ctx *ctx);
+int hh_batch_resident(const hh_batch *b, int32_t *n_out, int32_t *running_out, int64_t *bytes_out);
+
 /* Self-test of the bounded grid barrier of the batched kernel: a
  * cooperative launch of one CTA per SM runs 64 barriers; with skip_cta >= 0
  * that CTA never arrives, so every other CTA's wait must give up after its

@@ -98,6 +98,11 @@ _SIGS = {
     "hh_batch_destroy": (C.c_int, [_P]),
     "hh_batch_run": (C.c_int, [_P, C.c_int32, C.POINTER(_P), _D, C.c_int32, _I32, _D, _D, _D]),
     "hh_batch_last_error": (C.c_char_p, [_P]),
+    "hh_batch_set_budget": (C.c_int, [_P, C.c_int64, C.c_int64]),
+    "hh_batch_admit": (C.c_int, [_P, _P, C.c_double]),
+    "hh_batch_step": (C.c_int, [_P, C.c_int32, _I32, _I32, _I32, C.POINTER(_P), _D, _D]),
+    "hh_batch_retire": (C.c_int, [_P, _P]),
+    "hh_batch_resident": (C.c_int, [_P, _I32, _I32, _I64]),
     "hh_ctx_device_bytes": (C.c_int64, [_P]),
     "hh_barrier_selftest": (C.c_int, [C.c_int, C.c_int, _D]),
     "hh_selftest_aarseth": (C.c_int, [C.c_int, C.c_int64, _D, _D, _D, _D, C.c_double, _D]),
@@ -445,6 +450,7 @@ class Batch:
         _check(_lib.hh_batch_create(C.byref(h), int(device), int(precision), int(max_sims), int(max_steps)))
         self.h = h
         self.max_steps = int(max_steps)
+        self.max_sims = int(max_sims)
 
     def close(self):
         if getattr(self, "h", None):
@@ -486,6 +492,47 @@ class Batch:
             raise HHError(rc, (_lib.hh_batch_last_error(self.h) or b"").decode())
         self.last_phase_us = ph[:steps.value]
         return steps.value, tn, us[:steps.value]
+
+
+    def _bcheck(self, rc):
+        if rc != HH_OK:
+            raise HHError(rc, (_lib.hh_batch_last_error(self.h) or b"").decode())
+
+    # -- resident set (admission by budget, continuous batching) --------------
+    def hh_batch_set_budget(self, budget_bytes=0, launch_particles=0):
+        self._bcheck(_lib.hh_batch_set_budget(self.h, int(budget_bytes), int(launch_particles)))
+
+    def hh_batch_admit(self, ctx, t_end):
+        """Admits ctx to run to t_end; returns False (nothing changes) when no
+        slot is free or its device bytes do not fit the budget."""
+        rc = _lib.hh_batch_admit(self.h, ctx.h, float(t_end))
+        if rc == HH_ENOMEM:
+            return False
+        self._bcheck(rc)
+        return True
+
+    def hh_batch_step(self, max_steps=None):
+        """One launch over the running residents plus their due rebuilds.
+        Returns (global steps, simulations launched, handles of the contexts
+        that reached their end time, per-step microseconds)."""
+        ms = self.max_steps if max_steps is None else int(max_steps)
+        steps, launched, nd = C.c_int32(), C.c_int32(), C.c_int32()
+        done = (_P * self.max_sims)()
+        us = np.zeros(ms)
+        ph = np.zeros((ms, 3))
+        self._bcheck(_lib.hh_batch_step(self.h, ms, C.byref(steps), C.byref(launched), C.byref(nd), done, _ptr(us),
+                                        _ptr(ph)))
+        self.last_phase_us = ph[:steps.value]
+        return steps.value, launched.value, [done[k] for k in range(nd.value)], us[:steps.value]
+
+    def hh_batch_retire(self, ctx):
+        self._bcheck(_lib.hh_batch_retire(self.h, ctx.h))
+
+    def hh_batch_resident(self):
+        """(resident contexts, running ones, device bytes held against the budget)."""
+        n, r, b = C.c_int32(), C.c_int32(), C.c_int64()
+        self._bcheck(_lib.hh_batch_resident(self.h, C.byref(n), C.byref(r), C.byref(b)))
+        return n.value, r.value, b.value
 
 
 def hh_selftest_aarseth(A, J, S, T, eta, device=0):

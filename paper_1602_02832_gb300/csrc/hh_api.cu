@@ -953,7 +953,10 @@ int hh_set_rebuild_device(hh_ctx *ctx, int on_device)
     return HH_OK;
 }
 
-int hh_rebuild(hh_ctx *ctx, double t)
+}  // extern "C"
+
+namespace {
+int rebuild_impl(hh_ctx *ctx, double t)
 {
     int rc = check_ctx(ctx);
     if (rc) return rc;
@@ -1034,6 +1037,16 @@ int hh_rebuild(hh_ctx *ctx, double t)
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->rebuilds++;
     return HH_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int hh_rebuild(hh_ctx *ctx, double t)
+{
+    const int rc = rebuild_impl(ctx, t);
+    if (rc == HH_OK) ctx->t_tree = t;
+    return rc;
 }
 
 int hh_run(hh_ctx *ctx, double t0, double t_end)

@@ -26,6 +26,7 @@
 // HH_ETIMEOUT and every CTA returns.
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -684,6 +685,15 @@ struct BatchLayout {
     size_t down_bytes() const { return total - bs; }
 };
 
+// A simulation admitted to a batch's resident set.
+struct Resident {
+    hh_ctx *ctx;
+    double t_end;    // end of the run, a multiple of dt_tree
+    double t_stop;   // next rebuild time (<= t_end)
+    int64_t bytes;   // device bytes counted against the budget
+    int state;       // 0 running, 1 finished (reached t_end), 2 failed rebuild
+};
+
 struct hh_batch {
     int device = 0;
     int precision = HH_FP64;
@@ -697,6 +707,12 @@ struct hh_batch {
     WorkItem *d_items = nullptr;
     int64_t cap_items = 0;
     cudaGraphExec_t graph = nullptr;  // upload, k_batch, read-back
+    // resident set (hh_batch_admit / hh_batch_step / hh_batch_retire)
+    int64_t budget = 0;               // device bytes of admitted contexts, 0 = no limit
+    int64_t used = 0;
+    int64_t launch_particles = 0;     // particles per launch, 0 = no limit
+    size_t rr = 0;                    // round-robin start of the next launch
+    std::vector<Resident> res;
     std::string err;
 };
 
@@ -952,6 +968,151 @@ extern "C" int hh_batch_run(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const d
 }
 
 extern "C" const char *hh_batch_last_error(const hh_batch *b) { return b ? b->err.c_str() : hh_last_error(nullptr); }
+
+// ---- resident set: admission by memory budget, continuous batching --------
+
+extern "C" int hh_batch_set_budget(hh_batch *b, int64_t budget_bytes, int64_t launch_particles)
+{
+    if (!b) return hh_set_global_error(HH_EINVAL, "hh_batch_set_budget: NULL batch");
+    if (budget_bytes < 0 || launch_particles < 0)
+        return bfail(b, HH_EINVAL, "hh_batch_set_budget: negative budget or particle cap");
+    b->budget = budget_bytes;
+    b->launch_particles = launch_particles;
+    return HH_OK;
+}
+
+extern "C" int hh_batch_admit(hh_batch *b, hh_ctx *ctx, double t_end)
+{
+    if (!b) return hh_set_global_error(HH_EINVAL, "hh_batch_admit: NULL batch");
+    if (!ctx) return bfail(b, HH_EINVAL, "hh_batch_admit: NULL context");
+    if (ctx->device != b->device || ctx->cfg.precision != b->precision)
+        return bfail(b, HH_EINVAL, "hh_batch_admit: context device or precision differs from the batch");
+    if (!ctx->have_lists || !ctx->have_dt)
+        return bfail(b, HH_ESTATE, "hh_batch_admit: the context lacks lists or steps (call hh_run(ctx, t0, t0))");
+    for (const Resident &r : b->res)
+        if (r.ctx == ctx) return bfail(b, HH_EINVAL, "hh_batch_admit: context already admitted");
+    const double dtt = ctx->cfg.dt_tree;
+    const double k = t_end / dtt;
+    if (!(t_end >= ctx->t_tree) || k != std::floor(k))
+        return bfail(b, HH_EINVAL, "hh_batch_admit: t_end must be a multiple of dt_tree, not before the tree time");
+    if (int32_t(b->res.size()) >= b->max_sims) return bfail(b, HH_ENOMEM, "hh_batch_admit: every slot is taken");
+    const int64_t bytes = ctx->device_bytes;
+    if (b->budget > 0 && b->used + bytes > b->budget)
+        return bfail(b, HH_ENOMEM, "hh_batch_admit: the context's device memory does not fit the budget");
+    Resident r;
+    r.ctx = ctx;
+    r.t_end = t_end;
+    r.t_stop = std::min(ctx->t_tree + dtt, t_end);
+    r.bytes = bytes;
+    r.state = t_end > ctx->t_tree ? 0 : 1;  // nothing to run: finished at once
+    b->res.push_back(r);
+    b->used += bytes;
+    return HH_OK;
+}
+
+extern "C" int hh_batch_retire(hh_batch *b, hh_ctx *ctx)
+{
+    if (!b) return hh_set_global_error(HH_EINVAL, "hh_batch_retire: NULL batch");
+    for (size_t q = 0; q < b->res.size(); q++)
+        if (b->res[q].ctx == ctx) {
+            b->used -= b->res[q].bytes;
+            b->res.erase(b->res.begin() + q);
+            if (b->rr > q) b->rr--;
+            return HH_OK;
+        }
+    return bfail(b, HH_EINVAL, "hh_batch_retire: context not resident");
+}
+
+extern "C" int hh_batch_resident(const hh_batch *b, int32_t *n_out, int32_t *running_out, int64_t *bytes_out)
+{
+    if (!b) return hh_set_global_error(HH_EINVAL, "hh_batch_resident: NULL batch");
+    int32_t run = 0;
+    for (const Resident &r : b->res) run += r.state == 0;
+    if (n_out) *n_out = int32_t(b->res.size());
+    if (running_out) *running_out = run;
+    if (bytes_out) *bytes_out = b->used;
+    return HH_OK;
+}
+
+extern "C" int hh_batch_step(hh_batch *b, int32_t max_steps, int32_t *steps_out, int32_t *launched_out,
+                             int32_t *n_done_out, hh_ctx **done_out, double *step_us_out, double *phase_us_out)
+{
+    if (!b) return hh_set_global_error(HH_EINVAL, "hh_batch_step: NULL batch");
+    if (steps_out) *steps_out = 0;
+    if (launched_out) *launched_out = 0;
+    if (n_done_out) *n_done_out = 0;
+    // this launch: running residents in round-robin order from b->rr, up to
+    // the particle cap (at least one simulation per launch)
+    const size_t R = b->res.size();
+    std::vector<size_t> pick;
+    int64_t parts = 0;
+    for (size_t q = 0; q < R; q++) {
+        const size_t i = (b->rr + q) % R;
+        const Resident &r = b->res[i];
+        if (r.state != 0) continue;
+        if (b->launch_particles > 0 && !pick.empty() && parts + r.ctx->n > b->launch_particles) break;
+        pick.push_back(i);
+        parts += r.ctx->n;
+    }
+    int32_t nd = 0;
+    if (!pick.empty()) {
+        b->rr = (pick.back() + 1) % R;
+        std::vector<hh_ctx *> ctxs(pick.size());
+        std::vector<double> stop(pick.size()), tn(pick.size());
+        for (size_t q = 0; q < pick.size(); q++) {
+            ctxs[q] = b->res[pick[q]].ctx;
+            stop[q] = b->res[pick[q]].t_stop;
+        }
+        int32_t steps = 0;
+        int rc = hh_batch_run(b, int32_t(pick.size()), ctxs.data(), stop.data(), max_steps, &steps, tn.data(),
+                              step_us_out, phase_us_out);
+        if (rc) return rc;
+        if (steps_out) *steps_out = steps;
+        if (launched_out) *launched_out = int32_t(pick.size());
+        // simulations past their stop time: finished, or rebuilt on their own
+        // streams (concurrently, one host thread each) for the next interval
+        std::vector<size_t> rebuild;
+        for (size_t q = 0; q < pick.size(); q++) {
+            Resident &r = b->res[pick[q]];
+            if (!(tn[q] > r.t_stop)) continue;
+            if (r.t_stop >= r.t_end) r.state = 1;
+            else rebuild.push_back(pick[q]);
+        }
+        std::vector<int> rcs(rebuild.size(), HH_OK);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(int(std::min<size_t>(8, std::max<size_t>(1, rebuild.size()))))
+        for (int64_t q = 0; q < int64_t(rebuild.size()); q++) {
+            Resident &r = b->res[rebuild[size_t(q)]];
+            rcs[size_t(q)] = hh_rebuild(r.ctx, r.t_stop);
+        }
+        int first_rc = HH_OK;
+        std::string first_msg;
+        for (size_t q = 0; q < rebuild.size(); q++) {
+            Resident &r = b->res[rebuild[q]];
+            if (rcs[q] != HH_OK) {
+                r.state = 2;
+                if (first_rc == HH_OK) {
+                    first_rc = rcs[q];
+                    first_msg = std::string("hh_batch_step: rebuild failed: ") + hh_last_error(r.ctx);
+                }
+            } else {
+                r.t_stop = std::min(r.t_stop + r.ctx->cfg.dt_tree, r.t_end);
+            }
+        }
+        if (first_rc != HH_OK) {
+            cudaSetDevice(b->device);
+            return bfail(b, first_rc, first_msg);
+        }
+    }
+    // every finished resident not yet reported is reported once
+    for (Resident &r : b->res)
+        if (r.state == 1) {
+            if (done_out) done_out[nd] = r.ctx;
+            nd++;
+            r.state = 3;  // reported; stays resident until retired
+        }
+    if (n_done_out) *n_done_out = nd;
+    return HH_OK;
+}
 
 namespace {
 

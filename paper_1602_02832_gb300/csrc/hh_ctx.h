@@ -75,6 +75,7 @@ struct hh_ctx {
     // state flags
     bool have_j = false, have_lists = false, have_dt = false, predicted = false, have_forces = false;
     int64_t rebuilds = 0;
+    double t_tree = 0.0;  // time of the last successful rebuild (the j entries' base time)
     std::string err;
 };
 

@@ -2,17 +2,20 @@
 
 Requests (independent N-body simulations with their own N, masses and end
 time) are admitted while their device memory fits a budget, stay resident on
-the GPU, and advance together: every iteration runs ONE persistent batched
-launch (hh_batch_run) that gives each resident simulation up to `max_steps`
-block steps, stopping each at its next tree rebuild time (Section 2: lists are
-rebuilt every dt_tree).  Simulations that reached a rebuild time are rebuilt on
-host threads while the next launch runs the others; finished ones release
-their memory and waiting requests take their place.  With rebuild_device the
-rebuilds run on the device (on the simulation's own stream) instead of the
-host tree builder.  A simulation's result
-does not depend on what else shares the launches (see hh_batch_run).
+the GPU, and advance together.  Admission, launches and rebuilds are libhh's
+resident set (hh_batch_admit / hh_batch_step / hh_batch_retire): every
+iteration is ONE persistent batched launch that gives each running resident up
+to `max_steps` block steps, stopping each at its next tree rebuild time
+(Section 2: lists are rebuilt every dt_tree), followed by the rebuilds of the
+simulations that reached it.  Finished simulations are read back, retired
+(their memory returns to the budget) and waiting requests take their place.
+With `launch_particles` a launch advances at most that many particles (round
+robin over the residents), which bounds the latency of each global block step.
 
-The loop itself is thin Python; every step of the path runs in libhh.
+This module keeps only the host side: request preparation (initial conditions,
+a memory estimate) and context creation (initial forces) run on worker
+threads so the launches keep running meanwhile.  A simulation's result does
+not depend on what else shares the launches (see hh_batch_run).
 """
 from __future__ import annotations
 
@@ -61,10 +64,8 @@ class SimResult:
 class _Live:
     req: SimRequest
     ctx: Context
-    bytes: int
-    t_stop: float          # next rebuild time (<= t_end)
+    bytes: int             # device bytes of the context
     admit_s: float
-    busy: bool = False     # being rebuilt on a host thread
 
 
 @dataclass
@@ -91,16 +92,16 @@ class Server:
 
     def __init__(self, precision=HH_MIXED, budget_bytes=150 * 10 ** 9, max_sims=256, max_steps=64,
                  eps2=1e-8, eta=0.02, theta=0.5, n_crit=64, dt_tree=2.0 ** -6, rebuild_threads=4, device=0,
-                 rebuild_device=False, order=0, gang=True):
+                 rebuild_device=False, order=0, launch_particles=0):
         self.precision = precision
         # True / False, or "auto": the device builder from AUTO_DEVICE_MIN_N
         # particles up, the host builder below (a small tree's device build
         # is bound by kernel-launch latency)
         self.rebuild_device = rebuild_device if rebuild_device == "auto" else bool(rebuild_device)
-        self.gang = bool(gang)
         self.budget = int(budget_bytes)
         self.max_sims = int(max_sims)
         self.max_steps = int(max_steps)
+        self.launch_particles = int(launch_particles)
         self.device = device
         self.cfg = hh_config_default()
         self.cfg.eps2, self.cfg.eta, self.cfg.theta, self.cfg.n_crit = eps2, eta, theta, n_crit
@@ -109,9 +110,15 @@ class Server:
         self.cfg.precision = precision
         self.cfg.order = order
         self.batch = Batch(precision, max_sims=max_sims, max_steps=max_steps, device=device)
+        self.batch.hh_batch_set_budget(self.budget, self.launch_particles)
         self.pool = ThreadPoolExecutor(max_workers=rebuild_threads)
         self.stats = ServerStats()
-        self.used_bytes = 0
+        self._reserved = 0  # estimated bytes of contexts created but not yet resident
+
+    @property
+    def used_bytes(self):
+        """Device bytes held by resident contexts plus those being created."""
+        return self.batch.hh_batch_resident()[2] + self._reserved
 
     def close(self):
         self.pool.shutdown(wait=True)
@@ -144,7 +151,9 @@ class Server:
                + (n // 32 + G) * (16 + 4 + 16 + 32 * 56) * 2)
         return int(est), caps
 
-    def _admit(self, req: SimRequest, caps: dict, now_s: float) -> _Live:
+    def _create(self, req: SimRequest, caps: dict, now_s: float) -> _Live:
+        """Context with the request's particles, tree, initial forces and steps
+        (not yet resident)."""
         for attempt in range(2):
             ctx = Context(self.cfg, device=self.device, **caps)
             try:
@@ -158,7 +167,7 @@ class Server:
                     raise
                 n = caps["n_max"]  # more groups or cells than guessed: the bounds themselves
                 caps = dict(caps, nj_max=3 * n + 64, groups_max=n)
-        return _Live(req, ctx, ctx.device_bytes, min(self.cfg.dt_tree, req.t_end), now_s)
+        return _Live(req, ctx, ctx.device_bytes, now_s)
 
     def _finish(self, s: _Live, now_s: float) -> SimResult:
         st = s.ctx.hh_get_state()
@@ -177,16 +186,16 @@ class Server:
     def run(self, requests: list[SimRequest], realtime: bool = True, max_wall_s: float = math.inf):
         """Serves the requests (sorted by arrival); returns (results, stats).
         With realtime, a request becomes visible at its arrival offset.
-        Preparation (initial conditions, tree-based memory estimate) and
-        admission (context, initial forces) run on the worker threads, so
-        the batched launches keep running meanwhile."""
+        Preparation (initial conditions, memory estimate) and context creation
+        (initial forces) run on the worker threads; contexts are admitted to
+        the batch's resident set in arrival order as slots and budget allow."""
         pending = sorted(requests, key=lambda r: r.arrival_s)
         preparing = []                                   # futures -> (req, est, caps)
         waiting: list[tuple[SimRequest, int, dict]] = []  # prepared, in arrival order
-        admitting = []                                   # (future -> _Live, reserved bytes)
-        live: list[_Live] = []
+        creating = []                                    # (future -> _Live, estimated bytes)
+        created: list[_Live] = []                        # not yet admitted, in order
+        live: dict[int, _Live] = {}                      # resident, by context handle
         results: list[SimResult] = []
-        rebuilding = {}
         t0 = time.perf_counter()
 
         def prepare(r):
@@ -194,85 +203,80 @@ class Server:
             est, caps = self.estimate_bytes(r)
             return r, est, caps
 
-        def admit(r, caps):
-            return self._admit(r, caps, time.perf_counter() - t0)
+        def create(r, caps):
+            return self._create(r, caps, time.perf_counter() - t0)
 
-        def rebuild(s: _Live):
-            s.ctx.hh_rebuild(s.t_stop)
-            s.t_stop = min(s.t_stop + self.cfg.dt_tree, s.req.t_end)
-
-        while pending or preparing or waiting or admitting or live:
-            now = time.perf_counter() - t0
-            if now > max_wall_s:
-                break
-            while pending and (not realtime or pending[0].arrival_s <= now):
-                preparing.append(self.pool.submit(prepare, pending.pop(0)))
-            # prepared requests join the queue in arrival order
-            while preparing and preparing[0].done():
-                waiting.append(preparing.pop(0).result())
-            # admit in arrival order while memory and slots allow (bytes reserved now)
-            while (waiting and len(live) + len(admitting) < self.max_sims
-                   and self.used_bytes + waiting[0][1] <= self.budget):
-                r, est, caps = waiting.pop(0)
-                self.used_bytes += est
-                admitting.append((self.pool.submit(admit, r, caps), est))
-            if waiting and not live and not admitting and self.used_bytes == 0:
-                raise MemoryError(f"request {waiting[0][0].rid} needs {waiting[0][1]} bytes, above the budget")
-            for f, est in [x for x in admitting if x[0].done()]:
-                admitting.remove((f, est))
-                s = f.result()
-                self.used_bytes += s.bytes - est
-                live.append(s)
-            # Gang scheduling: the rebuilds of the simulations that reached a
-            # rebuild time are finished before the next launch, so every live
-            # simulation takes part in it.  (Their kernels cannot run beside
-            # a batched launch, which fills every SM; launching without them
-            # leaves them waiting a whole launch with most simulations idle.)
-            for s in [s for s in live if s.busy and (self.gang or rebuilding[id(s)].done())]:
-                rebuilding.pop(id(s)).result()
-                s.busy = False
-            runnable = [s for s in live if not s.busy]
-            if not runnable:
-                busy = [f for f in list(rebuilding.values()) + [x[0] for x in admitting] + preparing]
-                if busy:
-                    busy[0].result()
-                elif pending and realtime:
-                    time.sleep(max(0.0, min(0.01, pending[0].arrival_s - (time.perf_counter() - t0))))
-                continue
-            steps, tn, us = self.batch.hh_batch_run([s.ctx for s in runnable], [s.t_stop for s in runnable],
-                                                    max_steps=self.max_steps)
-            self.stats.launches += 1
-            self.stats.step_us.extend(us.tolist())
-            self.stats.live_per_step.extend([len(runnable)] * len(us))
-            ph = getattr(self.batch, "last_phase_us", None)
-            if ph is not None and len(ph):
-                self.stats.phase_us[0] += float(ph[:, 0].sum())
-                self.stats.phase_us[1] += float(ph[:, 1].sum() + ph[:, 2].sum())
-            for s, t_next in zip(runnable, tn):
-                if t_next <= s.t_stop:
-                    continue  # still inside its interval
-                if s.t_stop >= s.req.t_end:
-                    self.used_bytes -= s.bytes
-                    live.remove(s)
+        try:
+            while pending or preparing or waiting or creating or created or live:
+                now = time.perf_counter() - t0
+                if now > max_wall_s:
+                    break
+                while pending and (not realtime or pending[0].arrival_s <= now):
+                    preparing.append(self.pool.submit(prepare, pending.pop(0)))
+                # prepared requests join the queue in arrival order
+                while preparing and preparing[0].done():
+                    waiting.append(preparing.pop(0).result())
+                # contexts are created while slots and the estimated memory allow
+                held = self.batch.hh_batch_resident()[2]
+                while (waiting and len(live) + len(creating) + len(created) < self.max_sims
+                       and held + self._reserved + waiting[0][1] <= self.budget):
+                    r, est, caps = waiting.pop(0)
+                    self._reserved += est
+                    creating.append((self.pool.submit(create, r, caps), est))
+                if waiting and not (live or creating or created) and waiting[0][1] > self.budget:
+                    raise MemoryError(f"request {waiting[0][0].rid} needs {waiting[0][1]} bytes, above the budget")
+                while creating and creating[0][0].done():
+                    f, est = creating.pop(0)
+                    self._reserved -= est
+                    s = f.result()
+                    self._reserved += s.bytes
+                    created.append(s)
+                # admission by the contexts' measured bytes (libhh's resident set)
+                while created and self.batch.hh_batch_admit(created[0].ctx, created[0].req.t_end):
+                    s = created.pop(0)
+                    self._reserved -= s.bytes
+                    live[s.ctx.h.value] = s
+                if created and not live and not creating:
+                    raise MemoryError(f"request {created[0].req.rid} needs {created[0].bytes} bytes, above the budget")
+                if not live:
+                    busy = [x[0] for x in creating] + preparing
+                    if busy:
+                        busy[0].result()
+                    elif pending and realtime:
+                        time.sleep(max(0.0, min(0.01, pending[0].arrival_s - (time.perf_counter() - t0))))
+                    continue
+                steps, launched, done, us = self.batch.hh_batch_step(self.max_steps)
+                if launched:
+                    self.stats.launches += 1
+                    self.stats.step_us.extend(us.tolist())
+                    self.stats.live_per_step.extend([launched] * len(us))
+                    ph = getattr(self.batch, "last_phase_us", None)
+                    if ph is not None and len(ph):
+                        self.stats.phase_us[0] += float(ph[:, 0].sum())
+                        self.stats.phase_us[1] += float(ph[:, 1].sum() + ph[:, 2].sum())
+                for h in done:
+                    s = live.pop(h)
+                    self.batch.hh_batch_retire(s.ctx)
                     res = self._finish(s, time.perf_counter() - t0)
                     self.stats.block_steps += res.block_steps
                     self.stats.interactions += res.interactions
                     results.append(res)
-                else:
-                    s.busy = True
-                    rebuilding[id(s)] = self.pool.submit(rebuild, s)
-        for f in list(rebuilding.values()) + preparing:
-            f.result()
-        for f, est in admitting:
-            s = f.result()
-            s.ctx.close()
-            self.used_bytes -= est
-        for s in live:  # stopped by max_wall_s
-            c = s.ctx.hh_get_counters()
-            self.stats.block_steps += c["block_steps"]
-            self.stats.interactions += c["interactions"]
-            self.used_bytes -= s.bytes
-            s.ctx.close()
+        finally:
+            for f in preparing:
+                f.result()
+            for f, est in creating:
+                s = f.result()
+                self._reserved -= est
+                s.ctx.close()
+            for s in created:
+                self._reserved -= s.bytes
+                s.ctx.close()
+            for s in live.values():  # stopped by max_wall_s (or an error)
+                c = s.ctx.hh_get_counters()
+                self.stats.block_steps += c["block_steps"]
+                self.stats.interactions += c["interactions"]
+                self.batch.hh_batch_retire(s.ctx)
+                s.ctx.close()
         self.stats.wall_s = time.perf_counter() - t0
         return results, self.stats
 

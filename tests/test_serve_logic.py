@@ -1,10 +1,14 @@
 """Host logic of the continuous-batching server, with fake GPU objects (no GPU).
 
 The fakes stand in for libhh's Context and Batch: each fake simulation needs a
-fixed number of block steps per tree interval.  The checks: admission never
-exceeds the memory budget, requests are admitted in arrival order as memory
-frees up, every request finishes exactly once at its end time, and batches
-mix simulations of different sizes.
+fixed number of block steps per tree interval, and the fake batch keeps a
+resident set with the semantics include/hh.h gives hh_batch_admit (slots and a
+byte budget), hh_batch_step (one launch over the running residents, rebuilds at
+each interval end, each finished simulation reported once) and
+hh_batch_retire.  The checks: memory in use never exceeds the budget, requests
+are admitted in arrival order as memory frees up, every request finishes
+exactly once at its end time, launches mix simulations of different sizes, and
+a particle cap per launch bounds the work of every launch.
 """
 import numpy as np
 import pytest
@@ -18,12 +22,18 @@ except ImportError:  # libhh not built in this checkout
 pytestmark = pytest.mark.skipif(serve is None, reason="libhh.so not built")
 
 
+class _Handle:
+    def __init__(self, obj):
+        self.value = id(obj)
+
+
 class FakeCtx:
     live = 0
     peak = 0
 
     def __init__(self, cfg, n_max=1, nj_max=1, list_max=1, groups_max=1, device=0):
         self.n = n_max
+        self.h = _Handle(self)
         self.device_bytes = 1000 * n_max
         self.t = 0.0
         self.steps_per_interval = 3 + n_max % 5
@@ -59,23 +69,82 @@ class FakeCtx:
 
 
 class FakeBatch:
-    def __init__(self, precision, max_sims, max_steps, device=0):
-        self.calls = []
+    """Resident set as include/hh.h describes it, advancing FakeCtx objects."""
 
-    def hh_batch_run(self, ctxs, t_stop, max_steps=None):
-        self.calls.append(len(ctxs))
-        tn = []
-        for c, ts in zip(ctxs, t_stop):
-            k = 0
-            while k < max_steps and c.t < ts:
-                c.done_steps += 1
-                k += 1
-                if c.done_steps % c.steps_per_interval == 0:
-                    c.t = ts
-            tn.append(ts + 1.0 / 128 if c.t >= ts else c.t + 1e-3)
+    def __init__(self, precision, max_sims, max_steps, device=0):
+        self.calls = []      # simulations launched per call
+        self.particles = []  # particles launched per call
+        self.max_sims, self.max_steps = max_sims, max_steps
+        self.res = []        # [ctx, t_end, t_stop, state]
+        self.budget = self.cap = 0
+        self.rr = 0
+        self.peak_bytes = 0
+
+    def hh_batch_set_budget(self, budget_bytes=0, launch_particles=0):
+        self.budget, self.cap = budget_bytes, launch_particles
+
+    def _used(self):
+        return sum(r[0].device_bytes for r in self.res)
+
+    def hh_batch_admit(self, ctx, t_end):
+        if len(self.res) >= self.max_sims or (self.budget and self._used() + ctx.device_bytes > self.budget):
+            return False
+        self.res.append([ctx, t_end, min(ctx.t + 1 / 64, t_end), 0])
+        self.peak_bytes = max(self.peak_bytes, self._used())
+        return True
+
+    def hh_batch_step(self, max_steps=None):
+        max_steps = max_steps or self.max_steps
+        R = len(self.res)
+        pick, parts = [], 0
+        for q in range(R):
+            r = self.res[(self.rr + q) % R]
+            if r[3] != 0:
+                continue
+            if self.cap and pick and parts + r[0].n > self.cap:
+                break
+            pick.append((self.rr + q) % R)
+            parts += r[0].n
+        if pick:
+            self.rr = (pick[-1] + 1) % R
+            self.calls.append(len(pick))
+            self.particles.append(parts)
+            for i in pick:
+                r = self.res[i]
+                c, ts = r[0], r[2]
+                k = 0
+                while k < max_steps and c.t < ts:
+                    c.done_steps += 1
+                    k += 1
+                    if c.done_steps % c.steps_per_interval == 0:
+                        c.t = ts
+                if c.t >= ts:
+                    if ts >= r[1]:
+                        r[3] = 1
+                    else:
+                        c.hh_rebuild(ts)
+                        r[2] = min(ts + 1 / 64, r[1])
+        done = []
+        for r in self.res:
+            if r[3] == 1:
+                done.append(r[0].h.value)
+                r[3] = 3
         # per global step: predict + select, force (+ corrector), an empty third phase
-        self.last_phase_us = np.tile([0.25, 0.75, 0.0], (max_steps, 1))
-        return max_steps, np.array(tn), np.ones(max_steps)
+        n = max_steps if pick else 0
+        self.last_phase_us = np.tile([0.25, 0.75, 0.0], (n, 1))
+        return n, len(pick), done, np.ones(n)
+
+    def hh_batch_retire(self, ctx):
+        for q, r in enumerate(self.res):
+            if r[0] is ctx:
+                del self.res[q]
+                if self.rr > q:
+                    self.rr -= 1
+                return
+        raise AssertionError("retire of a context that is not resident")
+
+    def hh_batch_resident(self):
+        return len(self.res), sum(r[3] == 0 for r in self.res), self._used()
 
     def close(self):
         pass
@@ -101,6 +170,7 @@ def test_server_budget_order_and_completion(monkeypatch):
     assert srv.used_bytes == 0
     # never more resident than the budget allows (1500 units, sizes as above)
     assert FakeCtx.peak <= 4
+    assert srv.batch.peak_bytes <= 1000 * 1500
     assert max(srv.batch.calls) >= 2  # simulations were batched together
     assert stats.launches == len(srv.batch.calls)
     # the device-time split adds up the kernel's phases over every launch
@@ -170,3 +240,23 @@ def test_admission_error_other_than_memory_is_raised(monkeypatch):
         srv.run([req], realtime=False)
     srv.close()
     assert FakeCtx.live == 0
+
+
+def test_particle_cap_bounds_every_launch_and_all_finish(monkeypatch):
+    # launch_particles: each launch advances at most that many particles (at
+    # least one simulation), round robin, and every request still finishes
+    monkeypatch.setattr(serve, "Context", FakeCtx)
+    monkeypatch.setattr(serve, "Batch", FakeBatch)
+    monkeypatch.setattr(serve.Server, "estimate_bytes",
+                        lambda self, r: (1000 * len(r.m), dict(n_max=len(r.m), nj_max=1, list_max=1, groups_max=1)))
+    FakeCtx.live = FakeCtx.peak = 0
+    sizes = [100, 700, 300, 900, 200, 500, 800, 400]
+    reqs = [serve.SimRequest(i, np.zeros((n, 3)) + i, np.zeros((n, 3)), np.ones(n) / n,
+                             t_end=(1 + i % 3) / 64, arrival_s=0.0) for i, n in enumerate(sizes)]
+    srv = serve.Server(budget_bytes=10 ** 9, max_sims=8, max_steps=2, launch_particles=1000)
+    res, stats = srv.run(reqs, realtime=False)
+    srv.close()
+    assert sorted(r.rid for r in res) == list(range(len(sizes)))
+    assert all(p <= 1000 or c == 1 for p, c in zip(srv.batch.particles, srv.batch.calls))
+    assert max(srv.batch.particles) <= max(1000, max(sizes))
+    assert FakeCtx.live == 0 and srv.used_bytes == 0
