@@ -93,6 +93,13 @@ def _args(argv=None):
     p.add_argument("--ensemble-t-end", type=float, default=0.5,
                    help="end time of every ensemble cluster (a multiple of dt_tree = 1/64)")
     p.add_argument("--serve-seconds", type=float, default=20.0, help="wall time of the serving measurement (0: skip)")
+    p.add_argument("--serve-sustained-rate", type=float, default=4.0,
+                   help="arrival rate (1/s) of the second serving measurement, a load the server keeps up with "
+                        "(0: skip)")
+    p.add_argument("--serve-sustained-seconds", type=float, default=40.0,
+                   help="wall time of the second serving measurement")
+    p.add_argument("--serve-launch-particles", type=int, default=1 << 21,
+                   help="particles advanced per launch in both serving measurements (latency control; 0: no cap)")
     p.add_argument("--no-autotune", action="store_true", help="skip the tile-shape autotuner (use the defaults)")
     p.add_argument("--order", default="morton", choices=["morton", "hilbert"],
                    help="order of particles and nodes in the tree (Peano-Hilbert is the paper's)")
@@ -460,26 +467,58 @@ def _ensemble(hh, a):
                     "block steps are summed over clusters; latency = device time of one global block step"}
 
 
-def _serving(hh, a):
-    """Serving: Poisson arrivals (20/s) of Plummer + Salpeter cluster requests,
-    N log-uniform in [2^10, 2^18], t_end in {1/8, 1/4, 1/2}, admitted within a
-    150 GB device-memory budget, run for a bounded wall time."""
+def _lat_by_live(step_us, live):
+    """Block-step latency (p50 / p99, microseconds) binned by the number of
+    simulations in the launch that ran the step."""
+    import numpy as np
+    if not step_us:
+        return None
+    u, n = np.asarray(step_us), np.asarray(live)
+    out = []
+    lo = 1
+    while lo <= n.max():
+        hi = 2 * lo
+        sel = (n >= lo) & (n < hi)
+        if sel.any():
+            out.append({"live": [int(lo), int(hi - 1)], "steps": int(sel.sum()),
+                        "p50_us": float(np.quantile(u[sel], 0.5)), "p99_us": float(np.quantile(u[sel], 0.99))})
+        lo = hi
+    return out
+
+
+def _serving(hh, a, rate=20.0, seconds=None, launch_particles=0):
+    """Serving: Poisson arrivals of Plummer + Salpeter cluster requests, N
+    log-uniform in [2^10, 2^18], t_end in {1/8, 1/4, 1/2}, admitted within a
+    150 GB device-memory budget, run for a bounded wall time.  With
+    launch_particles, each launch advances at most that many particles."""
     import synth
     from paper_1602_02832_gb300 import serve
 
-    n_req = max(1, int(20 * a.serve_seconds))
-    stream = synth.request_stream(n_req, rate_per_s=20.0, seed=0)
+    seconds = a.serve_seconds if seconds is None else seconds
+    n_req = max(1, int(rate * seconds))
+    stream = synth.request_stream(n_req, rate_per_s=rate, seed=0)
     reqs = [serve.SimRequest(r.rid, None, None, None, r.t_end, arrival_s=r.arrival_s,
                              make=(lambda n=r.n, sd=r.seed: synth.plummer_salpeter(n, sd))) for r in stream]
     srv = serve.Server(precision=hh.HH_MIXED, budget_bytes=150 * 10 ** 9, max_sims=256, max_steps=32,
                        n_crit=a.n_crit, rebuild_threads=8, rebuild_device=_server_rebuild(a),
-                       order=hh.HH_ORDER_HILBERT if a.order == "hilbert" else hh.HH_ORDER_MORTON)
-    res, st = srv.run(reqs, realtime=True, max_wall_s=a.serve_seconds)
+                       order=hh.HH_ORDER_HILBERT if a.order == "hilbert" else hh.HH_ORDER_MORTON,
+                       launch_particles=launch_particles)
+    res, st = srv.run(reqs, realtime=True, max_wall_s=seconds)
     srv.close()
-    return {"requests_arrived": sum(1 for r in stream if r.arrival_s <= st.wall_s), "completed": len(res),
+    arrived = sum(1 for r in stream if r.arrival_s <= st.wall_s)
+    # requests that arrived at least 10 s before the end (the longest request,
+    # N = 2^18 to t = 1/2, takes about that long): all of them finish when the
+    # server keeps up with the arrivals
+    early = [r for r in stream if r.arrival_s <= st.wall_s - 10.0]
+    done_ids = {r.rid for r in res}
+    return {"arrival_rate_per_s": rate, "window_s": seconds, "launch_particles": launch_particles or None,
+            "requests_arrived": arrived, "completed": len(res),
+            "completion_rate_per_s": len(res) / st.wall_s,
+            "completed_of_arrived_10s_before_end": [sum(1 for r in early if r.rid in done_ids), len(early)],
             "wall_s": st.wall_s, "launches": st.launches,
             "block_steps_per_s": st.block_steps / st.wall_s, "interactions_per_s": st.interactions / st.wall_s,
             "block_step_latency_us": _lat(st.step_us),
+            "block_step_latency_by_live": _lat_by_live(st.step_us, st.live_per_step),
             "request_latency_s": _lat([r.done_s - r.arrival_s for r in res],
                                       "wall seconds from a request's arrival to its completion") if res else None,
             "note": "requests arrive in real time over the window; unfinished ones are stopped at its end"}
@@ -865,7 +904,11 @@ def main():
             line["batched"] = _ensemble(hh, a)
             line["batched"]["block_steps_per_s_vs_plain"] = line["batched"]["block_steps_per_s"] / line["block_steps_per_s"]
         if a.serve_seconds > 0:
-            line["serving"] = _serving(hh, a)
+            line["serving"] = _serving(hh, a, launch_particles=a.serve_launch_particles)
+            if a.serve_sustained_rate > 0:
+                line["serving_sustained"] = _serving(hh, a, rate=a.serve_sustained_rate,
+                                                     seconds=a.serve_sustained_seconds,
+                                                     launch_particles=a.serve_launch_particles)
         line["clocks"] = clk.summary()
         if cpu:
             line["cpu_baseline"] = cpu

@@ -100,3 +100,11 @@ def test_cpu_leg_resumes_the_given_state_and_checks_sampled_forces(orc):
     assert ck["particles"] == len(s)
     assert ck["acc_max_rel"] == pytest.approx(1e-9, rel=1e-3)
     assert ck["jerk_max_rel"] == 0.0 and ck["pot_max_rel"] == 0.0
+
+
+def test_latency_by_live_count_bins():
+    out = bench._lat_by_live([10.0, 20.0, 30.0, 40.0, 50.0], [1, 1, 2, 3, 5])
+    assert [b["live"] for b in out] == [[1, 1], [2, 3], [4, 7]]
+    assert [b["steps"] for b in out] == [2, 2, 1]
+    assert out[0]["p50_us"] == pytest.approx(15.0) and out[2]["p99_us"] == pytest.approx(50.0)
+    assert bench._lat_by_live([], []) is None
