@@ -31,6 +31,7 @@ timed with CUDA events around the force kernel.  The tree-loop runs give
 n_i of only ~4-6, too narrow a range to separate the two terms.
 
 Usage (on a GPU): python -m paper_1602_02832_gb300.perfmodel --out DIR
+List run statistics (host only): python -m paper_1602_02832_gb300.perfmodel --list-runs
 """
 from __future__ import annotations
 
@@ -238,7 +239,66 @@ def table_markdown(rows, fits):
     return "\n".join(lines) + "\n"
 
 
+def list_run_stats(off, idx, n_particles, rec_bytes=(48, 64)):
+    """Run statistics of CSR interaction lists, for the (start, count) encoding
+    of the paper's cell-index memory (Section 2): a run is a maximal stretch
+    of one list whose entries are consecutive j indices.  Returns entries,
+    runs and entries per run (all, particle entries < n_particles, node
+    entries), index bytes as 4-byte CSR entries and as 8-byte (start, count)
+    pairs, and the share of index bytes in the staged bytes of each record
+    size (record + its 4-byte index)."""
+    off = np.asarray(off, dtype=np.int64)
+    idx = np.asarray(idx, dtype=np.int64)
+    L = int(off[-1])
+    idx = idx[:L]
+    starts = np.ones(L, dtype=bool)
+    if L > 1:
+        starts[1:] = idx[1:] != idx[:-1] + 1
+    first = off[:-1][off[1:] > off[:-1]]  # a run never crosses into the next list
+    starts[first] = True
+    is_p = idx < n_particles
+    out = {"entries": L, "runs": int(starts.sum()),
+           "entries_per_run": L / max(1, int(starts.sum())),
+           "particle_entries_per_run": int(is_p.sum()) / max(1, int((starts & is_p).sum())),
+           "node_entries_per_run": int((~is_p).sum()) / max(1, int((starts & ~is_p).sum())),
+           "index_bytes_csr": 4 * L, "index_bytes_ranges": 8 * int(starts.sum())}
+    out["range_bytes_over_csr"] = out["index_bytes_ranges"] / max(1, out["index_bytes_csr"])
+    for rb in rec_bytes:
+        out[f"index_share_of_staged_{rb}B"] = 4.0 / (rb + 4.0)
+    return out
+
+
+def list_runs_main(argv=None):
+    """Run statistics of the library's host-built lists for Plummer spheres
+    (no GPU needed): python -m paper_1602_02832_gb300.perfmodel --list-runs"""
+    import synth
+    from . import HH_ORDER_HILBERT, HH_ORDER_MORTON, hh_tree_build
+
+    p = argparse.ArgumentParser()
+    p.add_argument("--list-runs", action="store_true")
+    p.add_argument("--n", type=int, nargs="+", default=[65536])
+    p.add_argument("--theta", type=float, nargs="+", default=[0.5])
+    p.add_argument("--n-crit", type=int, nargs="+", default=[64, 4000])
+    a = p.parse_args(argv)
+    rows = []
+    for n in a.n:
+        x, v, m = synth.plummer(n, 0)
+        z = np.zeros((3, n))
+        for th in a.theta:
+            for nc in a.n_crit:
+                for order, name in ((HH_ORDER_MORTON, "morton"), (HH_ORDER_HILBERT, "hilbert")):
+                    T = hh_tree_build(x.T, v.T, z, z, m, leaf=8, n_crit=nc, theta=th, order=order)
+                    r = dict(n=n, theta=th, n_crit=nc, order=name, **list_run_stats(T.off, T.idx, n))
+                    rows.append(r)
+                    print(json.dumps(r), flush=True)
+    return rows
+
+
 def main(argv=None):
+    import sys
+    if "--list-runs" in (argv if argv is not None else sys.argv[1:]):
+        list_runs_main(argv)
+        return 0
     from . import HH_FP64, HH_MIXED
 
     p = argparse.ArgumentParser(description=__doc__.splitlines()[0])

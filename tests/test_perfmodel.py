@@ -2,6 +2,7 @@
 paper's Table 1 and the Eq. 3 fit): the fit recovers known parameters and
 the report carries the paper's rows."""
 import numpy as np
+import pytest
 
 from paper_1602_02832_gb300 import perfmodel
 
@@ -69,3 +70,17 @@ def test_equivalent_performance_formula(monkeypatch):
     assert abs(e["S_tree_tflops"] - 57 * 950 * 4096 / 1e-3 / 1e12) < 1e-9
     assert abs(e["speedup_over_direct"] - (950 * 2e-5) / 1e-3) < 1e-12
     assert abs(e["steps_ratio_direct_over_tree"] - 0.95) < 1e-12
+
+
+def test_list_run_stats_counts_runs_within_lists():
+    from paper_1602_02832_gb300 import perfmodel
+    # two lists: [0 1 2 | 5 6] [7 3 4 10 11] with n_particles = 10 (10, 11 are nodes);
+    # 6 -> 7 crosses into the next list, so it starts a new run
+    off = np.array([0, 5, 10])
+    idx = np.array([0, 1, 2, 5, 6, 7, 3, 4, 10, 11])
+    r = perfmodel.list_run_stats(off, idx, 10)
+    assert r["entries"] == 10 and r["runs"] == 5  # [0 1 2] [5 6] [7] [3 4] [10 11]
+    assert r["entries_per_run"] == 2.0
+    assert r["particle_entries_per_run"] == 8 / 4 and r["node_entries_per_run"] == 2.0
+    assert r["index_bytes_csr"] == 40 and r["index_bytes_ranges"] == 40
+    assert r["index_share_of_staged_48B"] == pytest.approx(4 / 52)
