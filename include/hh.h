@@ -78,6 +78,13 @@ typedef struct hh_config {
                           default) or HH_ORDER_HILBERT (1, Peano-Hilbert, the paper's order,
                           Section 2).  The octree, groups and interaction sets are the same;
                           only the positions of particles, nodes and list entries differ */
+    int32_t work_split; /* 0 (default): work_item applies to every block step.  > 0: the
+                          batched loop (hh_batch_run, hh_batch_step) uses work_item only in
+                          block steps with at least work_split active particles and parts of
+                          tile_j in smaller ones (short parts spread a small step over more
+                          SMs; equal-cost parts balance a large one); the other loops then use
+                          parts of tile_j.  The count is the simulation's own, so results still
+                          do not depend on the rest of a batch */
 } hh_config;
 
 #define HH_ORDER_MORTON 0
@@ -308,7 +315,8 @@ const char *hh_last_error(const hh_ctx *ctx);
  * grid barriers and the force work of all simulations drawn from one queue.
  * A simulation's results do not depend on the others in the batch (its
  * tiles, active sets and list parts are its own; sums run in fixed order),
- * so they equal what hh_advance computes for it alone.
+ * so they equal what hh_advance computes for it alone (with work_split = 0;
+ * with step-adaptive parts they equal the simulation alone in a batch).
  *
  * hh_batch_create: device, precision (every context of a run must match it),
  *   up to max_sims (1..32767) simulations per run and max_steps (1..2^20)

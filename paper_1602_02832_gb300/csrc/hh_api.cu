@@ -90,13 +90,14 @@ bool is_pow2(double x)
 }
 
 __global__ void k_set_sizes(DevScalars *ds, int64_t n, int64_t nj, int32_t n_tiles, int32_t part_len,
-                            int32_t work_item)
+                            int32_t work_item, int32_t work_split)
 {
     ds->n = n;
     ds->nj = nj;
     ds->n_tiles = n_tiles;
     ds->part_len = part_len;
     ds->work_item = work_item;
+    ds->work_split = work_split;
 }
 
 __global__ void k_begin_loop(DevScalars *ds, double t_end)
@@ -413,6 +414,7 @@ int hh_create(hh_ctx **out, int device, const hh_config *cfg, int64_t n_max, int
     const int chunk = c.precision == HH_MIXED ? kTjMix : kTjF64;
     if (c.tile_j == 0) c.tile_j = c.precision == HH_MIXED ? 512 : 256;
     if (c.work_item < 0) c.work_item = 0;
+    if (c.work_split < 0) c.work_split = 0;
     if (c.tile_j < chunk || c.tile_j % chunk != 0 || c.tile_j > (1 << 20))
         return hh_set_global_error(HH_EINVAL, "hh_create: tile_j (list part length) must be a multiple of 128 "
                                               "(HH_FP64) or 256 (HH_MIXED)");
@@ -617,7 +619,7 @@ int set_lists_core(hh_ctx *ctx, int64_t n_particles, int64_t n_j, int32_t n_grou
     CK(cudaMemcpyAsync(ctx->group_of, group_of, sizeof(int32_t) * n_particles, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, ctx->stream));
     k_set_sizes<<<1, 1, 0, ctx->stream>>>(ctx->ds, n_particles, n_j, int32_t(tiles.size()), ctx->part_len,
-                                           ctx->cfg.work_item);
+                                           ctx->cfg.work_item, ctx->cfg.work_split);
     CKL();
     CK(cudaStreamSynchronize(ctx->stream));  // host arrays may be freed after return
     ctx->n = n_particles;
@@ -928,7 +930,8 @@ int hh_finish_device_rebuild(hh_ctx *ctx, int64_t total_parts)
         cudaGraphExecDestroy(ctx->graph);
         ctx->graph = nullptr;
     }
-    k_set_sizes<<<1, 1, 0, ctx->stream>>>(ctx->ds, ctx->n, ctx->nj, ctx->n_tiles, ctx->part_len, ctx->cfg.work_item);
+    k_set_sizes<<<1, 1, 0, ctx->stream>>>(ctx->ds, ctx->n, ctx->nj, ctx->n_tiles, ctx->part_len, ctx->cfg.work_item,
+                                          ctx->cfg.work_split);
     CKL();
     if (ctx->st.base) {
         k_refresh_base<<<ctx->elem_grid, 256, 0, ctx->stream>>>(ctx->st, 0, ctx->nj);

@@ -55,7 +55,7 @@ struct SimDesc {
     uint32_t *tile_lv;  // levels present in each tile
     DevScalars *ds;
     int64_t n, nj;
-    int32_t n_tiles, pj, work;
+    int32_t n_tiles, pj, work, work_split;
     Params prm;
     double t_end;
 };
@@ -544,9 +544,19 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                 const int4 td = sd.L.tiles[tile];
                 const int64_t p = td.x + lane;
                 const bool act = (p < td.y) && (sd.st.t[p] + sd.st.dt[p] == tnow);
+                // equal-cost items in this step?  With work_split the
+                // simulation's due particles (levels >= kmin, from its level
+                // histogram, fixed during this phase) must reach work_split:
+                // small steps keep short parts, which spread over more SMs
+                int work = sd.work;
+                if (work > 0 && sd.work_split > 0) {
+                    const int cnt = sd.ds->lvl_cnt[lane];
+                    const int due = __reduce_add_sync(0xffffffffu, lane >= kmin_of(tnow) ? cnt : 0);
+                    if (due < sd.work_split) work = 0;
+                }
                 const uint32_t mask = __ballot_sync(0xffffffffu, act);
                 if (mask)
-                    append_tile_items(sd.L, tile, td, mask, sd.pj, sd.work, &B.bs->n_items[par], &sd.ds->slot_par[par], items,
+                    append_tile_items(sd.L, tile, td, mask, sd.pj, work, &B.bs->n_items[par], &sd.ds->slot_par[par], items,
                                       s, sd.ds->na_hist);
             }
         }
@@ -595,7 +605,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                         reinterpret_cast<const long long *>(&B.sims[s])[gt - 64];
                 }
                 unsigned long long n_int = 0;
-                const bool done = force_item<Rec, TJ, false>(sd.st, (const Rec *)sd.rec, sd.L, sd.pj, sd.work,
+                const bool done = force_item<Rec, TJ, false>(sd.st, (const Rec *)sd.rec, sd.L,
                                                              (typename Traits<Rec>::Eps)sd.prm.eps2, it, sm, n_int,
                                                              gt, bar);
                 if (gt == 0 && n_int) atomicAdd(&sd.ds->interactions, n_int);
@@ -906,6 +916,7 @@ extern "C" int hh_batch_run(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const d
         d.n_tiles = c->n_tiles;
         d.pj = c->part_len;
         d.work = c->cfg.work_item;
+        d.work_split = c->cfg.work_split;
         d.prm.eps2 = c->cfg.eps2;
         d.prm.eta = c->cfg.eta;
         d.prm.eta_s = c->cfg.eta_s;

@@ -33,6 +33,7 @@ struct DevScalars {
     uint32_t n_items;            // work items of this step
     int32_t part_len;            // shortest list part (a multiple of the staging chunk)
     int32_t work_item;           // target interactions per work item (0: every part is part_len long)
+    int32_t work_split;          // > 0: work_item applies only to batched steps with this many active particles
     uint32_t slot_ctr;           // partial-sum slots handed out this step
     uint32_t slot_par[2];        // the same for the batched loop, by step parity
     int32_t n_act_last;          // active particles of the last corrected step
@@ -99,12 +100,13 @@ struct __align__(16) WorkItem {
     int32_t part_sim;  // list part | simulation << 16
     uint32_t mask;     // active lanes of the tile
     int32_t slot;      // first partial-sum slot of the tile's parts (0 with one part)
-    int32_t p_begin, p_end, group, pad;  // the tile's particles and list group
+    int32_t p_begin, p_end, group;  // the tile's particles and list group
+    int32_t part_len;               // list entries per part of this tile (the last part may be shorter)
     int64_t gb, ge;    // the group's list [gb, ge) in idx
 };
 
 __device__ __forceinline__ WorkItem make_item(int tile, int part_sim, uint32_t mask, int slot, const int4 td, int64_t gb,
-                                              int64_t ge)
+                                              int64_t ge, int part_len)
 {
     WorkItem w;
     w.tile = tile;
@@ -114,7 +116,7 @@ __device__ __forceinline__ WorkItem make_item(int tile, int part_sim, uint32_t m
     w.p_begin = td.x;
     w.p_end = td.y;
     w.group = td.z;
-    w.pad = 0;
+    w.part_len = part_len;
     w.gb = gb;
     w.ge = ge;
     return w;
@@ -184,7 +186,8 @@ __device__ __forceinline__ int part_len_for(int n_a, int pj_min, int work)
 __device__ __forceinline__ int parts_of(int64_t len, int pj) { return len > 0 ? (int)((len + pj - 1) / pj) : 1; }
 
 // Warp-collective: appends one work item per part of tile `tile`'s list;
-// item = (tile, part | sim << 16, active mask, first partial-sum slot).
+// item = (tile, part | sim << 16, active mask, first partial-sum slot, part
+// length).  `work` is the equal-cost target of this step (0: parts of pj_min).
 __device__ __forceinline__ void append_tile_items(const Lists &L, int tile, const int4 td, uint32_t mask, int pj_min,
                                                   int work, uint32_t *n_items, uint32_t *slot_ctr, WorkItem *items,
                                                   int sim, unsigned long long *na_hist)
@@ -192,7 +195,8 @@ __device__ __forceinline__ void append_tile_items(const Lists &L, int tile, cons
     const int lane = threadIdx.x & 31;
     const int64_t gb = L.off[td.z], ge = L.off[td.z + 1];
     const int64_t len = ge - gb;
-    const int n_parts = parts_of(len, part_len_for(__popc(mask), pj_min, work));
+    const int pj = part_len_for(__popc(mask), pj_min, work);
+    const int n_parts = parts_of(len, pj);
     int base = 0, slot = 0;
     if (lane == 0) {
         base = (int)atomicAdd(n_items, (uint32_t)n_parts);
@@ -201,7 +205,7 @@ __device__ __forceinline__ void append_tile_items(const Lists &L, int tile, cons
     }
     base = __shfl_sync(0xffffffffu, base, 0);
     slot = __shfl_sync(0xffffffffu, slot, 0);
-    for (int q = lane; q < n_parts; q += 32) items[base + q] = make_item(tile, q | (sim << 16), mask, slot, td, gb, ge);
+    for (int q = lane; q < n_parts; q += 32) items[base + q] = make_item(tile, q | (sim << 16), mask, slot, td, gb, ge, pj);
 }
 
 __device__ __forceinline__ void select_tiles(const State &s, const Lists &L, DevScalars *ds, const StepCtl &c,
@@ -211,7 +215,9 @@ __device__ __forceinline__ void select_tiles(const State &s, const Lists &L, Dev
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int n_tiles = ds->n_tiles;
-    const int pj = ds->part_len, work = ds->work_item;
+    // (this loop does not count a step's active particles first, so a
+    // work_item limited to large steps, work_split > 0, is not used here)
+    const int pj = ds->part_len, work = ds->work_split > 0 ? 0 : ds->work_item;
     for (int64_t tile = warp0; tile < n_tiles; tile += nwarps) {
         const int4 td = L.tiles[tile];
         const int64_t p = td.x + lane;
@@ -772,8 +778,8 @@ __device__ __forceinline__ void group_sync(int bar_id)
 // the thread's index in its 128-thread group.  Returns true (in every thread
 // of the group) for the item that wrote the tile's final forces.
 template <typename Rec, int TJ, bool kMapI>
-__device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict__ rec, const Lists &L, int pj_min,
-                                           int work, typename Traits<Rec>::Eps eps2, const WorkItem &it,
+__device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict__ rec, const Lists &L,
+                                           typename Traits<Rec>::Eps eps2, const WorkItem &it,
                                            ForceSmem<Rec, TJ> &sm, unsigned long long &n_int, const int tid,
                                            const int bar_id)
 {
@@ -784,7 +790,7 @@ __device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict
     const int p0 = it.p_begin;
     const uint32_t mask = it.mask;
     const int n_a = __popc(mask);
-    const int pj = part_len_for(n_a, pj_min, work);
+    const int pj = it.part_len;
     const int part = it.part_sim & 0xFFFF, slot0 = it.slot;
 
     // Lane mapping: every warp holds K = floor(32 / n_a) j slices of n_a lanes
@@ -1010,7 +1016,6 @@ __global__ void __launch_bounds__(kThreads, 6) k_force(State s, const Rec *__res
     if (!step_time(ds, c, &tnow)) return;
     __shared__ ForceSmem<Rec, TJ> sm;
     const int n_items = (int)ds->n_items;
-    const int pj = ds->part_len, work = ds->work_item;
     const typename Traits<Rec>::Eps eps2 = (typename Traits<Rec>::Eps)prm.eps2;
     unsigned long long n_int = 0;
     for (;;) {
@@ -1018,7 +1023,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_force(State s, const Rec *__res
         __syncthreads();
         const int item = sm.item;
         if (item >= n_items) break;
-        force_item<Rec, TJ, kMapI>(s, rec, L, pj, work, eps2, L.items[item], sm, n_int, threadIdx.x, 0);
+        force_item<Rec, TJ, kMapI>(s, rec, L, eps2, L.items[item], sm, n_int, threadIdx.x, 0);
         // the next iteration's first barrier protects sm reuse
     }
     if (threadIdx.x == 0 && n_int) atomicAdd(&ds->interactions, n_int);

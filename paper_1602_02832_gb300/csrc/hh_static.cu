@@ -121,7 +121,7 @@ __global__ void k_static_tiles(const int32_t *gid, int32_t n_act, int32_t n_grou
                 const int4 td = make_int4((int)k, (int)k + n_a, g, (int)base);
                 tiles[t] = td;
                 const uint32_t mask = n_a == 32 ? 0xffffffffu : ((1u << n_a) - 1u);
-                for (int q = 0; q < n_parts; q++) items[base + q] = make_item(t, q, mask, (int)base, td, off[g], off[g + 1]);
+                for (int q = 0; q < n_parts; q++) items[base + q] = make_item(t, q, mask, (int)base, td, off[g], off[g + 1], kStaticPartLen);
             }
         }
     }

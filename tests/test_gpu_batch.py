@@ -3,7 +3,8 @@
 Every simulation of a batch must give the same state as when it runs alone
 through hh_advance (same tiles, active masks and list parts; fixed-order
 sums), whatever else shares the launch and however the run is cut into
-launches.
+launches.  With step-adaptive list parts (work_split > 0, the batched loop
+only) the reference is the simulation alone in a batch.
 """
 import numpy as np
 import pytest
@@ -147,3 +148,49 @@ def test_bounded_barrier_reports_timeout(hh):
     assert rc == hh.HH_ETIMEOUT and 0.05 < t < 30.0
     rc, t = hh.hh_barrier_selftest(skip_cta=-1)
     assert rc == hh.HH_OK
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_step_adaptive_parts_do_not_depend_on_the_batch(hh, prec):
+    # work_split: equal-cost list parts only in block steps with at least 64
+    # active particles (the count is each simulation's own), so a simulation
+    # alone and the same simulation beside others reach the same bits; the
+    # graph loop (parts of tile_j throughout) agrees within FP64 reordering
+    P = hh.HH_FP64 if prec == "fp64" else hh.HH_MIXED
+    t1 = 2.0 ** -6
+
+    alone = []
+    for n, seed, th, sal in SPECS:
+        x, v, m = (synth.plummer_salpeter if sal else synth.plummer)(n, seed)
+        alone.append((x, v, m, th))
+
+    def make(x, v, m, th):
+        c = hh.hh_config_default()
+        c.eps2, c.precision, c.theta, c.n_crit = 1e-6, P, th, 32
+        c.tile_j = 256 if P == hh.HH_FP64 else 512
+        c.work_item, c.work_split = 2048, 64
+        ctx = hh.Context(c, len(m), 2 * len(m), 64 * len(m) * max(1, len(m) // 16), len(m))
+        ctx.hh_load_particles(x.T, v.T, m)
+        ctx.hh_run(0.0, 0.0)
+        return ctx
+
+    ref = []
+    for spec in alone:
+        with make(*spec) as c, hh.Batch(P, max_sims=1, max_steps=4096) as b:
+            b.hh_batch_run([c], [t1])
+            ref.append(c.hh_get_state())
+    ctxs = [make(*spec) for spec in alone]
+    with hh.Batch(P, max_sims=8, max_steps=4096) as b:
+        b.hh_batch_run(ctxs, [t1] * len(ctxs))
+    for c, st in zip(ctxs, ref):
+        got = c.hh_get_state()
+        for k in ("x", "v", "a", "jk", "t", "dt"):
+            assert np.array_equal(got[k], st[k]), k
+        c.close()
+    if P == hh.HH_FP64:
+        for spec, st in zip(alone, ref):
+            with make(*spec) as c:
+                c.hh_advance(t1)
+                g = c.hh_get_state()
+            assert np.array_equal(g["t"], st["t"])
+            assert np.abs(g["x"] - st["x"]).max() < 1e-9
