@@ -86,6 +86,10 @@ def _args(argv=None):
     p.add_argument("--tile-j-mixed", type=int, default=0, help="list part length of the mixed form (0: tuned default)")
     p.add_argument("--work-item", type=int, default=0, help="interactions per work item, plain form (0: default)")
     p.add_argument("--work-item-mixed", type=int, default=0, help="interactions per work item, mixed form (0: default)")
+    p.add_argument("--work-split", type=int, default=0,
+                   help="active particles from which work items apply, plain form (0: every step)")
+    p.add_argument("--work-split-mixed", type=int, default=0,
+                   help="active particles from which work items apply, mixed form (0: every step)")
     p.add_argument("--no-mixed", action="store_true")
     p.add_argument("--mixed-only", action="store_true", help="run only the mixed form (profiling aid)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -137,6 +141,7 @@ def _cfg(hh, prec, a):
     c.tile_i = a.tile_i or 0
     c.tile_j = (a.tile_j if prec == hh.HH_FP64 else a.tile_j_mixed) or 0
     c.work_item = (a.work_item if prec == hh.HH_FP64 else a.work_item_mixed) or 0
+    c.work_split = (a.work_split if prec == hh.HH_FP64 else a.work_split_mixed) or 0
     c.order = hh.HH_ORDER_HILBERT if a.order == "hilbert" else hh.HH_ORDER_MORTON
     return c
 

@@ -98,6 +98,8 @@ typedef struct hh_counters {
     int64_t tile_steps;     /* static i tiles with active particles, summed over block steps:
                                particle_steps / tile_steps is the mean number of particles that
                                share one staged list chunk (the paper's n_i, Eq. 3) */
+    int64_t list_steps;     /* block steps of the batched loop that predicted only the entries of their
+                               list parts instead of every j entry (small steps of large simulations) */
 } hh_counters;
 
 /* Fills cfg with defaults: eps2 = 1e-8, eta = 0.02, eta_s = 0.01,

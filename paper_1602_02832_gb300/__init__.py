@@ -47,7 +47,7 @@ class hh_config(C.Structure):
 
 class hh_counters(C.Structure):
     _fields_ = [("block_steps", C.c_int64), ("particle_steps", C.c_int64), ("interactions", C.c_int64),
-                ("rebuilds", C.c_int64), ("tile_steps", C.c_int64)]
+                ("rebuilds", C.c_int64), ("tile_steps", C.c_int64), ("list_steps", C.c_int64)]
 
 
 _P = C.c_void_p
@@ -320,7 +320,7 @@ class Context:
         c = hh_counters()
         self._c(_lib.hh_get_counters(self.h, C.byref(c)))
         return dict(block_steps=c.block_steps, particle_steps=c.particle_steps, interactions=c.interactions,
-                    rebuilds=c.rebuilds, tile_steps=c.tile_steps)
+                    rebuilds=c.rebuilds, tile_steps=c.tile_steps, list_steps=c.list_steps)
 
     def hh_get_tile_histogram(self):
         """counts[k] = active i tiles evaluated with k + 1 active particles."""

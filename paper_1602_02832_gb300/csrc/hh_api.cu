@@ -861,6 +861,7 @@ int hh_get_counters(hh_ctx *ctx, hh_counters *out)
     out->rebuilds = ctx->rebuilds;
     out->tile_steps = 0;
     for (int k = 0; k < 32; k++) out->tile_steps += int64_t(ctx->h_ds->na_hist[k]);
+    out->list_steps = int64_t(ctx->h_ds->list_steps);
     return HH_OK;
 }
 
@@ -878,7 +879,7 @@ int hh_reset_counters(hh_ctx *ctx)
 {
     int rc = check_ctx(ctx);
     if (rc) return rc;
-    CK(cudaMemsetAsync(&ctx->ds->block_steps, 0, 3 * sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(&ctx->ds->block_steps, 0, 4 * sizeof(unsigned long long), ctx->stream));
     CK(cudaMemsetAsync(ctx->ds->na_hist, 0, sizeof(ctx->ds->na_hist), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->rebuilds = 0;

@@ -56,6 +56,7 @@ struct SimDesc {
     DevScalars *ds;
     int64_t n, nj;
     int32_t n_tiles, pj, work, work_split;
+    int64_t lbar;  // mean list length per group (list entries / groups)
     Params prm;
     double t_end;
 };
@@ -285,15 +286,55 @@ __device__ __forceinline__ double correct_tile_3lane(const SimDesc &sd, const in
 struct StepCache {
     double t[kSimCache];
     double t_end[kSimCache];
+    unsigned char list_mode[kSimCache];  // predict only the entries of this step's list parts
+    int any_list;                        // some simulation of the batch is in list mode this step
 };
+
+// A small block step of a large simulation references few of its j entries:
+// its due tiles' lists.  Then predicting those (in a phase after the tile
+// selection) is cheaper than predicting every entry.  The choice compares the
+// due particles (the levels >= kmin(t) of the simulation's level histogram,
+// which nobody writes during this phase, so every CTA decides alike) times
+// the mean list length with the number of j entries, and applies only to
+// simulations whose every-entry pass costs more than the extra phase and
+// grid barrier (a few microseconds): at least kListModeMinJ entries.  It
+// changes no result: a predicted record is the same whoever computes it.
+constexpr int64_t kListModeMinJ = 1 << 18;
+
+__device__ __forceinline__ bool list_mode_of(const SimDesc &sd, double tnow)
+{
+    constexpr int64_t kDiv = 2;  // list entries counted with their repeats across a step's tiles
+    if (sd.nj < kListModeMinJ || !(tnow <= sd.t_end) || !(tnow > 0.0)) return false;
+    const int k0 = kmin_of(tnow);
+    int64_t due = 0;
+#pragma unroll
+    for (int k = 0; k < 32; k++) {
+        const int c = __ldcg(&sd.ds->lvl_cnt[k]);
+        due += k >= k0 ? c : 0;
+    }
+    return due * sd.lbar * kDiv < sd.nj;
+}
 
 __device__ __forceinline__ void cache_times(StepCache &c, const SimDesc *sims, int n_sims, int par)
 {
+    if (threadIdx.x == 0) c.any_list = 0;
+    __syncthreads();
+    int any = 0;
     for (int s = threadIdx.x; s < n_sims && s < kSimCache; s += blockDim.x) {
         c.t[s] = __longlong_as_double((long long)__ldcg(&sims[s].ds->tmin[par]));
         c.t_end[s] = sims[s].t_end;
+        const bool lm = list_mode_of(sims[s], c.t[s]);
+        c.list_mode[s] = lm;
+        any |= lm;
     }
+    if (any) c.any_list = 1;
     __syncthreads();
+}
+
+// List mode of simulation s (simulations beyond the cache predict every entry).
+__device__ __forceinline__ bool cached_list_mode(const StepCache &c, int s)
+{
+    return s < kSimCache && c.list_mode[s];
 }
 
 __device__ __forceinline__ double cached_time(const StepCache &c, const SimDesc *sims, int s, int par)
@@ -519,6 +560,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                     ds->n_act_last = 0;
                     ds->slot_par[par ^ 1] = 0u;
                     if (live) ds->block_steps += 1ull;
+                    if (live && cached_list_mode(sc, s)) ds->list_steps += 1ull;
                 }
             }
         }
@@ -526,7 +568,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
             const int s = g == gtid ? s_p0 : find_sim(JB, n_sims, g);
             const SimDesc &sd = SD(s);
             const double tnow = cached_time(sc, B.sims, s, par);
-            if (!(tnow <= sd.t_end)) continue;
+            if (!(tnow <= sd.t_end) || cached_list_mode(sc, s)) continue;
             if (kEarly && g == gtid) pred_store<Rec>(in0, (Rec *)sd.rec, g - JB[s], tnow);
             else predict_entry<Rec>(sd.st, (Rec *)sd.rec, g - JB[s], tnow);
         }
@@ -561,6 +603,32 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
             }
         }
         if (!grid_sync(B.bs)) return;
+        if (sc.any_list) {
+            // ---- phase 1b: list-mode simulations predict the entries of
+            // this step's list parts.  A task is 32 consecutive entries of
+            // one work item (lane = entry); entries shared by several parts
+            // are predicted more than once, with the same result.
+            const uint32_t n_items = __ldcg(&B.bs->n_items[par]);
+            const int lane = tid & 31;
+            const int64_t w0 = gtid >> 5, nw = nth >> 5;
+            int maxc = 1;  // tasks per item: the longest part length of a list-mode simulation / 32
+            for (int s = 0; s < n_sims && s < kSimCache; s++)
+                if (sc.list_mode[s]) maxc = max(maxc, (SD(s).pj + 31) / 32);
+            const int64_t n_tasks = (int64_t)n_items * maxc;
+            for (int64_t task = w0; task < n_tasks; task += nw) {
+                const int64_t i = task / maxc;
+                const int c = (int)(task - i * maxc);
+                const WorkItem &it = items[i];
+                const int s = it.part_sim >> 16;
+                if (!cached_list_mode(sc, s)) continue;  // warp-uniform
+                const SimDesc &sd = SD(s);
+                const int64_t lb = it.gb + (int64_t)(it.part_sim & 0xFFFF) * it.part_len;
+                const int64_t le = min(it.ge, lb + (int64_t)it.part_len);
+                const int64_t e = lb + 32 * (int64_t)c + lane;
+                if (e < le) predict_entry<Rec>(sd.st, (Rec *)sd.rec, sd.L.idx[e], cached_time(sc, B.sims, s, par));
+            }
+            if (!grid_sync(B.bs)) return;
+        }
         if (blockIdx.x == 0 && tid == 0) B.step_ns[3 * step + 1] = globaltimer_ns();
 
         // ---- phase 2: forces from the shared queue, one item per worker
@@ -917,6 +985,7 @@ extern "C" int hh_batch_run(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const d
         d.pj = c->part_len;
         d.work = c->cfg.work_item;
         d.work_split = c->cfg.work_split;
+        d.lbar = c->n_groups > 0 ? std::max<int64_t>(1, c->list_len / c->n_groups) : 1;
         d.prm.eps2 = c->cfg.eps2;
         d.prm.eta = c->cfg.eta;
         d.prm.eta_s = c->cfg.eta_s;

@@ -42,6 +42,7 @@ struct DevScalars {
     int32_t n_tiles;             // static i tiles
     int32_t pad0;
     unsigned long long block_steps, particle_steps, interactions;
+    unsigned long long list_steps;  // batched steps that predicted only their list parts' entries
     unsigned long long na_hist[32];  // active i tiles summed over block steps, by n_a - 1
     // block-step levels (level k <=> dt = 2^-k), kept by the batched loop
     int32_t lvl_cnt[32];          // particles per level

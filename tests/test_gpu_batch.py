@@ -194,3 +194,41 @@ def test_step_adaptive_parts_do_not_depend_on_the_batch(hh, prec):
                 g = c.hh_get_state()
             assert np.array_equal(g["t"], st["t"])
             assert np.abs(g["x"] - st["x"]).max() < 1e-9
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_list_mode_prediction_changes_no_bit(hh, prec):
+    # N = 2^18 (about 3.4e5 j entries, above the size from which the batched
+    # loop predicts only the entries of a small step's list parts): the
+    # batched run equals, bit for bit, the graph loop, which predicts every
+    # entry at every step
+    P = hh.HH_FP64 if prec == "fp64" else hh.HH_MIXED
+    n = 1 << 18
+    x, v, m = synth.plummer(n, 9)
+    t1 = 2.0 ** -9
+
+    def make():
+        c = hh.hh_config_default()
+        c.eps2, c.precision, c.n_crit = 1e-8, P, 64
+        z = np.zeros((3, n))
+        T0 = hh.hh_tree_build(x.T, v.T, z, z, m, leaf=8, n_crit=64, theta=0.5)
+        ctx = hh.Context(c, n, 2 * n, 2 * len(T0.idx) + 1024, 2 * T0.n_groups + 64)
+        ctx.hh_load_particles(x.T, v.T, m)
+        ctx.hh_set_rebuild_device(True)
+        ctx.hh_run(0.0, 0.0)
+        assert ctx.nj >= 1 << 18
+        return ctx
+
+    with make() as c:
+        c.hh_advance(t1)
+        ref = c.hh_get_state()
+        ref_c = c.hh_get_counters()
+    with make() as c, hh.Batch(P, max_sims=1, max_steps=4096) as b:
+        steps, tn, _ = b.hh_batch_run([c], [t1])
+        got = c.hh_get_state()
+        got_c = c.hh_get_counters()
+    assert tn[0] > t1 and steps > 10
+    assert 0 < got_c["list_steps"] < steps and ref_c["list_steps"] == 0  # the mode was used, not always
+    for k in ("x", "v", "a", "jk", "t", "dt"):
+        assert np.array_equal(got[k], ref[k]), k
+    assert got_c["interactions"] == ref_c["interactions"]
