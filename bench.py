@@ -97,6 +97,11 @@ def _args(argv=None):
     p.add_argument("--ensemble-t-end", type=float, default=0.5,
                    help="end time of every ensemble cluster (a multiple of dt_tree = 1/64)")
     p.add_argument("--serve-seconds", type=float, default=20.0, help="wall time of the serving measurement (0: skip)")
+    p.add_argument("--batch-work-item", type=int, default=8192,
+                   help="equal-cost work items (interactions) of the ensemble and serving runs, mixed form (0: off); "
+                        "with many simulations per launch the queue stays full, so balance pays in every step")
+    p.add_argument("--batch-work-split", type=int, default=0,
+                   help="active particles from which those work items apply (0: every step)")
     p.add_argument("--serve-sustained-rate", type=float, default=4.0,
                    help="arrival rate (1/s) of the second serving measurement, a load the server keeps up with "
                         "(0: skip)")
@@ -447,7 +452,8 @@ def _ensemble(hh, a):
         srv = serve.Server(precision=hh.HH_MIXED, budget_bytes=150 * 10 ** 9, max_sims=256, max_steps=256,
                            theta=th, n_crit=a.n_crit, rebuild_threads=8,
                            rebuild_device=_server_rebuild(a),
-                           order=hh.HH_ORDER_HILBERT if a.order == "hilbert" else hh.HH_ORDER_MORTON)
+                           order=hh.HH_ORDER_HILBERT if a.order == "hilbert" else hh.HH_ORDER_MORTON,
+                           work_item=a.batch_work_item, work_split=a.batch_work_split)
         res, st = srv.run(sub, realtime=False)
         srv.close()
         results += res
@@ -507,7 +513,8 @@ def _serving(hh, a, rate=20.0, seconds=None, launch_particles=0):
     srv = serve.Server(precision=hh.HH_MIXED, budget_bytes=150 * 10 ** 9, max_sims=256, max_steps=32,
                        n_crit=a.n_crit, rebuild_threads=8, rebuild_device=_server_rebuild(a),
                        order=hh.HH_ORDER_HILBERT if a.order == "hilbert" else hh.HH_ORDER_MORTON,
-                       launch_particles=launch_particles)
+                       launch_particles=launch_particles, work_item=a.batch_work_item,
+                       work_split=a.batch_work_split)
     res, st = srv.run(reqs, realtime=True, max_wall_s=seconds)
     srv.close()
     arrived = sum(1 for r in stream if r.arrival_s <= st.wall_s)

@@ -92,7 +92,7 @@ class Server:
 
     def __init__(self, precision=HH_MIXED, budget_bytes=150 * 10 ** 9, max_sims=256, max_steps=64,
                  eps2=1e-8, eta=0.02, theta=0.5, n_crit=64, dt_tree=2.0 ** -6, rebuild_threads=4, device=0,
-                 rebuild_device=False, order=0, launch_particles=0):
+                 rebuild_device=False, order=0, launch_particles=0, tile_i=0, tile_j=0, work_item=0, work_split=0):
         self.precision = precision
         # True / False, or "auto": the device builder from AUTO_DEVICE_MIN_N
         # particles up, the host builder below (a small tree's device build
@@ -109,6 +109,11 @@ class Server:
         self.cfg.dt_tree = dt_tree
         self.cfg.precision = precision
         self.cfg.order = order
+        # list decomposition (0: the library's defaults); see hh_config
+        self.cfg.tile_i = tile_i or self.cfg.tile_i
+        self.cfg.tile_j = tile_j
+        self.cfg.work_item = work_item
+        self.cfg.work_split = work_split
         self.batch = Batch(precision, max_sims=max_sims, max_steps=max_steps, device=device)
         self.batch.hh_batch_set_budget(self.budget, self.launch_particles)
         self.pool = ThreadPoolExecutor(max_workers=rebuild_threads)
