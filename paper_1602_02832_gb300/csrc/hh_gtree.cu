@@ -875,15 +875,21 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
     const int64_t cap_cells = ctx->cap_j - n;
     for (int d = 0; d <= kMaxDepth; d++)
         k_level<<<grid, 256, 0, st>>>(g->C, g->key2, d, ctx->cfg.leaf, g->gc, int32_t(std::min<int64_t>(cap_cells, INT32_MAX)));
-    for (int d = kMaxDepth; d >= 0; d--) k_subtree_size<<<grid, 256, 0, st>>>(g->C, g->gc, d);
-    for (int d = 0; d <= kMaxDepth; d++) k_preorder<<<grid, 256, 0, st>>>(g->C, g->gc, d);
     k_cells_done<<<1, 1, 0, st>>>(g->gc, g->box);
-    launches += 3 * (kMaxDepth + 1) + 1;
+    launches += (kMaxDepth + 1) + 1;
     if (!read_counts()) return gfail(ctx, HH_ECUDA, "hh_rebuild: tree build failed");
     if (g->gc_host->bad) return gfail(ctx, HH_ESTATE, "hh_rebuild: particles are not synchronised at t");
     if (g->gc_host->overflow)
         return gfail(ctx, HH_ENOMEM, "hh_rebuild: tree exceeds nj_max (more cells than room for nodes)");
     const int32_t ncells = g->gc_host->ncells;
+    // the deepest level that holds cells: the level loops below stop there
+    // (a Plummer tree of 2^16 particles is 12-14 levels deep, the limit 21)
+    int depth = 0;
+    for (int d = 0; d <= kMaxDepth; d++)
+        if (g->gc_host->lvl_n[d] > 0) depth = d;
+    for (int d = depth; d >= 0; d--) k_subtree_size<<<grid, 256, 0, st>>>(g->C, g->gc, d);
+    for (int d = 0; d <= depth; d++) k_preorder<<<grid, 256, 0, st>>>(g->C, g->gc, d);
+    launches += 2 * (depth + 1);
     k_to_preorder<<<grid, 256, 0, st>>>(g->C, ncells, g->P, g->root_side);
     // 3. particles into Morton order (into the second buffer), then swap
     k_permute<<<grid, 256, 0, st>>>(ctx->st, g->alt, g->perm, n, g->ids, g->ids2);
@@ -897,7 +903,7 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
     std::swap(g->ids, g->ids2);
     // 4. node records (bottom-up moments), groups and their boxes
     const int64_t cap_c = g->cap_c;
-    for (int d = kMaxDepth; d >= 0; d--) k_moments_level<<<grid, 256, 0, st>>>(ctx->st, g->C, g->gc, d, cap_c, g->mom);
+    for (int d = depth; d >= 0; d--) k_moments_level<<<grid, 256, 0, st>>>(ctx->st, g->C, g->gc, d, cap_c, g->mom);
     k_node_records<<<grid, 256, 0, st>>>(ctx->st, g->C, g->P, ncells, cap_c, g->mom, n, t);
     k_group_flags<<<grid, 256, 0, st>>>(g->P, ncells, ctx->cfg.n_crit, g->gflag);
     int rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->gflag, g->gpos, ncells, st);
@@ -918,7 +924,7 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
         return gfail(ctx, rc, "hh_rebuild: scan failed");
     k_store_count<<<1, 1, 0, st>>>(&g->gc->A, g->gflag, g->gpos, ncells);
     k_cut_write<<<grid, 256, 0, st>>>(ncells, g->gflag, g->gpos, g->above);
-    launches += (kMaxDepth + 1) + 16;
+    launches += (depth + 1) + 16;
     if (!read_counts()) return gfail(ctx, HH_ECUDA, "hh_rebuild: group build failed");
     const int32_t G = g->gc_host->G, R = g->gc_host->R, A = g->gc_host->A;
     if (G > ctx->cap_g) return gfail(ctx, HH_ENOMEM, "hh_rebuild: more groups than groups_max");
