@@ -85,6 +85,11 @@ typedef struct hh_config {
                           SMs; equal-cost parts balance a large one); the other loops then use
                           parts of tile_j.  The count is the simulation's own, so results still
                           do not depend on the rest of a batch */
+    int32_t tile_j_small; /* 0 (default): off.  Otherwise a multiple of 32 in [32, tile_j]: the
+                          batched loop splits the lists of block steps with at most 16 due
+                          particles into parts of this length, so that such a step's few tiles
+                          spread over more SMs (the item and partial-sum buffers are sized for
+                          16 tiles of the longest list in such parts) */
 } hh_config;
 
 #define HH_ORDER_MORTON 0

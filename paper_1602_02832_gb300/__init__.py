@@ -42,7 +42,8 @@ class hh_config(C.Structure):
     _fields_ = [("eps2", C.c_double), ("eta", C.c_double), ("eta_s", C.c_double), ("dt_min", C.c_double),
                 ("dt_max", C.c_double), ("dt_tree", C.c_double), ("theta", C.c_double), ("leaf", C.c_int32),
                 ("n_crit", C.c_int32), ("precision", C.c_int32), ("tile_i", C.c_int32), ("tile_j", C.c_int32),
-                ("work_item", C.c_int32), ("order", C.c_int32), ("work_split", C.c_int32)]
+                ("work_item", C.c_int32), ("order", C.c_int32), ("work_split", C.c_int32),
+                ("tile_j_small", C.c_int32)]
 
 
 class hh_counters(C.Structure):

@@ -415,6 +415,8 @@ int hh_create(hh_ctx **out, int device, const hh_config *cfg, int64_t n_max, int
     if (c.tile_j == 0) c.tile_j = c.precision == HH_MIXED ? 512 : 256;
     if (c.work_item < 0) c.work_item = 0;
     if (c.work_split < 0) c.work_split = 0;
+    if (c.tile_j_small != 0 && (c.tile_j_small < 32 || c.tile_j_small % 32 != 0 || c.tile_j_small > c.tile_j))
+        return hh_set_global_error(HH_EINVAL, "hh_create: tile_j_small must be 0 or a multiple of 32 in [32, tile_j]");
     if (c.tile_j < chunk || c.tile_j % chunk != 0 || c.tile_j > (1 << 20))
         return hh_set_global_error(HH_EINVAL, "hh_create: tile_j (list part length) must be a multiple of 128 "
                                               "(HH_FP64) or 256 (HH_MIXED)");
@@ -550,6 +552,16 @@ namespace {
 // index scan (they are valid by construction); everything else is checked.
 // Work items and partial sums grow with the lists; kernels captured in the
 // loop graph hold the old pointers, so the graph is rebuilt.
+// Work items a block step with at most kSmallDue due particles can have when
+// it uses parts of tile_j_small: at most kSmallDue tiles, each with the
+// longest list.
+int64_t small_parts_bound(const hh_ctx *ctx, int64_t n_tiles, int64_t lmax)
+{
+    const int64_t pj = ctx->cfg.tile_j_small;
+    if (pj <= 0) return 0;
+    return std::min<int64_t>(n_tiles, kSmallDue) * std::max<int64_t>(1, (lmax + pj - 1) / pj);
+}
+
 int ensure_parts(hh_ctx *ctx, int64_t total_parts)
 {
     if (total_parts <= ctx->cap_parts) return HH_OK;
@@ -613,7 +625,11 @@ int set_lists_core(hh_ctx *ctx, int64_t n_particles, int64_t n_j, int32_t n_grou
     }
     if (int64_t(tiles.size()) > ctx->cap_tiles) return fail(ctx, HH_ENOMEM, "hh_set_lists: too many tiles");
     if (total_parts > INT32_MAX / 2) return fail(ctx, HH_ENOMEM, "hh_set_lists: too many list parts");
-    if ((rc = ensure_parts(ctx, total_parts))) return rc;
+    int64_t lmax = 0;
+    for (int32_t g = 0; g < n_groups; g++) lmax = std::max<int64_t>(lmax, off[g + 1] - off[g]);
+    const int64_t small_parts = small_parts_bound(ctx, int64_t(tiles.size()), lmax);
+    if (small_parts > INT32_MAX / 2) return fail(ctx, HH_ENOMEM, "hh_set_lists: too many short list parts");
+    if ((rc = ensure_parts(ctx, std::max(total_parts, small_parts)))) return rc;
     CK(cudaMemcpyAsync(ctx->off, off, sizeof(int64_t) * (n_groups + 1), cudaMemcpyHostToDevice, ctx->stream));
     if (L) CK(cudaMemcpyAsync(ctx->idx, idx, sizeof(int32_t) * L, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->group_of, group_of, sizeof(int32_t) * n_particles, cudaMemcpyHostToDevice, ctx->stream));
@@ -628,6 +644,7 @@ int set_lists_core(hh_ctx *ctx, int64_t n_particles, int64_t n_j, int32_t n_grou
     ctx->list_len = L;
     ctx->n_tiles = int32_t(tiles.size());
     ctx->total_parts = total_parts;
+    ctx->small_parts = small_parts;
     ctx->h_group_of.assign(group_of, group_of + n_particles);
     if (int64_t(ctx->ids.size()) != n_particles) {
         ctx->ids.resize(size_t(n_particles));
@@ -923,9 +940,11 @@ int hh_load_particles(hh_ctx *ctx, int64_t n, const double *x, const double *v, 
 // Completes a device rebuild (hh_gtree.cu): work-item capacity, sizes,
 // mixed-form base records; the state buffers were swapped, so the loop graph
 // is rebuilt on the next hh_advance.
-int hh_finish_device_rebuild(hh_ctx *ctx, int64_t total_parts)
+int hh_finish_device_rebuild(hh_ctx *ctx, int64_t total_parts, int64_t lmax)
 {
-    int rc = ensure_parts(ctx, total_parts);
+    const int64_t small_parts = small_parts_bound(ctx, ctx->n_tiles, lmax);
+    if (small_parts > INT32_MAX / 2) return fail(ctx, HH_ENOMEM, "hh_rebuild: too many short list parts");
+    int rc = ensure_parts(ctx, std::max(total_parts, small_parts));
     if (rc) return rc;
     if (ctx->graph) {
         cudaGraphExecDestroy(ctx->graph);
@@ -940,6 +959,7 @@ int hh_finish_device_rebuild(hh_ctx *ctx, int64_t total_parts)
     }
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->total_parts = total_parts;
+    ctx->small_parts = small_parts;
     ctx->have_j = true;
     ctx->have_lists = true;
     ctx->predicted = false;

@@ -55,7 +55,7 @@ struct SimDesc {
     uint32_t *tile_lv;  // levels present in each tile
     DevScalars *ds;
     int64_t n, nj;
-    int32_t n_tiles, pj, work, work_split;
+    int32_t n_tiles, pj, work, work_split, pj_small;
     int64_t lbar;  // mean list length per group (list entries / groups)
     Params prm;
     double t_end;
@@ -590,15 +590,21 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                 // simulation's due particles (levels >= kmin, from its level
                 // histogram, fixed during this phase) must reach work_split:
                 // small steps keep short parts, which spread over more SMs
-                int work = sd.work;
-                if (work > 0 && sd.work_split > 0) {
+                // and with tile_j_small, steps of at most kSmallDue due
+                // particles take parts of that length
+                int work = sd.work, pj = sd.pj;
+                if ((work > 0 && sd.work_split > 0) || sd.pj_small > 0) {
                     const int cnt = sd.ds->lvl_cnt[lane];
                     const int due = __reduce_add_sync(0xffffffffu, lane >= kmin_of(tnow) ? cnt : 0);
-                    if (due < sd.work_split) work = 0;
+                    if (sd.work_split > 0 && due < sd.work_split) work = 0;
+                    if (sd.pj_small > 0 && due <= kSmallDue) {
+                        work = 0;
+                        pj = sd.pj_small;
+                    }
                 }
                 const uint32_t mask = __ballot_sync(0xffffffffu, act);
                 if (mask)
-                    append_tile_items(sd.L, tile, td, mask, sd.pj, work, &B.bs->n_items[par], &sd.ds->slot_par[par], items,
+                    append_tile_items(sd.L, tile, td, mask, pj, work, &B.bs->n_items[par], &sd.ds->slot_par[par], items,
                                       s, sd.ds->na_hist);
             }
         }
@@ -985,6 +991,7 @@ extern "C" int hh_batch_run(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const d
         d.pj = c->part_len;
         d.work = c->cfg.work_item;
         d.work_split = c->cfg.work_split;
+        d.pj_small = c->cfg.tile_j_small;
         d.lbar = c->n_groups > 0 ? std::max<int64_t>(1, c->list_len / c->n_groups) : 1;
         d.prm.eps2 = c->cfg.eps2;
         d.prm.eta = c->cfg.eta;
@@ -995,7 +1002,7 @@ extern "C" int hh_batch_run(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const d
         jb[s + 1] = jb[s] + c->nj;
         pb[s + 1] = pb[s] + c->n;
         tb[s + 1] = tb[s] + c->n_tiles;
-        items_needed += c->total_parts;
+        items_needed += std::max(c->total_parts, c->small_parts);
         // pending work of the context must be finished before the batch stream uses its memory
         if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bfail(b, HH_ECUDA, "hh_batch_run: context stream failed");
     }

@@ -22,7 +22,10 @@ int64_t *hh_gtree_ids(GTreeBuf *g);
 int hh_gtree_set_ids(GTreeBuf *g, const int64_t *ids, int64_t n, cudaStream_t st);
 struct hh_ctx;
 int hh_rebuild_device(hh_ctx *ctx, double t);        // hh_gtree.cu
-int hh_finish_device_rebuild(hh_ctx *ctx, int64_t total_parts);  // hh_api.cu
+int hh_finish_device_rebuild(hh_ctx *ctx, int64_t total_parts, int64_t lmax);  // hh_api.cu
+// Block steps of the batched loop with at most this many due particles use
+// list parts of tile_j_small (when set).
+constexpr int kSmallDue = 16;
 
 struct hh_ctx {
     int device = 0;
@@ -45,6 +48,7 @@ struct hh_ctx {
     uint32_t *tile_lv = nullptr;  // [cap_tiles] levels present in each tile (batched loop)
     int64_t cap_parts = 0;
     int64_t total_parts = 0;    // work items of a step with every tile active
+    int64_t small_parts = 0;    // work items a step with <= kSmallDue due particles can have (tile_j_small)
     int64_t device_bytes = 0;   // device memory allocated for this context
     int32_t part_len = 512;
     hh::DevScalars *ds = nullptr;

@@ -171,6 +171,7 @@ struct GCounts {
     int32_t lvl_n[kMaxDepth + 2];
     int32_t ncells, overflow, bad, G, R, A, pad[2];
     int64_t L, n_tiles, total_parts;
+    unsigned long long lmax;  // longest list
 };
 
 __global__ void k_root_init(Cells C, int32_t n, GCounts *gc)
@@ -183,6 +184,7 @@ __global__ void k_root_init(Cells C, int32_t n, GCounts *gc)
     for (int d = 0; d < kMaxDepth + 2; d++) gc->lvl_c0[d] = gc->lvl_n[d] = 0;
     gc->lvl_n[0] = 1;
     gc->ncells = gc->overflow = gc->bad = gc->G = gc->R = gc->A = 0;
+    gc->lmax = 0ull;
 }
 
 // Splits the cells of level d that hold more than `leaf` particles (and are
@@ -656,8 +658,9 @@ __global__ void k_list_off(int32_t G, int32_t R, const int64_t *scan_p, const in
 
 // tiles of <= tile_i particles per group, written at tile_off[g]
 __global__ void k_tile_counts(const int32_t *g_cell, PCells P, int32_t G, int tile_i, const int64_t *off, int pj,
-                              int64_t *ntile, int64_t *nparts)
+                              int64_t *ntile, int64_t *nparts, GCounts *gc)
 {
+    unsigned long long lmax = 0ull;
     for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
         const int32_t c = g_cell[g];
         const int64_t cnt = P.end[c] - P.begin[c];
@@ -666,7 +669,9 @@ __global__ void k_tile_counts(const int32_t *g_cell, PCells P, int32_t G, int ti
         const int64_t parts = L > 0 ? (L + pj - 1) / pj : 1;
         ntile[g] = nt;
         nparts[g] = nt * parts;
+        lmax = max(lmax, (unsigned long long)L);
     }
+    if (lmax) atomicMax(&gc->lmax, lmax);
 }
 
 __global__ void k_tiles(const int32_t *g_cell, PCells P, int32_t G, int tile_i, const int64_t *tile_off, int4 *tiles)
@@ -979,7 +984,8 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
         return gfail(ctx, rc, "hh_rebuild: scan failed");
     k_list_off<<<grid, 256, 0, st>>>(G, R, scan_p, scan_n, ctx->off);
     // 6. tiles and their work-item capacity (from the list lengths)
-    k_tile_counts<<<grid, 256, 0, st>>>(g->g_cell, g->P, G, ctx->tile_i, ctx->off, ctx->part_len, g->ntile, g->nparts);
+    k_tile_counts<<<grid, 256, 0, st>>>(g->g_cell, g->P, G, ctx->tile_i, ctx->off, ctx->part_len, g->ntile, g->nparts,
+                                        g->gc);
     cudaMemsetAsync(g->ntile + G, 0, sizeof(int64_t), st);
     cudaMemsetAsync(g->nparts + G, 0, sizeof(int64_t), st);
     if ((rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->ntile, g->tile_off, G + 1, st)) ||
@@ -1014,5 +1020,5 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
     ctx->list_len = L;
     ctx->n_tiles = int32_t(n_tiles);
     ctx->ids_on_device = true;
-    return hh_finish_device_rebuild(ctx, total_parts);
+    return hh_finish_device_rebuild(ctx, total_parts, int64_t(g->gc_host->lmax));
 }

@@ -977,13 +977,46 @@ __device__ __forceinline__ bool force_item(const State &s, const Rec *__restrict
         write_out = sm.last;
         if (write_out) {
             const Red *base = partials + (int64_t)slot0 * kMaxTileI;
+            // Parts are added in blocks of kMergeBlock consecutive parts (more
+            // if the block sums would not fit the staging buffers, idle now):
+            // (output, block) pairs over all the group's threads each add
+            // their block's parts in part order, every load issued first;
+            // then each output adds its block sums in block order.  The order
+            // depends only on the number of parts, so results stay
+            // deterministic; with at most kMergeBlock parts it is the plain
+            // sequence p0 + p1 + p2 + ...  A long sequential chain of
+            // dependent adds would otherwise dominate a small block step split
+            // into many short parts.
+            E *buf = reinterpret_cast<E *>(&sm.rec[0][0]);
+            constexpr int kBuf = (int)(sizeof(sm.rec) / sizeof(E));
+            constexpr int kMergeBlock = 8;
+            int blk = kMergeBlock;
+            while ((int64_t)n_out * ((n_parts + blk - 1) / blk) > kBuf) blk *= 2;
+            const int n_blk = (n_parts + blk - 1) / blk;
+            for (int x = tid; x < n_out * n_blk; x += kThreads) {
+                const int b = x / n_out, o = x - b * n_out;
+                const int q0 = b * blk, q1 = min(n_parts, q0 + blk);
+                const Red *src = base + o / 7;
+                const int comp = o - 7 * (o / 7);
+                E vals[kMergeBlock];
+#pragma unroll
+                for (int k = 0; k < kMergeBlock; k++)
+                    if (q0 + k < q1) vals[k] = ld_comp_cg(&src[(int64_t)(q0 + k) * kMaxTileI].v[comp]);
+                E acc = vals[0];
+#pragma unroll
+                for (int k = 1; k < kMergeBlock; k++)
+                    if (q0 + k < q1) comp_add(acc, vals[k]);
+                for (int q = q0 + kMergeBlock; q < q1; q++)  // blocks longer than kMergeBlock
+                    comp_add(acc, ld_comp_cg(&src[(int64_t)q * kMaxTileI].v[comp]));
+                buf[x] = acc;
+            }
+            group_sync(bar_id);
 #pragma unroll
             for (int u = 0; u < 2; u++) {
-                const int t = tid + u * kThreads, slot = t / 7, comp = t - 7 * (t / 7);
+                const int t = tid + u * kThreads;
                 if (t < n_out) {
-                    r[u] = ld_comp_cg(&base[slot].v[comp]);
-                    for (int q = 1; q < n_parts; q++)
-                        comp_add(r[u], ld_comp_cg(&base[(int64_t)q * kMaxTileI + slot].v[comp]));
+                    r[u] = buf[t];
+                    for (int b = 1; b < n_blk; b++) comp_add(r[u], buf[b * n_out + t]);
                 }
             }
             if (tid == 0) L.tile_cnt[it.tile] = 0;

@@ -151,11 +151,13 @@ def test_bounded_barrier_reports_timeout(hh):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_step_adaptive_parts_do_not_depend_on_the_batch(hh, prec):
+@pytest.mark.parametrize("small", [False, True])
+def test_step_adaptive_parts_do_not_depend_on_the_batch(hh, prec, small):
     # work_split: equal-cost list parts only in block steps with at least 64
-    # active particles (the count is each simulation's own), so a simulation
-    # alone and the same simulation beside others reach the same bits; the
-    # graph loop (parts of tile_j throughout) agrees within FP64 reordering
+    # active particles; tile_j_small: short parts in steps with at most 16
+    # (both counts are each simulation's own), so a simulation alone and the
+    # same simulation beside others reach the same bits; the graph loop (parts
+    # of tile_j throughout) agrees within FP64 reordering
     P = hh.HH_FP64 if prec == "fp64" else hh.HH_MIXED
     t1 = 2.0 ** -6
 
@@ -169,6 +171,7 @@ def test_step_adaptive_parts_do_not_depend_on_the_batch(hh, prec):
         c.eps2, c.precision, c.theta, c.n_crit = 1e-6, P, th, 32
         c.tile_j = 256 if P == hh.HH_FP64 else 512
         c.work_item, c.work_split = 2048, 64
+        c.tile_j_small = (64 if P == hh.HH_FP64 else 128) if small else 0
         ctx = hh.Context(c, len(m), 2 * len(m), 64 * len(m) * max(1, len(m) // 16), len(m))
         ctx.hh_load_particles(x.T, v.T, m)
         ctx.hh_run(0.0, 0.0)
