@@ -45,12 +45,16 @@ FLOP_PER_INT = 60
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_batch
 # launch, plain FP64, one 1/64 interval of the N = 65536 run, from one ncu
 # capture of that launch.  It holds only for the kernel sources it was taken
-# with (their digest below): when they differ, the line reports null.
-TRAFFIC_FP64 = {"bytes": None, "sources_sha16": None,
+# with (their digest below) and for the tile shape it was taken with: when
+# either differs, the line reports null.
+TRAFFIC_FP64 = {"bytes": 82916608 + 53274880, "sources_sha16": "4b1609ed441c3773",
+                "shape": {"n_crit": 64, "tile_i": 8, "tile_j": 256, "work_item": 2048, "work_split": 2048,
+                          "tile_j_small": 64},
                 "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none "
                            "-k regex:k_batch -s 1 -c 1 on bench.py --steps 1 --warmup 1 --no-mixed "
-                           "--no-autotune --ensemble 0 --serve-seconds 0 --no-cpu-baseline --no-config1 "
-                           "--no-config3"}
+                           "--no-autotune --n-crit 64 --tile-i 8 --tile-j 256 --work-item 2048 "
+                           "--work-split 2048 --tile-j-small 64 --ensemble 0 --serve-seconds 0 "
+                           "--no-cpu-baseline --no-config1 --no-config3"}
 KERNEL_SOURCES = ("paper_1602_02832_gb300/csrc/hh_batch.cu", "paper_1602_02832_gb300/csrc/hh_kernels.cuh")
 METRIC = "interactions/s & equiv. Tflops (60 flop/int); block-steps/s, p50/p99 latency vs plain"
 CPU_SAMPLE_T = 1.0 / 256  # oracle sample: the first quarter of the first timed interval
@@ -65,11 +69,16 @@ def _sources_sha16():
     return h.hexdigest()[:16]
 
 
-def _traffic():
-    """Captured DRAM bytes per launch if the kernel sources are those of the capture, else None."""
-    if TRAFFIC_FP64["bytes"] and TRAFFIC_FP64["sources_sha16"] == _sources_sha16():
+def _traffic(shape):
+    """Captured DRAM bytes per launch if the kernel sources and the tile shape
+    are those of the capture, else None."""
+    if (TRAFFIC_FP64["bytes"] and TRAFFIC_FP64["sources_sha16"] == _sources_sha16()
+            and shape == TRAFFIC_FP64["shape"]):
         return TRAFFIC_FP64["bytes"]
     return None
+
+
+SHAPE_KEYS = ("n_crit", "tile_i", "tile_j", "work_item", "work_split", "tile_j_small")
 
 
 def _args(argv=None):
@@ -90,6 +99,10 @@ def _args(argv=None):
                    help="active particles from which work items apply, plain form (0: every step)")
     p.add_argument("--work-split-mixed", type=int, default=0,
                    help="active particles from which work items apply, mixed form (0: every step)")
+    p.add_argument("--tile-j-small", type=int, default=0,
+                   help="list part length of block steps with at most 16 due particles, plain form (0: tile_j)")
+    p.add_argument("--tile-j-small-mixed", type=int, default=0,
+                   help="list part length of block steps with at most 16 due particles, mixed form (0: tile_j)")
     p.add_argument("--no-mixed", action="store_true")
     p.add_argument("--mixed-only", action="store_true", help="run only the mixed form (profiling aid)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -147,6 +160,7 @@ def _cfg(hh, prec, a):
     c.tile_j = (a.tile_j if prec == hh.HH_FP64 else a.tile_j_mixed) or 0
     c.work_item = (a.work_item if prec == hh.HH_FP64 else a.work_item_mixed) or 0
     c.work_split = (a.work_split if prec == hh.HH_FP64 else a.work_split_mixed) or 0
+    c.tile_j_small = (a.tile_j_small if prec == hh.HH_FP64 else a.tile_j_small_mixed) or 0
     c.order = hh.HH_ORDER_HILBERT if a.order == "hilbert" else hh.HH_ORDER_MORTON
     return c
 
@@ -352,6 +366,7 @@ def _run_form(hh, torch, a, prec, seed, steps, warmup, flush, e2e_steps=0, over=
     stream = torch.cuda.Stream()
     ctx.hh_set_stream(stream.cuda_stream)
     dtt = cfg.dt_tree
+    shape = {k: int(getattr(cfg, k)) for k in SHAPE_KEYS}
     ctx.hh_load_particles(x.T, v.T, m)
     ctx.hh_set_rebuild_device(_on_device(a, a.n))
     ctx.hh_run(0.0, 0.0)  # rebuild, initial forces, rebuild with node derivatives, initial steps
@@ -392,7 +407,7 @@ def _run_form(hh, torch, a, prec, seed, steps, warmup, flush, e2e_steps=0, over=
         "block_steps": c1["block_steps"] - c0["block_steps"],
         "particle_steps": c1["particle_steps"] - c0["particle_steps"],
         "force_ms": force_ms, "force_launches": force_launches, "gpu_launches": launches, "t_end": t,
-        "n_i_hist": hist, "warm_state": warm_state,
+        "n_i_hist": hist, "warm_state": warm_state, "shape": shape,
     }
     if e2e_steps:
         # end to end through host buffers: upload the step's particle state,
@@ -867,7 +882,7 @@ def main():
                          "bound": "alu",
                          "achieved": achieved, "peak": peaks.get("fp64_tflops"), "unit": "TFLOP/s",
                          "frac": achieved / peaks["fp64_tflops"] if peaks.get("fp64_tflops") else None,
-                         "traffic": _traffic() if a.loop == "persistent" else None,
+                         "traffic": _traffic(res["shape"]) if a.loop == "persistent" else None,
                          "traffic_capture": TRAFFIC_FP64["capture"],
                          "note": "achieved = 60 algorithmic flop per interaction / device time of the force "
                                  "phases (persistent loop: %globaltimer stamps at the phase barriers, the phase "
@@ -875,7 +890,8 @@ def main():
                                  "the force kernel); peak = measured FP64 FMA throughput "
                                  "(of measured, libhh_peaks.so); traffic = DRAM bytes of one k_batch launch "
                                  "(one interval, all phases) from one ncu capture of that launch "
-                                 "(traffic_capture), null when the kernel sources differ from the captured ones"},
+                                 "(traffic_capture), null when the kernel sources or the tile shape differ from the "
+                                 "captured ones"},
             "e2e": {"value": tot[4] / (mx[1] * 1e-3), "unit": "interactions/s",
                     "h2d_bytes_per_step": res["e2e"]["bi"], "d2h_bytes_per_step": res["e2e"]["bo"]},
             "gpu_launches": int(tot[3]),

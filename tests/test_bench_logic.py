@@ -65,13 +65,16 @@ def test_reference_arm_prints_one_contract_line():
 
 
 def test_traffic_is_reported_only_for_the_captured_kernel_sources(monkeypatch):
+    shape = dict(bench.TRAFFIC_FP64["shape"])
+    assert set(shape) == set(bench.SHAPE_KEYS)
     monkeypatch.setitem(bench.TRAFFIC_FP64, "bytes", 123.0)
     monkeypatch.setitem(bench.TRAFFIC_FP64, "sources_sha16", bench._sources_sha16())
-    assert bench._traffic() == 123.0
+    assert bench._traffic(shape) == 123.0
+    assert bench._traffic(dict(shape, tile_j=512)) is None  # another tile shape
     monkeypatch.setitem(bench.TRAFFIC_FP64, "sources_sha16", "0" * 16)
-    assert bench._traffic() is None
+    assert bench._traffic(shape) is None
     monkeypatch.setitem(bench.TRAFFIC_FP64, "bytes", None)
-    assert bench._traffic() is None
+    assert bench._traffic(shape) is None
 
 
 def test_cpu_leg_resumes_the_given_state_and_checks_sampled_forces(orc):
