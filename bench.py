@@ -57,7 +57,8 @@ TRAFFIC_FP64 = {"bytes": 82916608 + 53274880, "sources_sha16": "4b1609ed441c3773
                            "--no-cpu-baseline --no-config1 --no-config3"}
 KERNEL_SOURCES = ("paper_1602_02832_gb300/csrc/hh_batch.cu", "paper_1602_02832_gb300/csrc/hh_kernels.cuh")
 METRIC = "interactions/s & equiv. Tflops (60 flop/int); block-steps/s, p50/p99 latency vs plain"
-CPU_SAMPLE_T = 1.0 / 256  # oracle sample: the first quarter of the first timed interval
+CPU_SAMPLE_T = 1.0 / 256  # reference arm, per step: the first quarter of the first timed interval
+CPU_BASELINE_T = 4.0 / 64  # cpu_baseline leg: the first four timed intervals (about 12 s on 16 cores)
 
 
 def _sources_sha16():
@@ -512,6 +513,37 @@ def _lat_by_live(step_us, live):
     return out
 
 
+def _queue_by_quarter(queue, wall_s):
+    """Mean requests waiting (arrived, not yet resident) and mean resident
+    simulations over each quarter of the window, from the per-launch samples:
+    a queue that grows from quarter to quarter means the arrivals outrun the
+    server."""
+    out = []
+    for q in range(4):
+        lo, hi = wall_s * q / 4, wall_s * (q + 1) / 4
+        s = [(w, r) for t, w, r in queue if lo <= t < hi]
+        out.append({"quarter": q + 1, "launches": len(s),
+                    "waiting_mean": sum(w for w, _ in s) / len(s) if s else None,
+                    "resident_mean": sum(r for _, r in s) / len(s) if s else None})
+    return out
+
+
+def _lat_by_n(results, n_of):
+    """Request latency (arrival to completion) by request size: N in
+    [2^10, 2^12), [2^12, 2^14), [2^14, 2^16), [2^16, 2^18]."""
+    import numpy as np
+
+    out = []
+    for lo in (1 << 10, 1 << 12, 1 << 14, 1 << 16):
+        top = lo == 1 << 16
+        u = [r.done_s - r.arrival_s for r in results
+             if lo <= n_of[r.rid] and (n_of[r.rid] <= 4 * lo if top else n_of[r.rid] < 4 * lo)]
+        if u:
+            out.append({"n": [lo, 4 * lo if top else 4 * lo - 1], "completed": len(u),
+                        "p50_s": float(np.quantile(u, 0.5)), "max_s": float(max(u))})
+    return out or None
+
+
 def _serving(hh, a, rate=20.0, seconds=None, launch_particles=0):
     """Serving: Poisson arrivals of Plummer + Salpeter cluster requests, N
     log-uniform in [2^10, 2^18], t_end in {1/8, 1/4, 1/2}, admitted within a
@@ -533,21 +565,24 @@ def _serving(hh, a, rate=20.0, seconds=None, launch_particles=0):
     res, st = srv.run(reqs, realtime=True, max_wall_s=seconds)
     srv.close()
     arrived = sum(1 for r in stream if r.arrival_s <= st.wall_s)
-    # requests that arrived at least 10 s before the end (the longest request,
-    # N = 2^18 to t = 1/2, takes about that long): all of them finish when the
-    # server keeps up with the arrivals
-    early = [r for r in stream if r.arrival_s <= st.wall_s - 10.0]
     done_ids = {r.rid for r in res}
+    # requests that arrived in the first half of the window: all of them
+    # finish when the server keeps up with the arrivals (the longest request,
+    # N = 2^18 to t = 1/2, takes several seconds under load)
+    early = [r for r in stream if r.arrival_s <= st.wall_s / 2]
     return {"arrival_rate_per_s": rate, "window_s": seconds, "launch_particles": launch_particles or None,
             "requests_arrived": arrived, "completed": len(res),
             "completion_rate_per_s": len(res) / st.wall_s,
-            "completed_of_arrived_10s_before_end": [sum(1 for r in early if r.rid in done_ids), len(early)],
+            "completed_of_first_half_arrivals": [sum(1 for r in early if r.rid in done_ids), len(early)],
+            "unfinished_at_end": arrived - len(res),
+            "queue_by_quarter": _queue_by_quarter(st.queue, st.wall_s),
             "wall_s": st.wall_s, "launches": st.launches,
             "block_steps_per_s": st.block_steps / st.wall_s, "interactions_per_s": st.interactions / st.wall_s,
             "block_step_latency_us": _lat(st.step_us),
             "block_step_latency_by_live": _lat_by_live(st.step_us, st.live_per_step),
             "request_latency_s": _lat([r.done_s - r.arrival_s for r in res],
                                       "wall seconds from a request's arrival to its completion") if res else None,
+            "request_latency_by_n": _lat_by_n(res, {r.rid: r.n for r in stream}),
             "note": "requests arrive in real time over the window; unfinished ones are stopped at its end"}
 
 
@@ -725,8 +760,8 @@ def _cpu_baseline(a, state, cfg3=None):
     """The CPU leg: the FP64 oracle, as it stands, on the host cores.
     (1) Timed on a bounded sample of the timed window: resumed from the GPU
     arm's synchronised state at the start of its first timed interval, over
-    the first quarter of that interval (the same block steps, lists and
-    interactions, up to rounding).  (2) With cfg3, the oracle's list force on
+    its first four intervals, rebuilds included (the same block steps, lists
+    and interactions, up to rounding).  (2) With cfg3, the oracle's list force on
     the sampled particles of the N = 2^20 run, on the GPU's own j entries and
     lists, compared with the GPU's forces."""
     import numpy as np
@@ -736,13 +771,13 @@ def _cpu_baseline(a, state, cfg3=None):
     p = _oracle_params(a)
     t0 = state["t"]
     w0 = time.perf_counter()
-    r = oracle.resume(state["x"], state["v"], state["a"], state["jk"], state["dt"], state["m"], t0,
-                      t0 + CPU_SAMPLE_T, p)
+    t1 = t0 + min(CPU_BASELINE_T, a.steps * p.dt_tree)
+    r = oracle.resume(state["x"], state["v"], state["a"], state["jk"], state["dt"], state["m"], t0, t1, p)
     dt = time.perf_counter() - w0
     out = {"value": r["stats"]["interactions"] / dt, "unit": "interactions/s", "cores": oracle.num_threads(),
            "kind": "oracle",
            "sample": f"FP64 oracle tree loop resumed from the GPU arm's state at t = {t0:g} (the start of its "
-                     f"first timed interval, N={a.n}) over t in [{t0:g}, {t0 + CPU_SAMPLE_T:g}] "
+                     f"first timed interval, N={a.n}) over t in [{t0:g}, {t1:g}] "
                      f"({r['stats']['particle_steps']} particle steps, {r['stats']['interactions']} "
                      f"interactions, {dt:.1f} s)"}
     if cfg3:

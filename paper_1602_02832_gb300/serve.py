@@ -73,6 +73,8 @@ class ServerStats:
     step_us: list = field(default_factory=list)       # duration of each global block step
     live_per_step: list = field(default_factory=list)  # simulations advanced in that launch
     phase_us: list = field(default_factory=lambda: [0.0, 0.0])  # device time in predict + select, force + correct
+    # per launch: (wall seconds, requests arrived but not yet resident, resident simulations)
+    queue: list = field(default_factory=list)
     launches: int = 0
     block_steps: int = 0          # sum over simulations of block steps
     interactions: int = 0
@@ -252,6 +254,8 @@ class Server:
                     continue
                 steps, launched, done, us = self.batch.hh_batch_step(self.max_steps)
                 if launched:
+                    self.stats.queue.append((time.perf_counter() - t0,
+                                             len(preparing) + len(waiting) + len(creating) + len(created), len(live)))
                     self.stats.launches += 1
                     self.stats.step_us.extend(us.tolist())
                     self.stats.live_per_step.extend([launched] * len(us))

@@ -111,3 +111,23 @@ def test_latency_by_live_count_bins():
     assert [b["steps"] for b in out] == [2, 2, 1]
     assert out[0]["p50_us"] == pytest.approx(15.0) and out[2]["p99_us"] == pytest.approx(50.0)
     assert bench._lat_by_live([], []) is None
+
+
+def test_queue_by_quarter_and_latency_by_size():
+    q = [(0.5, 0, 1), (1.0, 2, 3), (3.0, 4, 5), (3.5, 6, 7), (7.9, 1, 1)]
+    out = bench._queue_by_quarter(q, 8.0)
+    assert [b["launches"] for b in out] == [2, 2, 0, 1]
+    assert out[0]["waiting_mean"] == 1.0 and out[1]["resident_mean"] == 6.0
+    assert out[2]["waiting_mean"] is None and out[3]["waiting_mean"] == 1.0
+
+    class R:
+        def __init__(self, rid, arrival_s, done_s):
+            self.rid, self.arrival_s, self.done_s = rid, arrival_s, done_s
+
+    n_of = {0: 1024, 1: 4095, 2: 4096, 3: 1 << 18}
+    res = [R(0, 0.0, 1.0), R(1, 0.0, 3.0), R(2, 1.0, 2.0), R(3, 0.0, 9.0)]
+    by = bench._lat_by_n(res, n_of)
+    assert [b["n"] for b in by] == [[1024, 4095], [4096, 16383], [65536, 1 << 18]]
+    assert by[0]["completed"] == 2 and by[0]["max_s"] == 3.0
+    assert by[2]["p50_s"] == 9.0
+    assert bench._lat_by_n([], n_of) is None

@@ -172,7 +172,10 @@ def test_server_budget_order_and_completion(monkeypatch):
     assert FakeCtx.peak <= 4
     assert srv.batch.peak_bytes <= 1000 * 1500
     assert max(srv.batch.calls) >= 2  # simulations were batched together
-    assert stats.launches == len(srv.batch.calls)
+    assert stats.launches == len(srv.batch.calls) == len(stats.queue)
+    # every launch sampled the queue: (wall s, waiting, resident), resident >= 1
+    assert all(w >= 0 and r >= 1 for _, w, r in stats.queue)
+    assert [t for t, _, _ in stats.queue] == sorted(t for t, _, _ in stats.queue)
     # the device-time split adds up the kernel's phases over every launch
     assert stats.phase_us[0] == pytest.approx(0.25 * len(stats.step_us))
     assert stats.phase_us[1] == pytest.approx(0.75 * len(stats.step_us))
