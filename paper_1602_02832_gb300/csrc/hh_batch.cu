@@ -66,6 +66,7 @@ struct BatchScalars {
     int32_t err;
     uint32_t work[2];     // force queue head, by step parity
     uint32_t n_items[2];  // work items, by step parity
+    uint32_t max_chunks[2];  // longest list part of a list-mode simulation in 32-entry chunks, by step parity
     int32_t steps_done;
 };
 
@@ -286,33 +287,42 @@ __device__ __forceinline__ double correct_tile_3lane(const SimDesc &sd, const in
 struct StepCache {
     double t[kSimCache];
     double t_end[kSimCache];
+    int due[kSimCache];                  // particles due at t (levels >= kmin(t)); -1: not counted
     unsigned char list_mode[kSimCache];  // predict only the entries of this step's list parts
     int any_list;                        // some simulation of the batch is in list mode this step
 };
 
-// A small block step of a large simulation references few of its j entries:
-// its due tiles' lists.  Then predicting those (in a phase after the tile
-// selection) is cheaper than predicting every entry.  The choice compares the
-// due particles (the levels >= kmin(t) of the simulation's level histogram,
-// which nobody writes during this phase, so every CTA decides alike) times
-// the mean list length with the number of j entries, and applies only to
-// simulations whose every-entry pass costs more than the extra phase and
-// grid barrier (a few microseconds): at least kListModeMinJ entries.  It
-// changes no result: a predicted record is the same whoever computes it.
-constexpr int64_t kListModeMinJ = 1 << 18;
-
-__device__ __forceinline__ bool list_mode_of(const SimDesc &sd, double tnow)
+// Due particles of a simulation at block time tnow: its level histogram's
+// levels >= kmin(tnow) (nobody writes the histogram during phase 1, so
+// every CTA counts alike).
+__device__ __forceinline__ int due_count(const SimDesc &sd, double tnow)
 {
-    constexpr int64_t kDiv = 2;  // list entries counted with their repeats across a step's tiles
-    if (sd.nj < kListModeMinJ || !(tnow <= sd.t_end) || !(tnow > 0.0)) return false;
     const int k0 = kmin_of(tnow);
-    int64_t due = 0;
+    int due = 0;
 #pragma unroll
     for (int k = 0; k < 32; k++) {
         const int c = __ldcg(&sd.ds->lvl_cnt[k]);
         due += k >= k0 ? c : 0;
     }
-    return due * sd.lbar * kDiv < sd.nj;
+    return due;
+}
+
+// A small block step of a large simulation references few of its j entries:
+// its due tiles' lists.  Then predicting those (in a phase after the tile
+// selection) is cheaper than predicting every entry.  The choice compares the
+// due particles times the mean list length with the number of j entries, and
+// applies only to simulations whose every-entry pass costs more than the
+// extra phase and grid barrier (a few microseconds): at least kListModeMinJ
+// entries.  (Many small simulations together gain nothing from it: their
+// every-entry passes are short and run side by side.)  It changes no result:
+// a predicted record is the same whoever computes it.
+constexpr int64_t kListModeMinJ = 1 << 18;
+
+__device__ __forceinline__ bool list_mode_of(const SimDesc &sd, double tnow, int due)
+{
+    constexpr int64_t kDiv = 2;  // list entries counted with their repeats across a step's tiles
+    if (sd.nj < kListModeMinJ || !(tnow <= sd.t_end) || !(tnow > 0.0)) return false;
+    return (int64_t)due * sd.lbar * kDiv < sd.nj;
 }
 
 __device__ __forceinline__ void cache_times(StepCache &c, const SimDesc *sims, int n_sims, int par)
@@ -323,7 +333,11 @@ __device__ __forceinline__ void cache_times(StepCache &c, const SimDesc *sims, i
     for (int s = threadIdx.x; s < n_sims && s < kSimCache; s += blockDim.x) {
         c.t[s] = __longlong_as_double((long long)__ldcg(&sims[s].ds->tmin[par]));
         c.t_end[s] = sims[s].t_end;
-        const bool lm = list_mode_of(sims[s], c.t[s]);
+        // (counted here only where list mode may apply: the count is one
+        // more round trip to L2 on the path of every step)
+        const int due = sims[s].nj >= kListModeMinJ ? due_count(sims[s], c.t[s]) : -1;
+        c.due[s] = due;
+        const bool lm = due >= 0 && list_mode_of(sims[s], c.t[s], due);
         c.list_mode[s] = lm;
         any |= lm;
     }
@@ -537,15 +551,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
         PredIn<Rec> in0;
         const int s_p0 = gtid < NJ ? find_sim(JB, n_sims, gtid) : 0;
         if (kEarly && gtid < NJ) pred_load<Rec>(SD(s_p0).st, gtid - JB[s_p0], in0);
-        const int64_t w_first = gtid >> 5;
-        const int s_t0 = w_first < NT ? find_sim(TB, n_sims, w_first) : 0;
-        const uint32_t lv_first = w_first < NT ? SD(s_t0).tile_lv[w_first - TB[s_t0]] : 0u;
         cache_times(sc, B.sims, n_sims, par);
         if (blockIdx.x == 0) {
             // counters of the previous step (other parity) are free again
             if (tid == 0) {
                 B.bs->work[par ^ 1] = 0u;
                 B.bs->n_items[par ^ 1] = 0u;
+                B.bs->max_chunks[par ^ 1] = 0u;
             }
             for (int s = tid >> 5; s < n_sims; s += blockDim.x >> 5) {
                 // the next block time starts from the due times of the levels
@@ -573,53 +585,79 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
             else predict_entry<Rec>(sd.st, (Rec *)sd.rec, g - JB[s], tnow);
         }
         {
+            // Tile selection: warp w takes tiles w + k W (W warps, k = 0,
+            // 1, ...); its lanes read the level masks of 32 of them per round
+            // trip, and the warp then builds the items of the due ones among
+            // them, one tile at a time.
             const int lane = tid & 31;
             const int64_t w0 = gtid >> 5, nw = nth >> 5;
-            for (int64_t wt = w0; wt < NT; wt += nw) {
-                const int s = find_sim(TB, n_sims, wt);  // warp-uniform
-                const SimDesc &sd = SD(s);
-                const double tnow = cached_time(sc, B.sims, s, par);
-                if (!(tnow <= sd.t_end)) continue;
-                const int tile = (int)(wt - TB[s]);
-                const uint32_t lv = wt == w_first ? lv_first : sd.tile_lv[tile];
-                if ((lv >> kmin_of(tnow)) == 0u) continue;  // no due level in this tile
-                const int4 td = sd.L.tiles[tile];
-                const int64_t p = td.x + lane;
-                const bool act = (p < td.y) && (sd.st.t[p] + sd.st.dt[p] == tnow);
-                // equal-cost items in this step?  With work_split the
-                // simulation's due particles (levels >= kmin, from its level
-                // histogram, fixed during this phase) must reach work_split:
-                // small steps keep short parts, which spread over more SMs
-                // and with tile_j_small, steps of at most kSmallDue due
-                // particles take parts of that length
-                int work = sd.work, pj = sd.pj;
-                if ((work > 0 && sd.work_split > 0) || sd.pj_small > 0) {
-                    const int cnt = sd.ds->lvl_cnt[lane];
-                    const int due = __reduce_add_sync(0xffffffffu, lane >= kmin_of(tnow) ? cnt : 0);
-                    if (sd.work_split > 0 && due < sd.work_split) work = 0;
-                    if (sd.pj_small > 0 && due <= kSmallDue) {
-                        work = 0;
-                        pj = sd.pj_small;
+            for (int64_t k0 = 0; w0 + k0 * nw < NT; k0 += 32) {
+                const int64_t wt = w0 + (k0 + lane) * nw;
+                int s_l = 0;
+                bool due_l = false;
+                if (wt < NT) {
+                    s_l = find_sim(TB, n_sims, wt);
+                    const SimDesc &sd = SD(s_l);
+                    const double tnow = cached_time(sc, B.sims, s_l, par);
+                    const uint32_t lv = sd.tile_lv[wt - TB[s_l]];
+                    due_l = tnow <= sd.t_end && (lv >> kmin_of(tnow)) != 0u;  // a due level in this tile
+                }
+                for (uint32_t dmask = __ballot_sync(0xffffffffu, due_l); dmask; dmask &= dmask - 1) {
+                    const int l = __ffs(dmask) - 1;
+                    const int s = __shfl_sync(0xffffffffu, s_l, l);
+                    const SimDesc &sd = SD(s);
+                    const double tnow = cached_time(sc, B.sims, s, par);
+                    const int tile = (int)(w0 + (k0 + l) * nw - TB[s]);
+                    const int4 td = sd.L.tiles[tile];
+                    const int64_t p = td.x + lane;
+                    const bool act = (p < td.y) && (sd.st.t[p] + sd.st.dt[p] == tnow);
+                    // equal-cost items in this step?  With work_split the
+                    // simulation's due particles (levels >= kmin, from its
+                    // level histogram, fixed during this phase) must reach
+                    // work_split: small steps keep short parts, which spread
+                    // over more SMs, and with tile_j_small, steps of at most
+                    // kSmallDue due particles take parts of that length
+                    int work = sd.work, pj = sd.pj;
+                    if ((work > 0 && sd.work_split > 0) || sd.pj_small > 0) {
+                        int due;
+                        if (s < kSimCache && sc.due[s] >= 0) {
+                            due = sc.due[s];
+                        } else {
+                            const int cnt = __ldcg(&sd.ds->lvl_cnt[lane]);
+                            due = __reduce_add_sync(0xffffffffu, lane >= kmin_of(tnow) ? cnt : 0);
+                        }
+                        if (sd.work_split > 0 && due < sd.work_split) work = 0;
+                        if (sd.pj_small > 0 && due <= kSmallDue) {
+                            work = 0;
+                            pj = sd.pj_small;
+                        }
+                    }
+                    const uint32_t mask = __ballot_sync(0xffffffffu, act);
+                    if (mask) {
+                        append_tile_items(sd.L, tile, td, mask, pj, work, &B.bs->n_items[par], &sd.ds->slot_par[par],
+                                          items, s, sd.ds->na_hist);
+                        if (lane == 0 && cached_list_mode(sc, s)) {
+                            // the entries phase 1b predicts per item, at most
+                            const int64_t len = sd.L.off[td.z + 1] - sd.L.off[td.z];
+                            const int64_t pe = min((int64_t)part_len_for(__popc(mask), pj, work), len);
+                            atomicMax(&B.bs->max_chunks[par], (uint32_t)((pe + 31) / 32));
+                        }
                     }
                 }
-                const uint32_t mask = __ballot_sync(0xffffffffu, act);
-                if (mask)
-                    append_tile_items(sd.L, tile, td, mask, pj, work, &B.bs->n_items[par], &sd.ds->slot_par[par], items,
-                                      s, sd.ds->na_hist);
             }
         }
         if (!grid_sync(B.bs)) return;
         if (sc.any_list) {
             // ---- phase 1b: list-mode simulations predict the entries of
             // this step's list parts.  A task is 32 consecutive entries of
-            // one work item (lane = entry); entries shared by several parts
-            // are predicted more than once, with the same result.
+            // one work item (lane = entry), up to the step's longest part, so
+            // the few items of a small step spread over every SM.  Entries
+            // shared by several parts are predicted more than once, with the
+            // same result.
             const uint32_t n_items = __ldcg(&B.bs->n_items[par]);
+            const int maxc = max(1, (int)__ldcg(&B.bs->max_chunks[par]));
             const int lane = tid & 31;
             const int64_t w0 = gtid >> 5, nw = nth >> 5;
-            int maxc = 1;  // tasks per item: the longest part length of a list-mode simulation / 32
-            for (int s = 0; s < n_sims && s < kSimCache; s++)
-                if (sc.list_mode[s]) maxc = max(maxc, (SD(s).pj + 31) / 32);
             const int64_t n_tasks = (int64_t)n_items * maxc;
             for (int64_t task = w0; task < n_tasks; task += nw) {
                 const int64_t i = task / maxc;

@@ -200,11 +200,13 @@ def test_step_adaptive_parts_do_not_depend_on_the_batch(hh, prec, small):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_list_mode_prediction_changes_no_bit(hh, prec):
+@pytest.mark.parametrize("work", [(0, 0), (8192, 0)])
+def test_list_mode_prediction_changes_no_bit(hh, prec, work):
     # N = 2^18 (about 3.4e5 j entries, above the size from which the batched
     # loop predicts only the entries of a small step's list parts): the
     # batched run equals, bit for bit, the graph loop, which predicts every
-    # entry at every step
+    # entry at every step; with equal-cost parts in every step, a lone active
+    # particle's part is 8192 entries long, and every entry of it is predicted
     P = hh.HH_FP64 if prec == "fp64" else hh.HH_MIXED
     n = 1 << 18
     x, v, m = synth.plummer(n, 9)
@@ -213,6 +215,7 @@ def test_list_mode_prediction_changes_no_bit(hh, prec):
     def make():
         c = hh.hh_config_default()
         c.eps2, c.precision, c.n_crit = 1e-8, P, 64
+        c.work_item, c.work_split = work
         z = np.zeros((3, n))
         T0 = hh.hh_tree_build(x.T, v.T, z, z, m, leaf=8, n_crit=64, theta=0.5)
         ctx = hh.Context(c, n, 2 * n, 2 * len(T0.idx) + 1024, 2 * T0.n_groups + 64)
@@ -235,3 +238,4 @@ def test_list_mode_prediction_changes_no_bit(hh, prec):
     for k in ("x", "v", "a", "jk", "t", "dt"):
         assert np.array_equal(got[k], ref[k]), k
     assert got_c["interactions"] == ref_c["interactions"]
+
