@@ -197,22 +197,46 @@ __global__ void k_level(Cells C, const uint64_t *key, int d, int leaf, GCounts *
     if (gc->overflow) return;
     const int32_t c0 = gc->lvl_c0[d], nc = gc->lvl_n[d], next0 = c0 + nc;
     if (blockIdx.x == 0 && threadIdx.x == 0) gc->lvl_c0[d + 1] = next0;
-    for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
-        const int32_t c = c0 + q;
-        const int32_t b = C.begin[c], e = C.end[c];
-        int32_t bound[9];
-        int nch = 0;
-        if (e - b > leaf && d < kMaxDepth) {
-            int32_t lo = b;
-            for (int o = 0; o < 8 && lo < e; o++) {
-                int32_t l = lo, h = e;  // first index with digit > o
+    // Eight lanes per cell: lane o finds where octant o ends (the first
+    // index of the cell's sorted range whose digit at this depth exceeds o)
+    // by its own binary search, so a large cell costs one search, not
+    // eight in a row.  The digit is monotone over the range, so these ends
+    // are the octant boundaries.
+    const int lane = threadIdx.x & 31;
+    const int64_t n_q = (int64_t)nc * 8;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;  // a multiple of 32: warps stay whole
+    for (int64_t q0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x - lane; q0 < n_q; q0 += stride) {
+        const int64_t q = q0 + lane;
+        const bool valid = q < n_q;
+        const int32_t c = c0 + (int32_t)(q >> 3);
+        const int o = (int)(q & 7);
+        int32_t b = 0, e = 0, hi = 0;
+        bool split = false;
+        if (valid) {
+            b = C.begin[c];
+            e = C.end[c];
+            split = e - b > leaf && d < kMaxDepth;
+            if (split) {
+                int32_t l = b, h = e;
                 while (l < h) {
                     const int32_t mid = (l + h) >> 1;
                     if (digit_at(key[mid], d) <= o) l = mid + 1;
                     else h = mid;
                 }
-                if (l > lo) bound[nch++] = lo;
-                lo = l;
+                hi = l;
+            }
+        }
+        int32_t ends[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) ends[k] = __shfl_sync(0xffffffffu, hi, (lane & ~7) | k);
+        if (!valid || o != 0) continue;
+        int32_t bound[9];
+        int nch = 0;
+        if (split) {
+            int32_t lo = b;
+            for (int k = 0; k < 8 && lo < e; k++) {
+                if (ends[k] > lo) bound[nch++] = lo;
+                lo = ends[k];
             }
             bound[nch] = e;
         }
@@ -324,28 +348,28 @@ __global__ void k_moments_level(const State s, Cells C, const GCounts *gc, int d
 {
     if (gc->overflow) return;
     const int32_t c0 = gc->lvl_c0[d], nc = gc->lvl_n[d];
-    for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
-        const int32_t c = c0 + q;
-        double acc[13];
-        for (int k = 0; k < 13; k++) acc[k] = 0.0;
+    // one thread per (cell, moment): the 13 sums of a cell run side by side
+    // (each in the same order as a single thread would take them), since a
+    // warp's FP64 instruction costs the pipe the same however few lanes use it
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < (int64_t)nc * 13;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = c0 + (int32_t)(q / 13);
+        const int w = (int)(q - (q / 13) * 13);
+        double acc = 0.0;
         const int nch = C.nchild[c];
         if (nch == 0) {
+            // w = 0: mass; 1 + 3k + dim: mass times x, v, a, jerk (k = 0..3)
+            const double *f = w == 0 ? nullptr : (w < 4 ? s.x : w < 7 ? s.v : w < 10 ? s.a : s.jk) +
+                                                     (int64_t)((w - 1) % 3) * s.cap_j;
             for (int32_t p = C.begin[c]; p < C.end[c]; p++) {
                 const double mi = s.m[p];
-                acc[0] += mi;
-                for (int d = 0; d < 3; d++) {
-                    acc[1 + d] += mi * s.x[d * s.cap_j + p];
-                    acc[4 + d] += mi * s.v[d * s.cap_j + p];
-                    acc[7 + d] += mi * s.a[d * s.cap_j + p];
-                    acc[10 + d] += mi * s.jk[d * s.cap_j + p];
-                }
+                acc = w == 0 ? acc + mi : fma(mi, f[p], acc);
             }
         } else {
             const int32_t f = C.first[c];
-            for (int k = 0; k < nch; k++)
-                for (int w = 0; w < 13; w++) acc[w] += mom[w * cap + f + k];
+            for (int k = 0; k < nch; k++) acc += mom[w * cap + f + k];
         }
-        for (int w = 0; w < 13; w++) mom[w * cap + c] = acc[w];
+        mom[w * cap + c] = acc;
     }
 }
 
