@@ -541,12 +541,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
     int step = 0;
     for (; step < max_steps; step++) {
         const int par = step & 1;
-        // ---- phase 1: predict + select
+        // ---- phase 1: select + predict
         // The inputs of this thread's first predicted entry (mixed form; the
         // plain form's FP64 inputs would not fit in registers, and its
-        // predictor is bound by the FP64 pipe) and the level mask of its
-        // warp's first tile do not depend on the block time: their loads go
-        // out before the block times are read.
+        // predictor is bound by the FP64 pipe) do not depend on the block
+        // time: their loads go out before the block times are read.
         constexpr bool kEarly = std::is_same<Rec, RecMix>::value;
         PredIn<Rec> in0;
         const int s_p0 = gtid < NJ ? find_sim(JB, n_sims, gtid) : 0;
@@ -576,19 +575,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                 }
             }
         }
-        for (int64_t g = gtid; g < NJ; g += nth) {
-            const int s = g == gtid ? s_p0 : find_sim(JB, n_sims, g);
-            const SimDesc &sd = SD(s);
-            const double tnow = cached_time(sc, B.sims, s, par);
-            if (!(tnow <= sd.t_end) || cached_list_mode(sc, s)) continue;
-            if (kEarly && g == gtid) pred_store<Rec>(in0, (Rec *)sd.rec, g - JB[s], tnow);
-            else predict_entry<Rec>(sd.st, (Rec *)sd.rec, g - JB[s], tnow);
-        }
         {
             // Tile selection: warp w takes tiles w + k W (W warps, k = 0,
             // 1, ...); its lanes read the level masks of 32 of them per round
             // trip, and the warp then builds the items of the due ones among
-            // them, one tile at a time.
+            // them, one tile at a time.  It runs before the prediction: the
+            // few warps of a small step that find due tiles wait on chains of
+            // loads and atomics while the others' predictions use the pipes.
             const int lane = tid & 31;
             const int64_t w0 = gtid >> 5, nw = nth >> 5;
             for (int64_t k0 = 0; w0 + k0 * nw < NT; k0 += 32) {
@@ -645,6 +638,14 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                     }
                 }
             }
+        }
+        for (int64_t g = gtid; g < NJ; g += nth) {
+            const int s = g == gtid ? s_p0 : find_sim(JB, n_sims, g);
+            const SimDesc &sd = SD(s);
+            const double tnow = cached_time(sc, B.sims, s, par);
+            if (!(tnow <= sd.t_end) || cached_list_mode(sc, s)) continue;
+            if (kEarly && g == gtid) pred_store<Rec>(in0, (Rec *)sd.rec, g - JB[s], tnow);
+            else predict_entry<Rec>(sd.st, (Rec *)sd.rec, g - JB[s], tnow);
         }
         if (!grid_sync(B.bs)) return;
         if (sc.any_list) {
