@@ -642,6 +642,7 @@ int set_lists_core(hh_ctx *ctx, int64_t n_particles, int64_t n_j, int32_t n_grou
     ctx->nj = n_j;
     ctx->n_groups = n_groups;
     ctx->list_len = L;
+    ctx->list_max = lmax;
     ctx->n_tiles = int32_t(tiles.size());
     ctx->total_parts = total_parts;
     ctx->small_parts = small_parts;
@@ -944,6 +945,7 @@ int hh_finish_device_rebuild(hh_ctx *ctx, int64_t total_parts, int64_t lmax)
 {
     const int64_t small_parts = small_parts_bound(ctx, ctx->n_tiles, lmax);
     if (small_parts > INT32_MAX / 2) return fail(ctx, HH_ENOMEM, "hh_rebuild: too many short list parts");
+    ctx->list_max = lmax;
     int rc = ensure_parts(ctx, std::max(total_parts, small_parts));
     if (rc) return rc;
     if (ctx->graph) {

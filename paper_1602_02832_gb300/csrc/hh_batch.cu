@@ -56,6 +56,7 @@ struct SimDesc {
     DevScalars *ds;
     int64_t n, nj;
     int32_t n_tiles, pj, work, work_split, pj_small;
+    int32_t lmax;  // longest group list
     int64_t lbar;  // mean list length per group (list entries / groups)
     Params prm;
     double t_end;
@@ -547,6 +548,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
         // predictor is bound by the FP64 pipe) do not depend on the block
         // time: their loads go out before the block times are read.
         constexpr bool kEarly = std::is_same<Rec, RecMix>::value;
+        constexpr bool kExactChunks = std::is_same<Rec, RecMix>::value;
         PredIn<Rec> in0;
         const int s_p0 = gtid < NJ ? find_sim(JB, n_sims, gtid) : 0;
         if (kEarly && gtid < NJ) pred_load<Rec>(SD(s_p0).st, gtid - JB[s_p0], in0);
@@ -626,16 +628,10 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                         }
                     }
                     const uint32_t mask = __ballot_sync(0xffffffffu, act);
-                    if (mask) {
+                    if (mask)
                         append_tile_items(sd.L, tile, td, mask, pj, work, &B.bs->n_items[par], &sd.ds->slot_par[par],
-                                          items, s, sd.ds->na_hist);
-                        if (lane == 0 && cached_list_mode(sc, s)) {
-                            // the entries phase 1b predicts per item, at most
-                            const int64_t len = sd.L.off[td.z + 1] - sd.L.off[td.z];
-                            const int64_t pe = min((int64_t)part_len_for(__popc(mask), pj, work), len);
-                            atomicMax(&B.bs->max_chunks[par], (uint32_t)((pe + 31) / 32));
-                        }
-                    }
+                                          items, s, sd.ds->na_hist,
+                                          kExactChunks && cached_list_mode(sc, s) ? &B.bs->max_chunks[par] : nullptr);
                 }
             }
         }
@@ -651,12 +647,25 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
         if (sc.any_list) {
             // ---- phase 1b: list-mode simulations predict the entries of
             // this step's list parts.  A task is 32 consecutive entries of
-            // one work item (lane = entry), up to the step's longest part, so
-            // the few items of a small step spread over every SM.  Entries
-            // shared by several parts are predicted more than once, with the
-            // same result.
+            // one work item (lane = entry), up to the longest part, so the few
+            // items of a small step spread over every SM.  The mixed form
+            // tracks the step's longest part during the selection; the plain
+            // form (whose registers that would spill) bounds it by the longest
+            // part a list-mode simulation can have.  Entries shared by
+            // several parts are predicted more than once, with the same
+            // result.
             const uint32_t n_items = __ldcg(&B.bs->n_items[par]);
-            const int maxc = max(1, (int)__ldcg(&B.bs->max_chunks[par]));
+            int maxc = 1;
+            if (kExactChunks) {
+                maxc = max(1, (int)__ldcg(&B.bs->max_chunks[par]));
+            } else {
+                for (int s = 0; s < n_sims && s < kSimCache; s++)
+                    if (cached_list_mode(sc, s)) {
+                        const SimDesc &sd = SD(s);
+                        const int plen = sd.work > 0 ? part_len_for(1, sd.pj, sd.work) : sd.pj;
+                        maxc = max(maxc, (min(plen, sd.lmax) + 31) / 32);
+                    }
+            }
             const int lane = tid & 31;
             const int64_t w0 = gtid >> 5, nw = nth >> 5;
             const int64_t n_tasks = (int64_t)n_items * maxc;
@@ -1031,6 +1040,7 @@ extern "C" int hh_batch_run(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const d
         d.work = c->cfg.work_item;
         d.work_split = c->cfg.work_split;
         d.pj_small = c->cfg.tile_j_small;
+        d.lmax = int32_t(std::min<int64_t>(c->list_max, INT32_MAX));
         d.lbar = c->n_groups > 0 ? std::max<int64_t>(1, c->list_len / c->n_groups) : 1;
         d.prm.eps2 = c->cfg.eps2;
         d.prm.eta = c->cfg.eta;

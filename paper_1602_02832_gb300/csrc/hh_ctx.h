@@ -35,6 +35,7 @@ struct hh_ctx {
     int32_t cap_g = 0;
     int64_t cap_tiles = 0;
     int64_t n = 0, nj = 0, list_len = 0;
+    int64_t list_max = 0;  // longest group list
     int32_t n_groups = 0, n_tiles = 0, tile_i = 32;
     // device memory
     hh::State st{};

@@ -191,7 +191,7 @@ __device__ __forceinline__ int parts_of(int64_t len, int pj) { return len > 0 ? 
 // length).  `work` is the equal-cost target of this step (0: parts of pj_min).
 __device__ __forceinline__ void append_tile_items(const Lists &L, int tile, const int4 td, uint32_t mask, int pj_min,
                                                   int work, uint32_t *n_items, uint32_t *slot_ctr, WorkItem *items,
-                                                  int sim, unsigned long long *na_hist)
+                                                  int sim, unsigned long long *na_hist, uint32_t *max_chunks = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const int64_t gb = L.off[td.z], ge = L.off[td.z + 1];
@@ -203,6 +203,8 @@ __device__ __forceinline__ void append_tile_items(const Lists &L, int tile, cons
         base = (int)atomicAdd(n_items, (uint32_t)n_parts);
         slot = n_parts > 1 ? (int)atomicAdd(slot_ctr, (uint32_t)n_parts) : 0;
         atomicAdd(&na_hist[__popc(mask) - 1], 1ull);
+        // (with max_chunks: the longest part so far, in 32-entry chunks)
+        if (max_chunks) atomicMax(max_chunks, (uint32_t)((min((int64_t)pj, len) + 31) / 32));
     }
     base = __shfl_sync(0xffffffffu, base, 0);
     slot = __shfl_sync(0xffffffffu, slot, 0);
