@@ -80,11 +80,13 @@ typedef struct hh_config {
                           only the positions of particles, nodes and list entries differ */
     int32_t work_split; /* 0 (default): work_item applies to every block step.  > 0: the
                           batched loop (hh_batch_run, hh_batch_step) uses work_item only in
-                          block steps with at least work_split active particles and parts of
-                          tile_j in smaller ones (short parts spread a small step over more
-                          SMs; equal-cost parts balance a large one); the other loops then use
-                          parts of tile_j.  The count is the simulation's own, so results still
-                          do not depend on the rest of a batch */
+                          block steps with at least work_split active particles; in smaller
+                          ones the mixed form takes parts of tile_j and the plain form
+                          equal-cost parts of 2 x tile_j interactions (at least 32 entries):
+                          short parts spread a small step over more SMs, equal-cost parts
+                          balance a large one.  The other loops then use parts of tile_j.
+                          The count is the simulation's own, so results still do not depend
+                          on the rest of a batch */
     int32_t tile_j_small; /* 0 (default): off.  Otherwise a multiple of 32 in [32, tile_j]: the
                           batched loop splits the lists of block steps with at most 16 due
                           particles into parts of this length, so that such a step's few tiles

@@ -552,14 +552,24 @@ namespace {
 // index scan (they are valid by construction); everything else is checked.
 // Work items and partial sums grow with the lists; kernels captured in the
 // loop graph hold the old pointers, so the graph is rebuilt.
-// Work items a block step with at most kSmallDue due particles can have when
-// it uses parts of tile_j_small: at most kSmallDue tiles, each with the
-// longest list.
+// Work items a block step of the batched loop can have beyond those of
+// parts of tile_j: with tile_j_small, a step with at most kSmallDue due
+// particles (at most kSmallDue tiles, each with the longest list, in parts
+// of tile_j_small); in the plain form with work_split, a step with fewer due
+// particles than work_split (as many tiles at most, in equal-cost parts of
+// kMedWork x tile_j interactions, the shortest for a full tile).
 int64_t small_parts_bound(const hh_ctx *ctx, int64_t n_tiles, int64_t lmax)
 {
-    const int64_t pj = ctx->cfg.tile_j_small;
-    if (pj <= 0) return 0;
-    return std::min<int64_t>(n_tiles, kSmallDue) * std::max<int64_t>(1, (lmax + pj - 1) / pj);
+    int64_t b = 0;
+    const int64_t pjs = ctx->cfg.tile_j_small;
+    if (pjs > 0) b = std::min<int64_t>(n_tiles, kSmallDue) * std::max<int64_t>(1, (lmax + pjs - 1) / pjs);
+    if (ctx->cfg.precision == HH_FP64 && ctx->cfg.work_split > 0) {
+        const int64_t want = (int64_t(kMedWork) * ctx->part_len + ctx->tile_i - 1) / ctx->tile_i;
+        const int64_t shortest = std::max<int64_t>(32, (want + 31) / 32 * 32);
+        b = std::max(b, std::min<int64_t>(n_tiles, ctx->cfg.work_split) * std::max<int64_t>(1, (lmax + shortest - 1) /
+                                                                                                  shortest));
+    }
+    return b;
 }
 
 int ensure_parts(hh_ctx *ctx, int64_t total_parts)

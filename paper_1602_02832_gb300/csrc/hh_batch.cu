@@ -548,6 +548,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
         // predictor is bound by the FP64 pipe) do not depend on the block
         // time: their loads go out before the block times are read.
         constexpr bool kEarly = std::is_same<Rec, RecMix>::value;
+        constexpr bool kPlain = std::is_same<Rec, RecF64>::value;
         constexpr bool kExactChunks = std::is_same<Rec, RecMix>::value;
         PredIn<Rec> in0;
         const int s_p0 = gtid < NJ ? find_sim(JB, n_sims, gtid) : 0;
@@ -609,11 +610,14 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                     // equal-cost items in this step?  With work_split the
                     // simulation's due particles (levels >= kmin, from its
                     // level histogram, fixed during this phase) must reach
-                    // work_split: small steps keep short parts, which spread
-                    // over more SMs, and with tile_j_small, steps of at most
+                    // work_split; below it the mixed form keeps parts of
+                    // tile_j and the plain form takes equal-cost parts of
+                    // kMedWork x tile_j interactions (an item's FP64 work
+                    // bounds its time, so smaller items spread such a step
+                    // over more SMs), and with tile_j_small, steps of at most
                     // kSmallDue due particles take parts of that length
                     int work = sd.work, pj = sd.pj;
-                    if ((work > 0 && sd.work_split > 0) || sd.pj_small > 0) {
+                    if (sd.work_split > 0 || sd.pj_small > 0) {
                         int due;
                         if (s < kSimCache && sc.due[s] >= 0) {
                             due = sc.due[s];
@@ -621,7 +625,10 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                             const int cnt = __ldcg(&sd.ds->lvl_cnt[lane]);
                             due = __reduce_add_sync(0xffffffffu, lane >= kmin_of(tnow) ? cnt : 0);
                         }
-                        if (sd.work_split > 0 && due < sd.work_split) work = 0;
+                        if (sd.work_split > 0 && due < sd.work_split) {
+                            work = kPlain ? kMedWork * sd.pj : 0;
+                            if (kPlain) pj = 32;
+                        }
                         if (sd.pj_small > 0 && due <= kSmallDue) {
                             work = 0;
                             pj = sd.pj_small;

@@ -26,6 +26,10 @@ int hh_finish_device_rebuild(hh_ctx *ctx, int64_t total_parts, int64_t lmax);  /
 // Block steps of the batched loop with at most this many due particles use
 // list parts of tile_j_small (when set).
 constexpr int kSmallDue = 16;
+// Block steps of the batched plain-form loop with fewer due particles than
+// work_split (when set) use equal-cost list parts of kMedWork x tile_j
+// interactions (32-entry granularity).
+constexpr int kMedWork = 2;
 
 struct hh_ctx {
     int device = 0;
@@ -49,7 +53,7 @@ struct hh_ctx {
     uint32_t *tile_lv = nullptr;  // [cap_tiles] levels present in each tile (batched loop)
     int64_t cap_parts = 0;
     int64_t total_parts = 0;    // work items of a step with every tile active
-    int64_t small_parts = 0;    // work items a step with <= kSmallDue due particles can have (tile_j_small)
+    int64_t small_parts = 0;    // work items a step below work_split can have beyond parts of tile_j
     int64_t device_bytes = 0;   // device memory allocated for this context
     int32_t part_len = 512;
     hh::DevScalars *ds = nullptr;
