@@ -32,6 +32,9 @@ n_i of only ~4-6, too narrow a range to separate the two terms.
 
 Usage (on a GPU): python -m paper_1602_02832_gb300.perfmodel --out DIR
 List run statistics (host only): python -m paper_1602_02832_gb300.perfmodel --list-runs
+Per-step profile of one tree interval (on a GPU):
+    python -m paper_1602_02832_gb300.perfmodel --step-profile --n 65536 --form fp64 \
+        --cfg '{"n_crit": 64, "tile_i": 8, "tile_j": 256, "work_item": 2048, "work_split": 2048, "tile_j_small": 64}'
 """
 from __future__ import annotations
 
@@ -294,9 +297,120 @@ def list_runs_main(argv=None):
     return rows
 
 
+STEP_EDGES = (1, 9, 33, 129, 513, 2049, 8193, 32769, 131073)
+
+
+def step_profile(n, precision, cfg=None, salpeter=False, warm=2, seed=0):
+    """One tree interval of the batched loop (`hh_batch_run`, device
+    rebuilds), step by step: the seeded Plummer sphere (with Salpeter masses
+    if `salpeter`) is advanced `warm` intervals, then the next interval runs
+    twice from the same state, once in one launch (each block step's device
+    phase times from the kernel's stamps) and once one block step per launch
+    (each step's active particles, interactions and list mode from the
+    counters).  Both runs take the same steps.  Returns an array of rows
+    (active particles, interactions, list mode, step us, select + predict
+    us, force + correct us)."""
+    import synth
+    from . import Batch, Context, hh_config_default, hh_tree_build
+
+    def make():
+        x, v, m = (synth.plummer_salpeter if salpeter else synth.plummer)(n, seed)
+        c = hh_config_default()
+        c.eps2, c.eta, c.theta, c.precision = 1e-8, 0.02, 0.5, precision
+        for k, val in (cfg or {}).items():
+            setattr(c, k, val)
+        z = np.zeros((3, n))
+        T0 = hh_tree_build(x.T, v.T, z, z, m, leaf=8, n_crit=c.n_crit, theta=c.theta)
+        ctx = Context(c, n, 2 * n, 2 * len(T0.idx) + 1024, 2 * T0.n_groups + 64)
+        ctx.hh_load_particles(x.T, v.T, m)
+        ctx.hh_set_rebuild_device(True)
+        ctx.hh_run(0.0, 0.0)
+        return ctx, c.dt_tree
+
+    def interval(b, ctx, t, dtt):
+        us, ph = [], []
+        while True:
+            steps, tn, u = b.hh_batch_run([ctx], [t + dtt])
+            if steps:
+                us.append(np.array(u[:steps]))
+                ph.append(np.array(b.last_phase_us[:steps]))
+            if tn[0] > t + dtt:
+                return np.concatenate(us), np.concatenate(ph)
+
+    ca, dtt = make()
+    cb, _ = make()
+    with ca, cb, Batch(precision, max_sims=1, max_steps=8192) as b:
+        t = 0.0
+        for _ in range(warm):
+            for ctx in (ca, cb):
+                interval(b, ctx, t, dtt)
+                ctx.hh_rebuild(t + dtt)
+            t += dtt
+        U, PH = interval(b, cb, t, dtt)
+        rows = []
+        while True:
+            c0 = ca.hh_get_counters()
+            steps, tn, _ = b.hh_batch_run([ca], [t + dtt], max_steps=1)
+            c1 = ca.hh_get_counters()
+            if steps:
+                rows.append((c1["particle_steps"] - c0["particle_steps"], c1["interactions"] - c0["interactions"],
+                             c1["list_steps"] - c0["list_steps"]))
+            if tn[0] > t + dtt:
+                break
+    if len(rows) != len(U):
+        raise RuntimeError(f"the two runs took {len(rows)} and {len(U)} steps")
+    r = np.array(rows, dtype=np.float64)
+    return np.column_stack([r, U, PH[:, 0], PH[:, 1] + PH[:, 2]])
+
+
+def step_bins(rows, edges=STEP_EDGES):
+    """Per-step rows (step_profile) binned by active particles [lo, hi):
+    steps, list-mode steps, time and interaction shares, sums and medians of
+    the two phases, and the force phase's interaction rate."""
+    rows = np.asarray(rows, dtype=np.float64)
+    A, I, LM, U, P1, P2 = rows.T
+    out = []
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        s = (A >= lo) & (A < hi)
+        if not s.any():
+            continue
+        out.append({"active": [int(lo), int(hi - 1)], "steps": int(s.sum()), "list_steps": int(LM[s].sum()),
+                    "time_share": float(U[s].sum() / U.sum()), "interaction_share": float(I[s].sum() / I.sum()),
+                    "select_predict_us_sum": float(P1[s].sum()), "select_predict_us_median": float(np.median(P1[s])),
+                    "force_us_sum": float(P2[s].sum()), "force_us_median": float(np.median(P2[s])),
+                    "force_rate": float(I[s].sum() / (P2[s].sum() * 1e-6)) if P2[s].sum() > 0 else None})
+    return out
+
+
+def step_profile_main(argv=None):
+    from . import HH_FP64, HH_MIXED
+
+    p = argparse.ArgumentParser()
+    p.add_argument("--step-profile", action="store_true")
+    p.add_argument("--n", type=int, default=65536)
+    p.add_argument("--form", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--salpeter", action="store_true")
+    p.add_argument("--warm", type=int, default=2)
+    p.add_argument("--cfg", default="{}", help="hh_config fields as JSON")
+    a = p.parse_args(argv)
+    rows = step_profile(a.n, HH_FP64 if a.form == "fp64" else HH_MIXED, json.loads(a.cfg), a.salpeter, a.warm)
+    A, I, LM, U, P1, P2 = rows.T
+    print(json.dumps({"n": a.n, "form": a.form, "salpeter": a.salpeter, "steps": len(rows),
+                      "interval_ms": float(U.sum() / 1e3), "select_predict_ms": float(P1.sum() / 1e3),
+                      "force_ms": float(P2.sum() / 1e3), "interactions": float(I.sum()),
+                      "list_steps": int(LM.sum())}), flush=True)
+    for b in step_bins(rows):
+        print(json.dumps(b), flush=True)
+    return rows
+
+
 def main(argv=None):
     import sys
-    if "--list-runs" in (argv if argv is not None else sys.argv[1:]):
+    args = argv if argv is not None else sys.argv[1:]
+    if "--step-profile" in args:
+        step_profile_main(argv)
+        return 0
+    if "--list-runs" in args:
         list_runs_main(argv)
         return 0
     from . import HH_FP64, HH_MIXED

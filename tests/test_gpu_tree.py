@@ -196,3 +196,16 @@ def test_device_rebuild_reports_too_few_cells(hh):
         assert np.array_equal(st["x"], np.ascontiguousarray(x.T))
         got = ctx.hh_get_j(0, n)
         assert np.array_equal(got["x"], np.ascontiguousarray(x.T)) and np.array_equal(ctx.hh_get_ids(), np.arange(n))
+
+
+def test_step_profile_takes_the_same_steps_twice(hh):
+    # the per-step profile runs one interval twice from the same state (one
+    # launch; one step per launch) and pairs their steps one to one
+    import numpy as np
+    from paper_1602_02832_gb300 import perfmodel
+    rows = perfmodel.step_profile(4096, hh.HH_FP64, {"n_crit": 64, "tile_i": 8, "tile_j": 256}, warm=1)
+    A, I, LM, U, P1, P2 = rows.T
+    assert len(rows) > 10 and np.all(A >= 1) and np.all(I > 0) and np.all(LM == 0)
+    assert np.allclose(U, P1 + P2, rtol=1e-9, atol=1e-3)
+    b = perfmodel.step_bins(rows)
+    assert sum(x["steps"] for x in b) == len(rows)
