@@ -291,6 +291,7 @@ struct StepCache {
     int due[kSimCache];                  // particles due at t (levels >= kmin(t)); -1: not counted
     unsigned char list_mode[kSimCache];  // predict only the entries of this step's list parts
     int any_list;                        // some simulation of the batch is in list mode this step
+    int any_full;                        // some live simulation predicts every entry this step
 };
 
 // Due particles of a simulation at block time tnow: its level histogram's
@@ -328,9 +329,12 @@ __device__ __forceinline__ bool list_mode_of(const SimDesc &sd, double tnow, int
 
 __device__ __forceinline__ void cache_times(StepCache &c, const SimDesc *sims, int n_sims, int par)
 {
-    if (threadIdx.x == 0) c.any_list = 0;
+    if (threadIdx.x == 0) {
+        c.any_list = 0;
+        c.any_full = n_sims > kSimCache;  // (simulations beyond the cache predict every entry)
+    }
     __syncthreads();
-    int any = 0;
+    int any = 0, full = 0;
     for (int s = threadIdx.x; s < n_sims && s < kSimCache; s += blockDim.x) {
         c.t[s] = __longlong_as_double((long long)__ldcg(&sims[s].ds->tmin[par]));
         c.t_end[s] = sims[s].t_end;
@@ -341,8 +345,10 @@ __device__ __forceinline__ void cache_times(StepCache &c, const SimDesc *sims, i
         const bool lm = due >= 0 && list_mode_of(sims[s], c.t[s], due);
         c.list_mode[s] = lm;
         any |= lm;
+        full |= !lm && c.t[s] <= c.t_end[s];
     }
     if (any) c.any_list = 1;
+    if (full) c.any_full = 1;
     __syncthreads();
 }
 
@@ -642,7 +648,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
                 }
             }
         }
-        for (int64_t g = gtid; g < NJ; g += nth) {
+        for (int64_t g = gtid; sc.any_full && g < NJ; g += nth) {
             const int s = g == gtid ? s_p0 : find_sim(JB, n_sims, g);
             const SimDesc &sd = SD(s);
             const double tnow = cached_time(sc, B.sims, s, par);
