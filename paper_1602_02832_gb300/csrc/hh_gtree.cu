@@ -287,9 +287,11 @@ __global__ void k_preorder(Cells C, const GCounts *gc, int d)
 }
 
 // cell count, and the synchronisation flag of the bounding-box pass
-__global__ void k_cells_done(GCounts *gc, const Box *b)
+// After the levels 0..d: the cells made so far (complete when level d made
+// no children, i.e. lvl_n[d + 1] == 0).
+__global__ void k_cells_done(GCounts *gc, const Box *b, int d)
 {
-    gc->ncells = gc->lvl_c0[kMaxDepth + 1] + gc->lvl_n[kMaxDepth + 1];
+    gc->ncells = gc->lvl_c0[d + 1] + gc->lvl_n[d + 1];
     gc->bad = b->bad;
 }
 
@@ -476,11 +478,14 @@ __global__ void k_store_count(int32_t *dst, const int32_t *flag, const int32_t *
 }
 
 // list length and tile / work-item totals, from the ends of their scans
-__global__ void k_store_totals(GCounts *gc, const int64_t *off_end, const int64_t *tiles_end, const int64_t *parts_end)
+// parts_scan: the second half of the one scan over [tile counts, part
+// counts], so its values are offset by its first entry (the tile total)
+__global__ void k_store_totals(GCounts *gc, const int64_t *off_end, const int64_t *tiles_end, const int64_t *parts_scan,
+                               int32_t G)
 {
     gc->L = *off_end;
     gc->n_tiles = *tiles_end;
-    gc->total_parts = *parts_end;
+    gc->total_parts = parts_scan[G] - parts_scan[0];
 }
 
 __global__ void k_cut_write(int32_t ncells, const int32_t *flag, const int32_t *pos, int32_t *cut)
@@ -604,8 +609,10 @@ __global__ void k_top_above(const WalkArgs W, const int32_t *above, int32_t A, i
 // the subtree of cut[k] in pre-order, skipping every emitted cell's subtree.
 // The list of a group is then the concatenation over k in pre-order:
 // particles ascending, then nodes ascending, as in the sequential walk.
-// Pass 0 counts into cnt_p/cnt_n[g * R + k]; pass 1 writes at the scanned
-// offsets.
+// Pass 0 counts into cnt_p/cnt_n[g * R + k] (and zeroes both arrays'
+// terminal entries); pass 1 writes at the scanned offsets.  cnt_n follows
+// cnt_p's terminal entry, so one exclusive scan covers both: scan_n's values
+// are then offset by scan_n[0], the particle total.
 template <bool kWrite>
 __global__ void k_lists_cut(const WalkArgs W, const int32_t *cut, int32_t R, const int32_t *above_pos,
                             const int32_t *top_above, int32_t A, int64_t *cnt_p, int64_t *cnt_n,
@@ -614,6 +621,8 @@ __global__ void k_lists_cut(const WalkArgs W, const int32_t *cut, int32_t R, con
     const float tol = walk_tol(W);
     const int64_t total = int64_t(W.G) * R;
     const int64_t n = W.n;
+    if (!kWrite && blockIdx.x == 0 && threadIdx.x == 0) cnt_p[total] = cnt_n[total] = 0;
+    const int64_t nb = kWrite ? scan_n[0] : 0;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
         const int32_t g = int32_t(q / R), k = int32_t(q - int64_t(g) * R);
         const int32_t r = cut[k], par = W.P.parent[r];
@@ -625,8 +634,8 @@ __global__ void k_lists_cut(const WalkArgs W, const int32_t *cut, int32_t R, con
         const GroupView V = group_view(W, g);
         int64_t wp = 0, wn = 0;
         if (kWrite) {
-            wp = scan_p[q] + scan_n[int64_t(g) * R];
-            wn = scan_p[int64_t(g + 1) * R] + scan_n[q];
+            wp = scan_p[q] + (scan_n[int64_t(g) * R] - nb);
+            wn = scan_p[int64_t(g + 1) * R] + (scan_n[q] - nb);
         }
         int64_t np = 0, nn = 0;
         int4 pk;
@@ -673,17 +682,20 @@ __global__ void k_lists_cut(const WalkArgs W, const int32_t *cut, int32_t R, con
     }
 }
 
-// off[g] = entries of all lists before group g (g = 0..G)
+// off[g] = entries of all lists before group g (g = 0..G); scan_n is offset
+// by scan_n[0] (one scan over both count arrays)
 __global__ void k_list_off(int32_t G, int32_t R, const int64_t *scan_p, const int64_t *scan_n, int64_t *off)
 {
+    const int64_t nb = scan_n[0];
     for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g <= G; g += gridDim.x * blockDim.x)
-        off[g] = scan_p[int64_t(g) * R] + scan_n[int64_t(g) * R];
+        off[g] = scan_p[int64_t(g) * R] + (scan_n[int64_t(g) * R] - nb);
 }
 
 // tiles of <= tile_i particles per group, written at tile_off[g]
 __global__ void k_tile_counts(const int32_t *g_cell, PCells P, int32_t G, int tile_i, const int64_t *off, int pj,
                               int64_t *ntile, int64_t *nparts, GCounts *gc)
 {
+    if (blockIdx.x == 0 && threadIdx.x == 0) ntile[G] = nparts[G] = 0;  // terminal entries of the scan
     unsigned long long lmax = 0ull;
     for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
         const int32_t c = g_cell[g];
@@ -740,7 +752,8 @@ struct GTreeBuf {
     PCells P{};
     int32_t *cnt = nullptr, *offs = nullptr, *gflag = nullptr, *gpos = nullptr, *g_cell = nullptr, *cut = nullptr,
             *above = nullptr;
-    int64_t *ntile = nullptr, *nparts = nullptr, *tile_off = nullptr, *parts_off = nullptr;
+    // [tile counts | part counts] and their one scan, each 2 (G + 1) long
+    int64_t *ntile = nullptr, *tile_off = nullptr;
     double *mom = nullptr;                    // [13][cap_c] cell sums (BFS order)
     double *box_lo = nullptr, *box_hi = nullptr;  // [3][cap_g] group boxes
     State alt{};                 // second particle-state buffer for the reordering
@@ -750,6 +763,7 @@ struct GTreeBuf {
     int64_t pair_cap = 0;
     int32_t *top_buf = nullptr;  // [G][A] topmost unopened cell above the cut
     int64_t top_cap = 0;
+    int depth = -1;              // depth of the last tree (-1: none yet)
     void *tmp = nullptr;
     size_t tmp_bytes = 0;
     std::vector<void *> all;
@@ -821,8 +835,7 @@ GTreeBuf *gtree_alloc(hh_ctx *ctx)
               galloc(g, &g->offs, cc) && galloc(g, &g->gflag, cc) && galloc(g, &g->gpos, cc) &&
               galloc(g, &g->g_cell, ctx->cap_g) && galloc(g, &g->cut, cc) && galloc(g, &g->above, cc) && galloc(g, &g->mom, 13 * cc) &&
               galloc(g, &g->box_lo, 3 * ctx->cap_g) && galloc(g, &g->box_hi, 3 * ctx->cap_g) &&
-              galloc(g, &g->ntile, ctx->cap_g + 1) && galloc(g, &g->nparts, ctx->cap_g + 1) &&
-              galloc(g, &g->tile_off, ctx->cap_g + 1) && galloc(g, &g->parts_off, ctx->cap_g + 1) &&
+              galloc(g, &g->ntile, 2 * (ctx->cap_g + 1)) && galloc(g, &g->tile_off, 2 * (ctx->cap_g + 1)) &&
               galloc(g, &g->ids, n) && galloc(g, &g->ids2, n);
     // the second state buffer mirrors the context's (same capacities)
     g->alt = ctx->st;
@@ -900,13 +913,24 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
             cudaSuccess)
             return gfail(ctx, HH_ECUDA, "hh_rebuild: key sort failed");
     }
-    // 2. cells level by level (BFS), subtree sizes bottom-up, pre-order numbers top-down
+    // 2. cells level by level (BFS), subtree sizes bottom-up, pre-order numbers top-down.
+    //    The levels run up to two below the last tree's depth (the tree
+    //    changes little in one dt_tree); if the last of them still made
+    //    children, the rest follow after the read of the counts.
     const int64_t cap_cells = ctx->cap_j - n;
-    for (int d = 0; d <= kMaxDepth; d++)
-        k_level<<<grid, 256, 0, st>>>(g->C, g->key2, d, ctx->cfg.leaf, g->gc, int32_t(std::min<int64_t>(cap_cells, INT32_MAX)));
-    k_cells_done<<<1, 1, 0, st>>>(g->gc, g->box);
-    launches += (kMaxDepth + 1) + 1;
+    const int32_t cap_c32 = int32_t(std::min<int64_t>(cap_cells, INT32_MAX));
+    const int d_guess = g->depth < 0 ? kMaxDepth : std::min(kMaxDepth, g->depth + 2);
+    for (int d = 0; d <= d_guess; d++) k_level<<<grid, 256, 0, st>>>(g->C, g->key2, d, ctx->cfg.leaf, g->gc, cap_c32);
+    k_cells_done<<<1, 1, 0, st>>>(g->gc, g->box, d_guess);
+    launches += (d_guess + 1) + 1;
     if (!read_counts()) return gfail(ctx, HH_ECUDA, "hh_rebuild: tree build failed");
+    if (!g->gc_host->overflow && g->gc_host->lvl_n[d_guess + 1] > 0) {
+        for (int d = d_guess + 1; d <= kMaxDepth; d++)
+            k_level<<<grid, 256, 0, st>>>(g->C, g->key2, d, ctx->cfg.leaf, g->gc, cap_c32);
+        k_cells_done<<<1, 1, 0, st>>>(g->gc, g->box, kMaxDepth);
+        launches += (kMaxDepth - d_guess) + 1;
+        if (!read_counts()) return gfail(ctx, HH_ECUDA, "hh_rebuild: tree build failed");
+    }
     if (g->gc_host->bad) return gfail(ctx, HH_ESTATE, "hh_rebuild: particles are not synchronised at t");
     if (g->gc_host->overflow)
         return gfail(ctx, HH_ENOMEM, "hh_rebuild: tree exceeds nj_max (more cells than room for nodes)");
@@ -916,6 +940,7 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
     int depth = 0;
     for (int d = 0; d <= kMaxDepth; d++)
         if (g->gc_host->lvl_n[d] > 0) depth = d;
+    g->depth = depth;
     for (int d = depth; d >= 0; d--) k_subtree_size<<<grid, 256, 0, st>>>(g->C, g->gc, d);
     for (int d = 0; d <= depth; d++) k_preorder<<<grid, 256, 0, st>>>(g->C, g->gc, d);
     launches += 2 * (depth + 1);
@@ -985,7 +1010,8 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
         launches++;
     }
     const int64_t pairs = int64_t(G) * R;
-    if (pairs + 1 >= int64_t(INT32_MAX)) return gfail(ctx, HH_ENOMEM, "hh_rebuild: too many (group, subtree) pairs");
+    if (2 * (pairs + 1) >= int64_t(INT32_MAX))  // (one scan covers both count arrays)
+        return gfail(ctx, HH_ENOMEM, "hh_rebuild: too many (group, subtree) pairs");
     if (4 * (pairs + 1) > g->pair_cap) {
         if (g->pair_buf) cudaFree(g->pair_buf);
         g->pair_buf = nullptr;
@@ -1001,22 +1027,17 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
     k_lists_cut<false><<<unsigned(lgrid), 128, 0, st>>>(W, g->cut, R, g->gpos, g->top_buf, A, cnt_p, cnt_n, nullptr,
                                                         nullptr, nullptr);
     launches++;
-    cudaMemsetAsync(cnt_p + pairs, 0, sizeof(int64_t), st);
-    cudaMemsetAsync(cnt_n + pairs, 0, sizeof(int64_t), st);
-    if ((rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, cnt_p, scan_p, pairs + 1, st)) ||
-        (rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, cnt_n, scan_n, pairs + 1, st)))
+    if ((rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, cnt_p, scan_p, 2 * (pairs + 1), st)))  // cnt_p, cnt_n at once
         return gfail(ctx, rc, "hh_rebuild: scan failed");
     k_list_off<<<grid, 256, 0, st>>>(G, R, scan_p, scan_n, ctx->off);
     // 6. tiles and their work-item capacity (from the list lengths)
-    k_tile_counts<<<grid, 256, 0, st>>>(g->g_cell, g->P, G, ctx->tile_i, ctx->off, ctx->part_len, g->ntile, g->nparts,
+    int64_t *nparts = g->ntile + (G + 1), *parts_off = g->tile_off + (G + 1);
+    k_tile_counts<<<grid, 256, 0, st>>>(g->g_cell, g->P, G, ctx->tile_i, ctx->off, ctx->part_len, g->ntile, nparts,
                                         g->gc);
-    cudaMemsetAsync(g->ntile + G, 0, sizeof(int64_t), st);
-    cudaMemsetAsync(g->nparts + G, 0, sizeof(int64_t), st);
-    if ((rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->ntile, g->tile_off, G + 1, st)) ||
-        (rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->nparts, g->parts_off, G + 1, st)))
+    if ((rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->ntile, g->tile_off, 2 * (int64_t(G) + 1), st)))
         return gfail(ctx, rc, "hh_rebuild: scan failed");
-    k_store_totals<<<1, 1, 0, st>>>(g->gc, ctx->off + G, g->tile_off + G, g->parts_off + G);
-    launches += 4;
+    k_store_totals<<<1, 1, 0, st>>>(g->gc, ctx->off + G, g->tile_off + G, parts_off, G);
+    launches += 3;
     if (!read_counts()) return gfail(ctx, HH_ECUDA, "hh_rebuild: list count failed");
     const int64_t L = g->gc_host->L, n_tiles = g->gc_host->n_tiles, total_parts = g->gc_host->total_parts;
     if (n_tiles > ctx->cap_tiles) return gfail(ctx, HH_ENOMEM, "hh_rebuild: too many tiles");
