@@ -259,30 +259,34 @@ __global__ void k_level(Cells C, const uint64_t *key, int d, int leaf, GCounts *
     }
 }
 
-__global__ void k_subtree_size(Cells C, const GCounts *gc, int d)
+// Pre-order numbers and subtree sizes without a pass per level: the cells
+// sorted by (first particle, depth) are in pre-order (children follow their
+// parent in octant order, which is particle order, and a cell's descendants
+// are the cells after it that start before it ends).  Key of a cell:
+// begin << 5 | depth (depth <= kMaxDepth < 32).
+__global__ void k_cell_keys(Cells C, int32_t ncells, uint64_t *key, int32_t *val)
 {
-    if (gc->overflow) return;
-    const int32_t c0 = gc->lvl_c0[d], nc = gc->lvl_n[d];
-    for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
-        const int32_t c = c0 + q;
-        int32_t sz = 1;
-        for (int k = 0; k < C.nchild[c]; k++) sz += C.size[C.first[c] + k];
-        C.size[c] = sz;
+    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+        key[c] = (uint64_t(C.begin[c]) << 5) | uint64_t(C.depth[c]);
+        val[c] = c;
     }
 }
 
-__global__ void k_preorder(Cells C, const GCounts *gc, int d)
+// From the sorted keys and cells: pre[c] = its rank; size[c] = the cells from
+// it to the first one that starts at or after its end.
+__global__ void k_pre_size(Cells C, int32_t ncells, const uint64_t *skey, const int32_t *sval)
 {
-    if (gc->overflow) return;
-    const int32_t c0 = gc->lvl_c0[d], nc = gc->lvl_n[d];
-    for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += gridDim.x * blockDim.x) {
-        const int32_t c = c0 + q;
-        int32_t run = C.pre[c] + 1;
-        for (int k = 0; k < C.nchild[c]; k++) {
-            const int32_t ch = C.first[c] + k;
-            C.pre[ch] = run;
-            run += C.size[ch];
+    for (int32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < ncells; p += gridDim.x * blockDim.x) {
+        const int32_t c = sval[p];
+        C.pre[c] = p;
+        const uint64_t lim = uint64_t(C.end[c]) << 5;
+        int32_t lo = p + 1, hi = ncells;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (skey[mid] < lim) lo = mid + 1;
+            else hi = mid;
         }
+        C.size[c] = lo - p;
     }
 }
 
@@ -720,6 +724,26 @@ __global__ void k_tiles(const int32_t *g_cell, PCells P, int32_t G, int tile_i, 
     }
 }
 
+template <typename K, typename V>
+int cub_sort_pairs(void *&tmp, size_t &tmp_bytes, const K *kin, K *kout, const V *vin, V *vout, int64_t n, int bits,
+                   cudaStream_t st)
+{
+    size_t need = 0;
+    if (cub::DeviceRadixSort::SortPairs(nullptr, need, kin, kout, vin, vout, (int)n, 0, bits, st) != cudaSuccess ||
+        need == 0)
+        return HH_ECUDA;
+    if (need > tmp_bytes) {
+        if (tmp) cudaFree(tmp);
+        tmp = nullptr;
+        tmp_bytes = 0;
+        if (cudaMalloc(&tmp, need) != cudaSuccess) return HH_ENOMEM;
+        tmp_bytes = need;
+    }
+    return cub::DeviceRadixSort::SortPairs(tmp, need, kin, kout, vin, vout, (int)n, 0, bits, st) == cudaSuccess
+               ? HH_OK
+               : HH_ECUDA;
+}
+
 template <typename T>
 int cub_exclusive_sum(void *&tmp, size_t &tmp_bytes, const T *in, T *out, int64_t n, cudaStream_t st)
 {
@@ -941,9 +965,20 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
     for (int d = 0; d <= kMaxDepth; d++)
         if (g->gc_host->lvl_n[d] > 0) depth = d;
     g->depth = depth;
-    for (int d = depth; d >= 0; d--) k_subtree_size<<<grid, 256, 0, st>>>(g->C, g->gc, d);
-    for (int d = 0; d <= depth; d++) k_preorder<<<grid, 256, 0, st>>>(g->C, g->gc, d);
-    launches += 2 * (depth + 1);
+    {
+        // pre-order numbers and subtree sizes from one sort of the cells by
+        // (first particle, depth); the moment sums and the flag arrays, not
+        // yet in use, hold its keys and values
+        uint64_t *ckey = reinterpret_cast<uint64_t *>(g->mom), *ckey2 = ckey + g->cap_c;
+        int32_t *cval = g->cnt, *cval2 = g->offs;
+        int bits = 5;
+        while (bits < 64 && (int64_t(1) << (bits - 5)) <= n) bits++;
+        k_cell_keys<<<grid, 256, 0, st>>>(g->C, ncells, ckey, cval);
+        int rs = cub_sort_pairs(g->tmp, g->tmp_bytes, ckey, ckey2, cval, cval2, ncells, bits, st);
+        if (rs) return gfail(ctx, rs, "hh_rebuild: cell sort failed");
+        k_pre_size<<<grid, 256, 0, st>>>(g->C, ncells, ckey2, cval2);
+        launches += 2;
+    }
     k_to_preorder<<<grid, 256, 0, st>>>(g->C, ncells, g->P, g->root_side);
     // 3. particles into Morton order (into the second buffer), then swap
     k_permute<<<grid, 256, 0, st>>>(ctx->st, g->alt, g->perm, n, g->ids, g->ids2);
