@@ -546,20 +546,25 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
         }
 
     int step = 0;
+    bool prev_full = true;  // the last step predicted every entry of some simulation
     for (; step < max_steps; step++) {
         const int par = step & 1;
         // ---- phase 1: select + predict
         // The inputs of this thread's first predicted entry (mixed form; the
         // plain form's FP64 inputs would not fit in registers, and its
         // predictor is bound by the FP64 pipe) do not depend on the block
-        // time: their loads go out before the block times are read.
+        // time: their loads go out before the block times are read, unless
+        // the last step predicted only list entries (then this one likely
+        // does too, and the loads would be wasted).
         constexpr bool kEarly = std::is_same<Rec, RecMix>::value;
         constexpr bool kPlain = std::is_same<Rec, RecF64>::value;
         constexpr bool kExactChunks = std::is_same<Rec, RecMix>::value;
         PredIn<Rec> in0;
         const int s_p0 = gtid < NJ ? find_sim(JB, n_sims, gtid) : 0;
-        if (kEarly && gtid < NJ) pred_load<Rec>(SD(s_p0).st, gtid - JB[s_p0], in0);
+        const bool early = kEarly && prev_full && gtid < NJ;
+        if (early) pred_load<Rec>(SD(s_p0).st, gtid - JB[s_p0], in0);
         cache_times(sc, B.sims, n_sims, par);
+        prev_full = sc.any_full;
         if (blockIdx.x == 0) {
             // counters of the previous step (other parity) are free again
             if (tid == 0) {
@@ -653,7 +658,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
             const SimDesc &sd = SD(s);
             const double tnow = cached_time(sc, B.sims, s, par);
             if (!(tnow <= sd.t_end) || cached_list_mode(sc, s)) continue;
-            if (kEarly && g == gtid) pred_store<Rec>(in0, (Rec *)sd.rec, g - JB[s], tnow);
+            if (early && g == gtid) pred_store<Rec>(in0, (Rec *)sd.rec, g - JB[s], tnow);
             else predict_entry<Rec>(sd.st, (Rec *)sd.rec, g - JB[s], tnow);
         }
         if (!grid_sync(B.bs)) return;
