@@ -297,7 +297,7 @@ def list_runs_main(argv=None):
     return rows
 
 
-STEP_EDGES = (1, 9, 33, 129, 513, 2049, 8193, 32769, 131073)
+STEP_EDGES = (1, 9, 33, 129, 513, 2049, 8193, 32769, 131073, 1 << 40)
 
 
 def step_profile(n, precision, cfg=None, salpeter=False, warm=2, seed=0):

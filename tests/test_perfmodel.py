@@ -89,10 +89,11 @@ def test_list_run_stats_counts_runs_within_lists():
 def test_step_bins_sum_and_rates():
     # rows: active, interactions, list mode, step us, select + predict us, force us
     rows = np.array([[1, 100, 1, 10, 4, 6], [5, 300, 0, 12, 5, 7], [40, 4000, 0, 30, 10, 20],
-                     [3000, 9e5, 0, 600, 20, 580]], dtype=float)
+                     [3000, 9e5, 0, 600, 20, 580], [5e5, 9e9, 0, 9e5, 50, 9e5 - 50]], dtype=float)
     b = perfmodel.step_bins(rows)
-    assert [x["active"] for x in b] == [[1, 8], [33, 128], [2049, 8192]]
-    assert [x["steps"] for x in b] == [2, 1, 1] and b[0]["list_steps"] == 1
+    assert [x["active"] for x in b][:3] == [[1, 8], [33, 128], [2049, 8192]]
+    assert b[3]["active"][0] == 131073 and b[3]["steps"] == 1  # the largest steps have a bin too
+    assert [x["steps"] for x in b] == [2, 1, 1, 1] and b[0]["list_steps"] == 1
     assert sum(x["time_share"] for x in b) == pytest.approx(1.0)
     assert sum(x["interaction_share"] for x in b) == pytest.approx(1.0)
     assert b[0]["force_us_sum"] == 13 and b[0]["select_predict_us_median"] == 4.5
