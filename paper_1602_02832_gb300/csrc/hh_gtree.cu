@@ -86,15 +86,6 @@ struct Box {
 };
 
 // ------------------------------------------------------------ kernels
-__global__ void k_box_init(Box *b)
-{
-    for (int d = 0; d < 3; d++) {
-        b->lo[d] = ~0ull;
-        b->hi[d] = 0ull;
-    }
-    b->bad = 0;
-}
-
 __global__ void k_box(const State s, int64_t n, double t_tree, Box *b)
 {
     unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
@@ -174,8 +165,13 @@ struct GCounts {
     unsigned long long lmax;  // longest list
 };
 
-__global__ void k_root_init(Cells C, int32_t n, GCounts *gc)
+__global__ void k_root_init(Cells C, int32_t n, GCounts *gc, Box *b)
 {
+    for (int d = 0; d < 3; d++) {  // empty bounding box
+        b->lo[d] = ~0ull;
+        b->hi[d] = 0ull;
+    }
+    b->bad = 0;
     C.begin[0] = 0;
     C.end[0] = n;
     C.depth[0] = 0;
@@ -402,34 +398,13 @@ __global__ void k_node_records(State s, Cells C, PCells P, int32_t ncells, int64
     }
 }
 
-// Groups (Barnes 1990): maximal cells with <= n_crit particles (or leaves).
-__global__ void k_group_flags(PCells P, int32_t ncells, int n_crit, int32_t *flag)
-{
-    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
-        const int32_t cnt = P.end[c] - P.begin[c];
-        const bool small = cnt <= n_crit || P.nchild[c] == 0;
-        const int32_t par = P.parent[c];
-        const bool parent_big = par < 0 || !((P.end[par] - P.begin[par]) <= n_crit || P.nchild[par] == 0);
-        flag[c] = (small && parent_big) ? 1 : 0;
-    }
-}
-
-__global__ void k_groups(PCells P, int32_t ncells, const int32_t *flag, const int32_t *gpos, int32_t *g_cell,
-                         int32_t *group_of)
-{
-    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
-        if (!flag[c]) continue;
-        const int32_t g = gpos[c];
-        g_cell[g] = c;
-        for (int32_t p = P.begin[c]; p < P.end[c]; p++) group_of[p] = g;
-    }
-}
-
-// Bounding box of each group's particles ([3][G] lo and hi), one warp per group.
-__global__ void k_group_box(const State s, PCells P, const GCounts *gc, const int32_t *g_cell, double *box_lo,
-                            double *box_hi, float4 *box_f)
+// Bounding box of each group's particles ([3][G] lo and hi), one warp per group
+// (none beyond cap_g groups: the host then reports the overflow).
+__global__ void k_group_box(const State s, PCells P, const GCounts *gc, int32_t cap_g, const int32_t *g_cell,
+                            double *box_lo, double *box_hi, float4 *box_f)
 {
     const int32_t G = gc->G;
+    if (G > cap_g) return;
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t g = w0; g < G; g += nw) {
@@ -458,28 +433,10 @@ __global__ void k_group_box(const State s, PCells P, const GCounts *gc, const in
     }
 }
 
+// Groups (Barnes 1990): maximal cells with <= n_crit particles (or leaves).
 // Cut through the tree: the maximal cells whose subtree holds <= S cells.
 // They partition the cells at or below the cut; every cell above it is an
-// ancestor of some cut cell.  Flags in pre-order, compacted by a scan.
-__global__ void k_cut_flags(PCells P, int32_t ncells, int32_t S, int32_t *flag)
-{
-    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
-        const int32_t par = P.parent[c];
-        flag[c] = (P.size[c] <= S && (par < 0 || P.size[par] > S)) ? 1 : 0;
-    }
-}
-
-__global__ void k_above_flags(PCells P, int32_t ncells, int32_t S, int32_t *flag)
-{
-    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x)
-        flag[c] = P.size[c] > S ? 1 : 0;
-}
-
-// *dst = number of flagged cells (from the exclusive scan of the flags)
-__global__ void k_store_count(int32_t *dst, const int32_t *flag, const int32_t *pos, int32_t ncells)
-{
-    *dst = pos[ncells - 1] + flag[ncells - 1];
-}
+// ancestor of some cut cell.  All three in pre-order (k_flags3 below).
 
 // list length and tile / work-item totals, from the ends of their scans
 // parts_scan: the second half of the one scan over [tile counts, part
@@ -492,10 +449,44 @@ __global__ void k_store_totals(GCounts *gc, const int64_t *off_end, const int64_
     gc->total_parts = parts_scan[G] - parts_scan[0];
 }
 
-__global__ void k_cut_write(int32_t ncells, const int32_t *flag, const int32_t *pos, int32_t *cut)
+// The three cell selections at once: flags [groups | cut cells | cells above
+// the cut], each ncells long, compacted by one exclusive scan (positions of
+// the second and third selections are offset by the counts before them).
+__global__ void k_flags3(PCells P, int32_t ncells, int n_crit, int32_t S, int32_t *flag)
 {
-    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x)
-        if (flag[c]) cut[pos[c]] = c;
+    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+        const int32_t cnt = P.end[c] - P.begin[c];
+        const bool small = cnt <= n_crit || P.nchild[c] == 0;
+        const int32_t par = P.parent[c];
+        const bool parent_big = par < 0 || !((P.end[par] - P.begin[par]) <= n_crit || P.nchild[par] == 0);
+        flag[c] = (small && parent_big) ? 1 : 0;                                         // group (Barnes 1990)
+        flag[ncells + c] = (P.size[c] <= S && (par < 0 || P.size[par] > S)) ? 1 : 0;     // cut cell
+        flag[2 * ncells + c] = P.size[c] > S ? 1 : 0;                                    // above the cut
+    }
+}
+
+__global__ void k_counts3(GCounts *gc, const int32_t *flag, const int32_t *pos, int32_t ncells)
+{
+    gc->G = pos[ncells];
+    gc->R = pos[2 * ncells] - pos[ncells];
+    gc->A = pos[3 * ncells - 1] + flag[3 * ncells - 1] - pos[2 * ncells];
+}
+
+// groups (g_cell, group_of), cut cells and cells above the cut, in pre-order
+// (group cells beyond cap_g are not stored: the host reports the overflow)
+__global__ void k_write3(PCells P, int32_t ncells, const int32_t *flag, const int32_t *pos, int32_t *g_cell,
+                         int32_t cap_g, int32_t *group_of, int32_t *cut, int32_t *above)
+{
+    const int32_t r0 = pos[ncells], a0 = pos[2 * ncells];
+    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+        if (flag[c]) {
+            const int32_t g = pos[c];
+            if (g < cap_g) g_cell[g] = c;
+            for (int32_t p = P.begin[c]; p < P.end[c]; p++) group_of[p] = g;
+        }
+        if (flag[ncells + c]) cut[pos[ncells + c] - r0] = c;
+        if (flag[2 * ncells + c]) above[pos[2 * ncells + c] - a0] = c;
+    }
 }
 
 enum : int { kOpen = 0, kEmitParticles = 1, kEmitNode = 2 };
@@ -630,7 +621,7 @@ __global__ void k_lists_cut(const WalkArgs W, const int32_t *cut, int32_t R, con
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
         const int32_t g = int32_t(q / R), k = int32_t(q - int64_t(g) * R);
         const int32_t r = cut[k], par = W.P.parent[r];
-        int32_t top = par >= 0 ? top_above[int64_t(g) * A + above_pos[par]] : -1;
+        int32_t top = par >= 0 ? top_above[int64_t(g) * A + (above_pos[par] - above_pos[0])] : -1;
         if (top >= 0 && k > 0 && cut[k - 1] >= top) {  // emitted by an earlier cut cell
             if (!kWrite) cnt_p[q] = cnt_n[q] = 0;
             continue;
@@ -774,8 +765,8 @@ struct GTreeBuf {
     float4 *box_f = nullptr;
     Cells C{};
     PCells P{};
-    int32_t *cnt = nullptr, *offs = nullptr, *gflag = nullptr, *gpos = nullptr, *g_cell = nullptr, *cut = nullptr,
-            *above = nullptr;
+    int32_t *flag3 = nullptr, *pos3 = nullptr;  // [3][cap_c] selection flags and their scan
+    int32_t *g_cell = nullptr, *cut = nullptr, *above = nullptr;
     // [tile counts | part counts] and their one scan, each 2 (G + 1) long
     int64_t *ntile = nullptr, *tile_off = nullptr;
     double *mom = nullptr;                    // [13][cap_c] cell sums (BFS order)
@@ -855,8 +846,8 @@ GTreeBuf *gtree_alloc(hh_ctx *ctx)
               galloc(g, &g->C.pre, cc) && galloc(g, &g->P.begin, cc) && galloc(g, &g->P.end, cc) &&
               galloc(g, &g->P.nchild, cc) && galloc(g, &g->P.parent, cc) && galloc(g, &g->P.child, 8 * cc) &&
               galloc(g, &g->P.side, cc) && galloc(g, &g->P.size, cc) && galloc(g, &g->P.pack, cc) &&
-              galloc(g, &g->P.cf, cc) && galloc(g, &g->xmax, 1) && galloc(g, &g->gc, 1) && galloc(g, &g->box_f, 2 * ctx->cap_g) && galloc(g, &g->cnt, cc) &&
-              galloc(g, &g->offs, cc) && galloc(g, &g->gflag, cc) && galloc(g, &g->gpos, cc) &&
+              galloc(g, &g->P.cf, cc) && galloc(g, &g->xmax, 1) && galloc(g, &g->gc, 1) && galloc(g, &g->box_f, 2 * ctx->cap_g) && galloc(g, &g->flag3, 3 * cc) &&
+              galloc(g, &g->pos3, 3 * cc) &&
               galloc(g, &g->g_cell, ctx->cap_g) && galloc(g, &g->cut, cc) && galloc(g, &g->above, cc) && galloc(g, &g->mom, 13 * cc) &&
               galloc(g, &g->box_lo, 3 * ctx->cap_g) && galloc(g, &g->box_hi, 3 * ctx->cap_g) &&
               galloc(g, &g->ntile, 2 * (ctx->cap_g + 1)) && galloc(g, &g->tile_off, 2 * (ctx->cap_g + 1)) &&
@@ -883,7 +874,7 @@ GTreeBuf *gtree_alloc(hh_ctx *ctx)
 int64_t gtree_bytes(const hh_ctx *ctx)
 {
     const int64_t n = ctx->cap_n, cc = ctx->cap_j, G = ctx->cap_g + 1;
-    return n * (8 * 2 + 4 * 2 + 8 * 2) + cc * (4 * 8 + 4 * 5 + 32 + 8 + 4 * 6 + 13 * 8 + 32) + G * (4 + 8 * 4 + 6 * 8 + 32) +
+    return n * (8 * 2 + 4 * 2 + 8 * 2) + cc * (4 * 8 + 4 * 5 + 32 + 8 + 4 * 8 + 13 * 8 + 32) + G * (4 + 8 * 4 + 6 * 8 + 32) +
            ctx->cap_j * 8 * (12 + 2) + n * 8;
 }
 
@@ -916,11 +907,10 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
         return cudaStreamSynchronize(st) == cudaSuccess;
     };
     // 1. bounding box, synchronisation check, keys, sort
-    k_root_init<<<1, 1, 0, st>>>(g->C, int32_t(n), g->gc);
-    k_box_init<<<1, 1, 0, st>>>(g->box);
+    k_root_init<<<1, 1, 0, st>>>(g->C, int32_t(n), g->gc, g->box);
     k_box<<<grid, 256, 0, st>>>(ctx->st, n, t, g->box);
     k_keys<<<grid, 256, 0, st>>>(ctx->st, n, g->box, g->key, g->idx, g->root_side, g->xmax, ctx->cfg.order);
-    launches += 4;
+    launches += 3;
     {
         size_t need = 0;
         if (cub::DeviceRadixSort::SortPairs(nullptr, need, g->key, g->key2, g->idx, g->perm, (int)n, 0, 63, st) !=
@@ -967,10 +957,10 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
     g->depth = depth;
     {
         // pre-order numbers and subtree sizes from one sort of the cells by
-        // (first particle, depth); the moment sums and the flag arrays, not
+        // (first particle, depth); the moment sums and the selection arrays, not
         // yet in use, hold its keys and values
         uint64_t *ckey = reinterpret_cast<uint64_t *>(g->mom), *ckey2 = ckey + g->cap_c;
-        int32_t *cval = g->cnt, *cval2 = g->offs;
+        int32_t *cval = g->flag3, *cval2 = g->pos3;
         int bits = 5;
         while (bits < 64 && (int64_t(1) << (bits - 5)) <= n) bits++;
         k_cell_keys<<<grid, 256, 0, st>>>(g->C, ncells, ckey, cval);
@@ -994,26 +984,18 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
     const int64_t cap_c = g->cap_c;
     for (int d = depth; d >= 0; d--) k_moments_level<<<grid, 256, 0, st>>>(ctx->st, g->C, g->gc, d, cap_c, g->mom);
     k_node_records<<<grid, 256, 0, st>>>(ctx->st, g->C, g->P, ncells, cap_c, g->mom, n, t);
-    k_group_flags<<<grid, 256, 0, st>>>(g->P, ncells, ctx->cfg.n_crit, g->gflag);
-    int rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->gflag, g->gpos, ncells, st);
-    if (rc) return gfail(ctx, rc, "hh_rebuild: scan failed");
-    k_store_count<<<1, 1, 0, st>>>(&g->gc->G, g->gflag, g->gpos, ncells);
-    k_groups<<<grid, 256, 0, st>>>(g->P, ncells, g->gflag, g->gpos, g->g_cell, ctx->group_of);
-    k_group_box<<<grid, 256, 0, st>>>(ctx->st, g->P, g->gc, g->g_cell, g->box_lo, g->box_hi, g->box_f);
-    // 5. lists: cut of subtrees of <= S cells and the cells above it, then
-    //    per-(group, cut cell) counts, scans, offsets, write
+    // 4b. groups, and (5.) the cut of subtrees of <= S cells and the cells
+    //    above it: flags, one scan, counts and the three compacted tables
     const int32_t S = std::max<int32_t>(32, ncells / 256);
-    k_cut_flags<<<grid, 256, 0, st>>>(g->P, ncells, S, g->cnt);
-    if ((rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->cnt, g->offs, ncells, st)))
-        return gfail(ctx, rc, "hh_rebuild: scan failed");
-    k_store_count<<<1, 1, 0, st>>>(&g->gc->R, g->cnt, g->offs, ncells);
-    k_cut_write<<<grid, 256, 0, st>>>(ncells, g->cnt, g->offs, g->cut);
-    k_above_flags<<<grid, 256, 0, st>>>(g->P, ncells, S, g->gflag);
-    if ((rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->gflag, g->gpos, ncells, st)))
-        return gfail(ctx, rc, "hh_rebuild: scan failed");
-    k_store_count<<<1, 1, 0, st>>>(&g->gc->A, g->gflag, g->gpos, ncells);
-    k_cut_write<<<grid, 256, 0, st>>>(ncells, g->gflag, g->gpos, g->above);
-    launches += (depth + 1) + 16;
+    k_flags3<<<grid, 256, 0, st>>>(g->P, ncells, ctx->cfg.n_crit, S, g->flag3);
+    int rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, g->flag3, g->pos3, 3 * int64_t(ncells), st);
+    if (rc) return gfail(ctx, rc, "hh_rebuild: scan failed");
+    k_counts3<<<1, 1, 0, st>>>(g->gc, g->flag3, g->pos3, ncells);
+    k_write3<<<grid, 256, 0, st>>>(g->P, ncells, g->flag3, g->pos3, g->g_cell, ctx->cap_g, ctx->group_of, g->cut,
+                                   g->above);
+    k_group_box<<<grid, 256, 0, st>>>(ctx->st, g->P, g->gc, ctx->cap_g, g->g_cell, g->box_lo, g->box_hi, g->box_f);
+    //    then per-(group, cut cell) list counts, scans, offsets, write
+    launches += (depth + 1) + 7;
     if (!read_counts()) return gfail(ctx, HH_ECUDA, "hh_rebuild: group build failed");
     const int32_t G = g->gc_host->G, R = g->gc_host->R, A = g->gc_host->A;
     if (G > ctx->cap_g) return gfail(ctx, HH_ENOMEM, "hh_rebuild: more groups than groups_max");
@@ -1059,7 +1041,7 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
     }
     int64_t *cnt_p = g->pair_buf, *cnt_n = cnt_p + pairs + 1, *scan_p = cnt_n + pairs + 1, *scan_n = scan_p + pairs + 1;
     const int64_t lgrid = std::min<int64_t>((pairs + 127) / 128, int64_t(1) << 30);
-    k_lists_cut<false><<<unsigned(lgrid), 128, 0, st>>>(W, g->cut, R, g->gpos, g->top_buf, A, cnt_p, cnt_n, nullptr,
+    k_lists_cut<false><<<unsigned(lgrid), 128, 0, st>>>(W, g->cut, R, g->pos3 + 2 * int64_t(ncells), g->top_buf, A, cnt_p, cnt_n, nullptr,
                                                         nullptr, nullptr);
     launches++;
     if ((rc = cub_exclusive_sum(g->tmp, g->tmp_bytes, cnt_p, scan_p, 2 * (pairs + 1), st)))  // cnt_p, cnt_n at once
@@ -1088,7 +1070,7 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
         ctx->device_bytes += (cap - ctx->cap_list) * int64_t(sizeof(int32_t));
         ctx->cap_list = cap;
     }
-    k_lists_cut<true><<<unsigned(lgrid), 128, 0, st>>>(W, g->cut, R, g->gpos, g->top_buf, A, nullptr, nullptr, scan_p,
+    k_lists_cut<true><<<unsigned(lgrid), 128, 0, st>>>(W, g->cut, R, g->pos3 + 2 * int64_t(ncells), g->top_buf, A, nullptr, nullptr, scan_p,
                                                        scan_n, ctx->idx);
     k_tiles<<<grid, 256, 0, st>>>(g->g_cell, g->P, G, ctx->tile_i, g->tile_off, ctx->tiles);
     launches += 2;

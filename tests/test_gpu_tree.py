@@ -209,3 +209,38 @@ def test_step_profile_takes_the_same_steps_twice(hh):
     assert np.allclose(U, P1 + P2, rtol=1e-9, atol=1e-3)
     b = perfmodel.step_bins(rows)
     assert sum(x["steps"] for x in b) == len(rows)
+
+
+def test_device_tree_deeper_than_the_last_one(hh, orc):
+    # the level loop first runs to two levels below the last tree's depth and
+    # finishes the deeper levels after reading the counts: a shallow tree (a
+    # uniform cube) followed by a deep one (a Plummer sphere) takes that path,
+    # and the deep tree still equals the oracle's
+    n = 20000
+    rng = np.random.default_rng(5)
+    xu = rng.uniform(-1.0, 1.0, size=(n, 3))
+    x, v, m = synth.plummer(n, 43)
+    z = np.zeros_like(x)
+    Tu = orc.tree_build(xu, v, z, z, m, leaf=8, n_crit=64, theta=0.5)
+    T = orc.tree_build(x, v, z, z, m, leaf=8, n_crit=64, theta=0.5)
+    cfg = hh.hh_config_default()
+    cfg.theta, cfg.n_crit = 0.5, 64
+    cells = max(Tu.n_cells, T.n_cells)
+    with hh.Context(cfg, n, n + 2 * cells + 64, 2 * max(len(Tu.list_idx), len(T.list_idx)) + 1024,
+                    2 * max(Tu.n_groups, T.n_groups) + 64) as ctx:
+        ctx.hh_set_rebuild_device(True)
+        ctx.hh_load_particles(xu.T, v.T, m)
+        ctx.hh_rebuild(0.0)
+        assert np.array_equal(ctx.hh_get_ids(), Tu.perm)
+        ctx.hh_load_particles(x.T, v.T, m)
+        ctx.hh_rebuild(0.0)
+        ids = ctx.hh_get_ids()
+        off, idx, gof = ctx.hh_get_lists()
+        nodes = ctx.hh_get_j(n, ctx.nj - n)
+    assert np.array_equal(ids, T.perm) and np.array_equal(gof, T.group_of)
+    assert len(nodes["m"]) == T.n_cells
+    # node masses summed in another order: within n eps (2e4 terms of 5e-5)
+    np.testing.assert_allclose(nodes["m"], T.node_m, rtol=n * 2.3e-16)
+    diff = sum(1 for g in range(T.n_groups)
+               if not np.array_equal(idx[off[g]:off[g + 1]], T.list_idx[T.list_off[g]:T.list_off[g + 1]]))
+    assert diff <= max(1, T.n_groups // 1000), diff
