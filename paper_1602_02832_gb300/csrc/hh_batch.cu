@@ -679,8 +679,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
             } else {
                 for (int s = 0; s < n_sims && s < kSimCache; s++)
                     if (cached_list_mode(sc, s)) {
+                        // the longest part of any rule: tile_j, an equal-cost
+                        // part of work_item or (below work_split) of kMedWork x
+                        // tile_j interactions for one active particle
                         const SimDesc &sd = SD(s);
-                        const int plen = sd.work > 0 ? part_len_for(1, sd.pj, sd.work) : sd.pj;
+                        int plen = sd.pj;
+                        if (sd.work > 0) plen = max(plen, part_len_for(1, sd.pj, sd.work));
+                        if (kPlain && sd.work_split > 0) plen = max(plen, part_len_for(1, 32, kMedWork * sd.pj));
                         maxc = max(maxc, (min(plen, sd.lmax) + 31) / 32);
                     }
             }
