@@ -246,3 +246,40 @@ def test_list_mode_prediction_changes_no_bit(hh, prec, work):
     for k in ("x", "v", "a", "jk", "t", "dt"):
         assert np.array_equal(got[k], ref[k]), k
 
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_beyond_the_cached_descriptors(hh, prec):
+    # 300 small simulations in one batch: beyond the 32 descriptors and the
+    # 256 step caches a CTA keeps in shared memory, the kernel reads them
+    # from global memory; every simulation still reaches its lone bits
+    P = hh.HH_FP64 if prec == "fp64" else hh.HH_MIXED
+    t1 = 2.0 ** -8
+    specs = [(64 + (k * 37) % 96, 1000 + k) for k in range(300)]
+
+    def make(n, seed):
+        x, v, m = synth.plummer(n, seed)
+        c = hh.hh_config_default()
+        c.eps2, c.precision, c.n_crit = 1e-6, P, 32
+        ctx = hh.Context(c, n, 2 * n, 64 * n * max(1, n // 16), n)
+        ctx.hh_load_particles(x.T, v.T, m)
+        ctx.hh_run(0.0, 0.0)
+        return ctx
+
+    ref = []
+    with hh.Batch(P, max_sims=1, max_steps=4096) as b:
+        for spec in specs:
+            with make(*spec) as c:
+                b.hh_batch_run([c], [t1])
+                ref.append(c.hh_get_state())
+    ctxs = [make(*spec) for spec in specs]
+    try:
+        with hh.Batch(P, max_sims=len(specs), max_steps=4096) as b:
+            b.hh_batch_run(ctxs, [t1] * len(ctxs))
+        for c, st in zip(ctxs, ref):
+            got = c.hh_get_state()
+            for k in ("x", "v", "a", "jk", "t", "dt"):
+                assert np.array_equal(got[k], st[k]), k
+    finally:
+        for c in ctxs:
+            c.close()
