@@ -403,7 +403,8 @@ const char *hh_batch_last_error(const hh_batch *b);
  *   HH_ESTATE for a context without lists or steps.
  * hh_batch_step: one launch (at most max_steps global steps) over the
  *   running residents, each to its next rebuild time, then the rebuilds of
- *   those that reached it (concurrently on their own streams).  Outputs (may
+ *   those that reached it (those that build on the device together, as by
+ *   hh_batch_rebuild; the others concurrently, one host thread each).  Outputs (may
  *   be NULL): global steps run, simulations launched, the number and the
  *   contexts (done_out, room for max_sims) that reached their end time since
  *   the last call, and the per-step times of hh_batch_run.  With no running
@@ -419,6 +420,21 @@ int hh_batch_step(hh_batch *b, int32_t max_steps, int32_t *steps_out, int32_t *l
                   hh_ctx **done_out, double *step_us_out, double *phase_us_out);
 int hh_batch_retire(hh_batch *b, hh_ctx *ctx);
 int hh_batch_resident(const hh_batch *b, int32_t *n_out, int32_t *running_out, int64_t *bytes_out);
+
+/* hh_rebuild (Section 2, step 1: tree, groups, interaction lists, node
+ * records) of n distinct contexts of the batch's device at times t[s].
+ * Contexts set to build on the device (hh_set_rebuild_device) are rebuilt
+ * together: each step of the device builder is one launch over all of them,
+ * its sorts are segmented sorts and its scans one scan over all of them, so
+ * the launch count does not grow with n.  Each context gets the tree, lists,
+ * node records and particle order that hh_rebuild gives it alone.  Others
+ * are rebuilt one after another on the host.  Returns HH_OK when every
+ * rebuild succeeded, else the first failed context's code; rc_out[n] (may be
+ * NULL) receives each context's code and hh_last_error(ctx) its message.  A
+ * context whose rebuild failed has no lists (as after a failed hh_rebuild).
+ * HH_EINVAL for n < 1, NULL arrays or contexts, or a context that appears
+ * twice; HH_ECUDA if the batch's rebuild stream cannot be made. */
+int hh_batch_rebuild(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const double *t, int *rc_out);
 
 /* Self-test of the bounded grid barrier of the batched kernel: a
  * cooperative launch of one CTA per SM runs 64 barriers; with skip_cta >= 0

@@ -104,6 +104,7 @@ _SIGS = {
     "hh_batch_step": (C.c_int, [_P, C.c_int32, _I32, _I32, _I32, C.POINTER(_P), _D, _D]),
     "hh_batch_retire": (C.c_int, [_P, _P]),
     "hh_batch_resident": (C.c_int, [_P, _I32, _I32, _I64]),
+    "hh_batch_rebuild": (C.c_int, [_P, C.c_int32, C.POINTER(_P), _D, C.POINTER(C.c_int)]),
     "hh_ctx_device_bytes": (C.c_int64, [_P]),
     "hh_barrier_selftest": (C.c_int, [C.c_int, C.c_int, _D]),
     "hh_selftest_aarseth": (C.c_int, [C.c_int, C.c_int64, _D, _D, _D, _D, C.c_double, _D]),
@@ -493,6 +494,19 @@ class Batch:
             raise HHError(rc, (_lib.hh_batch_last_error(self.h) or b"").decode())
         self.last_phase_us = ph[:steps.value]
         return steps.value, tn, us[:steps.value]
+
+    def hh_batch_rebuild(self, ctxs, t, check=True):
+        """Rebuilds the contexts at times t (device builders together, in one
+        batched build).  Returns each context's status code; with check, a
+        failure raises HHError."""
+        n = len(ctxs)
+        arr = (_P * n)(*[c.h for c in ctxs])
+        tt = np.ascontiguousarray(np.broadcast_to(np.asarray(t, dtype=np.float64), (n,)))
+        rcs = (C.c_int * n)()
+        rc = _lib.hh_batch_rebuild(self.h, n, arr, _ptr(tt), rcs)
+        if check and rc != HH_OK:
+            raise HHError(rc, (_lib.hh_batch_last_error(self.h) or b"").decode())
+        return [rcs[k] for k in range(n)]
 
 
     def _bcheck(self, rc):

@@ -951,8 +951,9 @@ int hh_load_particles(hh_ctx *ctx, int64_t n, const double *x, const double *v, 
 // Completes a device rebuild (hh_gtree.cu): work-item capacity, sizes,
 // mixed-form base records; the state buffers were swapped, so the loop graph
 // is rebuilt on the next hh_advance.
-int hh_finish_device_rebuild(hh_ctx *ctx, int64_t total_parts, int64_t lmax)
+int hh_finish_device_rebuild(hh_ctx *ctx, int64_t total_parts, int64_t lmax, cudaStream_t on)
 {
+    cudaStream_t st = on ? on : ctx->stream;
     const int64_t small_parts = small_parts_bound(ctx, ctx->n_tiles, lmax);
     if (small_parts > INT32_MAX / 2) return fail(ctx, HH_ENOMEM, "hh_rebuild: too many short list parts");
     ctx->list_max = lmax;
@@ -962,14 +963,14 @@ int hh_finish_device_rebuild(hh_ctx *ctx, int64_t total_parts, int64_t lmax)
         cudaGraphExecDestroy(ctx->graph);
         ctx->graph = nullptr;
     }
-    k_set_sizes<<<1, 1, 0, ctx->stream>>>(ctx->ds, ctx->n, ctx->nj, ctx->n_tiles, ctx->part_len, ctx->cfg.work_item,
-                                          ctx->cfg.work_split);
+    k_set_sizes<<<1, 1, 0, st>>>(ctx->ds, ctx->n, ctx->nj, ctx->n_tiles, ctx->part_len, ctx->cfg.work_item,
+                                 ctx->cfg.work_split);
     CKL();
     if (ctx->st.base) {
-        k_refresh_base<<<ctx->elem_grid, 256, 0, ctx->stream>>>(ctx->st, 0, ctx->nj);
+        k_refresh_base<<<ctx->elem_grid, 256, 0, st>>>(ctx->st, 0, ctx->nj);
         CKL();
     }
-    CK(cudaStreamSynchronize(ctx->stream));
+    if (!on) CK(cudaStreamSynchronize(st));
     ctx->total_parts = total_parts;
     ctx->small_parts = small_parts;
     ctx->have_j = true;
@@ -992,7 +993,9 @@ int hh_set_rebuild_device(hh_ctx *ctx, int on_device)
 }  // extern "C"
 
 namespace {
-int rebuild_impl(hh_ctx *ctx, double t)
+// Checks before a rebuild; for a device rebuild also brings the particle ids
+// to the device builder.
+int rebuild_begin(hh_ctx *ctx)
 {
     int rc = check_ctx(ctx);
     if (rc) return rc;
@@ -1000,12 +1003,17 @@ int rebuild_impl(hh_ctx *ctx, double t)
     // until this rebuild succeeds the lists are not valid (a failure part way
     // may have overwritten them); the state stays readable
     ctx->have_lists = false;
-    if (ctx->rebuild_device) {
-        if (ctx->gtree && !ctx->ids_on_device &&
-            hh_gtree_set_ids(ctx->gtree, ctx->ids.data(), ctx->n, ctx->stream) != HH_OK)
-            return fail(ctx, HH_ECUDA, "hh_rebuild: id upload failed");
-        return hh_rebuild_device(ctx, t);
-    }
+    if (ctx->rebuild_device && ctx->gtree && !ctx->ids_on_device &&
+        hh_gtree_set_ids(ctx->gtree, ctx->ids.data(), ctx->n, ctx->stream) != HH_OK)
+        return fail(ctx, HH_ECUDA, "hh_rebuild: id upload failed");
+    return HH_OK;
+}
+
+int rebuild_impl(hh_ctx *ctx, double t)
+{
+    int rc = rebuild_begin(ctx);
+    if (rc) return rc;
+    if (ctx->rebuild_device) return hh_rebuild_device(ctx, t);
     if ((rc = sync_ids_to_host(ctx))) return rc;
     if (!ctx->h_buf &&
         (cudaHostAlloc((void **)&ctx->h_buf, sizeof(double) * 14 * ctx->cap_j, cudaHostAllocDefault) != cudaSuccess ||
@@ -1084,6 +1092,38 @@ int hh_rebuild(hh_ctx *ctx, double t)
     if (rc == HH_OK) ctx->t_tree = t;
     return rc;
 }
+
+}  // extern "C"
+
+int hh_rebuild_many(hh_ctx *const *ctxs, const double *ts, int k, int *rcs, RbScratch *r)
+{
+    std::vector<hh_ctx *> dev;
+    std::vector<double> tdev;
+    std::vector<int> where;
+    for (int s = 0; s < k; s++) {
+        hh_ctx *ctx = ctxs[s];
+        if (ctx && ctx->rebuild_device) {
+            rcs[s] = rebuild_begin(ctx);
+            if (rcs[s] == HH_OK) {
+                dev.push_back(ctx);
+                tdev.push_back(ts[s]);
+                where.push_back(s);
+            }
+        } else {
+            rcs[s] = hh_rebuild(ctx, ts[s]);
+        }
+    }
+    if (dev.empty()) return HH_OK;
+    std::vector<int> rd(dev.size(), HH_OK);
+    const int rc = hh_rebuild_device_many(dev.data(), tdev.data(), int(dev.size()), rd.data(), r);
+    for (size_t q = 0; q < dev.size(); q++) {
+        rcs[where[q]] = rc ? fail(dev[q], rc, "hh_rebuild: batched device rebuild failed") : rd[q];
+        if (rcs[where[q]] == HH_OK) dev[q]->t_tree = tdev[q];
+    }
+    return HH_OK;
+}
+
+extern "C" {
 
 int hh_run(hh_ctx *ctx, double t0, double t_end)
 {

@@ -868,6 +868,7 @@ struct hh_batch {
     int64_t launch_particles = 0;     // particles per launch, 0 = no limit
     size_t rr = 0;                    // round-robin start of the next launch
     std::vector<Resident> res;
+    RbScratch *rb = nullptr;          // batched device rebuilds (made on first use)
     std::string err;
 };
 
@@ -1015,6 +1016,7 @@ extern "C" int hh_batch_destroy(hh_batch *b)
     if (b->d_blk) cudaFree(b->d_blk);
     if (b->d_items) cudaFree(b->d_items);
     if (b->h_blk) cudaFreeHost(b->h_blk);
+    if (b->rb) hh_rb_scratch_free(b->rb);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
     return HH_OK;
@@ -1193,6 +1195,31 @@ extern "C" int hh_batch_resident(const hh_batch *b, int32_t *n_out, int32_t *run
     return HH_OK;
 }
 
+extern "C" int hh_batch_rebuild(hh_batch *b, int32_t n, hh_ctx *const *ctxs, const double *t, int *rc_out)
+{
+    if (!b) return hh_set_global_error(HH_EINVAL, "hh_batch_rebuild: NULL batch");
+    if (n < 1 || !ctxs || !t) return bfail(b, HH_EINVAL, "hh_batch_rebuild: bad n or NULL arrays");
+    for (int32_t s = 0; s < n; s++) {
+        if (!ctxs[s]) return bfail(b, HH_EINVAL, "hh_batch_rebuild: NULL context");
+        for (int32_t u = 0; u < s; u++)
+            if (ctxs[u] == ctxs[s]) return bfail(b, HH_EINVAL, "hh_batch_rebuild: a context appears twice");
+    }
+    if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, HH_ECUDA, "hh_batch_rebuild: cudaSetDevice failed");
+    if (!b->rb && !(b->rb = hh_rb_scratch_create()))
+        return bfail(b, HH_ECUDA, "hh_batch_rebuild: rebuild stream creation failed");
+    std::vector<int> rcs(size_t(n), HH_OK);
+    hh_rebuild_many(ctxs, t, int(n), rcs.data(), b->rb);
+    int first = HH_OK;
+    for (int32_t s = 0; s < n; s++) {
+        if (rc_out) rc_out[s] = rcs[size_t(s)];
+        if (first == HH_OK && rcs[size_t(s)] != HH_OK) {
+            first = rcs[size_t(s)];
+            b->err = std::string("hh_batch_rebuild: ") + hh_last_error(ctxs[s]);
+        }
+    }
+    return first;
+}
+
 extern "C" int hh_batch_step(hh_batch *b, int32_t max_steps, int32_t *steps_out, int32_t *launched_out,
                              int32_t *n_done_out, hh_ctx **done_out, double *step_us_out, double *phase_us_out)
 {
@@ -1228,20 +1255,40 @@ extern "C" int hh_batch_step(hh_batch *b, int32_t max_steps, int32_t *steps_out,
         if (rc) return rc;
         if (steps_out) *steps_out = steps;
         if (launched_out) *launched_out = int32_t(pick.size());
-        // simulations past their stop time: finished, or rebuilt on their own
-        // streams (concurrently, one host thread each) for the next interval
-        std::vector<size_t> rebuild;
+        // simulations past their stop time: finished, or rebuilt for the next
+        // interval.  Device builders run as one batched build over all of
+        // them; host builders concurrently, one host thread each.
+        std::vector<size_t> rebuild, on_host;
+        std::vector<hh_ctx *> dev;
+        std::vector<double> tdev;
         for (size_t q = 0; q < pick.size(); q++) {
             Resident &r = b->res[pick[q]];
             if (!(tn[q] > r.t_stop)) continue;
-            if (r.t_stop >= r.t_end) r.state = 1;
-            else rebuild.push_back(pick[q]);
+            if (r.t_stop >= r.t_end) {
+                r.state = 1;
+                continue;
+            }
+            rebuild.push_back(pick[q]);
+            if (r.ctx->rebuild_device) {
+                dev.push_back(r.ctx);
+                tdev.push_back(r.t_stop);
+            } else {
+                on_host.push_back(rebuild.size() - 1);
+            }
         }
         std::vector<int> rcs(rebuild.size(), HH_OK);
-#pragma omp parallel for schedule(dynamic, 1) num_threads(int(std::min<size_t>(8, std::max<size_t>(1, rebuild.size()))))
-        for (int64_t q = 0; q < int64_t(rebuild.size()); q++) {
-            Resident &r = b->res[rebuild[size_t(q)]];
-            rcs[size_t(q)] = hh_rebuild(r.ctx, r.t_stop);
+        if (!dev.empty()) {
+            std::vector<int> rd(dev.size(), HH_OK);
+            const int rc = hh_batch_rebuild(b, int32_t(dev.size()), dev.data(), tdev.data(), rd.data());
+            if (rc == HH_ECUDA && !b->rb) return rc;
+            for (size_t q = 0, w = 0; q < rebuild.size(); q++)
+                if (b->res[rebuild[q]].ctx->rebuild_device) rcs[q] = rd[w++];
+        }
+#pragma omp parallel for schedule(dynamic, 1) num_threads(int(std::min<size_t>(8, std::max<size_t>(1, on_host.size()))))
+        for (int64_t q = 0; q < int64_t(on_host.size()); q++) {
+            const size_t i = on_host[size_t(q)];
+            Resident &r = b->res[rebuild[i]];
+            rcs[i] = hh_rebuild(r.ctx, r.t_stop);
         }
         int first_rc = HH_OK;
         std::string first_msg;

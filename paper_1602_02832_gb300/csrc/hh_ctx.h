@@ -22,7 +22,19 @@ int64_t *hh_gtree_ids(GTreeBuf *g);
 int hh_gtree_set_ids(GTreeBuf *g, const int64_t *ids, int64_t n, cudaStream_t st);
 struct hh_ctx;
 int hh_rebuild_device(hh_ctx *ctx, double t);        // hh_gtree.cu
-int hh_finish_device_rebuild(hh_ctx *ctx, int64_t total_parts, int64_t lmax);  // hh_api.cu
+// Batched device rebuild of k contexts (hh_gtree.cu): rcs[s] gets context
+// s's result; the scratch (and its stream) belongs to the caller.
+struct RbScratch;
+RbScratch *hh_rb_scratch_create();
+void hh_rb_scratch_free(RbScratch *r);
+int hh_rebuild_device_many(hh_ctx *const *ctxs, const double *ts, int k, int *rcs, RbScratch *r);
+// Ends a device rebuild (hh_api.cu).  With a stream the two closing kernels
+// go there and the caller synchronises it; without, on the context's stream,
+// synchronised here.
+int hh_finish_device_rebuild(hh_ctx *ctx, int64_t total_parts, int64_t lmax, cudaStream_t on = nullptr);
+// hh_rebuild for k contexts (hh_api.cu): those that build on the device are
+// rebuilt together by hh_rebuild_device_many, the others one by one.
+int hh_rebuild_many(hh_ctx *const *ctxs, const double *ts, int k, int *rcs, RbScratch *r);
 // Block steps of the batched loop with at most this many due particles use
 // list parts of tile_j_small (when set).
 constexpr int kSmallDue = 16;

@@ -81,8 +81,11 @@ class ServerStats:
     wall_s: float = 0.0
 
 
-# measured crossover: one rebuild at N = 1024 / 2048 / 4096 took 0.62 / 1.45 / 3.5 ms on the
-# host and 0.81 / 0.85 / 0.96 ms on the device (whose fixed cost is kernel-launch latency)
+# measured crossover for a rebuild alone: at N = 1024 / 2048 / 4096 it took 0.62 / 1.45 / 3.5 ms
+# on the host, and 0.39 ms at N = 1024 and 0.50 ms at N = 4096 on the device (whose fixed cost is
+# kernel-launch latency).
+# In the server the device rebuilds of one launch run as one batched build (hh_batch_rebuild),
+# 23 us per simulation at N = 1024; an ensemble of N in [1024, 32768] measured the same either way.
 AUTO_DEVICE_MIN_N = 2048
 
 
