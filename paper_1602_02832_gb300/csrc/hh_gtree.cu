@@ -175,41 +175,6 @@ __device__ __forceinline__ int decide(const State &s, const PCells &P, int64_t n
     return pk.z == 0 ? kEmitParticles : kOpen;
 }
 
-// What the list walk kernels read: the pre-order cells, the node records,
-// the groups and their boxes, the opening angle and the FP32 screen's
-// absolute margin (2^-19 theta X).
-struct WalkArgs {
-    State s;
-    PCells P;
-    int64_t n;
-    int32_t G;
-    const int32_t *g_cell;
-    const double *box_lo, *box_hi;
-    const float4 *box_f;
-    double theta;
-    float theta_f;
-    const float *xmax;
-};
-
-__device__ __forceinline__ GroupView group_view(const WalkArgs &W, int32_t g)
-{
-    GroupView V;
-    V.gc = W.g_cell[g];
-    V.gb = W.P.begin[V.gc];
-    V.ge = W.P.end[V.gc];
-    for (int d = 0; d < 3; d++) {
-        V.lo[d] = W.box_lo[d * W.G + g];
-        V.hi[d] = W.box_hi[d * W.G + g];
-    }
-    const float4 l = W.box_f[2 * g], h = W.box_f[2 * g + 1];
-    V.lof = make_float3(l.x, l.y, l.z);
-    V.hif = make_float3(h.x, h.y, h.z);
-    return V;
-}
-
-__device__ __forceinline__ float walk_tol(const WalkArgs &W) { return 0x1p-19f * W.theta_f * *W.xmax; }
-
-
 // Everything a rebuild kernel reads or writes for one simulation.  A kernel
 // runs for one simulation (the record passed by value) or for many (an array
 // in device memory, simulation = blockIdx.y): the same code either way.
@@ -248,7 +213,23 @@ struct RbSim {
 };
 
 #define RB_ARGS const RbSim one, const RbSim *many
-#define RB_SIM const RbSim &a = kMany ? many[blockIdx.y] : one
+
+// For many simulations a block first copies its record into shared memory:
+// read from there (as from the constant bank for one), the record's fields
+// can be fetched again where they are used instead of occupying registers.
+template <bool kMany>
+__device__ __forceinline__ const RbSim &rb_sim_of(const RbSim &one, const RbSim *many, unsigned char *sh)
+{
+    if (!kMany) return one;
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(many + blockIdx.y);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(sh);
+    for (int i = threadIdx.x; i < int(sizeof(RbSim) / 4); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    return *reinterpret_cast<const RbSim *>(sh);
+}
+#define RB_SIM                                                      \
+    __shared__ __align__(16) unsigned char rb_rec_[sizeof(RbSim)]; \
+    const RbSim &a = rb_sim_of<kMany>(one, many, rb_rec_)
 
 template <bool kMany>
 __global__ void k_box(RB_ARGS)
@@ -667,22 +648,26 @@ __global__ void k_write3(RB_ARGS)
     }
 }
 
-__device__ __forceinline__ WalkArgs walk_of(const RbSim &a)
+// The group's cell, its particle range and its box (FP64 and FP32), as the
+// list walk reads them.
+__device__ __forceinline__ GroupView group_view(const RbSim &a, int32_t g)
 {
-    WalkArgs W;
-    W.s = a.st;
-    W.P = a.P;
-    W.n = a.n;
-    W.G = a.G;
-    W.g_cell = a.g_cell;
-    W.box_lo = a.box_lo;
-    W.box_hi = a.box_hi;
-    W.box_f = a.box_f;
-    W.theta = a.theta;
-    W.theta_f = a.theta_f;
-    W.xmax = a.xmax;
-    return W;
+    GroupView V;
+    V.gc = a.g_cell[g];
+    V.gb = a.P.begin[V.gc];
+    V.ge = a.P.end[V.gc];
+    for (int d = 0; d < 3; d++) {
+        V.lo[d] = a.box_lo[d * a.G + g];
+        V.hi[d] = a.box_hi[d * a.G + g];
+    }
+    const float4 l = a.box_f[2 * g], h = a.box_f[2 * g + 1];
+    V.lof = make_float3(l.x, l.y, l.z);
+    V.hif = make_float3(h.x, h.y, h.z);
+    return V;
 }
+
+// the FP32 screen's absolute margin, 2^-19 theta X
+__device__ __forceinline__ float walk_tol(const RbSim &a) { return 0x1p-19f * a.theta_f * *a.xmax; }
 
 
 // For every (group g, cell above the cut a = above[i]): the topmost cell on
@@ -693,17 +678,16 @@ template <bool kMany>
 __global__ void k_top_above(RB_ARGS)
 {
     RB_SIM;
-    const WalkArgs W = walk_of(a);
-    const float tol = walk_tol(W);
+    const float tol = walk_tol(a);
     const int32_t A = a.A;
-    const int64_t total = int64_t(W.G) * A;
+    const int64_t total = int64_t(a.G) * A;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
         const int32_t g = int32_t(q / A), i = int32_t(q - int64_t(g) * A);
-        const GroupView V = group_view(W, g);
+        const GroupView V = group_view(a, g);
         int32_t top = -1;
         int4 pk;
-        for (int32_t c = a.above[i]; c >= 0; c = W.P.parent[c])
-            if (decide(W.s, W.P, W.n, W.theta, W.theta_f, tol, V, c, pk) != kOpen) top = c;
+        for (int32_t c = a.above[i]; c >= 0; c = a.P.parent[c])
+            if (decide(a.st, a.P, a.n, a.theta, a.theta_f, tol, V, c, pk) != kOpen) top = c;
         a.top[q] = top;
     }
 }
@@ -723,11 +707,10 @@ template <bool kMany, bool kWrite>
 __global__ void k_lists_cut(RB_ARGS)
 {
     RB_SIM;
-    const WalkArgs W = walk_of(a);
-    const float tol = walk_tol(W);
+    const float tol = walk_tol(a);
     const int32_t R = a.R, A = a.A;
-    const int64_t total = int64_t(W.G) * R;
-    const int64_t n = W.n;
+    const int64_t total = int64_t(a.G) * R;
+    const int64_t n = a.n;
     const int32_t *cut = a.cut, *above_pos = a.pos3 + 2 * int64_t(a.ncells);
     int64_t *cnt_p = a.pair2, *cnt_n = a.pair2 + a.pairs + 1;
     const int64_t *scan_p = a.pscan2, *scan_n = a.pscan2 + a.pairs + 1;
@@ -735,13 +718,13 @@ __global__ void k_lists_cut(RB_ARGS)
     const int64_t pb = kWrite ? scan_p[0] : 0, nb = kWrite ? scan_n[0] : 0;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
         const int32_t g = int32_t(q / R), k = int32_t(q - int64_t(g) * R);
-        const int32_t r = cut[k], par = W.P.parent[r];
+        const int32_t r = cut[k], par = a.P.parent[r];
         int32_t top = par >= 0 ? a.top[int64_t(g) * A + (above_pos[par] - above_pos[0])] : -1;
         if (top >= 0 && k > 0 && cut[k - 1] >= top) {  // emitted by an earlier cut cell
             if (!kWrite) cnt_p[q] = cnt_n[q] = 0;
             continue;
         }
-        const GroupView V = group_view(W, g);
+        const GroupView V = group_view(a, g);
         int64_t wp = 0, wn = 0;
         if (kWrite) {
             wp = (scan_p[q] - pb) + (scan_n[int64_t(g) * R] - nb);
@@ -751,9 +734,9 @@ __global__ void k_lists_cut(RB_ARGS)
         int4 pk;
         int top_dec;
         if (top >= 0) {
-            top_dec = decide(W.s, W.P, n, W.theta, W.theta_f, tol, V, top, pk);
+            top_dec = decide(a.st, a.P, n, a.theta, a.theta_f, tol, V, top, pk);
         } else {
-            top_dec = decide(W.s, W.P, n, W.theta, W.theta_f, tol, V, r, pk);
+            top_dec = decide(a.st, a.P, n, a.theta, a.theta_f, tol, V, r, pk);
             if (top_dec != kOpen) top = r;
         }
         if (top >= 0) {
@@ -769,7 +752,7 @@ __global__ void k_lists_cut(RB_ARGS)
             const int32_t end = r + pk.w;
             int32_t c = r + 1;
             while (c < end) {
-                const int dec = decide(W.s, W.P, n, W.theta, W.theta_f, tol, V, c, pk);
+                const int dec = decide(a.st, a.P, n, a.theta, a.theta_f, tol, V, c, pk);
                 if (dec == kOpen) {
                     c++;
                     continue;
