@@ -127,8 +127,9 @@ def _args(argv=None):
     p.add_argument("--order", default="morton", choices=["morton", "hilbert"],
                    help="order of particles and nodes in the tree (Peano-Hilbert is the paper's)")
     p.add_argument("--rebuild", default="auto", choices=["auto", "device", "host"],
-                   help="where the tree, groups and lists are rebuilt every dt_tree (auto: on the device from "
-                        "N = 2048, on the host below, where a device build is bound by launch latency)")
+                   help="where the tree, groups and lists are rebuilt every dt_tree (auto: a lone simulation "
+                        "on the device from N = 2048 and on the host below, where one device build is bound by "
+                        "launch latency; the ensemble and serving servers on the device, in batched builds)")
     p.add_argument("--loop", default="persistent", choices=["persistent", "graph"],
                    help="block-step loop: one persistent cooperative kernel per interval, or CUDA-graph replays")
     p.add_argument("--no-config1", action="store_true",
@@ -445,8 +446,8 @@ def _ensemble(hh, a):
     """Batched form: 256 independent Plummer clusters, N log-uniform in
     [1024, 32768], seeds 0..255, theta from {0.3, 0.5, 0.7}, mixed precision,
     each run to t_end = 0.5, all admitted at once and advanced by the
-    continuous-batching server (rebuilds on worker threads overlap the
-    batched launches of the other clusters)."""
+    continuous-batching server (the clusters that reach their rebuild time
+    in a launch are rebuilt together in one batched device build)."""
     import numpy as np
     import synth
     from paper_1602_02832_gb300 import serve

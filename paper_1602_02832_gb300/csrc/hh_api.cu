@@ -951,9 +951,9 @@ int hh_load_particles(hh_ctx *ctx, int64_t n, const double *x, const double *v, 
 // Completes a device rebuild (hh_gtree.cu): work-item capacity, sizes,
 // mixed-form base records; the state buffers were swapped, so the loop graph
 // is rebuilt on the next hh_advance.
-int hh_finish_device_rebuild(hh_ctx *ctx, int64_t total_parts, int64_t lmax, cudaStream_t on)
+int hh_finish_device_rebuild(hh_ctx *ctx, int64_t total_parts, int64_t lmax, bool batched)
 {
-    cudaStream_t st = on ? on : ctx->stream;
+    cudaStream_t st = ctx->stream;
     const int64_t small_parts = small_parts_bound(ctx, ctx->n_tiles, lmax);
     if (small_parts > INT32_MAX / 2) return fail(ctx, HH_ENOMEM, "hh_rebuild: too many short list parts");
     ctx->list_max = lmax;
@@ -963,14 +963,16 @@ int hh_finish_device_rebuild(hh_ctx *ctx, int64_t total_parts, int64_t lmax, cud
         cudaGraphExecDestroy(ctx->graph);
         ctx->graph = nullptr;
     }
-    k_set_sizes<<<1, 1, 0, st>>>(ctx->ds, ctx->n, ctx->nj, ctx->n_tiles, ctx->part_len, ctx->cfg.work_item,
-                                 ctx->cfg.work_split);
-    CKL();
-    if (ctx->st.base) {
-        k_refresh_base<<<ctx->elem_grid, 256, 0, st>>>(ctx->st, 0, ctx->nj);
+    if (!batched) {
+        k_set_sizes<<<1, 1, 0, st>>>(ctx->ds, ctx->n, ctx->nj, ctx->n_tiles, ctx->part_len, ctx->cfg.work_item,
+                                     ctx->cfg.work_split);
         CKL();
+        if (ctx->st.base) {
+            k_refresh_base<<<ctx->elem_grid, 256, 0, st>>>(ctx->st, 0, ctx->nj);
+            CKL();
+        }
+        CK(cudaStreamSynchronize(st));
     }
-    if (!on) CK(cudaStreamSynchronize(st));
     ctx->total_parts = total_parts;
     ctx->small_parts = small_parts;
     ctx->have_j = true;

@@ -28,10 +28,11 @@ struct RbScratch;
 RbScratch *hh_rb_scratch_create();
 void hh_rb_scratch_free(RbScratch *r);
 int hh_rebuild_device_many(hh_ctx *const *ctxs, const double *ts, int k, int *rcs, RbScratch *r);
-// Ends a device rebuild (hh_api.cu).  With a stream the two closing kernels
-// go there and the caller synchronises it; without, on the context's stream,
-// synchronised here.
-int hh_finish_device_rebuild(hh_ctx *ctx, int64_t total_parts, int64_t lmax, cudaStream_t on = nullptr);
+// Ends a device rebuild (hh_api.cu): work-item capacity, then the sizes on the
+// device and the mixed form's base records on the context's stream,
+// synchronised.  batched: the batched build's closing kernel (k_finish) sets
+// the sizes and base records, and it synchronises.
+int hh_finish_device_rebuild(hh_ctx *ctx, int64_t total_parts, int64_t lmax, bool batched = false);
 // hh_rebuild for k contexts (hh_api.cu): those that build on the device are
 // rebuilt together by hh_rebuild_device_many, the others one by one.
 int hh_rebuild_many(hh_ctx *const *ctxs, const double *ts, int k, int *rcs, RbScratch *r);

@@ -205,10 +205,11 @@ struct RbSim {
     int64_t *nt2, *tscan2;    // [tile counts | part counts], G + 1 each, and their scan
     int64_t *pair2, *pscan2;  // [particle | node entries per (group, cut cell)], pairs + 1 each, and their scan
     int32_t *top;             // [G][A] topmost unopened cell above the cut
+    DevScalars *ds;           // the context's device sizes (set by k_finish)
     double t, theta;
     float theta_f;
     int64_t n, cap_c, pairs;
-    int32_t cap_g, cap_cells, leaf, n_crit, order, tile_i, part_len;
+    int32_t cap_g, cap_cells, leaf, n_crit, order, tile_i, part_len, work_item, work_split;
     int32_t ncells, S, G, R, A;  // set by the host as they become known
 };
 
@@ -834,6 +835,28 @@ __global__ void k_tiles(RB_ARGS)
     }
 }
 
+// Closing step of a batched build: the context's sizes on the device and,
+// for the mixed form, the base records of every j entry (particles in their
+// new order, then the new nodes).
+template <bool kMany>
+__global__ void k_finish(RB_ARGS)
+{
+    RB_SIM;
+    const GCounts *gc = a.gc;
+    const int64_t nj = a.n + gc->ncells;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ds->n = a.n;
+        a.ds->nj = nj;
+        a.ds->n_tiles = int32_t(gc->n_tiles);
+        a.ds->part_len = a.part_len;
+        a.ds->work_item = a.work_item;
+        a.ds->work_split = a.work_split;
+    }
+    if (a.st.base)
+        for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nj; q += (int64_t)gridDim.x * blockDim.x)
+            refresh_base(a.st, q);
+}
+
 template <typename K, typename V>
 int cub_sort_pairs(void *&tmp, size_t &tmp_bytes, const K *kin, K *kout, const V *vin, V *vout, int64_t n, int bits,
                    cudaStream_t st)
@@ -1058,6 +1081,9 @@ RbSim rb_sim(hh_ctx *ctx, GTreeBuf *g, double t)
     a.order = ctx->cfg.order;
     a.tile_i = ctx->tile_i;
     a.part_len = ctx->part_len;
+    a.ds = ctx->ds;
+    a.work_item = ctx->cfg.work_item;
+    a.work_split = ctx->cfg.work_split;
     return a;
 }
 
@@ -1305,7 +1331,7 @@ struct RbScratch {
 
 namespace {
 
-constexpr int kStages = 5;  // the records of stages 0..4 (a stage per read of the counts)
+constexpr int kStages = 6;  // the records of stages 0..5 (a stage per read of the counts, and the close)
 
 void rb_free_sims(RbScratch *r)
 {
@@ -1661,8 +1687,9 @@ int hh_rebuild_device_many(hh_ctx *const *ctxs, const double *ts, int k, int *rc
     launches += 2;
     const cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) return fail_all(HH_ECUDA, cudaGetErrorString(ce));
-    hh_count_launches(launches);  // kernels of this file; the sorts and scans are CUB's
-    for (size_t q = 0; q < act.size(); q++) {
+    // 5. per context on the host: work-item capacity and sizes; then one
+    //    closing kernel over those that got them
+    next_stage([&](size_t q) {
         hh_ctx *ctx = ctxs[act[q]];
         const GCounts &c = cnt(q);
         ctx->nj = ctx->n + c.ncells;
@@ -1670,9 +1697,19 @@ int hh_rebuild_device_many(hh_ctx *const *ctxs, const double *ts, int k, int *rc
         ctx->list_len = c.L;
         ctx->n_tiles = int32_t(c.n_tiles);
         ctx->ids_on_device = true;
-        rcs[act[q]] = hh_finish_device_rebuild(ctx, c.total_parts, int64_t(c.lmax), st);
+        rcs[act[q]] = hh_finish_device_rebuild(ctx, c.total_parts, int64_t(c.lmax), true);
+        return rcs[act[q]] == HH_OK;
+    });
+    if (!act.empty()) {
+        int64_t fx = 1;
+        for (int s : act) fx = std::max<int64_t>(fx, std::min<int64_t>(ctxs[s]->elem_grid, (ctxs[s]->nj + 255) / 256));
+        if (!upload()) return fail_all(HH_ECUDA, "hh_rebuild: batch upload failed");
+        k_finish<true><<<dim3(unsigned(fx), unsigned(act.size())), 256, 0, st>>>(RbSim{}, D());
+        launches++;
     }
-    if (cudaStreamSynchronize(st) != cudaSuccess) {
+    hh_count_launches(launches);  // kernels of this file; the sorts and scans are CUB's
+    const cudaError_t ce2 = cudaGetLastError();
+    if (ce2 != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
         for (int s : act) ctxs[s]->have_lists = false;
         return fail_all(HH_ECUDA, "hh_rebuild: batch build failed");
     }

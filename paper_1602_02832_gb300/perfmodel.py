@@ -35,6 +35,9 @@ List run statistics (host only): python -m paper_1602_02832_gb300.perfmodel --li
 Per-step profile of one tree interval (on a GPU):
     python -m paper_1602_02832_gb300.perfmodel --step-profile --n 65536 --form fp64 \
         --cfg '{"n_crit": 64, "tile_i": 8, "tile_j": 256, "work_item": 2048, "work_split": 2048, "tile_j_small": 64}'
+T_tree of many simulations, one by one against one batched build (on a GPU):
+    python -m paper_1602_02832_gb300.perfmodel --rebuild-batch 85            # N log-uniform in [1024, 32768]
+    python -m paper_1602_02832_gb300.perfmodel --rebuild-batch 64 --n 1024   # 64 of one size
 """
 from __future__ import annotations
 
@@ -404,6 +407,71 @@ def step_profile_main(argv=None):
     return rows
 
 
+def rebuild_batch(ns, precision, reps=5, warm=2, seed=0):
+    """T_tree of many simulations: wall time of rebuilding K contexts (Plummer
+    spheres of sizes ns, seeds seed + k, device builders) one after another
+    with hh_rebuild and together with one hh_batch_rebuild, each averaged
+    over reps after warm rounds of both."""
+    import numpy as np
+    import synth
+    from . import Batch, Context, hh_config_default
+    ctxs = []
+    try:
+        for k, n in enumerate(ns):
+            x, v, m = synth.plummer(int(n), seed + k)
+            c = hh_config_default()
+            c.eps2, c.precision, c.n_crit = 1e-8, precision, 64
+            ctx = Context(c, int(n), 2 * int(n) + 64, 400 * int(n) + 4096, int(n) + 64)
+            ctxs.append(ctx)
+            ctx.hh_load_particles(x.T, v.T, m)
+            ctx.hh_set_rebuild_device(True)
+        with Batch(precision, max_sims=max(1, len(ns)), max_steps=8) as b:
+            for _ in range(warm):
+                for ctx in ctxs:
+                    ctx.hh_rebuild(0.0)
+                b.hh_batch_rebuild(ctxs, 0.0)
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                for ctx in ctxs:
+                    ctx.hh_rebuild(0.0)
+            t1 = time.perf_counter()
+            for _ in range(reps):
+                b.hh_batch_rebuild(ctxs, 0.0)
+            t2 = time.perf_counter()
+    finally:
+        for ctx in ctxs:
+            ctx.close()
+    one, many = (t1 - t0) / reps, (t2 - t1) / reps
+    return {"sims": len(ns), "n_total": int(np.sum(ns)), "n_min": int(np.min(ns)), "n_max": int(np.max(ns)),
+            "one_by_one_ms": one * 1e3, "batched_ms": many * 1e3, "batched_us_per_sim": many / len(ns) * 1e6,
+            "speedup": one / many}
+
+
+def rebuild_batch_main(argv=None):
+    """--rebuild-batch K: K sizes log-uniform in [--n-min, --n-max] (seeded),
+    or K copies of --n."""
+    import numpy as np
+    from . import HH_FP64, HH_MIXED
+    p = argparse.ArgumentParser()
+    p.add_argument("--rebuild-batch", type=int, required=True)
+    p.add_argument("--n", type=int, default=0, help="one size for all (0: log-uniform sizes)")
+    p.add_argument("--n-min", type=int, default=1024)
+    p.add_argument("--n-max", type=int, default=32768)
+    p.add_argument("--form", default="mixed", choices=["fp64", "mixed"])
+    p.add_argument("--reps", type=int, default=5)
+    p.add_argument("--warm", type=int, default=2)
+    a = p.parse_args(argv)
+    k = a.rebuild_batch
+    if a.n:
+        ns = [a.n] * k
+    else:
+        rng = np.random.default_rng(0)
+        ns = np.exp(rng.uniform(np.log(a.n_min), np.log(a.n_max), k)).astype(int).tolist()
+    r = rebuild_batch(ns, HH_FP64 if a.form == "fp64" else HH_MIXED, a.reps, a.warm)
+    print(json.dumps(r), flush=True)
+    return r
+
+
 def main(argv=None):
     import sys
     args = argv if argv is not None else sys.argv[1:]
@@ -412,6 +480,9 @@ def main(argv=None):
         return 0
     if "--list-runs" in args:
         list_runs_main(argv)
+        return 0
+    if "--rebuild-batch" in args:
+        rebuild_batch_main(argv)
         return 0
     from . import HH_FP64, HH_MIXED
 

@@ -81,11 +81,12 @@ class ServerStats:
     wall_s: float = 0.0
 
 
-# measured crossover for a rebuild alone: at N = 1024 / 2048 / 4096 it took 0.62 / 1.45 / 3.5 ms
-# on the host, and 0.39 ms at N = 1024 and 0.50 ms at N = 4096 on the device (whose fixed cost is
-# kernel-launch latency).
-# In the server the device rebuilds of one launch run as one batched build (hh_batch_rebuild),
-# 23 us per simulation at N = 1024; an ensemble of N in [1024, 32768] measured the same either way.
+# Measured crossover for a context rebuilt alone: at N = 1024 / 2048 / 4096 a rebuild took
+# 0.62 / 1.45 / 3.5 ms on the host, and 0.39 ms at N = 1024 and 0.50 ms at N = 4096 on the device
+# (whose fixed cost is kernel-launch latency): callers that rebuild one context at a time use the
+# device from AUTO_DEVICE_MIN_N.  The server's rebuilds run batched (hh_batch_step builds all due
+# device contexts of a launch at once, 13 us a simulation for 64 at N = 1024), so its "auto" takes
+# the device at every size.
 AUTO_DEVICE_MIN_N = 2048
 
 
@@ -93,15 +94,14 @@ class Server:
     """Continuous batching of block steps across resident simulations."""
 
     def _on_device(self, n):
-        return n >= AUTO_DEVICE_MIN_N if self.rebuild_device == "auto" else self.rebuild_device
+        return True if self.rebuild_device == "auto" else self.rebuild_device
 
     def __init__(self, precision=HH_MIXED, budget_bytes=150 * 10 ** 9, max_sims=256, max_steps=64,
                  eps2=1e-8, eta=0.02, theta=0.5, n_crit=64, dt_tree=2.0 ** -6, rebuild_threads=4, device=0,
                  rebuild_device=False, order=0, launch_particles=0, tile_i=0, tile_j=0, work_item=0, work_split=0):
         self.precision = precision
-        # True / False, or "auto": the device builder from AUTO_DEVICE_MIN_N
-        # particles up, the host builder below (a small tree's device build
-        # is bound by kernel-launch latency)
+        # True / False, or "auto": the device builder (batched rebuilds make
+        # it the faster one at every size)
         self.rebuild_device = rebuild_device if rebuild_device == "auto" else bool(rebuild_device)
         self.budget = int(budget_bytes)
         self.max_sims = int(max_sims)

@@ -136,3 +136,10 @@ def test_batched_rebuild_of_a_deeper_tree_and_of_failing_contexts(hh):
     assert np.array_equal(st["x"], np.ascontiguousarray(x1.T))
     for c in (ref, ref3, c0, c1, c2, c3):
         c.close()
+
+
+def test_perfmodel_times_batched_rebuilds(hh):
+    from paper_1602_02832_gb300 import perfmodel
+    r = perfmodel.rebuild_batch([1024, 3000, 700, 5000], hh.HH_MIXED, reps=1, warm=1)
+    assert r["sims"] == 4 and r["n_total"] == 9724
+    assert r["one_by_one_ms"] > 0 and r["batched_ms"] > 0 and r["speedup"] > 0
