@@ -682,8 +682,11 @@ __global__ void k_top_above(RB_ARGS)
     const float tol = walk_tol(a);
     const int32_t A = a.A;
     const int64_t total = int64_t(a.G) * A;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t g = int32_t(q / A), i = int32_t(q - int64_t(g) * A);
+    // neighbouring threads take neighbouring groups under the same cell: the
+    // same path, similar decisions, coalesced group records
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = int32_t(t / a.G), g = int32_t(t - int64_t(i) * a.G);
+        const int64_t q = int64_t(g) * A + i;
         const GroupView V = group_view(a, g);
         int32_t top = -1;
         int4 pk;
@@ -717,8 +720,12 @@ __global__ void k_lists_cut(RB_ARGS)
     const int64_t *scan_p = a.pscan2, *scan_n = a.pscan2 + a.pairs + 1;
     if (!kWrite && blockIdx.x == 0 && threadIdx.x == 0) cnt_p[total] = cnt_n[total] = 0;
     const int64_t pb = kWrite ? scan_p[0] : 0, nb = kWrite ? scan_n[0] : 0;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t g = int32_t(q / R), k = int32_t(q - int64_t(g) * R);
+    // neighbouring threads take neighbouring groups (in space too) under the
+    // same cut cell: they walk the same subtree, mostly alike, and read the
+    // same cells; the counts stay indexed by g * R + k
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t k = int32_t(t / a.G), g = int32_t(t - int64_t(k) * a.G);
+        const int64_t q = int64_t(g) * R + k;
         const int32_t r = cut[k], par = a.P.parent[r];
         int32_t top = par >= 0 ? a.top[int64_t(g) * A + (above_pos[par] - above_pos[0])] : -1;
         if (top >= 0 && k > 0 && cut[k - 1] >= top) {  // emitted by an earlier cut cell
