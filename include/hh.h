@@ -423,12 +423,14 @@ int hh_batch_resident(const hh_batch *b, int32_t *n_out, int32_t *running_out, i
 
 /* hh_rebuild (Section 2, step 1: tree, groups, interaction lists, node
  * records) of n distinct contexts of the batch's device at times t[s].
- * Contexts set to build on the device (hh_set_rebuild_device) are rebuilt
- * together: each step of the device builder is one launch over all of them,
- * its sorts are segmented sorts and its scans one scan over all of them, so
- * the launch count does not grow with n.  Each context gets the tree, lists,
- * node records and particle order that hh_rebuild gives it alone.  Others
- * are rebuilt one after another on the host.  Returns HH_OK when every
+ * Contexts set to build on the device (hh_set_rebuild_device) with at most
+ * 32768 particles are rebuilt together when there are two or more of them:
+ * each step of the device builder is one launch over all of them, its sorts
+ * are segmented sorts and its scans one scan over all of them, so the launch
+ * count does not grow with n.  Each context gets the tree, lists, node
+ * records and particle order that hh_rebuild gives it alone.  The others are
+ * rebuilt one after another by hh_rebuild (larger trees sort faster alone).
+ * Returns HH_OK when every
  * rebuild succeeded, else the first failed context's code; rc_out[n] (may be
  * NULL) receives each context's code and hh_last_error(ctx) its message.  A
  * context whose rebuild failed has no lists (as after a failed hh_rebuild).

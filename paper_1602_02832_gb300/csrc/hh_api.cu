@@ -1099,12 +1099,19 @@ int hh_rebuild(hh_ctx *ctx, double t)
 
 int hh_rebuild_many(hh_ctx *const *ctxs, const double *ts, int k, int *rcs, RbScratch *r)
 {
+    // device builders of at most kBatchRebuildMaxN particles build together
+    // when there are two or more of them; the rest one by one (a large tree's
+    // key sort is faster as one device-wide sort than as a segment sorted by
+    // one CTA, and one context alone gains nothing from the batch)
+    int small = 0;
+    for (int s = 0; s < k; s++)
+        small += ctxs[s] && ctxs[s]->rebuild_device && ctxs[s]->n <= kBatchRebuildMaxN;
     std::vector<hh_ctx *> dev;
     std::vector<double> tdev;
     std::vector<int> where;
     for (int s = 0; s < k; s++) {
         hh_ctx *ctx = ctxs[s];
-        if (ctx && ctx->rebuild_device) {
+        if (small >= 2 && ctx && ctx->rebuild_device && ctx->n <= kBatchRebuildMaxN) {
             rcs[s] = rebuild_begin(ctx);
             if (rcs[s] == HH_OK) {
                 dev.push_back(ctx);

@@ -33,8 +33,10 @@ int hh_rebuild_device_many(hh_ctx *const *ctxs, const double *ts, int k, int *rc
 // synchronised.  batched: the batched build's closing kernel (k_finish) sets
 // the sizes and base records, and it synchronises.
 int hh_finish_device_rebuild(hh_ctx *ctx, int64_t total_parts, int64_t lmax, bool batched = false);
-// hh_rebuild for k contexts (hh_api.cu): those that build on the device are
-// rebuilt together by hh_rebuild_device_many, the others one by one.
+// hh_rebuild for k contexts (hh_api.cu): device builders of at most
+// kBatchRebuildMaxN particles are rebuilt together by hh_rebuild_device_many
+// (when there are two or more), the others one by one.
+constexpr int64_t kBatchRebuildMaxN = 32768;
 int hh_rebuild_many(hh_ctx *const *ctxs, const double *ts, int k, int *rcs, RbScratch *r);
 // Block steps of the batched loop with at most this many due particles use
 // list parts of tile_j_small (when set).

@@ -1493,13 +1493,17 @@ int hh_rebuild_device_many(hh_ctx *const *ctxs, const double *ts, int k, int *rc
         return cudaMemcpyAsync(r->d_seg + which * (r->cap_sims + 1), h, sizeof(int32_t) * (act.size() + 1),
                                cudaMemcpyHostToDevice, st) == cudaSuccess;
     };
-    // blocks per simulation: a thread per particle of the largest one (the
-    // kernels stride over cells, groups and particles alike)
+    // blocks per simulation of the element-wise kernels (they stride over
+    // cells, groups and particles alike): a thread per particle of the
+    // largest one, but no more than about twice the threads the SMs hold in
+    // all, since a level or a moment pass has little work for most blocks
     int64_t launches = 0, gx = 1, max_n = 1;
     for (int s : act) {
         gx = std::max<int64_t>(gx, std::min<int64_t>(ctxs[s]->elem_grid, (ctxs[s]->n + 255) / 256));
         max_n = std::max<int64_t>(max_n, ctxs[s]->n);
     }
+    const int64_t gx_full = gx;  // (the group boxes, a warp per group, take every block)
+    gx = std::max<int64_t>(1, std::min<int64_t>(gx, 2 * int64_t(ctxs[act[0]]->elem_grid) / int64_t(act.size())));
     // 1. bounding boxes, keys, one segmented key sort, levels, counts
     int64_t tot = 0;
     if (!segments(0, [&](size_t q) { return ctxs[act[q]]->n; }, &tot))
@@ -1613,7 +1617,7 @@ int hh_rebuild_device_many(hh_ctx *const *ctxs, const double *ts, int k, int *rc
         return fail_all(rc, "hh_rebuild: batch scan failed");
     k_counts3<true><<<one2, 1, 0, st>>>(RbSim{}, D());
     k_write3<true><<<g2, 256, 0, st>>>(RbSim{}, D());
-    k_group_box<true><<<g2, 256, 0, st>>>(RbSim{}, D());
+    k_group_box<true><<<dim3(unsigned(gx_full), unsigned(K2)), 256, 0, st>>>(RbSim{}, D());
     launches += 6 + (depth + 1) + 6;
     if (!read_counts()) return fail_all(HH_ECUDA, "hh_rebuild: group build failed");
     next_stage([&](size_t q) {

@@ -20,7 +20,8 @@ SPECS = [(2, 1, False, 0.5, 64, "morton"),
          (3000, 4, False, 0.5, 64, "hilbert"),
          (5000, 5, True, 0.3, 256, "morton"),
          (20000, 6, False, 0.7, 64, "morton"),
-         (1500, 7, False, 0.5, 16, "hilbert")]
+         (1500, 7, False, 0.5, 16, "hilbert"),
+         (40000, 8, False, 0.5, 64, "morton")]  # above the batched builder's size: rebuilt alone
 
 
 @pytest.fixture(scope="module")
@@ -35,7 +36,8 @@ def _ctx(hh, n, theta, n_crit, order, x, v, m, cells=None):
     cfg = hh.hh_config_default()
     cfg.eps2, cfg.theta, cfg.n_crit = 1e-6, theta, n_crit
     cfg.order = hh.HH_ORDER_HILBERT if order == "hilbert" else hh.HH_ORDER_MORTON
-    ctx = hh.Context(cfg, n, n + (2 * n + 64 if cells is None else cells), 64 * n * max(1, n // 16) + 1024, n + 64)
+    # (the list buffer starts small: a device rebuild grows it to the need)
+    ctx = hh.Context(cfg, n, n + (2 * n + 64 if cells is None else cells), 64 * n + 4096, n + 64)
     ctx.hh_load_particles(x.T, v.T, m)
     ctx.hh_set_rebuild_device(True)
     return ctx
