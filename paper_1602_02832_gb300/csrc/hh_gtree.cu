@@ -248,6 +248,11 @@ __global__ void k_box(RB_ARGS)
         }
         bad |= s.t[i] != t_tree;
     }
+    // warp, then block reduction (blockDim.x = 256): one atomic per block and
+    // bound, and none from a block that saw no particle
+    __shared__ unsigned long long s_lo[8][3], s_hi[8][3];
+    __shared__ int s_bad[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int d = 0; d < 3; d++) {
         for (int off = 16; off > 0; off >>= 1) {
             const unsigned long long l2 = __shfl_xor_sync(0xffffffffu, lo[d], off);
@@ -255,12 +260,30 @@ __global__ void k_box(RB_ARGS)
             lo[d] = l2 < lo[d] ? l2 : lo[d];
             hi[d] = h2 > hi[d] ? h2 : hi[d];
         }
-        if ((threadIdx.x & 31) == 0) {
-            atomicMin(&a.box->lo[d], lo[d]);
-            atomicMax(&a.box->hi[d], hi[d]);
+        if (lane == 0) {
+            s_lo[w][d] = lo[d];
+            s_hi[w][d] = hi[d];
         }
     }
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(&a.box->bad, 1);
+    const bool any_bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) s_bad[w] = any_bad;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int b = 0;
+        for (int k = 0; k < int(blockDim.x >> 5); k++) {
+            b |= s_bad[k];
+            for (int d = 0; d < 3; d++) {
+                lo[d] = s_lo[k][d] < lo[d] ? s_lo[k][d] : lo[d];
+                hi[d] = s_hi[k][d] > hi[d] ? s_hi[k][d] : hi[d];
+            }
+        }
+        if (lo[0] <= hi[0])
+            for (int d = 0; d < 3; d++) {
+                atomicMin(&a.box->lo[d], lo[d]);
+                atomicMax(&a.box->hi[d], hi[d]);
+            }
+        if (b) atomicExch(&a.box->bad, 1);
+    }
 }
 
 template <bool kMany>
@@ -1174,7 +1197,9 @@ int hh_rebuild_device(hh_ctx *ctx, double t)
     cudaStream_t st = ctx->stream;
     const int64_t n = ctx->n;
     GTreeBuf *g = ctx->gtree;
-    const int grid = ctx->elem_grid;
+    // element-wise kernels: a thread per particle at most (they stride over
+    // cells, groups and particles alike), so a small tree launches few blocks
+    const int grid = int(std::max<int64_t>(1, std::min<int64_t>(ctx->elem_grid, (n + 255) / 256)));
     int64_t launches = 0;
     RbSim a = rb_sim(ctx, g, t);
     // Sizes stay on the device (GCounts) and the host reads them three times:
