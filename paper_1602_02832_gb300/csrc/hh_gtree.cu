@@ -1018,10 +1018,11 @@ GTreeBuf *gtree_alloc(hh_ctx *ctx)
               galloc(g, &g->C.pre, cc) && galloc(g, &g->P.begin, cc) && galloc(g, &g->P.end, cc) &&
               galloc(g, &g->P.nchild, cc) && galloc(g, &g->P.parent, cc) && galloc(g, &g->P.child, 8 * cc) &&
               galloc(g, &g->P.side, cc) && galloc(g, &g->P.size, cc) && galloc(g, &g->P.pack, cc) &&
-              galloc(g, &g->P.cf, cc) && galloc(g, &g->xmax, 1) && galloc(g, &g->gc, 1) && galloc(g, &g->box_f, 2 * ctx->cap_g) && galloc(g, &g->flag3, 3 * cc) &&
-              galloc(g, &g->pos3, 3 * cc) &&
-              galloc(g, &g->g_cell, ctx->cap_g) && galloc(g, &g->cut, cc) && galloc(g, &g->above, cc) && galloc(g, &g->mom, 13 * cc) &&
-              galloc(g, &g->box_lo, 3 * ctx->cap_g) && galloc(g, &g->box_hi, 3 * ctx->cap_g) &&
+              galloc(g, &g->P.cf, cc) && galloc(g, &g->xmax, 1) && galloc(g, &g->gc, 1) &&
+              galloc(g, &g->box_f, 2 * ctx->cap_g) && galloc(g, &g->flag3, 3 * cc) && galloc(g, &g->pos3, 3 * cc) &&
+              galloc(g, &g->g_cell, ctx->cap_g) && galloc(g, &g->cut, cc) && galloc(g, &g->above, cc) &&
+              galloc(g, &g->mom, 13 * cc) && galloc(g, &g->box_lo, 3 * ctx->cap_g) &&
+              galloc(g, &g->box_hi, 3 * ctx->cap_g) &&
               galloc(g, &g->ntile, 2 * (ctx->cap_g + 1)) && galloc(g, &g->tile_off, 2 * (ctx->cap_g + 1)) &&
               galloc(g, &g->ids, n) && galloc(g, &g->ids2, n);
     // the second state buffer mirrors the context's (same capacities)
@@ -1046,10 +1047,9 @@ GTreeBuf *gtree_alloc(hh_ctx *ctx)
 int64_t gtree_bytes(const hh_ctx *ctx)
 {
     const int64_t n = ctx->cap_n, cc = ctx->cap_j, G = ctx->cap_g + 1;
-    return n * (8 * 2 + 4 * 2 + 8 * 2) + cc * (4 * 8 + 4 * 5 + 32 + 8 + 4 * 8 + 13 * 8 + 32) + G * (4 + 8 * 4 + 6 * 8 + 32) +
-           ctx->cap_j * 8 * (12 + 2) + n * 8;
+    return n * (8 * 2 + 4 * 2 + 8 * 2) + cc * (4 * 8 + 4 * 5 + 32 + 8 + 4 * 8 + 13 * 8 + 32) +
+           G * (4 + 8 * 4 + 6 * 8 + 32) + ctx->cap_j * 8 * (12 + 2) + n * 8;
 }
-
 
 }  // namespace
 
