@@ -1,7 +1,9 @@
 """Continuous-batching server on the GPU: every simulation's result is the same
 alone and in the mix (bitwise: its tiles, active sets and list parts are its
 own and its sums run in fixed order), also when a small memory budget makes
-requests queue."""
+requests queue, with host rebuilds and with the server's automatic choice
+(device builds, batched when several simulations reach their rebuild time in
+one launch, single when one does)."""
 import numpy as np
 import pytest
 
@@ -28,24 +30,25 @@ def _requests(serve):
     return out
 
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_same_alone_and_in_the_mix(env, prec):
+@pytest.mark.parametrize("prec,rebuild", [("mixed", False), ("fp64", False), ("mixed", "auto"), ("fp64", "auto")])
+def test_same_alone_and_in_the_mix(env, prec, rebuild):
     hh, serve = env
     P = hh.HH_MIXED if prec == "mixed" else hh.HH_FP64
     reqs = _requests(serve)
     alone = {}
+    kw = dict(precision=P, max_sims=4, max_steps=16, eps2=1e-6, n_crit=32, rebuild_device=rebuild)
     for r in reqs:
-        srv = serve.Server(precision=P, budget_bytes=10 ** 11, max_sims=4, max_steps=16, eps2=1e-6, n_crit=32)
+        srv = serve.Server(budget_bytes=10 ** 11, **kw)
         res, _ = srv.run([r], realtime=False)
         srv.close()
         alone[r.rid] = res[0]
     for budget in (10 ** 11, None):
         if budget is None:  # room for about two of the simulations at a time
-            srv0 = serve.Server(precision=P, eps2=1e-6, n_crit=32)
+            srv0 = serve.Server(**kw)
             est = sorted(srv0.estimate_bytes(r)[0] for r in reqs)
             srv0.close()
             budget = est[-1] + est[-2]
-        srv = serve.Server(precision=P, budget_bytes=budget, max_sims=4, max_steps=16, eps2=1e-6, n_crit=32)
+        srv = serve.Server(budget_bytes=budget, **kw)
         res, stats = srv.run(reqs, realtime=False)
         srv.close()
         assert sorted(r.rid for r in res) == [0, 1, 2, 3]
