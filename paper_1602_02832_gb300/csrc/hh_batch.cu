@@ -565,14 +565,17 @@ __global__ void __launch_bounds__(kBlock, 1) k_batch(BatchDev B)
         if (early) pred_load<Rec>(SD(s_p0).st, gtid - JB[s_p0], in0);
         cache_times(sc, B.sims, n_sims, par);
         prev_full = sc.any_full;
-        if (blockIdx.x == 0) {
-            // counters of the previous step (other parity) are free again
-            if (tid == 0) {
-                B.bs->work[par ^ 1] = 0u;
-                B.bs->n_items[par ^ 1] = 0u;
-                B.bs->max_chunks[par ^ 1] = 0u;
-            }
-            for (int s = tid >> 5; s < n_sims; s += blockDim.x >> 5) {
+        // counters of the previous step (other parity) are free again
+        if (blockIdx.x == 0 && tid == 0) {
+            B.bs->work[par ^ 1] = 0u;
+            B.bs->n_items[par ^ 1] = 0u;
+            B.bs->max_chunks[par ^ 1] = 0u;
+        }
+        {
+            // one warp per simulation, spread over the CTAs (a loop in one
+            // CTA put a latency chain per 16 simulations on every step)
+            const int wpb = (int)(blockDim.x >> 5);
+            for (int s = (int)blockIdx.x * wpb + (tid >> 5); s < n_sims; s += (int)gridDim.x * wpb) {
                 // the next block time starts from the due times of the levels
                 // not corrected now; the corrector lowers it with the
                 // corrected ones.  A finished simulation keeps its time.
