@@ -26,6 +26,7 @@
 // HH_ETIMEOUT and every CTA returns.
 
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -1202,11 +1203,11 @@ extern "C" int hh_batch_rebuild(hh_batch *b, int32_t n, hh_ctx *const *ctxs, con
 {
     if (!b) return hh_set_global_error(HH_EINVAL, "hh_batch_rebuild: NULL batch");
     if (n < 1 || !ctxs || !t) return bfail(b, HH_EINVAL, "hh_batch_rebuild: bad n or NULL arrays");
-    for (int32_t s = 0; s < n; s++) {
-        if (!ctxs[s]) return bfail(b, HH_EINVAL, "hh_batch_rebuild: NULL context");
-        for (int32_t u = 0; u < s; u++)
-            if (ctxs[u] == ctxs[s]) return bfail(b, HH_EINVAL, "hh_batch_rebuild: a context appears twice");
-    }
+    std::vector<hh_ctx *> sorted(ctxs, ctxs + n);
+    std::sort(sorted.begin(), sorted.end(), std::less<hh_ctx *>());
+    if (!sorted[0]) return bfail(b, HH_EINVAL, "hh_batch_rebuild: NULL context");
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+        return bfail(b, HH_EINVAL, "hh_batch_rebuild: a context appears twice");
     if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, HH_ECUDA, "hh_batch_rebuild: cudaSetDevice failed");
     if (!b->rb && !(b->rb = hh_rb_scratch_create()))
         return bfail(b, HH_ECUDA, "hh_batch_rebuild: rebuild stream creation failed");
