@@ -5,7 +5,8 @@ order, groups, lists and node records (all j entries, bit for bit) that
 hh_rebuild gives it alone, whatever else is in the batch: contexts of other
 sizes, orders, opening angles and group sizes, a first build (no depth guess)
 beside later ones, a tree deeper than the last one, and contexts whose
-rebuild fails."""
+rebuild fails; and block steps from a batched build's lists, node records and
+(mixed form) base records give the bits of those from a build alone."""
 import numpy as np
 import pytest
 
@@ -32,9 +33,11 @@ def hh():
     return hh
 
 
-def _ctx(hh, n, theta, n_crit, order, x, v, m, cells=None):
+def _ctx(hh, n, theta, n_crit, order, x, v, m, cells=None, prec=None):
     cfg = hh.hh_config_default()
     cfg.eps2, cfg.theta, cfg.n_crit = 1e-6, theta, n_crit
+    if prec is not None:
+        cfg.precision = prec
     cfg.order = hh.HH_ORDER_HILBERT if order == "hilbert" else hh.HH_ORDER_MORTON
     # (the list buffer starts small: a device rebuild grows it to the need)
     ctx = hh.Context(cfg, n, n + (2 * n + 64 if cells is None else cells), 64 * n + 4096, n + 64)
@@ -63,23 +66,27 @@ def _inputs(spec):
     return (synth.plummer_salpeter if sal else synth.plummer)(n, seed)
 
 
-def test_batched_rebuild_equals_alone(hh):
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batched_rebuild_equals_alone(hh, prec):
+    # Each context is rebuilt twice at t = 0 from its own forces and steps
+    # (hh_run), once alone and once in a batched build; then a stretch of
+    # block steps runs from the rebuilt lists and node records (and, mixed,
+    # the base records the batched build's closing kernel refreshed).
+    P = hh.HH_FP64 if prec == "fp64" else hh.HH_MIXED
     alone, many = [], []
     for s in SPECS:
         x, v, m = _inputs(s)
-        alone.append(_ctx(hh, s[0], s[3], s[4], s[5], x, v, m))
-        many.append(_ctx(hh, s[0], s[3], s[4], s[5], x, v, m))
-    with hh.Batch(hh.HH_FP64, max_sims=len(SPECS), max_steps=8) as b:
-        for rep in range(2):  # a first build, then one with the last depth as guess
+        alone.append(_ctx(hh, s[0], s[3], s[4], s[5], x, v, m, prec=P))
+        many.append(_ctx(hh, s[0], s[3], s[4], s[5], x, v, m, prec=P))
+    for c in alone + many:
+        c.hh_run(0.0, 0.0)
+    with hh.Batch(P, max_sims=len(SPECS), max_steps=8) as b:
+        for rep in range(2):
             for c in alone:
                 c.hh_rebuild(0.0)
             assert b.hh_batch_rebuild(many, 0.0) == [hh.HH_OK] * len(SPECS)
             for c, d in zip(alone, many):
                 _same(_snap(c), _snap(d))
-        # forces and one interval of block steps from the rebuilt trees: the
-        # same bits (the batched loop reads only what the builds wrote)
-        for c in alone + many:
-            c.hh_run(0.0, 0.0)
         _, tn, _ = b.hh_batch_run(alone, 2.0 ** -6)
         _, tm, _ = b.hh_batch_run(many, 2.0 ** -6)
         assert np.array_equal(tn, tm)
